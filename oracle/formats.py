@@ -1,0 +1,201 @@
+"""Storage formats of the fields, restated independently of the CUDA library.
+
+TEST INFRASTRUCTURE ONLY.  These are the encoders that produce reduced-precision inputs
+for parity tests and the decoders that turn stored fields back into the FP64 numbers the
+oracle computes with.  They follow the format definitions in include/lq.h; the CUDA pack
+kernels implement the same definitions in their own code.
+
+Precisions:  "f64", "f32", "f16s".  Link formats: 18 (full 3x3) or 12 (rows 0 and 1;
+row 2 is conj(row0 x row1), an exact identity for SU(3)).  Layouts: "lex" (site-major,
+lexicographic) and "eo" (parity-split, chunked structure of arrays).
+
+Scaled FP16 spinors ("f16s"): per site, s = max over the 24 reals of |fl32(v)| (an FP32
+number) and h = fl16(fl32(v) / s), the division in FP32 with round-to-nearest-even and the
+conversion to FP16 round-to-nearest-even (h = 0 when s = 0).  The stored value of a
+component is the exact product h * s.  FP16 links are fl16(fl32(v)) with no scale.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import reconstruct12
+
+PRECS = ("f64", "f32", "f16s")
+_ELEM = {"f64": np.float64, "f32": np.float32, "f16s": np.float16}
+
+
+def _vol(dims) -> int:
+    return int(np.prod(np.asarray(dims, dtype=np.int64)))
+
+
+def eo_site_map(dims):
+    """(parity, checkerboard index) of every lexicographic site: p = (x+y+z+t) mod 2,
+    cb = n // 2 (x is the fastest index and Lx is even, so the two sites sharing cb in an
+    x-row pair have opposite parity)."""
+    lx, ly, lz, lt = (int(v) for v in dims)
+    n = np.arange(lx * ly * lz * lt, dtype=np.int64)
+    x = n % lx
+    y = (n // lx) % ly
+    z = (n // (lx * ly)) % lz
+    t = n // (lx * ly * lz)
+    return ((x + y + z + t) % 2).astype(np.int64), n // 2
+
+
+# chunk widths (number of reals per chunk) of the eo layout
+def _spinor_chunk(prec):
+    return {"f64": 2, "f32": 4, "f16s": 8}[prec]
+
+
+def _link_chunk(prec, fmt):
+    if fmt == 18:
+        return {"f64": 2, "f32": 2, "f16s": 2}[prec]
+    return {"f64": 2, "f32": 4, "f16s": 4}[prec]
+
+
+def _round(v, prec):
+    """fl_prec(v) for links (no scale): f16 goes through f32 first."""
+    v = np.asarray(v, dtype=np.float64)
+    if prec == "f64":
+        return v.copy()
+    if prec == "f32":
+        return v.astype(np.float32)
+    return v.astype(np.float32).astype(np.float16)
+
+
+# ------------------------------------------------------------------------------------
+# spinors
+# ------------------------------------------------------------------------------------
+def spinor_bytes(dims, prec) -> int:
+    V = _vol(dims)
+    return {"f64": 192 * V, "f32": 96 * V, "f16s": 52 * V}[prec]
+
+
+def _f16s_encode_sites(reals):
+    """reals: float64 (V, 24) -> (halves (V, 24) float16, scales (V,) float32)."""
+    v32 = np.asarray(reals, dtype=np.float64).astype(np.float32)
+    s = np.max(np.abs(v32), axis=1).astype(np.float32)
+    safe = np.where(s > 0, s, np.float32(1.0)).astype(np.float32)
+    q = (v32 / safe[:, None]).astype(np.float32)
+    h = q.astype(np.float16)
+    h[s == 0] = 0
+    return h, s
+
+
+def encode_spinor(psi, dims, prec="f64", layout="lex") -> np.ndarray:
+    """complex (V, 4, 3) -> the stored buffer as a flat uint8 array."""
+    V = _vol(dims)
+    reals = np.ascontiguousarray(psi, dtype=np.complex128).reshape(V, 12).view(np.float64)
+    reals = reals.reshape(V, 24)
+    if prec == "f16s":
+        h, s = _f16s_encode_sites(reals)
+        data = h
+    else:
+        data = _round(reals, prec)
+        s = None
+    if layout == "eo":
+        data = _to_eo_spinor(data, dims, _spinor_chunk(prec))
+        if s is not None:
+            p, cb = eo_site_map(dims)
+            s2 = np.empty(V, dtype=np.float32)
+            s2[p * (V // 2) + cb] = s
+            s = s2
+    out = np.ascontiguousarray(data).view(np.uint8).reshape(-1)
+    if s is not None:
+        out = np.concatenate([out, np.ascontiguousarray(s).view(np.uint8).reshape(-1)])
+    return out
+
+
+def decode_spinor(buf, dims, prec="f64", layout="lex") -> np.ndarray:
+    """Stored buffer -> complex128 (V, 4, 3) holding the exact stored values."""
+    V = _vol(dims)
+    buf = np.ascontiguousarray(np.asarray(buf).view(np.uint8).reshape(-1))
+    if buf.size != spinor_bytes(dims, prec):
+        raise ValueError("spinor buffer has the wrong size")
+    elem = _ELEM[prec]
+    nb = V * 24 * np.dtype(elem).itemsize
+    data = buf[:nb].view(elem).reshape(V, 24)
+    s = buf[nb:].view(np.float32) if prec == "f16s" else None
+    if layout == "eo":
+        data = _from_eo_spinor(data.reshape(-1), dims, _spinor_chunk(prec))
+        if s is not None:
+            p, cb = eo_site_map(dims)
+            s = s[p * (V // 2) + cb]
+    vals = data.astype(np.float64)
+    if s is not None:
+        vals = vals * s.astype(np.float64)[:, None]
+    return np.ascontiguousarray(vals).view(np.complex128).reshape(V, 4, 3)
+
+
+def _to_eo_spinor(data, dims, w):
+    """(V, 24) site-major -> [parity][chunk][cb][w] flat."""
+    V = _vol(dims)
+    K = 24 // w
+    p, cb = eo_site_map(dims)
+    out = np.empty((2, K, V // 2, w), dtype=data.dtype)
+    out[p, :, cb, :] = data.reshape(V, K, w)
+    return out.reshape(-1)
+
+
+def _from_eo_spinor(flat, dims, w):
+    V = _vol(dims)
+    K = 24 // w
+    p, cb = eo_site_map(dims)
+    arr = flat.reshape(2, K, V // 2, w)
+    return arr[p, :, cb, :].reshape(V, 24)
+
+
+# ------------------------------------------------------------------------------------
+# gauge links
+# ------------------------------------------------------------------------------------
+def gauge_bytes(dims, prec, fmt) -> int:
+    V = _vol(dims)
+    per = {"f64": 8, "f32": 4, "f16s": 2}[prec]
+    return V * 4 * fmt * per
+
+
+def encode_gauge(U, dims, prec="f64", fmt=18, layout="lex") -> np.ndarray:
+    """complex (V, 4, 3, 3) -> stored buffer (uint8).  fmt 12 keeps rows 0 and 1."""
+    V = _vol(dims)
+    U = np.ascontiguousarray(U, dtype=np.complex128).reshape(V, 4, 3, 3)
+    rows = U if fmt == 18 else U[:, :, :2, :]
+    reals = np.ascontiguousarray(rows).view(np.float64).reshape(V, 4, fmt)
+    data = _round(reals, prec)
+    if layout == "eo":
+        data = _to_eo_gauge(data, dims, fmt, _link_chunk(prec, fmt))
+    return np.ascontiguousarray(data).view(np.uint8).reshape(-1)
+
+
+def decode_gauge(buf, dims, prec="f64", fmt=18, layout="lex") -> np.ndarray:
+    """Stored buffer -> complex128 (V, 4, 3, 3); 12-real links get row 2 rebuilt in FP64."""
+    V = _vol(dims)
+    buf = np.ascontiguousarray(np.asarray(buf).view(np.uint8).reshape(-1))
+    if buf.size != gauge_bytes(dims, prec, fmt):
+        raise ValueError("gauge buffer has the wrong size")
+    data = buf.view(_ELEM[prec])
+    if layout == "eo":
+        data = _from_eo_gauge(data, dims, fmt, _link_chunk(prec, fmt))
+    vals = np.ascontiguousarray(data.reshape(V, 4, fmt).astype(np.float64))
+    c = vals.view(np.complex128).reshape(V, 4, fmt // 6, 3)
+    if fmt == 12:
+        c = reconstruct12(c)
+    return np.ascontiguousarray(c)
+
+
+def _to_eo_gauge(data, dims, fmt, w):
+    """(V, 4, fmt) -> [mu][parity][chunk][cb][w] flat."""
+    V = _vol(dims)
+    K = fmt // w
+    p, cb = eo_site_map(dims)
+    out = np.empty((4, 2, K, V // 2, w), dtype=data.dtype)
+    # the two index arrays are separated by a slice, so the site axis comes first
+    out[:, p, :, cb, :] = data.reshape(V, 4, K, w)
+    return out.reshape(-1)
+
+
+def _from_eo_gauge(flat, dims, fmt, w):
+    V = _vol(dims)
+    K = fmt // w
+    p, cb = eo_site_map(dims)
+    arr = flat.reshape(4, 2, K, V // 2, w)
+    d = arr[:, p, :, cb, :]          # (V, 4, K, w): advanced indices first
+    return d.reshape(V, 4, fmt)

@@ -1,0 +1,401 @@
+"""Pins of the CPU oracle against facts fixed outside it (CPU only).
+
+Each test ties the oracle to something other than its own formula: Clifford algebra of the
+gamma basis, an independently assembled dense matrix, the closed-form free-field action
+and spectrum, gamma5-hermiticity, gauge covariance, the staggered-sign identity, the
+SU(3) cofactor identity, dense linear solves and the counts the paper prints.
+"""
+import json
+import math
+import os
+from itertools import product
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import dense
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _inner(a, b):
+    return np.vdot(np.asarray(a).ravel(), np.asarray(b).ravel())
+
+
+def _gamma5_apply(psi):
+    g5 = dense.gamma5()
+    return np.einsum("ab,nbc->nac", g5, psi)
+
+
+# ----------------------------------------------------------------------------- gammas
+def test_gamma_clifford_and_hermitian():
+    g = [oracle.gamma(mu) for mu in range(4)]
+    one = np.eye(4)
+    for mu in range(4):
+        assert np.allclose(g[mu], g[mu].conj().T, atol=0)
+        for nu in range(4):
+            anti = g[mu] @ g[nu] + g[nu] @ g[mu]
+            assert np.allclose(anti, 2.0 * one * (mu == nu), atol=0)
+    g5 = g[0] @ g[1] @ g[2] @ g[3]
+    assert np.allclose(g5, np.diag([1, 1, -1, -1]), atol=0)
+    # the dense brute force builds its own copy of the basis: they must agree
+    for mu in range(4):
+        assert np.array_equal(g[mu], dense.gammas()[mu])
+
+
+# ----------------------------------------------------------------------------- dense
+@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (2, 4, 2, 6), (4, 2, 6, 2)])
+def test_stencil_equals_dense_matrix(dims):
+    """Eq. (1) as a stencil equals the independently assembled (12V)x(12V) matrix."""
+    U = synth.gauge_field(dims, seed=11)
+    m = 0.1
+    Dd = dense.dense_dirac(dims, m, U)
+    V = synth.volume(dims)
+    psi = synth.gaussian_spinor(dims, seed=12)
+    got = oracle.dslash(dims, m, U, psi)
+    assert oracle.rel_l2(got.ravel(), Dd @ psi.ravel()) < 1e-15
+    # D^dag equals the conjugate transpose of the dense matrix
+    gotd = oracle.dslash(dims, m, U, psi, dagger=True)
+    assert oracle.rel_l2(gotd.ravel(), Dd.conj().T @ psi.ravel()) < 1e-15
+    # column by column on a few basis vectors, including the wrap-around sites
+    for col in (0, 5, 12 * (V - 1) + 11, 12 * (V // 2) + 7):
+        e = np.zeros(12 * V, np.complex128)
+        e[col] = 1.0
+        got = oracle.dslash(dims, m, U, e.reshape(V, 4, 3)).ravel()
+        assert np.max(np.abs(got - Dd[:, col])) < 1e-15
+
+
+def test_dense_4x4x4x4_sampled_columns():
+    dims = (4, 4, 4, 4)
+    U = synth.gauge_field(dims, seed=13)
+    m = 0.1
+    Dd = dense.dense_dirac(dims, m, U)
+    psi = synth.gaussian_spinor(dims, seed=14)
+    assert oracle.rel_l2(oracle.dslash(dims, m, U, psi).ravel(), Dd @ psi.ravel()) < 1e-15
+
+
+# ----------------------------------------------------------------------------- free field
+def test_free_field_plane_wave_closed_form():
+    """U = 1, psi(n) = exp(i p.n) u:
+    D psi = exp(i p.n) [ (m + 4 + sum cos p_mu) u - i sum sin p_mu gamma_mu u ],
+    D^dag psi flips the sign of the gamma term."""
+    dims = (4, 6, 4, 8)
+    m = 0.37
+    U = synth.unit_gauge_field(dims)
+    V = synth.volume(dims)
+    rng = np.random.default_rng(5)
+    g = dense.gammas()
+    lx, ly, lz, lt = dims
+    n = np.arange(V)
+    coords = np.stack([n % lx, (n // lx) % ly, (n // (lx * ly)) % lz, n // (lx * ly * lz)], 1)
+    for _ in range(4):
+        k = [rng.integers(0, L) for L in dims]
+        p = np.array([2 * math.pi * k[mu] / dims[mu] for mu in range(4)])
+        u = rng.standard_normal((4, 3)) + 1j * rng.standard_normal((4, 3))
+        phase = np.exp(1j * coords @ p)
+        psi = phase[:, None, None] * u[None]
+        mom = (m + 4 + np.cos(p).sum()) * u
+        gs = sum(np.sin(p[mu]) * g[mu] for mu in range(4))
+        want = phase[:, None, None] * (mom - 1j * gs @ u)[None]
+        wantd = phase[:, None, None] * (mom + 1j * gs @ u)[None]
+        assert oracle.rel_l2(oracle.dslash(dims, m, U, psi), want) < 1e-14
+        assert oracle.rel_l2(oracle.dslash(dims, m, U, psi, dagger=True), wantd) < 1e-14
+
+
+def test_free_field_constant_spinor():
+    dims = (2, 4, 2, 4)
+    m = 0.1
+    U = synth.unit_gauge_field(dims)
+    psi = np.ones((synth.volume(dims), 4, 3), np.complex128) * (0.3 - 0.7j)
+    assert oracle.rel_l2(oracle.dslash(dims, m, U, psi), (m + 8) * psi) < 1e-15
+
+
+def test_free_field_spectrum_2222():
+    """On 2^4 every momentum is 0 or pi, so the spectrum is m + 8 - 2j with multiplicity
+    12 * C(4, j); this needs the two hops on an extent-2 axis to add."""
+    dims = (2, 2, 2, 2)
+    m = 0.1
+    Dd = dense.dense_dirac(dims, m, synth.unit_gauge_field(dims))
+    ev = np.sort(np.linalg.eigvals(Dd).real)
+    want = np.sort(np.concatenate([np.full(12 * math.comb(4, j), m + 8 - 2 * j) for j in range(5)]))
+    assert np.max(np.abs(ev - want)) < 1e-12
+
+
+def test_free_field_spectrum_closed_form_4444():
+    dims = (4, 4, 4, 4)
+    m = 0.05
+    Dd = dense.dense_dirac(dims, m, synth.unit_gauge_field(dims))
+    ev = np.linalg.eigvals(Dd)
+    want = []
+    for k in product(range(4), repeat=4):
+        p = 2 * math.pi * np.array(k) / 4
+        re = m + 4 + np.cos(p).sum()
+        im = math.sqrt(max((np.sin(p) ** 2).sum(), 0.0))
+        want += [re + 1j * im] * 6 + [re - 1j * im] * 6
+    key = lambda z: (round(z.real, 9), round(z.imag, 9))
+    got = sorted(ev, key=key)
+    want = sorted(want, key=key)
+    assert np.max(np.abs(np.array(got) - np.array(want))) < 1e-10
+
+
+# ----------------------------------------------------------------------------- symmetries
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (2, 2, 2, 2), (6, 4, 2, 8)])
+def test_gamma5_hermiticity(dims):
+    U = synth.gauge_field(dims, seed=21)
+    m = 0.1
+    psi = synth.gaussian_spinor(dims, seed=22)
+    chi = synth.gaussian_spinor(dims, seed=23)
+    lhs = _inner(chi, oracle.dslash(dims, m, U, psi))
+    g5Dg5chi = _gamma5_apply(oracle.dslash(dims, m, U, _gamma5_apply(chi)))
+    rhs = _inner(g5Dg5chi, psi)
+    assert abs(lhs - rhs) / abs(lhs) < 1e-14
+    # the explicit D^dag route and the gamma5 D gamma5 route agree
+    assert oracle.rel_l2(oracle.dslash(dims, m, U, chi, dagger=True), g5Dg5chi) < 1e-14
+    # and D^dag is the adjoint of D
+    rhs2 = _inner(oracle.dslash(dims, m, U, chi, dagger=True), psi)
+    assert abs(lhs - rhs2) / abs(lhs) < 1e-14
+
+
+def test_gauge_covariance():
+    dims = (4, 2, 4, 6)
+    V = synth.volume(dims)
+    U = synth.gauge_field(dims, seed=31)
+    psi = synth.gaussian_spinor(dims, seed=32)
+    om = synth.haar_su3(synth.make_rng(33), V)
+    m = 0.2
+    Up = np.empty_like(U)
+    for mu in range(4):
+        fwd = dense.shift_index(dims, mu, +1)
+        Up[:, mu] = om @ U[:, mu] @ om[fwd].conj().transpose(0, 2, 1)
+    psip = np.einsum("nab,nsb->nsa", om, psi)
+    for dag in (False, True):
+        lhs = oracle.dslash(dims, m, Up, psip, dagger=dag)
+        rhs = np.einsum("nab,nsb->nsa", om, oracle.dslash(dims, m, U, psi, dagger=dag))
+        assert oracle.rel_l2(lhs, rhs) < 1e-14
+
+
+def test_staggered_sign_identity():
+    """S D(m) S = 2(m+4) - D(m) with S = (-1)^(x+y+z+t): the hopping term flips sign."""
+    dims = (4, 6, 2, 4)
+    U = synth.gauge_field(dims, seed=41)
+    psi = synth.gaussian_spinor(dims, seed=42)
+    m = 0.3
+    s = 1 - 2 * oracle.parity_of_sites(dims)
+    lhs = s[:, None, None] * oracle.dslash(dims, m, U, s[:, None, None] * psi)
+    rhs = 2 * (m + 4) * psi - oracle.dslash(dims, m, U, psi)
+    assert oracle.rel_l2(lhs, rhs) < 1e-14
+
+
+def test_linear_in_mass():
+    dims = (4, 4, 2, 2)
+    U = synth.gauge_field(dims, seed=43)
+    psi = synth.gaussian_spinor(dims, seed=44)
+    d = oracle.dslash(dims, 0.7, U, psi) - oracle.dslash(dims, -0.2, U, psi)
+    assert oracle.rel_l2(d, 0.9 * psi) < 1e-14
+
+
+def test_sampled_sites_match_full():
+    dims = (4, 6, 4, 2)
+    U = synth.gauge_field(dims, seed=45)
+    psi = synth.gaussian_spinor(dims, seed=46)
+    full = oracle.dslash(dims, 0.1, U, psi, dagger=True)
+    sites = [0, 3, 17, synth.volume(dims) - 1]
+    got = oracle.dslash_sites(dims, 0.1, U, psi, sites, dagger=True)
+    assert np.array_equal(got, full[sites])
+
+
+# ----------------------------------------------------------------------------- links
+def test_generators_give_su3():
+    for kind, eps in (("haar", 0.0), ("near_identity", 0.3)):
+        U = synth.gauge_field((2, 2, 2, 4), seed=3, kind=kind, eps=eps).reshape(-1, 3, 3)
+        uu = U @ U.conj().transpose(0, 2, 1)
+        assert np.max(np.abs(uu - np.eye(3))) < 1e-14
+        assert np.max(np.abs(np.linalg.det(U) - 1.0)) < 1e-14
+
+
+def test_generators_deterministic():
+    a = synth.gauge_field((2, 2, 2, 2), seed=9)
+    b = synth.gauge_field((2, 2, 2, 2), seed=9)
+    assert np.array_equal(a, b)
+    assert not np.array_equal(a, synth.gauge_field((2, 2, 2, 2), seed=10))
+
+
+def test_reconstruct12_exact_for_su3():
+    U = synth.haar_su3(synth.make_rng(51), 500)
+    rec = oracle.reconstruct12(U[:, :2, :])
+    assert np.max(np.abs(rec - U)) < 1e-14
+    # a U(3) matrix with det != 1 is not reproduced: the identity needs det = 1
+    ph = np.exp(0.3j)
+    rec2 = oracle.reconstruct12((U * ph)[:, :2, :])
+    assert np.max(np.abs(rec2[:, 2] - (U * ph)[:, 2])) > 1e-2
+
+
+def test_dslash_with_reconstructed_links():
+    dims = (4, 4, 2, 2)
+    U = synth.gauge_field(dims, seed=52)
+    psi = synth.gaussian_spinor(dims, seed=53)
+    rec = oracle.reconstruct12(U[:, :, :2, :])
+    assert oracle.rel_l2(oracle.dslash(dims, 0.1, rec, psi), oracle.dslash(dims, 0.1, U, psi)) < 1e-14
+
+
+# ----------------------------------------------------------------------------- solvers
+@pytest.mark.parametrize("dims,kind", [((2, 2, 2, 2), "haar"), ((4, 4, 4, 4), "haar"),
+                                       ((4, 4, 2, 2), "near_identity")])
+def test_cg_against_dense_solve(dims, kind):
+    m = 0.1
+    U = synth.gauge_field(dims, seed=61, kind=kind, eps=0.3)
+    eta = synth.gaussian_spinor(dims, seed=62)
+    x, it, rel = oracle.cg(dims, m, U, eta, tol=1e-10)
+    assert rel <= 1e-10
+    Dd = dense.dense_dirac(dims, m, U)
+    A = Dd.conj().T @ Dd
+    xd = np.linalg.solve(A, eta.ravel())
+    cond = np.linalg.cond(A)
+    assert oracle.rel_l2(x.ravel(), xd) < 1e-10 * cond
+    # true residual recomputed here from the dense matrix
+    assert np.linalg.norm(eta.ravel() - A @ x.ravel()) / np.linalg.norm(eta.ravel()) <= 1e-10
+
+
+@pytest.mark.parametrize("low,delta", [("f64", 1e-2), ("f32", 1e-3), ("f32", 0.1)])
+def test_alg1_converges_to_cg_solution(low, delta):
+    dims = (4, 4, 2, 4)
+    m = 0.05
+    U = synth.gauge_field(dims, seed=71, kind="near_identity", eps=0.3)
+    eta = synth.gaussian_spinor(dims, seed=72)
+    x, cycles, inner, rel = oracle.alg1(dims, m, U, eta, tol=1e-10, low=low, delta=delta)
+    assert rel <= 1e-10
+    assert cycles >= 2 and inner > 0
+    Dd = dense.dense_dirac(dims, m, U)
+    A = Dd.conj().T @ Dd
+    assert np.linalg.norm(eta.ravel() - A @ x.ravel()) / np.linalg.norm(eta.ravel()) <= 1e-10
+    xc, _, _ = oracle.cg(dims, m, U, eta, tol=1e-12)
+    assert oracle.rel_l2(x, xc) < 1e-10 * np.linalg.cond(A)
+
+
+def test_alg1_single_cycle_is_cg():
+    """With an FP64 inner loop and delta below the target, Algorithm 1 is plain CG: one
+    cycle, and the same iterates as the textbook solver."""
+    dims = (2, 2, 2, 4)
+    m = 0.1
+    U = synth.gauge_field(dims, seed=73)
+    eta = synth.gaussian_spinor(dims, seed=74)
+    x, cycles, inner, rel = oracle.alg1(dims, m, U, eta, tol=1e-10, low="f64", delta=1e-14)
+    xc, itc, relc = oracle.cg(dims, m, U, eta, tol=1e-10)
+    assert cycles == 1
+    assert inner == itc
+    assert oracle.rel_l2(x, xc) < 1e-12
+
+
+# ----------------------------------------------------------------------------- even-odd
+def test_hopping_connects_opposite_parity_only():
+    dims = (4, 2, 4, 2)
+    m = 0.4
+    U = synth.gauge_field(dims, seed=81)
+    psi = synth.gaussian_spinor(dims, seed=82)
+    par = oracle.parity_of_sites(dims)
+    for p in (0, 1):
+        src = psi.copy()
+        src[par != p] = 0
+        out = oracle.dslash(dims, m, U, src)
+        assert oracle.rel_l2(out[par == p], (m + 4) * psi[par == p]) < 1e-15
+
+
+def test_schur_complement_solves_full_system():
+    dims = (2, 2, 2, 4)
+    m = 0.1
+    U = synth.gauge_field(dims, seed=83)
+    V = synth.volume(dims)
+    b = synth.gaussian_spinor(dims, seed=84)
+    par = oracle.parity_of_sites(dims)
+    Dd = dense.dense_dirac(dims, m, U)
+    x = np.linalg.solve(Dd, b.ravel()).reshape(V, 4, 3)
+    a = m + 4
+    # M_ee x_e = b_e - H_eo A^{-1} b_o
+    b_o = b.copy()
+    b_o[par == 0] = 0
+    rhs = b.copy()
+    rhs[par == 1] = 0
+    rhs = rhs - oracle.hop(dims, U, b_o / a, 0)
+    x_e = x.copy()
+    x_e[par == 1] = 0
+    lhs = oracle.schur_even(dims, m, U, x_e)
+    assert oracle.rel_l2(lhs[par == 0], rhs[par == 0]) < 1e-13
+    # x_o = A^{-1}(b_o - H_oe x_e)
+    xo = (b_o - oracle.hop(dims, U, x_e, 1)) / a
+    assert oracle.rel_l2(xo[par == 1], x[par == 1]) < 1e-13
+    # the adjoint Schur operator is the adjoint
+    y = synth.gaussian_spinor(dims, seed=85)
+    y[par == 1] = 0
+    l1 = _inner(y, oracle.schur_even(dims, m, U, x_e))
+    l2 = _inner(oracle.schur_even(dims, m, U, y, dagger=True), x_e)
+    assert abs(l1 - l2) / abs(l1) < 1e-13
+
+
+# ----------------------------------------------------------------------------- formats
+def test_f16s_encoding_pins():
+    from oracle import formats as F
+    dims = (2, 2, 2, 2)
+    psi = synth.gaussian_spinor(dims, seed=91)
+    psi[3] = 0.0            # an all-zero site encodes to scale 0
+    buf = F.encode_spinor(psi, dims, "f16s", "lex")
+    V = synth.volume(dims)
+    h = buf[:48 * V].view(np.float16).reshape(V, 24)
+    s = buf[48 * V:].view(np.float32)
+    assert s[3] == 0 and np.all(h[3] == 0)
+    # every site has one component of magnitude exactly 1 (the max-abs one)
+    nz = s > 0
+    assert np.all(np.max(np.abs(h[nz].astype(np.float32)), axis=1) == 1.0)
+    dec = F.decode_spinor(buf, dims, "f16s", "lex")
+    assert oracle.rel_l2(dec, psi) < 1e-3
+
+
+def test_eo_layout_roundtrip_and_parity_blocks():
+    from oracle import formats as F
+    dims = (4, 2, 2, 6)
+    psi = synth.gaussian_spinor(dims, seed=92)
+    U = synth.gauge_field(dims, seed=93)
+    for prec in F.PRECS:
+        b = F.encode_spinor(psi, dims, prec, "eo")
+        assert np.array_equal(F.decode_spinor(b, dims, prec, "eo"),
+                              F.decode_spinor(F.encode_spinor(psi, dims, prec, "lex"), dims, prec, "lex"))
+        for fmt in (18, 12):
+            g = F.encode_gauge(U, dims, prec, fmt, "eo")
+            assert np.array_equal(F.decode_gauge(g, dims, prec, fmt, "eo"),
+                                  F.decode_gauge(F.encode_gauge(U, dims, prec, fmt, "lex"), dims, prec, fmt, "lex"))
+    # the first half of an f64 eo spinor holds exactly the even sites
+    b = F.encode_spinor(psi, dims, "f64", "eo").view(np.float64)
+    par = oracle.parity_of_sites(dims)
+    V = synth.volume(dims)
+    even = b[: 12 * V].reshape(12, V // 2, 2)
+    assert np.array_equal(np.sort(even.ravel()), np.sort(psi[par == 0].view(np.float64).ravel()))
+
+
+# ----------------------------------------------------------------------------- paper counts
+def test_paper_stencil_counts():
+    """360 input words per stencil = 8 links x 18 + 9 spinors x 24 (Introduction)."""
+    g = json.load(open(os.path.join(GOLDEN, "paper_counts.json")))
+    words = g["links_per_stencil"] * g["words_per_link_full"] + g["spinors_per_stencil"] * 24
+    assert words == g["words_per_stencil"] == 360
+    assert 8 * words == g["bytes_per_stencil_f64"]
+    assert sum(g["stage_cycles"]) == g["latency_cycles"]
+    # stage 3: 8 directions x 2 half-spinors x 9 complex multiply-adds x 8 real operations
+    assert 8 * 2 * 9 * 8 == g["stage3_ops"]
+
+
+@pytest.mark.parametrize("delta", [1e-1, 1e-2])
+def test_alg1_fp64_restarts_continue_cg(delta):
+    """In exact arithmetic the restart p_0 = r_0 + beta_0 (p_k - <r_0,p_k> r_0) with
+    beta_0 = s_l / (s_{l-1} rho_k) is the CG direction p_k rescaled into the new units, so
+    with an FP64 inner loop the restarted solver takes the same iterations as plain CG.
+    A wrong beta_0 or a missing projection breaks the conjugacy and costs iterations."""
+    dims = (4, 4, 2, 4)
+    m = 0.05
+    U = synth.gauge_field(dims, seed=71, kind="near_identity", eps=0.3)
+    eta = synth.gaussian_spinor(dims, seed=72)
+    _, itc, _ = oracle.cg(dims, m, U, eta, tol=1e-10)
+    _, cycles, inner, rel = oracle.alg1(dims, m, U, eta, tol=1e-10, low="f64", delta=delta)
+    assert cycles >= 4
+    assert abs(inner - itc) <= 1
+    assert rel <= 1e-10
