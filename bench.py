@@ -1,0 +1,359 @@
+#!/usr/bin/env python3
+"""Benchmark: Wilson-Dirac site-updates/s inside a mixed-precision CG solve to 1e-10.
+
+Workload (one GPU): 32^4 periodic lattice (1,048,576 sites), m_q = 0.05, links
+exp(0.3 i H) with H random traceless Hermitian (near the free field, the ill-conditioned
+case), one Gaussian right-hand side.  One step = one full solve of D^dag D x = eta from
+x = 0 with Algorithm 1: link packing to the inner format, FP64 residual, inner CG in
+FP32 arithmetic (scaled-FP16 or FP32 storage, 12-real links, EO layout), FP64 reliable
+updates, until the FP64 true residual is <= 1e-10 ||eta||.
+
+value = Wilson-Dirac site-updates per second over the whole solve: every application of
+D or D^dag to a full lattice counts V site-updates (inner and FP64 applies alike).
+The line also carries the CG time-to-1e-10 of the mixed solver and of the plain FP64 CG
+on the same inputs, the roofline of the dominant kernel, the CPU oracle's rate on a
+bounded sample, and an end-to-end number with host buffers.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU (torchrun): every rank solves its own system (weak scaling, no collective on
+the data path); value = all ranks' site-updates / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DIMS = (32, 32, 32, 32)
+MASS = 0.05
+EPS = 0.3
+TOL = 1e-10
+SEED_U, SEED_ETA = 3, 4
+FLOPS_PER_SITE = 1464            # the paper's nominal count per stencil (Introduction)
+WORKLOAD = "mixed-precision CG to 1e-10 on 32^4, m_q=0.05, links exp(0.3iH)"
+
+# algorithmic bytes per site of the inner-loop kernels (each field read or written once)
+#   K1: p in, 4 links, t out.  K2: t in, 4 links, p, psi, r in, psi, r out.  K3: r, p in, p out.
+SPINOR_B = {"mixed_f16": 52, "mixed_f32": 96, "f64": 192}
+LINK4_B = {"mixed_f16": 96, "mixed_f32": 192, "f64": 576}
+
+
+def kernel_bytes(mode):
+    s, l = SPINOR_B[mode], LINK4_B[mode]
+    # K2 reads t, p, psi, r (4 spinors) and the links, writes psi and r (2 spinors)
+    return {"K1": 2 * s + l, "K2": 6 * s + l, "K3": 3 * s}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1904_08616_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, fn), "rb") as f:
+                h.update(fn.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_role):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
+    current kernel sources (else None)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            d = json.load(f)
+        if d.get("source_hash") != source_hash():
+            return None
+        return d["kernels"][kernel_role]["dram_bytes_per_launch_full_size"]
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+            sm = [float(r[1]) for r in rows]
+            mx = max(float(r[2]) for r in rows)
+            reasons = set()
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for r in rows:
+                for i, n in enumerate(names):
+                    if r[5 + i].strip().lower() == "active":
+                        reasons.add(n)
+            return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                    "samples": len(sm)}
+        except Exception as e:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "error": str(e)[:80]}
+
+
+def make_inputs():
+    import synth
+    U = synth.gauge_field(DIMS, seed=SEED_U, kind="near_identity", eps=EPS)
+    eta = synth.gaussian_spinor(DIMS, seed=SEED_ETA)
+    return U, eta
+
+
+def oracle_rate(U, eta, nsites, reps=1):
+    """The CPU oracle (plain C, one thread) applying D^dag D's two stencils on nsites
+    sampled sites of the same 32^4 fields; returns (site-updates/s, seconds)."""
+    import numpy as np
+    import oracle
+    V = U.shape[0]
+    sites = np.random.default_rng(0).integers(0, V, nsites)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle.dslash_sites(DIMS, MASS, U, eta, sites, dagger=False)
+        oracle.dslash_sites(DIMS, MASS, U, eta, sites, dagger=True)
+    dt = time.perf_counter() - t0
+    return 2 * nsites * reps / dt, dt
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    U, eta = make_inputs()
+    nsites = 1 << 17
+    for _ in range(args.warmup):
+        oracle_rate(U, eta, nsites)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_rate(U, eta, nsites)
+    dt = time.perf_counter() - t0
+    value = 2 * nsites * args.steps / dt
+    sample = f"D and D^dag of Eq. 1 on {nsites} sampled sites of the 32^4 fields per step (FP64 C oracle)"
+    line = {
+        "impl": "reference", "metric": "Dslash site-updates/s", "value": value, "unit": "site-updates/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "lattice": list(DIMS), "m_q": MASS},
+        "cpu_baseline": {"value": value, "unit": "site-updates/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "site-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import paper_1904_08616_gb300 as lq
+    import synth
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    lq.load()
+    V = int(np.prod(DIMS))
+    U, eta = make_inputs()
+    # complex128 (V,4,3,3) / (V,4,3) arrays are byte-for-byte the FP64 LEX ABI fields
+    Ub = synth.as_reals(U).view(np.uint8).reshape(-1)
+    eb = synth.as_reals(eta).view(np.uint8).reshape(-1)
+    U_h = torch.from_numpy(Ub.view(np.uint8)).pin_memory()
+    eta_h = torch.from_numpy(eb.view(np.uint8)).pin_memory()
+    x_h = torch.empty(eb.size, dtype=torch.uint8).pin_memory()
+    U_d = U_h.to(dev)
+    eta_d = eta_h.to(dev)
+    x_d = torch.zeros_like(eta_d)
+    mode = args.mode
+    ws = torch.empty(lq.cg_workspace_bytes(DIMS, mode), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def solve(m, profile=False):
+        x_d.zero_()
+        _, info, st = lq.cg_solve(DIMS, MASS, U_d, eta_d, x=x_d, mode=m, tol=TOL, workspace=ws,
+                                  stream=stream, profile=profile)
+        if st != 0:
+            raise RuntimeError(f"solve did not converge: {info}")
+        return info
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        solve(mode, profile=True)
+    torch.cuda.synchronize()
+    infos = []
+    with ClockSampler(local_rank) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            infos.append(solve(mode, profile=True))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    clocks = clk.summary()
+    info = infos[-1]
+    upd = 2 * V * (info["iters"] + info["high_applies"])
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * upd / (ms_max * 1e-3)
+    launches = sum(i["launches"] for i in infos)
+
+    # end to end through the public API with pinned host buffers
+    torch.cuda.synchronize()
+    barrier()
+    h0 = torch.cuda.Event(enable_timing=True)
+    h1 = torch.cuda.Event(enable_timing=True)
+    h0.record(stream)
+    for _ in range(args.steps):
+        U_d.copy_(U_h, non_blocking=True)
+        eta_d.copy_(eta_h, non_blocking=True)
+        solve(mode)
+        x_h.copy_(x_d, non_blocking=True)
+    h1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms = h0.elapsed_time(h1) / args.steps
+    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * upd / (float(te.item()) * 1e-3)
+
+    # plain FP64 CG and the other mixed variant on the same system (one run each after one warm run)
+    compare = {}
+    if not args.no_compare:
+        for m in ("f64", "mixed_f32" if mode == "mixed_f16" else "mixed_f16"):
+            solve(m)
+            torch.cuda.synchronize()
+            c0 = torch.cuda.Event(enable_timing=True)
+            c1 = torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
+            ci = solve(m, profile=True)
+            c1.record(stream)
+            torch.cuda.synchronize()
+            compare[m] = {"ms": c0.elapsed_time(c1), "iters": ci["iters"], "cycles": ci["cycles"],
+                          "true_rel_resid": ci["true_rel_resid"]}
+
+    if rank != 0:
+        return
+    peak, peak_kind = measured_peaks()
+    kb = kernel_bytes(mode)
+    kms = info["kernel_ms"]
+    kcalls = info["kernel_calls"]
+    kern = {}
+    for role, idx in (("K1", 0), ("K2", 1), ("K3", 2)):
+        if kcalls[idx] > 0:
+            avg = kms[idx] / kcalls[idx] * 1e-3
+            gbs = kb[role] * V / avg / 1e9
+            kern[role] = {"avg_us": avg * 1e6, "bytes_per_site": kb[role], "gbs": gbs, "frac": gbs / peak,
+                          "share_of_step": kms[idx] / ms}
+    if kcalls[3] > 0:
+        kern["HIGH_F64"] = {"avg_us": kms[3] / kcalls[3] * 1e3, "share_of_step": kms[3] / ms}
+    dom = max(("K1", "K2", "K3"), key=lambda r: kern.get(r, {}).get("share_of_step", 0))
+    bytes_per_launch = kb[dom] * V
+    avg_s = kern[dom]["avg_us"] * 1e-6
+    achieved = bytes_per_launch / avg_s / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": ncu_traffic(dom), "kernel": dom, "peak_kind": peak_kind,
+            "algorithmic_bytes_per_launch": bytes_per_launch}
+    cpu = None
+    if world == 1 and not args.no_cpu:
+        rate, secs = oracle_rate(U, eta, 1 << 21, reps=1)
+        cpu = {"value": rate, "unit": "site-updates/s", "cores": 1, "kind": "oracle",
+               "sample": f"D and D^dag of Eq. 1 on 2^21 sampled sites of the 32^4 fields ({secs:.1f} s, FP64 C oracle)"}
+    line = {
+        "metric": "Dslash site-updates/s (whole mixed-precision CG solve to 1e-10)",
+        "value": value, "unit": "site-updates/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (f16s storage) inner / f64 outer" if mode == "mixed_f16"
+        else ("f32 inner / f64 outer" if mode == "mixed_f32" else "f64"),
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "lattice": list(DIMS), "m_q": MASS, "links": "exp(0.3iH), 12-real inner",
+                   "inner": mode, "tol": TOL, "rhs_per_gpu": 1,
+                   "l2": "no flush: each inner kernel streams > 200 MB, above the 126 MB L2"},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "site-updates/s", "h2d_bytes_per_step": Ub.size + eb.size,
+                "d2h_bytes_per_step": eb.size},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "gflops_1464": value * FLOPS_PER_SITE / 1e9,
+        "cg": {"time_to_1e-10_ms": ms_max, "iters": info["iters"], "cycles": info["cycles"],
+               "high_applies": info["high_applies"], "true_rel_resid": info["true_rel_resid"],
+               "compare": compare,
+               "mixed_vs_fp64_speedup": (compare["f64"]["ms"] / ms_max) if "f64" in compare else None},
+        "kernels": kern,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="mixed_f16", choices=["mixed_f16", "mixed_f32", "f64"])
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP64 / other-mode comparison solves")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

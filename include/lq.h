@@ -1,0 +1,217 @@
+/*
+ * lq.h -- C ABI of the GB300 Wilson-Dirac library (liblq.so).
+ *
+ * The library applies the Wilson-Dirac operator of arXiv 1904.08616, Eq. (1),
+ *
+ *   (D psi)(n) = (m_q + 4) psi(n)
+ *              + 1/2 sum_{mu=0..3} [ U_mu(n) P^{-mu} psi(n + mu) + U_mu(n - mu)^dag P^{+mu} psi(n - mu) ],
+ *
+ * its adjoint, and solves D^dag D x = eta by conjugate gradients, including the
+ * residual-guided mixed-precision CG of the paper's Algorithm 1.  Every step runs in the
+ * library's own CUDA kernels on one GPU (sm_103a).
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ * Lattice: dims[4] = {Lx, Ly, Lz, Lt}; every extent must be even and >= 2, and the volume
+ *   V = Lx*Ly*Lz*Lt must satisfy V <= 2^31 - 2.  Boundaries are periodic in all four
+ *   directions.  Direction mu = 0, 1, 2, 3 is x, y, z, t.
+ * Gamma matrices: chiral Euclidean basis, P^{-mu} = 1 - gamma_{mu+1}, P^{+mu} = 1 + gamma_{mu+1},
+ *   gamma_k = [[0, -i sigma_k], [i sigma_k, 0]] (k = 1, 2, 3), gamma_4 = [[0, 1], [1, 0]],
+ *   gamma_5 = diag(1, 1, -1, -1).  The hopping term carries the paper's "+1/2".
+ * Site order, LQ_LAYOUT_LEX: n = x + Lx*(y + Ly*(z + Lz*t)), x fastest; site-major:
+ *   spinor  [n][spin 4][colour 3][re, im]
+ *   gauge   [n][mu 4][row r][col 3][re, im], r = 3 rows (LQ_LINK18) or the first 2 rows
+ *           (LQ_LINK12; row 2 is rebuilt as conj(row0 x row1), exact for SU(3)).
+ * Site order, LQ_LAYOUT_EO (parity-split structure of arrays, the fast internal layout):
+ *   parity p = (x+y+z+t) mod 2, checkerboard index cb = n / 2, Vh = V / 2.  A field is cut
+ *   into fixed-width chunks per site; chunk k of site (p, cb) is stored at chunk slot
+ *     spinor:  (p*K + k)*Vh + cb
+ *     gauge :  ((mu*2 + p)*K + k)*Vh + cb
+ *   chunk widths in reals: spinor F64 2, F32 4, F16S 8; gauge LINK18 2 (all precisions),
+ *   LINK12 F64 2, F32 4, F16S 4; K = reals per site (24) or per link (18/12) / width.
+ * Precisions (element types of the stored fields):
+ *   LQ_F64  double; LQ_F32 float;
+ *   LQ_F16S spinors: per site s = max |fl32(v)| over its 24 reals (float) and 24 halves
+ *           h = fl16(fl32(v) / s) (h = 0 if s = 0); the buffer holds all halves first
+ *           (48 V bytes, in the layout's order) followed by the V float scales (for EO the
+ *           scale of (p, cb) is at p*Vh + cb).  The stored value is h * s.
+ *           gauge fields: plain halves fl16(fl32(v)), no scale (SU(3) entries are <= 1).
+ *   Arithmetic is FP64 for LQ_F64 and FP32 for LQ_F32 / LQ_F16S.
+ *
+ * Buffers are device pointers owned by the caller, 16-byte aligned; the library neither
+ * keeps nor frees them.  Calls that take a cuda_stream (a cudaStream_t, NULL = legacy
+ * default stream) enqueue their kernels on it and return without waiting, except
+ * lq_cg_solve, which returns after the solve has finished.
+ *
+ * Errors: every call returns an lq_status.  Arguments are checked before any kernel is
+ * launched; on error nothing is written and lq_last_error() returns a message (per host
+ * thread).  No call aborts, traps or throws across the ABI.
+ */
+#ifndef LQ_H
+#define LQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum lq_status {
+    LQ_OK = 0,
+    LQ_NOT_CONVERGED = 1,     /* solver stopped at max_iter / stagnation; x holds the best iterate */
+    LQ_ERR_ARG = -1,          /* bad enum value, null pointer, bad tolerance or count       */
+    LQ_ERR_DIMS = -2,         /* odd, non-positive or too large lattice extents             */
+    LQ_ERR_ALIGN = -3,        /* pointer not 16-byte aligned, or output aliases an input    */
+    LQ_ERR_CUDA = -4,         /* a CUDA runtime call failed (message has the CUDA error)    */
+    LQ_ERR_WORKSPACE = -5,    /* workspace missing or smaller than lq_cg_workspace_bytes()  */
+    LQ_ERR_NONFINITE = -6,    /* a residual or a CG coefficient became NaN / Inf            */
+    LQ_ERR_BREAKDOWN = -7     /* <p, D^dag D p> <= 0: the operator or the inputs are broken */
+} lq_status;
+
+typedef enum lq_prec { LQ_F64 = 0, LQ_F32 = 1, LQ_F16S = 2 } lq_prec;
+typedef enum lq_link_fmt { LQ_LINK18 = 18, LQ_LINK12 = 12 } lq_link_fmt;
+typedef enum lq_layout { LQ_LAYOUT_LEX = 0, LQ_LAYOUT_EO = 1 } lq_layout;
+
+/* Field kinds for lq_field_bytes. */
+typedef enum lq_field_kind { LQ_FIELD_SPINOR = 0, LQ_FIELD_GAUGE = 1 } lq_field_kind;
+
+/* Size in bytes of a stored field (spinor: link_fmt ignored). Returns 0 on bad arguments. */
+size_t lq_field_bytes(const int32_t dims[4], int32_t kind, int32_t prec, int32_t link_fmt,
+                      int32_t layout);
+
+/*
+ * lq_dslash_apply -- out = D psi, Eq. (1) of the paper (Introduction), on the whole lattice.
+ *   m_q      quark mass of Eq. (1).
+ *   prec     precision of U, psi and out (all three the same).
+ *   link_fmt LQ_LINK18 or LQ_LINK12 (12-real links are rebuilt in registers).
+ *   layout   LQ_LAYOUT_LEX or LQ_LAYOUT_EO, shared by U, psi and out.
+ *   U, psi   inputs (device); out output (device), must not overlap psi or U.
+ * One kernel launch on cuda_stream; returns without waiting.
+ */
+int lq_dslash_apply(const int32_t dims[4], double m_q, int32_t prec, int32_t link_fmt,
+                    int32_t layout, const void *U, const void *psi, void *out,
+                    void *cuda_stream);
+
+/*
+ * lq_dslash_adjoint -- out = D^dag psi.  The paper uses D^dag only inside D^dag D
+ * (Algorithm 1, its three operator lines); it is Eq. (1) with P^{-mu} and P^{+mu}
+ * exchanged, equal to gamma_5 D gamma_5.  Arguments as lq_dslash_apply.
+ */
+int lq_dslash_adjoint(const int32_t dims[4], double m_q, int32_t prec, int32_t link_fmt,
+                      int32_t layout, const void *U, const void *psi, void *out,
+                      void *cuda_stream);
+
+/*
+ * lq_dslash_hop -- the parity-to-parity hopping term of Eq. (1):
+ *   out_p = a * y_p + b * H_{p,1-p} psi_{1-p},   H = 1/2 sum_mu [ ... ] of Eq. (1),
+ * on the half lattice of parity out_parity (the even-odd split of Eq. 1; the paper does
+ * not use it, it is this library's fast layout).  LQ_LAYOUT_EO only.  psi_other, y and out
+ * are half fields: Vh sites of one parity, chunk slot k*Vh + cb (F16S: halves then the Vh
+ * scales).  y may be NULL (then a is ignored); y may equal out.  dagger != 0 uses the
+ * hopping term of D^dag.  One kernel launch.
+ */
+int lq_dslash_hop(const int32_t dims[4], int32_t out_parity, int32_t dagger, double a,
+                  double b, int32_t prec, int32_t link_fmt, const void *U,
+                  const void *psi_other, const void *y, void *out, void *cuda_stream);
+
+/*
+ * lq_convert_spinor / lq_convert_gauge -- re-encode a field into another precision,
+ * link format or layout (the "pack/convert" step; the paper prepares its reduced link
+ * form beforehand, Section 2.2).  Gauge sources must be LQ_LINK18; LQ_LINK12 keeps rows
+ * 0 and 1.  Rounding is round-to-nearest-even, through FP32 for FP16 targets; F16S
+ * spinor encoding follows the rule in the header comment.  dst must not overlap src.
+ */
+int lq_convert_spinor(const int32_t dims[4], int32_t src_prec, int32_t src_layout,
+                      const void *src, int32_t dst_prec, int32_t dst_layout, void *dst,
+                      void *cuda_stream);
+int lq_convert_gauge(const int32_t dims[4], int32_t src_prec, int32_t src_layout,
+                     const void *src, int32_t dst_prec, int32_t dst_fmt, int32_t dst_layout,
+                     void *dst, void *cuda_stream);
+
+/* ---------------------------------------------------------------------------------- */
+/* Conjugate gradient on D^dag D.                                                       */
+/* ---------------------------------------------------------------------------------- */
+typedef enum lq_cg_mode {
+    LQ_CG_F64 = 0,        /* FP64 throughout (plain CG, true residual checked in FP64)     */
+    LQ_CG_MIXED_F32 = 1,  /* Algorithm 1: FP32 inner loop (EO layout, 12-real links), FP64 outer */
+    LQ_CG_MIXED_F16 = 2   /* Algorithm 1: scaled-FP16 inner storage, FP32 arithmetic, FP64 outer */
+} lq_cg_mode;
+
+typedef struct lq_cg_params {
+    double tol;              /* stop when ||eta - D^dag D x|| <= tol ||eta|| (FP64)        */
+    int32_t max_iter;        /* cap on inner iterations summed over all cycles (>= 1)      */
+    int32_t max_cycles;      /* cap on outer cycles (reliable updates); 0 -> 1000          */
+    double delta;            /* inner-loop residual reduction per cycle; <= 0 -> mode default */
+    int32_t chunk;           /* inner iterations between host checks; 0 -> automatic       */
+    int32_t flags;           /* LQ_CG_PROFILE: time the solver's kernels with CUDA events  */
+} lq_cg_params;
+
+/* lq_cg_params.flags */
+#define LQ_CG_PROFILE 1
+
+/* Kernel roles reported in lq_cg_info.kernel_ms / kernel_calls. */
+enum {
+    LQ_K_APPLY_D = 0,        /* inner t = D p with ||t||^2                                  */
+    LQ_K_APPLY_DDAG = 1,     /* inner q = D^dag t fused with the psi / r updates and ||r||^2 */
+    LQ_K_UPDATE_P = 2,       /* inner p = r + beta p                                        */
+    LQ_K_HIGH = 3            /* FP64 residual eta - D^dag D x (two operator kernels)        */
+};
+
+typedef struct lq_cg_info {
+    int32_t status;          /* same value as returned                                     */
+    int32_t iters;           /* inner iterations, all cycles                               */
+    int32_t cycles;          /* outer cycles (Algorithm 1 line 10 loop trips)              */
+    int32_t high_applies;    /* applications of the FP64 D^dag D (Algorithm 1 lines 2, 23) */
+    double true_rel_resid;   /* ||eta - D^dag D x|| / ||eta||, FP64 operator, at return    */
+    double eta_norm;         /* ||eta||                                                    */
+    int32_t launches;        /* kernels this call launched (all roles, including skips)     */
+    int32_t reserved;
+    double kernel_ms[4];     /* LQ_CG_PROFILE: summed device time per role (events)         */
+    int32_t kernel_calls[4]; /* LQ_CG_PROFILE: launches that did work, per role             */
+} lq_cg_info;
+
+/* Workspace bytes lq_cg_solve needs for these dims and mode (0 on bad arguments). */
+size_t lq_cg_workspace_bytes(const int32_t dims[4], int32_t mode);
+
+/*
+ * lq_cg_solve -- solve D^dag D x = eta (Algorithm 1 of the paper, Section 1).
+ *   U        gauge field, LQ_F64, LQ_LINK18, LQ_LAYOUT_LEX (device).
+ *   eta      right-hand side, LQ_F64 LEX spinor (device).
+ *   x        in: starting guess psi_0^high (Algorithm 1 line 1); out: solution (device,
+ *            LQ_F64 LEX spinor; must not overlap eta, U or the workspace).
+ *   params   tolerances and caps (see lq_cg_params); NULL -> tol 1e-10, max_iter 100000.
+ *            With LQ_CG_PROFILE set, CUDA events bracket the solver's kernels on cuda_stream
+ *            and info reports their device time per role (inner launches that found the
+ *            loop already stopped are not counted).
+ *   workspace, ws_bytes  device scratch of at least lq_cg_workspace_bytes(dims, mode),
+ *            16-byte aligned; its contents on entry are ignored.
+ *   info     optional (host) statistics.
+ * Kernels run on cuda_stream; the call returns after the solve has finished (it reads
+ * small convergence records back to the host between chunks of iterations).
+ * Returns LQ_OK when the FP64 true residual meets tol, LQ_NOT_CONVERGED otherwise.
+ */
+int lq_cg_solve(const int32_t dims[4], double m_q, int32_t mode, const void *U,
+                const void *eta, void *x, const lq_cg_params *params, void *workspace,
+                size_t ws_bytes, lq_cg_info *info, void *cuda_stream);
+
+/* Message of the last error on this host thread ("" if none). */
+const char *lq_last_error(void);
+
+/* Library version string. */
+const char *lq_version(void);
+
+/* Short aliases with the operation names of the design (same semantics). */
+int dslash_apply(const int32_t dims[4], double m_q, int32_t prec, int32_t link_fmt,
+                 int32_t layout, const void *U, const void *psi, void *out, void *cuda_stream);
+int dslash_adjoint(const int32_t dims[4], double m_q, int32_t prec, int32_t link_fmt,
+                   int32_t layout, const void *U, const void *psi, void *out, void *cuda_stream);
+int cg_solve(const int32_t dims[4], double m_q, int32_t mode, const void *U, const void *eta,
+             void *x, const lq_cg_params *params, void *workspace, size_t ws_bytes,
+             lq_cg_info *info, void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LQ_H */

@@ -1,0 +1,244 @@
+"""Python binding of liblq, the GB300 Wilson-Dirac library (arXiv 1904.08616).
+
+Argument marshalling only: every operation runs in the library's CUDA kernels through the
+C ABI of include/lq.h.  PyTorch provides device memory and streams.  There is no CPU
+fallback: if liblq.so cannot be built or loaded, every call raises.
+
+Fields are passed as CUDA tensors whose bytes hold the stored field (any dtype; a
+complex128 tensor of shape (V, 4, 3) is exactly an F64 LEX spinor, (V, 4, 3, 3) an F64
+LEX 18-real gauge field).  Precisions: "f64", "f32", "f16s"; layouts: "lex", "eo";
+link formats: 18, 12.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+__all__ = [
+    "LqError", "load", "lib_path", "PREC", "LAYOUT", "CG_MODE",
+    "field_bytes", "dslash_apply", "dslash_adjoint", "dslash_hop", "convert_spinor",
+    "convert_gauge", "cg_workspace_bytes", "cg_solve", "last_error", "version",
+]
+
+PREC = {"f64": 0, "f32": 1, "f16s": 2}
+LAYOUT = {"lex": 0, "eo": 1}
+CG_MODE = {"f64": 0, "mixed_f32": 1, "mixed_f16": 2}
+STATUS = {0: "OK", 1: "NOT_CONVERGED", -1: "ERR_ARG", -2: "ERR_DIMS", -3: "ERR_ALIGN",
+          -4: "ERR_CUDA", -5: "ERR_WORKSPACE", -6: "ERR_NONFINITE", -7: "ERR_BREAKDOWN"}
+
+
+class LqError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class CgParams(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("max_cycles", ctypes.c_int32),
+                ("delta", ctypes.c_double), ("chunk", ctypes.c_int32), ("flags", ctypes.c_int32)]
+
+
+class CgInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("cycles", ctypes.c_int32),
+                ("high_applies", ctypes.c_int32), ("true_rel_resid", ctypes.c_double),
+                ("eta_norm", ctypes.c_double), ("launches", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("kernel_ms", ctypes.c_double * 4), ("kernel_calls", ctypes.c_int32 * 4)]
+
+
+_lock = threading.Lock()
+_lib = None
+_Dims = ctypes.c_int32 * 4
+_vp = ctypes.c_void_p
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load liblq.so (compiling it with nvcc first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing:
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise LqError(-4, f"{_build.LIB} is missing; run paper_1904_08616_gb300.build")
+        L = ctypes.CDLL(_build.LIB)
+        i32, f64 = ctypes.c_int32, ctypes.c_double
+        L.lq_field_bytes.argtypes = [_Dims, i32, i32, i32, i32]
+        L.lq_field_bytes.restype = ctypes.c_size_t
+        for name in ("lq_dslash_apply", "lq_dslash_adjoint"):
+            fn = getattr(L, name)
+            fn.argtypes = [_Dims, f64, i32, i32, i32, _vp, _vp, _vp, _vp]
+            fn.restype = ctypes.c_int
+        L.lq_dslash_hop.argtypes = [_Dims, i32, i32, f64, f64, i32, i32, _vp, _vp, _vp, _vp, _vp]
+        L.lq_dslash_hop.restype = ctypes.c_int
+        L.lq_convert_spinor.argtypes = [_Dims, i32, i32, _vp, i32, i32, _vp, _vp]
+        L.lq_convert_spinor.restype = ctypes.c_int
+        L.lq_convert_gauge.argtypes = [_Dims, i32, i32, _vp, i32, i32, i32, _vp, _vp]
+        L.lq_convert_gauge.restype = ctypes.c_int
+        L.lq_cg_workspace_bytes.argtypes = [_Dims, i32]
+        L.lq_cg_workspace_bytes.restype = ctypes.c_size_t
+        L.lq_cg_solve.argtypes = [_Dims, f64, i32, _vp, _vp, _vp, ctypes.POINTER(CgParams), _vp,
+                                  ctypes.c_size_t, ctypes.POINTER(CgInfo), _vp]
+        L.lq_cg_solve.restype = ctypes.c_int
+        L.lq_last_error.restype = ctypes.c_char_p
+        L.lq_version.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return load().lq_last_error().decode()
+
+
+def version() -> str:
+    return load().lq_version().decode()
+
+
+def _check(status: int):
+    if status < 0:
+        raise LqError(status, last_error())
+    return status
+
+
+def _dims(dims):
+    d = [int(v) for v in dims]
+    if len(d) != 4:
+        raise ValueError("dims must have four extents")
+    return _Dims(*d)
+
+
+def _prec(p):
+    return PREC[p] if isinstance(p, str) else int(p)
+
+
+def _layout(l):
+    return LAYOUT[l] if isinstance(l, str) else int(l)
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        return _vp(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return _vp(stream)
+    return _vp(stream.cuda_stream)
+
+
+def _ptr(t, nbytes: int | None = None, name: str = "tensor"):
+    """Device pointer of a CUDA tensor, checking that it is contiguous and large enough."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if nbytes is not None and t.numel() * t.element_size() < nbytes:
+        raise ValueError(f"{name} holds {t.numel() * t.element_size()} bytes, {nbytes} needed")
+    return _vp(t.data_ptr())
+
+
+def field_bytes(dims, kind: str, prec="f64", link_fmt: int = 18, layout="lex") -> int:
+    k = {"spinor": 0, "gauge": 1}[kind]
+    return int(load().lq_field_bytes(_dims(dims), k, _prec(prec), int(link_fmt), _layout(layout)))
+
+
+def _empty_bytes(n, like):
+    import torch
+    return torch.empty(n, dtype=torch.uint8, device=like.device)
+
+
+def _apply(fn, dims, m_q, U, psi, out, prec, link_fmt, layout, stream):
+    sb = field_bytes(dims, "spinor", prec, link_fmt, layout)
+    gb = field_bytes(dims, "gauge", prec, link_fmt, layout)
+    if out is None:
+        out = _empty_bytes(sb, psi)
+    _check(fn(_dims(dims), float(m_q), _prec(prec), int(link_fmt), _layout(layout),
+              _ptr(U, gb, "U"), _ptr(psi, sb, "psi"), _ptr(out, sb, "out"), _stream(stream)))
+    return out
+
+
+def dslash_apply(dims, m_q, U, psi, out=None, prec="f64", link_fmt=18, layout="lex", stream=None):
+    """out = D psi (Eq. 1).  Returns out (a new uint8 tensor when out is None)."""
+    return _apply(load().lq_dslash_apply, dims, m_q, U, psi, out, prec, link_fmt, layout, stream)
+
+
+def dslash_adjoint(dims, m_q, U, psi, out=None, prec="f64", link_fmt=18, layout="lex", stream=None):
+    """out = D^dag psi."""
+    return _apply(load().lq_dslash_adjoint, dims, m_q, U, psi, out, prec, link_fmt, layout, stream)
+
+
+def dslash_hop(dims, out_parity, U, psi_other, out=None, a=0.0, b=1.0, y=None, dagger=False,
+               prec="f64", link_fmt=18, stream=None):
+    """out_p = a y_p + b H_{p,1-p} psi_{1-p} on EO half fields, H = the 1/2 sum_mu of Eq. (1)."""
+    hb = field_bytes(dims, "spinor", prec) // 2
+    gb = field_bytes(dims, "gauge", prec, link_fmt, "eo")
+    if out is None:
+        out = _empty_bytes(hb, psi_other)
+    _check(load().lq_dslash_hop(_dims(dims), int(out_parity), int(bool(dagger)), float(a), float(b),
+                                _prec(prec), int(link_fmt), _ptr(U, gb, "U"), _ptr(psi_other, hb, "psi_other"),
+                                _ptr(y, hb, "y"), _ptr(out, hb, "out"), _stream(stream)))
+    return out
+
+
+def convert_spinor(dims, src, src_prec="f64", src_layout="lex", dst=None, dst_prec="f32", dst_layout="eo",
+                   stream=None):
+    sb = field_bytes(dims, "spinor", src_prec)
+    db = field_bytes(dims, "spinor", dst_prec)
+    if dst is None:
+        dst = _empty_bytes(db, src)
+    _check(load().lq_convert_spinor(_dims(dims), _prec(src_prec), _layout(src_layout), _ptr(src, sb, "src"),
+                                    _prec(dst_prec), _layout(dst_layout), _ptr(dst, db, "dst"), _stream(stream)))
+    return dst
+
+
+def convert_gauge(dims, src, src_prec="f64", src_layout="lex", dst=None, dst_prec="f32", dst_fmt=12,
+                  dst_layout="eo", stream=None):
+    sb = field_bytes(dims, "gauge", src_prec, 18)
+    db = field_bytes(dims, "gauge", dst_prec, dst_fmt)
+    if dst is None:
+        dst = _empty_bytes(db, src)
+    _check(load().lq_convert_gauge(_dims(dims), _prec(src_prec), _layout(src_layout), _ptr(src, sb, "src"),
+                                   _prec(dst_prec), int(dst_fmt), _layout(dst_layout), _ptr(dst, db, "dst"),
+                                   _stream(stream)))
+    return dst
+
+
+def cg_workspace_bytes(dims, mode="f64") -> int:
+    m = CG_MODE[mode] if isinstance(mode, str) else int(mode)
+    return int(load().lq_cg_workspace_bytes(_dims(dims), m))
+
+
+def cg_solve(dims, m_q, U, eta, x=None, mode="f64", tol=1e-10, max_iter=100000, max_cycles=0, delta=0.0,
+             chunk=0, workspace=None, stream=None, profile=False):
+    """Solve D^dag D x = eta (Algorithm 1).  U: F64 LEX 18-real links, eta / x: F64 LEX spinors.
+
+    x (if given) is the starting guess and receives the solution.  Returns (x, info, status)
+    where info is a dict of the solver statistics; raises LqError on errors (status < 0).
+    """
+    import torch
+    m = CG_MODE[mode] if isinstance(mode, str) else int(mode)
+    sb = field_bytes(dims, "spinor", "f64")
+    gb = field_bytes(dims, "gauge", "f64", 18)
+    if x is None:
+        x = torch.zeros_like(eta)
+    wb = cg_workspace_bytes(dims, m)
+    if workspace is None:
+        workspace = _empty_bytes(wb, eta)
+    prm = CgParams(float(tol), int(max_iter), int(max_cycles), float(delta), int(chunk), 1 if profile else 0)
+    info = CgInfo()
+    st = load().lq_cg_solve(_dims(dims), float(m_q), m, _ptr(U, gb, "U"), _ptr(eta, sb, "eta"),
+                            _ptr(x, sb, "x"), ctypes.byref(prm), _ptr(workspace, wb, "workspace"),
+                            ctypes.c_size_t(workspace.numel() * workspace.element_size()),
+                            ctypes.byref(info), _stream(stream))
+    _check(st)
+    d = {k: getattr(info, k) for k, _ in CgInfo._fields_ if k != "reserved"}
+    d["kernel_ms"] = list(d["kernel_ms"])
+    d["kernel_calls"] = list(d["kernel_calls"])
+    return x, d, st

@@ -1,0 +1,242 @@
+// extern "C" entry points of liblq (declared in include/lq.h): argument checks, then
+// dispatch to the kernels.  Nothing is launched when a check fails.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "lq_abi_internal.h"
+#include "dslash_dispatch.cuh"
+
+namespace lq {
+
+thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+int fail(int status, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return status;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    return fail(LQ_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+size_t spinor_bytes(int64_t nsites, int prec) {
+    switch (prec) {
+        case LQ_F64: return (size_t)nsites * 192;
+        case LQ_F32: return (size_t)nsites * 96;
+        case LQ_F16S: return (size_t)nsites * 52;
+        default: return 0;
+    }
+}
+
+size_t gauge_bytes(int64_t V, int prec, int fmt) {
+    if (fmt != 18 && fmt != 12) return 0;
+    switch (prec) {
+        case LQ_F64: return (size_t)V * 4 * fmt * 8;
+        case LQ_F32: return (size_t)V * 4 * fmt * 4;
+        case LQ_F16S: return (size_t)V * 4 * fmt * 2;
+        default: return 0;
+    }
+}
+
+}  // namespace lq
+
+using namespace lq;
+
+namespace {
+
+bool valid_prec(int p) { return p == LQ_F64 || p == LQ_F32 || p == LQ_F16S; }
+bool valid_layout(int l) { return l == LQ_LAYOUT_LEX || l == LQ_LAYOUT_EO; }
+bool valid_fmt(int f) { return f == LQ_LINK18 || f == LQ_LINK12; }
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+bool overlap(const void* a, size_t na, const void* b, size_t nb) {
+    const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+    return x < y + nb && y < x + na;
+}
+
+int check_dims(const int32_t* dims, Geom* g) {
+    if (!dims) return fail(LQ_ERR_ARG, "dims is NULL");
+    long long v = 1;
+    for (int i = 0; i < 4; ++i) {
+        if (dims[i] < 2 || (dims[i] & 1))
+            return fail(LQ_ERR_DIMS, "lattice extent %d is %d: extents must be even and >= 2", i, (int)dims[i]);
+        v *= dims[i];
+        if (v > 2147483646LL) return fail(LQ_ERR_DIMS, "lattice volume exceeds 2^31 - 2 sites");
+    }
+    *g = make_geom(dims);
+    return LQ_OK;
+}
+
+int check_ptr(const void* p, const char* name) {
+    if (!p) return fail(LQ_ERR_ARG, "%s is NULL", name);
+    if (!aligned16(p)) return fail(LQ_ERR_ALIGN, "%s is not 16-byte aligned", name);
+    return LQ_OK;
+}
+
+int do_apply(const int32_t dims[4], double m_q, int32_t prec, int32_t fmt, int32_t layout, const void* U,
+             const void* psi, void* out, void* stream, bool dag) {
+    Geom g;
+    int r;
+    if ((r = check_dims(dims, &g)) != LQ_OK) return r;
+    if (!valid_prec(prec)) return fail(LQ_ERR_ARG, "bad precision %d", (int)prec);
+    if (!valid_fmt(fmt)) return fail(LQ_ERR_ARG, "bad link format %d", (int)fmt);
+    if (!valid_layout(layout)) return fail(LQ_ERR_ARG, "bad layout %d", (int)layout);
+    if (!isfinite(m_q)) return fail(LQ_ERR_ARG, "m_q is not finite");
+    if ((r = check_ptr(U, "U")) || (r = check_ptr(psi, "psi")) || (r = check_ptr(out, "out"))) return r;
+    const size_t sb = spinor_bytes(g.V, prec), gb = gauge_bytes(g.V, prec, fmt);
+    if (overlap(out, sb, psi, sb) || overlap(out, sb, U, gb))
+        return fail(LQ_ERR_ALIGN, "out overlaps psi or U");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    if (prec == LQ_F64) e = apply_f64(g, m_q, fmt, layout, dag, U, psi, out, st);
+    else if (prec == LQ_F32) e = apply_f32(g, m_q, fmt, layout, dag, U, psi, out, st);
+    else e = apply_f16(g, m_q, fmt, layout, dag, U, psi, out, st);
+    if (e != cudaSuccess) return cuda_fail(e, dag ? "dslash_adjoint launch" : "dslash_apply launch");
+    return LQ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lq_field_bytes(const int32_t dims[4], int32_t kind, int32_t prec, int32_t link_fmt, int32_t layout) {
+    Geom g;
+    if (check_dims(dims, &g) != LQ_OK || !valid_prec(prec) || !valid_layout(layout)) return 0;
+    if (kind == LQ_FIELD_SPINOR) return spinor_bytes(g.V, prec);
+    if (kind == LQ_FIELD_GAUGE) return valid_fmt(link_fmt) ? gauge_bytes(g.V, prec, link_fmt) : 0;
+    return 0;
+}
+
+int lq_dslash_apply(const int32_t dims[4], double m_q, int32_t prec, int32_t link_fmt, int32_t layout,
+                    const void* U, const void* psi, void* out, void* cuda_stream) {
+    return do_apply(dims, m_q, prec, link_fmt, layout, U, psi, out, cuda_stream, false);
+}
+
+int lq_dslash_adjoint(const int32_t dims[4], double m_q, int32_t prec, int32_t link_fmt, int32_t layout,
+                      const void* U, const void* psi, void* out, void* cuda_stream) {
+    return do_apply(dims, m_q, prec, link_fmt, layout, U, psi, out, cuda_stream, true);
+}
+
+int lq_dslash_hop(const int32_t dims[4], int32_t out_parity, int32_t dagger, double a, double b, int32_t prec,
+                  int32_t link_fmt, const void* U, const void* psi_other, const void* y, void* out,
+                  void* cuda_stream) {
+    Geom g;
+    int r;
+    if ((r = check_dims(dims, &g)) != LQ_OK) return r;
+    if (out_parity != 0 && out_parity != 1) return fail(LQ_ERR_ARG, "out_parity must be 0 or 1");
+    if (!valid_prec(prec)) return fail(LQ_ERR_ARG, "bad precision %d", (int)prec);
+    if (!valid_fmt(link_fmt)) return fail(LQ_ERR_ARG, "bad link format %d", (int)link_fmt);
+    if (!isfinite(a) || !isfinite(b)) return fail(LQ_ERR_ARG, "a and b must be finite");
+    if ((r = check_ptr(U, "U")) || (r = check_ptr(psi_other, "psi_other")) || (r = check_ptr(out, "out"))) return r;
+    if (y && (r = check_ptr(y, "y"))) return r;
+    const size_t hb = spinor_bytes(g.Vh, prec), gb = gauge_bytes(g.V, prec, link_fmt);
+    if (overlap(out, hb, psi_other, hb) || overlap(out, hb, U, gb))
+        return fail(LQ_ERR_ALIGN, "out overlaps psi_other or U");
+    if (y && y != out && overlap(out, hb, y, hb)) return fail(LQ_ERR_ALIGN, "out partially overlaps y");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    cudaError_t e;
+    const bool dag = dagger != 0;
+    if (prec == LQ_F64) e = hop_f64(g, out_parity, dag, a, b, link_fmt, U, psi_other, y, out, st);
+    else if (prec == LQ_F32) e = hop_f32(g, out_parity, dag, a, b, link_fmt, U, psi_other, y, out, st);
+    else e = hop_f16(g, out_parity, dag, a, b, link_fmt, U, psi_other, y, out, st);
+    if (e != cudaSuccess) return cuda_fail(e, "dslash_hop launch");
+    return LQ_OK;
+}
+
+int lq_convert_spinor(const int32_t dims[4], int32_t src_prec, int32_t src_layout, const void* src, int32_t dst_prec,
+                      int32_t dst_layout, void* dst, void* cuda_stream) {
+    Geom g;
+    int r;
+    if ((r = check_dims(dims, &g)) != LQ_OK) return r;
+    if (!valid_prec(src_prec) || !valid_prec(dst_prec)) return fail(LQ_ERR_ARG, "bad precision");
+    if (!valid_layout(src_layout) || !valid_layout(dst_layout)) return fail(LQ_ERR_ARG, "bad layout");
+    if ((r = check_ptr(src, "src")) || (r = check_ptr(dst, "dst"))) return r;
+    if (overlap(src, spinor_bytes(g.V, src_prec), dst, spinor_bytes(g.V, dst_prec)))
+        return fail(LQ_ERR_ALIGN, "dst overlaps src");
+    cudaError_t e = convert_spinor(g, src_prec, src_layout, src, dst_prec, dst_layout, dst, (cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "convert_spinor launch");
+    return LQ_OK;
+}
+
+int lq_convert_gauge(const int32_t dims[4], int32_t src_prec, int32_t src_layout, const void* src, int32_t dst_prec,
+                     int32_t dst_fmt, int32_t dst_layout, void* dst, void* cuda_stream) {
+    Geom g;
+    int r;
+    if ((r = check_dims(dims, &g)) != LQ_OK) return r;
+    if (!valid_prec(src_prec) || !valid_prec(dst_prec)) return fail(LQ_ERR_ARG, "bad precision");
+    if (!valid_layout(src_layout) || !valid_layout(dst_layout)) return fail(LQ_ERR_ARG, "bad layout");
+    if (!valid_fmt(dst_fmt)) return fail(LQ_ERR_ARG, "bad link format %d", (int)dst_fmt);
+    if ((r = check_ptr(src, "src")) || (r = check_ptr(dst, "dst"))) return r;
+    if (overlap(src, gauge_bytes(g.V, src_prec, 18), dst, gauge_bytes(g.V, dst_prec, dst_fmt)))
+        return fail(LQ_ERR_ALIGN, "dst overlaps src");
+    cudaError_t e = convert_gauge(g, src_prec, src_layout, src, dst_prec, dst_fmt, dst_layout, dst,
+                                  (cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "convert_gauge launch");
+    return LQ_OK;
+}
+
+size_t lq_cg_workspace_bytes(const int32_t dims[4], int32_t mode) {
+    Geom g;
+    if (check_dims(dims, &g) != LQ_OK) return 0;
+    if (mode != LQ_CG_F64 && mode != LQ_CG_MIXED_F32 && mode != LQ_CG_MIXED_F16) return 0;
+    return cg_workspace_bytes(g, mode);
+}
+
+int lq_cg_solve(const int32_t dims[4], double m_q, int32_t mode, const void* U, const void* eta, void* x,
+                const lq_cg_params* params, void* workspace, size_t ws_bytes, lq_cg_info* info,
+                void* cuda_stream) {
+    if (info) memset(info, 0, sizeof(*info));
+    Geom g;
+    int r;
+    if ((r = check_dims(dims, &g)) != LQ_OK) return r;
+    if (mode != LQ_CG_F64 && mode != LQ_CG_MIXED_F32 && mode != LQ_CG_MIXED_F16)
+        return fail(LQ_ERR_ARG, "bad CG mode %d", (int)mode);
+    if (!isfinite(m_q)) return fail(LQ_ERR_ARG, "m_q is not finite");
+    lq_cg_params prm{1e-10, 100000, 0, 0.0, 0, 0};
+    if (params) prm = *params;
+    if (!(prm.tol > 0.0) || !isfinite(prm.tol)) return fail(LQ_ERR_ARG, "tol must be positive and finite");
+    if (prm.max_iter < 1) return fail(LQ_ERR_ARG, "max_iter must be >= 1");
+    if (prm.max_cycles < 0 || prm.chunk < 0) return fail(LQ_ERR_ARG, "max_cycles and chunk must be >= 0");
+    if (!(prm.delta < 1.0) || !isfinite(prm.delta)) return fail(LQ_ERR_ARG, "delta must be < 1");
+    if ((r = check_ptr(U, "U")) || (r = check_ptr(eta, "eta")) || (r = check_ptr(x, "x"))) return r;
+    if ((r = check_ptr(workspace, "workspace"))) return r == LQ_ERR_ARG ? fail(LQ_ERR_WORKSPACE, "workspace is NULL") : r;
+    const size_t sb = spinor_bytes(g.V, LQ_F64), gb = gauge_bytes(g.V, LQ_F64, 18);
+    if (overlap(x, sb, eta, sb) || overlap(x, sb, U, gb) || overlap(x, sb, workspace, ws_bytes))
+        return fail(LQ_ERR_ALIGN, "x overlaps eta, U or the workspace");
+    if (overlap(workspace, ws_bytes, eta, sb) || overlap(workspace, ws_bytes, U, gb))
+        return fail(LQ_ERR_ALIGN, "workspace overlaps eta or U");
+    r = cg_solve(g, m_q, mode, U, eta, x, prm, workspace, ws_bytes, info, (cudaStream_t)cuda_stream);
+    if (info) info->status = r;
+    return r;
+}
+
+const char* lq_last_error(void) { return g_err; }
+
+const char* lq_version(void) { return "lq 0.1 (sm_103a)"; }
+
+int dslash_apply(const int32_t dims[4], double m_q, int32_t prec, int32_t link_fmt, int32_t layout, const void* U,
+                 const void* psi, void* out, void* cuda_stream) {
+    return lq_dslash_apply(dims, m_q, prec, link_fmt, layout, U, psi, out, cuda_stream);
+}
+
+int dslash_adjoint(const int32_t dims[4], double m_q, int32_t prec, int32_t link_fmt, int32_t layout, const void* U,
+                   const void* psi, void* out, void* cuda_stream) {
+    return lq_dslash_adjoint(dims, m_q, prec, link_fmt, layout, U, psi, out, cuda_stream);
+}
+
+int cg_solve(const int32_t dims[4], double m_q, int32_t mode, const void* U, const void* eta, void* x,
+             const lq_cg_params* params, void* workspace, size_t ws_bytes, lq_cg_info* info, void* cuda_stream) {
+    return lq_cg_solve(dims, m_q, mode, U, eta, x, params, workspace, ws_bytes, info, cuda_stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,113 @@
+// Field re-encoding between precisions, link formats and layouts (the pack/convert
+// step: the paper streams links in a reduced form prepared beforehand, Section 2.2).
+// One thread per site; formats are the ones documented in include/lq.h.
+#include "lq_abi_internal.h"
+#include "dslash_kernels.cuh"
+
+namespace lq {
+
+namespace {
+
+constexpr int kConvBS = 256;
+
+__host__ __device__ inline int spinor_chunk(int prec) { return prec == LQ_F64 ? 2 : (prec == LQ_F32 ? 4 : 8); }
+__host__ __device__ inline int link_chunk(int prec, int fmt) { return fmt == 18 ? 2 : (prec == LQ_F64 ? 2 : 4); }
+
+struct FieldDesc {
+    void* ptr;
+    int prec, layout, fmt;
+};
+
+// element index of real j of a spinor site
+__device__ inline int64_t sp_elem(const FieldDesc& f, const Geom& g, const Site& s, int j) {
+    if (f.layout == LQ_LAYOUT_LEX) return (int64_t)s.lex * 24 + j;
+    const int w = spinor_chunk(f.prec), K = 24 / w;
+    return (((int64_t)s.p * K + j / w) * g.Vh + s.cb) * w + (j % w);
+}
+__device__ inline int64_t sp_scale_idx(const FieldDesc& f, const Geom& g, const Site& s) {
+    return f.layout == LQ_LAYOUT_LEX ? (int64_t)s.lex : (int64_t)s.p * g.Vh + s.cb;
+}
+// element index of real j of link (s, mu)
+__device__ inline int64_t lk_elem(const FieldDesc& f, const Geom& g, const Site& s, int mu, int j) {
+    if (f.layout == LQ_LAYOUT_LEX) return ((int64_t)s.lex * 4 + mu) * f.fmt + j;
+    const int w = link_chunk(f.prec, f.fmt), K = f.fmt / w;
+    return ((((int64_t)mu * 2 + s.p) * K + j / w) * g.Vh + s.cb) * w + (j % w);
+}
+
+__device__ inline double load_real(const void* base, int prec, int64_t i) {
+    if (prec == LQ_F64) return ((const double*)base)[i];
+    if (prec == LQ_F32) return (double)((const float*)base)[i];
+    return (double)__half2float(((const __half*)base)[i]);
+}
+
+__global__ void __launch_bounds__(kConvBS) convert_spinor_kernel(Geom g, FieldDesc src, FieldDesc dst) {
+    const int64_t sc_off = 48 * (int64_t)g.V;   // F16S scales follow the halves
+    for (int lex = blockIdx.x * kConvBS + threadIdx.x; lex < g.V; lex += gridDim.x * kConvBS) {
+        int c[4];
+        const Site s = site_from_lex(g, lex, c);
+        double v[24];
+        double sc = 1.0;
+        if (src.prec == LQ_F16S) sc = (double)((const float*)((const char*)src.ptr + sc_off))[sp_scale_idx(src, g, s)];
+#pragma unroll
+        for (int j = 0; j < 24; ++j) v[j] = load_real(src.ptr, src.prec, sp_elem(src, g, s, j)) * sc;
+        if (dst.prec == LQ_F64) {
+#pragma unroll
+            for (int j = 0; j < 24; ++j) ((double*)dst.ptr)[sp_elem(dst, g, s, j)] = v[j];
+        } else if (dst.prec == LQ_F32) {
+#pragma unroll
+            for (int j = 0; j < 24; ++j) ((float*)dst.ptr)[sp_elem(dst, g, s, j)] = (float)v[j];
+        } else {
+            float f[24];
+            float m = 0.f;
+#pragma unroll
+            for (int j = 0; j < 24; ++j) { f[j] = (float)v[j]; m = fmaxf(m, fabsf(f[j])); }
+            ((float*)((char*)dst.ptr + sc_off))[sp_scale_idx(dst, g, s)] = m;
+            const bool z = !(m > 0.f);
+#pragma unroll
+            for (int j = 0; j < 24; ++j)
+                ((__half*)dst.ptr)[sp_elem(dst, g, s, j)] = __float2half_rn(z ? 0.f : __fdiv_rn(f[j], m));
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kConvBS) convert_gauge_kernel(Geom g, FieldDesc src, FieldDesc dst) {
+    for (int lex = blockIdx.x * kConvBS + threadIdx.x; lex < g.V; lex += gridDim.x * kConvBS) {
+        int c[4];
+        const Site s = site_from_lex(g, lex, c);
+        for (int mu = 0; mu < 4; ++mu) {
+            for (int j = 0; j < dst.fmt; ++j) {
+                const double v = load_real(src.ptr, src.prec, lk_elem(src, g, s, mu, j));
+                const int64_t i = lk_elem(dst, g, s, mu, j);
+                if (dst.prec == LQ_F64) ((double*)dst.ptr)[i] = v;
+                else if (dst.prec == LQ_F32) ((float*)dst.ptr)[i] = (float)v;
+                else ((__half*)dst.ptr)[i] = __float2half_rn((float)v);
+            }
+        }
+    }
+}
+
+int conv_grid(const Geom& g) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long want = ((long long)g.V + kConvBS - 1) / kConvBS;
+    long long cap = (long long)sms * 8;
+    return (int)(want < cap ? (want > 0 ? want : 1) : cap);
+}
+
+}  // namespace
+
+cudaError_t convert_spinor(const Geom& g, int sp, int sl, const void* src, int dp, int dl, void* dst, cudaStream_t st) {
+    convert_spinor_kernel<<<conv_grid(g), kConvBS, 0, st>>>(g, FieldDesc{(void*)src, sp, sl, 0},
+                                                            FieldDesc{dst, dp, dl, 0});
+    return cudaGetLastError();
+}
+
+cudaError_t convert_gauge(const Geom& g, int sp, int sl, const void* src, int dp, int dfmt, int dl, void* dst,
+                          cudaStream_t st) {
+    convert_gauge_kernel<<<conv_grid(g), kConvBS, 0, st>>>(g, FieldDesc{(void*)src, sp, sl, 18},
+                                                           FieldDesc{dst, dp, dl, dfmt});
+    return cudaGetLastError();
+}
+
+}  // namespace lq

@@ -1,0 +1,270 @@
+// The Wilson-Dirac stencil of Eq. (1) and the kernel templates built on it.
+//
+// Per output site n the stencil forms, for each of the 8 hops, the rank-2 spin
+// projection of the neighbour spinor (Section 1, stage 2: adds and subtracts of spin
+// components), multiplies the resulting two colour vectors by the link or its adjoint
+// (stage 3: the SU(3) x vector products, 12-real links rebuilt in registers), and
+// expands the two products back into four spin components while accumulating
+// (stage 4).  The diagonal (m_q + 4) term and the 1/2 of Eq. (1) are applied by the
+// epilogue, which is also where the solver kernels fuse their vector updates and norms.
+//
+// Chiral basis: gamma_mu = [[0, B_mu], [B_mu^dag, 0]] with B_0 = -i sigma_1,
+// B_1 = -i sigma_2, B_2 = -i sigma_3, B_3 = 1.  For P = 1 + S gamma_mu (S = +/-1):
+//   upper(P psi) = psi_up + S B psi_dn =: h,   lower(P psi) = S B^dag h,
+// so U P psi = [U h ; S B^dag (U h)] and only the two colour vectors of h need the link.
+#pragma once
+
+#include "lq_internal.cuh"
+
+namespace lq {
+
+template <int S, typename R> LQ_HD cplx<R> pm(cplx<R> a, cplx<R> b) {
+    if constexpr (S > 0) return cadd(a, b);
+    else return csub(a, b);
+}
+
+// acc += U' (1 + S gamma_MU) q,  U' = U (BACK = false) or U^dag (BACK = true)
+template <int MU, int S, bool BACK, typename R>
+LQ_HD void hop_dir(Spinor<R>& acc, const Spinor<R>& q, const Link<R>& U) {
+    cplx<R> h0[3], h1[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const cplx<R> p0 = q.v[c], p1 = q.v[3 + c], p2 = q.v[6 + c], p3 = q.v[9 + c];
+        if constexpr (MU == 0) {          // B psi_dn = (-i p3, -i p2)
+            h0[c] = pm<S>(p0, ctimes_mi(p3));
+            h1[c] = pm<S>(p1, ctimes_mi(p2));
+        } else if constexpr (MU == 1) {   // B psi_dn = (-p3, p2)
+            h0[c] = pm<-S>(p0, p3);
+            h1[c] = pm<S>(p1, p2);
+        } else if constexpr (MU == 2) {   // B psi_dn = (-i p2, i p3)
+            h0[c] = pm<S>(p0, ctimes_mi(p2));
+            h1[c] = pm<S>(p1, ctimes_i(p3));
+        } else {                          // B psi_dn = (p2, p3)
+            h0[c] = pm<S>(p0, p2);
+            h1[c] = pm<S>(p1, p3);
+        }
+    }
+    cplx<R> g0[3], g1[3];
+#pragma unroll
+    for (int A = 0; A < 3; ++A) {
+        if constexpr (!BACK) {
+            g0[A] = cmul(U.u[A][0], h0[0]);
+            g1[A] = cmul(U.u[A][0], h1[0]);
+#pragma unroll
+            for (int B = 1; B < 3; ++B) {
+                g0[A] = cfma(U.u[A][B], h0[B], g0[A]);
+                g1[A] = cfma(U.u[A][B], h1[B], g1[A]);
+            }
+        } else {
+            g0[A] = cmul(cconj(U.u[0][A]), h0[0]);
+            g1[A] = cmul(cconj(U.u[0][A]), h1[0]);
+#pragma unroll
+            for (int B = 1; B < 3; ++B) {
+                g0[A] = cfmac(U.u[B][A], h0[B], g0[A]);
+                g1[A] = cfmac(U.u[B][A], h1[B], g1[A]);
+            }
+        }
+    }
+#pragma unroll
+    for (int A = 0; A < 3; ++A) {
+        acc.v[A] = cadd(acc.v[A], g0[A]);
+        acc.v[3 + A] = cadd(acc.v[3 + A], g1[A]);
+        // lower components: S B^dag (g0, g1)
+        if constexpr (MU == 0) {          // B^dag g = (i g1, i g0)
+            acc.v[6 + A] = pm<S>(acc.v[6 + A], ctimes_i(g1[A]));
+            acc.v[9 + A] = pm<S>(acc.v[9 + A], ctimes_i(g0[A]));
+        } else if constexpr (MU == 1) {   // B^dag g = (g1, -g0)
+            acc.v[6 + A] = pm<S>(acc.v[6 + A], g1[A]);
+            acc.v[9 + A] = pm<-S>(acc.v[9 + A], g0[A]);
+        } else if constexpr (MU == 2) {   // B^dag g = (i g0, -i g1)
+            acc.v[6 + A] = pm<S>(acc.v[6 + A], ctimes_i(g0[A]));
+            acc.v[9 + A] = pm<S>(acc.v[9 + A], ctimes_mi(g1[A]));
+        } else {                          // B^dag g = (g0, g1)
+            acc.v[6 + A] = pm<S>(acc.v[6 + A], g0[A]);
+            acc.v[9 + A] = pm<S>(acc.v[9 + A], g1[A]);
+        }
+    }
+}
+
+// The hopping sum  sum_mu [ U_mu(n) P_f psi(n+mu) + U_mu(n-mu)^dag P_b psi(n-mu) ]
+// (without the 1/2), P_f = 1 - gamma (D) or 1 + gamma (D^dag), P_b the other one.
+// GA: gauge accessor (full field), SA: spinor accessor of the neighbours.
+template <class GA, class SA, bool DAG>
+struct Stencil {
+    using Real = typename GA::Real;
+    Geom g;
+    GA ga;
+    SA sa;
+
+    template <int MU>
+    LQ_HD void dir(const Site& s, const int c[4], Spinor<Real>& acc) const {
+        constexpr int SF = DAG ? +1 : -1;
+        const Site nf = nb_site(lex_fwd(g, s.lex, c, MU), s.p);
+        const Site nb = nb_site(lex_bwd(g, s.lex, c, MU), s.p);
+        Spinor<Real> q;
+        Link<Real> U;
+        sa.load(nf, q);
+        ga.load(s, MU, U);
+        hop_dir<MU, SF, false>(acc, q, U);
+        sa.load(nb, q);
+        ga.load(nb, MU, U);
+        hop_dir<MU, -SF, true>(acc, q, U);
+    }
+
+    LQ_HD void apply(const Site& s, const int c[4], Spinor<Real>& acc) const {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc.v[k] = {Real(0), Real(0)};
+        dir<0>(s, c, acc);
+        dir<1>(s, c, acc);
+        dir<2>(s, c, acc);
+        dir<3>(s, c, acc);
+    }
+};
+
+// ------------------------------------------------------------------------------------
+// Site maps: tile -> sites.  A tile is one block's worth of consecutive sites.
+// ------------------------------------------------------------------------------------
+template <int BS> struct MapLex {            // all V sites, lexicographic
+    Geom g;
+    __host__ __device__ int ntiles() const { return (g.V + BS - 1) / BS; }
+    __device__ __forceinline__ bool site(int tile, Site& s, int c[4]) const {
+        const int lex = tile * BS + (int)threadIdx.x;
+        if (lex >= g.V) return false;
+        s = site_from_lex(g, lex, c);
+        return true;
+    }
+};
+
+template <int BS> struct MapEoFull {         // all V sites; tiles alternate parity over the same cb range
+    Geom g;
+    __host__ __device__ int ntiles() const { return 2 * ((g.Vh + BS - 1) / BS); }
+    __device__ __forceinline__ bool site(int tile, Site& s, int c[4]) const {
+        const int cb = (tile >> 1) * BS + (int)threadIdx.x;
+        if (cb >= g.Vh) return false;
+        s = site_from_eo(g, tile & 1, cb, c);
+        return true;
+    }
+};
+
+template <int BS> struct MapEoHalf {         // the Vh sites of one parity
+    Geom g;
+    int p;
+    __host__ __device__ int ntiles() const { return (g.Vh + BS - 1) / BS; }
+    __device__ __forceinline__ bool site(int tile, Site& s, int c[4]) const {
+        const int cb = tile * BS + (int)threadIdx.x;
+        if (cb >= g.Vh) return false;
+        s = site_from_eo(g, p, cb, c);
+        return true;
+    }
+};
+
+template <typename R> LQ_HD R norm2(const Spinor<R>& a) {
+    R s = R(0);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) s = fma(a.v[k].re, a.v[k].re, fma(a.v[k].im, a.v[k].im, s));
+    return s;
+}
+
+// ------------------------------------------------------------------------------------
+// Epilogues.  init() runs once per thread before the site loop and returns false to skip
+// the whole kernel (uniformly); apply() consumes the hopping sum of one site; finish()
+// performs the grid reduction (if NRED > 0).
+// ------------------------------------------------------------------------------------
+
+// out = a * y(n) + b * hop(n)        (y = the centre input for the full operator)
+// NORM: also reduce ||out||^2 into st->red[slot].
+template <class OutA, class YA, bool HASY, bool NORM>
+struct EpiAxpby {
+    using Real = typename OutA::Real;
+    static constexpr int NRED = NORM ? 1 : 0;
+    OutA out;
+    YA y;
+    Real a, b;
+    RedCtx rc;
+    int slot;
+    LQ_HD bool init() { return true; }
+    template <typename R>
+    LQ_HD void apply(const Site& s, const Spinor<R>& acc, double* red) const {
+        Spinor<R> o;
+        if constexpr (HASY) {
+            Spinor<R> yv;
+            y.load(s, yv);
+#pragma unroll
+            for (int k = 0; k < 12; ++k)
+                o.v[k] = {fma((R)b, acc.v[k].re, (R)a * yv.v[k].re), fma((R)b, acc.v[k].im, (R)a * yv.v[k].im)};
+        } else {
+#pragma unroll
+            for (int k = 0; k < 12; ++k) o.v[k] = cscale((R)b, acc.v[k]);
+        }
+        out.store(s, o);
+        if constexpr (NORM) red[0] += (double)norm2(o);
+    }
+    template <int BS> __device__ __forceinline__ void finish(const double (&red)[NRED > 0 ? NRED : 1]) const {
+        if constexpr (NORM) {
+            const double v[1] = {red[0]};
+            SolverState* st = rc.st;
+            const int sl = slot;
+            grid_reduce<BS, 1>(rc, kTicketMisc, v, [st, sl](const double* t) { st->red[sl] = t[0]; });
+        }
+    }
+};
+
+// Generic stencil kernel: grid-stride over tiles, one thread per site.
+template <int BS, class Map, class Sten, class Epi>
+__global__ void __launch_bounds__(BS) stencil_kernel(Map map, Sten sten, Epi epi) {
+    if (!epi.init()) return;
+    constexpr int NR = Epi::NRED > 0 ? Epi::NRED : 1;
+    double red[NR];
+#pragma unroll
+    for (int j = 0; j < NR; ++j) red[j] = 0.0;
+    const int nt = map.ntiles();
+    for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+        Site s;
+        int c[4];
+        if (!map.site(tile, s, c)) continue;
+        Spinor<typename Sten::Real> acc;
+        sten.apply(s, c, acc);
+        epi.apply(s, acc, red);
+    }
+    epi.template finish<BS>(red);
+}
+
+// Grid size for a grid-stride kernel: every SM filled to its occupancy, never more
+// blocks than tiles, never more than the partial-sum buffer holds.
+template <class KernelPtr>
+inline int grid_for(KernelPtr k, int bs, int ntiles) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, bs, 0);
+    if (per_sm < 1) per_sm = 1;
+    long long g = (long long)sms * per_sm;
+    if (g > ntiles) g = ntiles;
+    if (g > kMaxPartials) g = kMaxPartials;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+template <int BS, class Map, class Sten, class Epi>
+inline cudaError_t launch_stencil(const Map& map, const Sten& sten, const Epi& epi, cudaStream_t st) {
+    auto k = stencil_kernel<BS, Map, Sten, Epi>;
+    static thread_local int cached_grid_tiles = -1, cached_grid = 0;
+    const int nt = map.ntiles();
+    int grid;
+    if (cached_grid_tiles == nt) {
+        grid = cached_grid;
+    } else {
+        grid = grid_for(k, BS, nt);
+        cached_grid_tiles = nt;
+        cached_grid = grid;
+    }
+    k<<<grid, BS, 0, st>>>(map, sten, epi);
+    return cudaGetLastError();
+}
+
+// EoIdx for a full EO field of K chunks per site, and for a half field of one parity.
+inline EoIdx eo_full(const Geom& g, int K) { return EoIdx{g.Vh, (int64_t)K * g.Vh, g.Vh}; }
+inline EoIdx eo_half(const Geom& g) { return EoIdx{g.Vh, 0, 0}; }
+inline EoIdx eo_none() { return EoIdx{0, 0, 0}; }
+
+}  // namespace lq

@@ -1,0 +1,457 @@
+// Internal definitions of liblq: complex arithmetic, lattice geometry, field accessors
+// for every (precision, layout, link format) the C ABI exposes, and the deterministic
+// grid reduction used by the fused solver kernels.
+//
+// Field formats are the ones documented in include/lq.h.  Nothing here is shared with
+// the CPU oracle.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/lq.h"
+
+// Helpers are callable from host code as well, so the index arithmetic and the stencil
+// algebra can be exercised off the GPU; the library itself only runs them on the device.
+#define LQ_HD __host__ __device__ __forceinline__
+
+namespace lq {
+
+// ------------------------------------------------------------------------------------
+// complex numbers in the compute precision
+// ------------------------------------------------------------------------------------
+template <typename R> struct cplx { R re, im; };
+
+template <typename R> LQ_HD cplx<R> cmk(R a, R b) { return {a, b}; }
+template <typename R> LQ_HD cplx<R> cadd(cplx<R> a, cplx<R> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename R> LQ_HD cplx<R> csub(cplx<R> a, cplx<R> b) { return {a.re - b.re, a.im - b.im}; }
+// i*a and -i*a
+template <typename R> LQ_HD cplx<R> ctimes_i(cplx<R> a) { return {-a.im, a.re}; }
+template <typename R> LQ_HD cplx<R> ctimes_mi(cplx<R> a) { return {a.im, -a.re}; }
+template <typename R> LQ_HD cplx<R> cconj(cplx<R> a) { return {a.re, -a.im}; }
+template <typename R> LQ_HD cplx<R> cmul(cplx<R> a, cplx<R> b) {
+    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+// c + a*b
+template <typename R> LQ_HD cplx<R> cfma(cplx<R> a, cplx<R> b, cplx<R> c) {
+    return {fma(a.re, b.re, fma(-a.im, b.im, c.re)), fma(a.re, b.im, fma(a.im, b.re, c.im))};
+}
+// c + conj(a)*b
+template <typename R> LQ_HD cplx<R> cfmac(cplx<R> a, cplx<R> b, cplx<R> c) {
+    return {fma(a.re, b.re, fma(a.im, b.im, c.re)), fma(a.re, b.im, fma(-a.im, b.re, c.im))};
+}
+template <typename R> LQ_HD cplx<R> cscale(R s, cplx<R> a) { return {s * a.re, s * a.im}; }
+// c + s*a
+template <typename R> LQ_HD cplx<R> caxpy(R s, cplx<R> a, cplx<R> c) {
+    return {fma(s, a.re, c.re), fma(s, a.im, c.im)};
+}
+
+// A spinor in registers: 12 complex numbers, index spin*3 + colour.
+template <typename R> struct Spinor { cplx<R> v[12]; };
+// A link in registers: u[row][col].
+template <typename R> struct Link { cplx<R> u[3][3]; };
+
+// ------------------------------------------------------------------------------------
+// precision traits
+// ------------------------------------------------------------------------------------
+template <int PREC> struct PrecT;
+template <> struct PrecT<LQ_F64> { using Real = double; };
+template <> struct PrecT<LQ_F32> { using Real = float; };
+template <> struct PrecT<LQ_F16S> { using Real = float; };
+
+// ------------------------------------------------------------------------------------
+// lattice geometry
+// ------------------------------------------------------------------------------------
+struct Geom {
+    int L[4];       // extents x, y, z, t
+    int S[4];       // lexicographic strides 1, Lx, Lx*Ly, Lx*Ly*Lz
+    int V, Vh;
+    int Lxh;        // Lx / 2
+};
+
+inline Geom make_geom(const int32_t d[4]) {
+    Geom g;
+    for (int i = 0; i < 4; ++i) g.L[i] = d[i];
+    g.S[0] = 1;
+    g.S[1] = d[0];
+    g.S[2] = d[0] * d[1];
+    g.S[3] = d[0] * d[1] * d[2];
+    g.V = d[0] * d[1] * d[2] * d[3];
+    g.Vh = g.V / 2;
+    g.Lxh = d[0] / 2;
+    return g;
+}
+
+// A site seen from every layout: lexicographic index, parity and checkerboard index.
+struct Site { int lex, p, cb; };
+
+LQ_HD void coords_from_lex(const Geom& g, int lex, int c[4]) {
+    int r = lex;
+    c[0] = r % g.L[0]; r /= g.L[0];
+    c[1] = r % g.L[1]; r /= g.L[1];
+    c[2] = r % g.L[2];
+    c[3] = r / g.L[2];
+}
+
+LQ_HD Site site_from_lex(const Geom& g, int lex, int c[4]) {
+    coords_from_lex(g, lex, c);
+    return Site{lex, (c[0] + c[1] + c[2] + c[3]) & 1, lex >> 1};
+}
+
+// (p, cb) -> coordinates: cb = x/2 + (Lx/2)*(y + Ly*(z + Lz*t)), x's low bit fixed by p.
+LQ_HD Site site_from_eo(const Geom& g, int p, int cb, int c[4]) {
+    int r = cb;
+    const int xh = r % g.Lxh; r /= g.Lxh;
+    c[1] = r % g.L[1]; r /= g.L[1];
+    c[2] = r % g.L[2];
+    c[3] = r / g.L[2];
+    c[0] = 2 * xh + ((p + c[1] + c[2] + c[3]) & 1);
+    const int lex = 2 * cb + (c[0] & 1);
+    return Site{lex, p, cb};
+}
+
+// lexicographic index of n + mu (fwd) and n - mu (bwd), periodic
+LQ_HD int lex_fwd(const Geom& g, int lex, const int c[4], int mu) {
+    return (c[mu] == g.L[mu] - 1) ? lex - (g.L[mu] - 1) * g.S[mu] : lex + g.S[mu];
+}
+LQ_HD int lex_bwd(const Geom& g, int lex, const int c[4], int mu) {
+    return (c[mu] == 0) ? lex + (g.L[mu] - 1) * g.S[mu] : lex - g.S[mu];
+}
+LQ_HD Site nb_site(int lexn, int p) { return Site{lexn, p ^ 1, lexn >> 1}; }
+
+// ------------------------------------------------------------------------------------
+// load helpers (read-only path for fields that are constant during a kernel)
+// ------------------------------------------------------------------------------------
+template <bool RO, typename T> LQ_HD T ld(const T* p) {
+#ifdef __CUDA_ARCH__
+    if constexpr (RO) return __ldg(p);
+    else return *p;
+#else
+    return *p;
+#endif
+}
+
+// x / y in FP32, correctly rounded
+LQ_HD float div_rn(float x, float y) {
+#ifdef __CUDA_ARCH__
+    return __fdiv_rn(x, y);
+#else
+    return x / y;
+#endif
+}
+
+LQ_HD float2 h2f2(uint32_t w) {
+    __half2 h = *reinterpret_cast<__half2*>(&w);
+    return __half22float2(h);
+}
+LQ_HD uint32_t f22h2(float a, float b) {
+    __half2 h = __halves2half2(__float2half_rn(a), __float2half_rn(b));
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// ------------------------------------------------------------------------------------
+// Spinor field accessors.
+//   LEX: chunk k of site n at slot n*K + k.
+//   EO : chunk k of (p, cb) at slot p*pstride + k*Vh + cb (pstride = K*Vh for a full
+//        field, 0 for a half field holding one parity).
+// F16S scales: LEX at n, EO at p*sstride + cb (sstride = Vh full, 0 half).
+// ------------------------------------------------------------------------------------
+template <int PREC, int LAYOUT, bool RO> struct SpinorAcc;
+
+struct EoIdx {
+    int64_t Vh, pstride, sstride;
+};
+
+template <int LAYOUT> LQ_HD int64_t sp_base(const Site& s, int K, const EoIdx& e) {
+    if constexpr (LAYOUT == LQ_LAYOUT_LEX) return (int64_t)s.lex * K;
+    else return (int64_t)s.p * e.pstride + s.cb;
+}
+template <int LAYOUT> LQ_HD int64_t sp_kstride(const EoIdx& e) {
+    if constexpr (LAYOUT == LQ_LAYOUT_LEX) return 1;
+    else return e.Vh;
+}
+template <int LAYOUT> LQ_HD int64_t sp_sidx(const Site& s, const EoIdx& e) {
+    if constexpr (LAYOUT == LQ_LAYOUT_LEX) return s.lex;
+    else return (int64_t)s.p * e.sstride + s.cb;
+}
+
+template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F64, LAYOUT, RO> {
+    using Real = double;
+    static constexpr int K = 12;
+    double2* ptr;
+    EoIdx e;
+    template <typename T> LQ_HD void load(const Site& s, Spinor<T>& out) const {
+        const int64_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            double2 v = ld<RO>(ptr + b + k * ks);
+            out.v[k] = {(T)v.x, (T)v.y};
+        }
+    }
+    template <typename T> LQ_HD void store(const Site& s, const Spinor<T>& in) const {
+        const int64_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) ptr[b + k * ks] = make_double2((double)in.v[k].re, (double)in.v[k].im);
+    }
+};
+
+template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F32, LAYOUT, RO> {
+    using Real = float;
+    static constexpr int K = 6;
+    float4* ptr;
+    EoIdx e;
+    template <typename T> LQ_HD void load(const Site& s, Spinor<T>& out) const {
+        const int64_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            float4 v = ld<RO>(ptr + b + k * ks);
+            out.v[2 * k] = {(T)v.x, (T)v.y};
+            out.v[2 * k + 1] = {(T)v.z, (T)v.w};
+        }
+    }
+    template <typename T> LQ_HD void store(const Site& s, const Spinor<T>& in) const {
+        const int64_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            ptr[b + k * ks] = make_float4((float)in.v[2 * k].re, (float)in.v[2 * k].im,
+                                          (float)in.v[2 * k + 1].re, (float)in.v[2 * k + 1].im);
+    }
+};
+
+// Scaled FP16: value = half * scale, scale = max |fl32(v)| of the site.  Loads compute
+// half * scale in T (exact when T = double); stores round to FP32 first, then divide by
+// the scale in FP32 (correctly rounded) and round to FP16.
+template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F16S, LAYOUT, RO> {
+    using Real = float;
+    static constexpr int K = 3;
+    uint4* ptr;
+    float* scale;
+    EoIdx e;
+    template <typename T> LQ_HD void load(const Site& s, Spinor<T>& out) const {
+        const int64_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
+        const T sc = (T)ld<RO>(scale + sp_sidx<LAYOUT>(s, e));
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            uint4 w = ld<RO>(ptr + b + k * ks);
+            const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float2 a = h2f2(ww[j]);
+                out.v[4 * k + j] = {(T)a.x * sc, (T)a.y * sc};
+            }
+        }
+    }
+    template <typename T> LQ_HD void store(const Site& s, const Spinor<T>& in) const {
+        const int64_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
+        float f[24];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) { f[2 * k] = (float)in.v[k].re; f[2 * k + 1] = (float)in.v[k].im; }
+        float m = 0.f;
+#pragma unroll
+        for (int k = 0; k < 24; ++k) m = fmaxf(m, fabsf(f[k]));
+        scale[sp_sidx<LAYOUT>(s, e)] = m;
+        const bool z = !(m > 0.f);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float q[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) q[j] = z ? 0.f : div_rn(f[8 * k + j], m);
+            ptr[b + k * ks] = make_uint4(f22h2(q[0], q[1]), f22h2(q[2], q[3]), f22h2(q[4], q[5]), f22h2(q[6], q[7]));
+        }
+    }
+};
+
+// ------------------------------------------------------------------------------------
+// Gauge field accessors.
+//   LEX: chunk k of link (n, mu) at slot (n*4 + mu)*K + k.
+//   EO : chunk k of link (mu, p, cb) at slot ((mu*2 + p)*K + k)*Vh + cb.
+// LINK12 rebuilds row 2 = conj(row0 x row1).
+// ------------------------------------------------------------------------------------
+template <typename R> LQ_HD void reconstruct_row2(Link<R>& U) {
+    const cplx<R>* a = U.u[0];
+    const cplx<R>* b = U.u[1];
+    // (a x b)_0 = a1 b2 - a2 b1 etc.; row 2 is the complex conjugate
+    cplx<R> c0 = csub(cmul(a[1], b[2]), cmul(a[2], b[1]));
+    cplx<R> c1 = csub(cmul(a[2], b[0]), cmul(a[0], b[2]));
+    cplx<R> c2 = csub(cmul(a[0], b[1]), cmul(a[1], b[0]));
+    U.u[2][0] = cconj(c0);
+    U.u[2][1] = cconj(c1);
+    U.u[2][2] = cconj(c2);
+}
+
+template <int LAYOUT> LQ_HD int64_t lk_base(const Site& s, int mu, int K, int64_t Vh) {
+    if constexpr (LAYOUT == LQ_LAYOUT_LEX) return ((int64_t)s.lex * 4 + mu) * K;
+    else return ((int64_t)(mu * 2 + s.p) * K) * Vh + s.cb;
+}
+template <int LAYOUT> LQ_HD int64_t lk_kstride(int64_t Vh) {
+    if constexpr (LAYOUT == LQ_LAYOUT_LEX) return 1;
+    else return Vh;
+}
+
+template <int PREC, int FMT, int LAYOUT> struct GaugeAcc;
+
+// FP64: double2 chunks (one complex), 9 or 6 per link
+template <int FMT, int LAYOUT> struct GaugeAcc<LQ_F64, FMT, LAYOUT> {
+    using Real = double;
+    static constexpr int K = FMT / 2;
+    const double2* ptr;
+    int64_t Vh;
+    LQ_HD void load(const Site& s, int mu, Link<double>& U) const {
+        const int64_t b = lk_base<LAYOUT>(s, mu, K, Vh), ks = lk_kstride<LAYOUT>(Vh);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double2 v = ld<true>(ptr + b + k * ks);
+            U.u[k / 3][k % 3] = {v.x, v.y};
+        }
+        if constexpr (FMT == 12) reconstruct_row2(U);
+    }
+};
+
+// FP32 18: float2 chunks; FP32 12: float4 chunks (two complex)
+template <int LAYOUT> struct GaugeAcc<LQ_F32, 18, LAYOUT> {
+    using Real = float;
+    static constexpr int K = 9;
+    const float2* ptr;
+    int64_t Vh;
+    LQ_HD void load(const Site& s, int mu, Link<float>& U) const {
+        const int64_t b = lk_base<LAYOUT>(s, mu, K, Vh), ks = lk_kstride<LAYOUT>(Vh);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            float2 v = ld<true>(ptr + b + k * ks);
+            U.u[k / 3][k % 3] = {v.x, v.y};
+        }
+    }
+};
+template <int LAYOUT> struct GaugeAcc<LQ_F32, 12, LAYOUT> {
+    using Real = float;
+    static constexpr int K = 3;
+    const float4* ptr;
+    int64_t Vh;
+    LQ_HD void load(const Site& s, int mu, Link<float>& U) const {
+        const int64_t b = lk_base<LAYOUT>(s, mu, K, Vh), ks = lk_kstride<LAYOUT>(Vh);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float4 v = ld<true>(ptr + b + k * ks);
+            const int c0 = 2 * k, c1 = 2 * k + 1;
+            U.u[c0 / 3][c0 % 3] = {v.x, v.y};
+            U.u[c1 / 3][c1 % 3] = {v.z, v.w};
+        }
+        reconstruct_row2(U);
+    }
+};
+
+// FP16 18: one half2 (one complex) per chunk; FP16 12: uint2 = four halves (two complex)
+template <int LAYOUT> struct GaugeAcc<LQ_F16S, 18, LAYOUT> {
+    using Real = float;
+    static constexpr int K = 9;
+    const uint32_t* ptr;
+    int64_t Vh;
+    LQ_HD void load(const Site& s, int mu, Link<float>& U) const {
+        const int64_t b = lk_base<LAYOUT>(s, mu, K, Vh), ks = lk_kstride<LAYOUT>(Vh);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            float2 v = h2f2(ld<true>(ptr + b + k * ks));
+            U.u[k / 3][k % 3] = {v.x, v.y};
+        }
+    }
+};
+template <int LAYOUT> struct GaugeAcc<LQ_F16S, 12, LAYOUT> {
+    using Real = float;
+    static constexpr int K = 3;
+    const uint2* ptr;
+    int64_t Vh;
+    LQ_HD void load(const Site& s, int mu, Link<float>& U) const {
+        const int64_t b = lk_base<LAYOUT>(s, mu, K, Vh), ks = lk_kstride<LAYOUT>(Vh);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            uint2 w = ld<true>(ptr + b + k * ks);
+            float2 a = h2f2(w.x), c = h2f2(w.y);
+            const int c0 = 2 * k, c1 = 2 * k + 1;
+            U.u[c0 / 3][c0 % 3] = {a.x, a.y};
+            U.u[c1 / 3][c1 % 3] = {c.x, c.y};
+        }
+        reconstruct_row2(U);
+    }
+};
+
+// ------------------------------------------------------------------------------------
+// Solver state in device memory (part of the caller's workspace).  Written only by the
+// last block of a reducing kernel (the "finisher"), read by later kernels.
+// ------------------------------------------------------------------------------------
+struct SolverState {
+    double rho;         // ||r||^2 of the inner iterate, in the cycle's units
+    double alpha, beta;
+    double sigma;       // <p, D^dag D p> = ||D p||^2 of the last iteration
+    double stop_rho;    // inner loop stops when rho <= stop_rho
+    double red[4];      // results of standalone reductions
+    int iter;           // inner iterations in the current cycle
+    int k_max;          // inner iteration cap for the current cycle
+    int stop;           // 0 running; 1 criterion met / cap; 2 breakdown; 3 non-finite
+    int p_iter;         // iteration whose search-direction update has been written
+    unsigned int ticket[4];
+};
+
+constexpr int kMaxPartials = 4096;     // per-block partial sums (x 2 for complex dots)
+constexpr int kTicketK1 = 0, kTicketK2 = 1, kTicketK3 = 2, kTicketMisc = 3;
+
+struct RedCtx {
+    SolverState* st;
+    double* partials;   // at least 2 * gridDim.x doubles
+};
+
+// Sum of v over the block (deterministic tree); result valid in thread 0.
+template <int BS> __device__ __forceinline__ double block_sum(double v, double* sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < BS / 32; ++i) t += sh[i];
+    }
+    return t;
+}
+
+// Grid-wide deterministic reduction of NV values per thread.  Every block stores its
+// partials; the block that arrives last sums them in block order and calls fin(total)
+// from thread 0.  Returns nothing; no block waits for another.
+template <int BS, int NV, class Fin>
+__device__ __forceinline__ void grid_reduce(const RedCtx& rc, int ticket_id, const double (&v)[NV], Fin fin) {
+    __shared__ double sh[BS / 32];
+    __shared__ bool last;
+    double tot[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        tot[j] = block_sum<BS>(v[j], sh);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) rc.partials[(size_t)j * gridDim.x + blockIdx.x] = tot[j];
+        __threadfence();
+        const unsigned int t = atomicAdd(&rc.st->ticket[ticket_id], 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double fin_v[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        double s = 0.0;
+        for (int i = threadIdx.x; i < (int)gridDim.x; i += BS) s += __ldcg(rc.partials + (size_t)j * gridDim.x + i);
+        fin_v[j] = block_sum<BS>(s, sh);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        rc.st->ticket[ticket_id] = 0u;
+        fin(fin_v);
+    }
+}
+
+}  // namespace lq

@@ -1,0 +1,116 @@
+"""The C ABI without a GPU: the library builds and loads, exports every entry point that
+include/lq.h declares, and its argument checks reject bad calls before touching CUDA."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import formats as F
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lq.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?(?:int|size_t|char|void)\s*\*?\s*(\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("lq_dslash_apply", "lq_dslash_adjoint", "lq_cg_solve", "lq_cg_workspace_bytes",
+                 "lq_last_error", "dslash_apply", "dslash_adjoint", "cg_solve"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lqlib):
+    L = lqlib.load()
+    for name in declared_functions():
+        assert hasattr(L, name), name
+        assert ctypes.cast(getattr(L, name), ctypes.c_void_p).value
+
+
+def test_field_bytes_match_format_definitions(lqlib):
+    for dims in [(2, 2, 2, 2), (4, 6, 2, 8)]:
+        for prec in ("f64", "f32", "f16s"):
+            for layout in ("lex", "eo"):
+                assert lqlib.field_bytes(dims, "spinor", prec, 18, layout) == F.spinor_bytes(dims, prec)
+                for fmt in (18, 12):
+                    assert lqlib.field_bytes(dims, "gauge", prec, fmt, layout) == F.gauge_bytes(dims, prec, fmt)
+    assert lqlib.field_bytes((3, 4, 4, 4), "spinor") == 0
+    assert lqlib.field_bytes((4, 4, 4, 4), "gauge", "f32", 10) == 0
+
+
+def test_workspace_query(lqlib):
+    a = lqlib.cg_workspace_bytes((4, 4, 4, 4), "f64")
+    b = lqlib.cg_workspace_bytes((8, 8, 8, 8), "f64")
+    assert 0 < a < b
+    assert lqlib.cg_workspace_bytes((8, 8, 8, 8), "mixed_f16") < lqlib.cg_workspace_bytes((8, 8, 8, 8), "mixed_f32")
+    assert lqlib.cg_workspace_bytes((4, 4, 4, 5), "f64") == 0
+    assert lqlib.load().lq_cg_workspace_bytes((ctypes.c_int32 * 4)(4, 4, 4, 4), 7) == 0
+
+
+# fake device addresses: the checks below fail before any CUDA call, nothing is dereferenced
+P0, P1, P2 = 0x10000, 0x20000000, 0x40000000
+
+
+def _apply(L, dims, prec=0, fmt=18, layout=0, U=P0, psi=P1, out=P2, m=0.1):
+    vp = ctypes.c_void_p
+    return L.lq_dslash_apply((ctypes.c_int32 * 4)(*dims), m, prec, fmt, layout, vp(U), vp(psi), vp(out), None)
+
+
+def test_apply_argument_checks(lqlib):
+    L = lqlib.load()
+    assert _apply(L, (4, 4, 4, 3)) == -2
+    assert "even" in lqlib.last_error()
+    assert _apply(L, (0, 4, 4, 4)) == -2
+    assert _apply(L, (4096, 4096, 4096, 2)) == -2          # volume beyond 2^31 - 2
+    assert _apply(L, (4, 4, 4, 4), prec=5) == -1
+    assert _apply(L, (4, 4, 4, 4), fmt=10) == -1
+    assert _apply(L, (4, 4, 4, 4), layout=2) == -1
+    assert _apply(L, (4, 4, 4, 4), U=0) == -1
+    assert _apply(L, (4, 4, 4, 4), psi=P1 + 8) == -3          # misaligned
+    assert _apply(L, (4, 4, 4, 4), out=P1) == -3              # out aliases psi
+    assert _apply(L, (4, 4, 4, 4), out=P1 + 4096) == -3       # partial overlap
+    assert _apply(L, (4, 4, 4, 4), m=float("nan")) == -1
+    assert L.lq_dslash_adjoint((ctypes.c_int32 * 4)(4, 4, 4, 3), 0.1, 0, 18, 0, None, None, None, None) == -2
+
+
+def test_hop_and_convert_argument_checks(lqlib):
+    L = lqlib.load()
+    vp = ctypes.c_void_p
+    d = (ctypes.c_int32 * 4)(4, 4, 4, 4)
+    assert L.lq_dslash_hop(d, 2, 0, 0.0, 1.0, 0, 18, vp(P0), vp(P1), None, vp(P2), None) == -1
+    assert L.lq_dslash_hop(d, 0, 0, 0.0, float("inf"), 0, 18, vp(P0), vp(P1), None, vp(P2), None) == -1
+    assert L.lq_dslash_hop(d, 0, 0, 0.0, 1.0, 0, 18, vp(P0), vp(P1), vp(P2 + 16), vp(P2), None) == -3
+    assert L.lq_convert_spinor(d, 0, 0, vp(P0), 1, 1, vp(P0), None) == -3
+    assert L.lq_convert_gauge(d, 0, 0, vp(P0), 1, 11, 1, vp(P1), None) == -1
+
+
+def test_cg_argument_checks(lqlib):
+    L = lqlib.load()
+    vp = ctypes.c_void_p
+    d = (ctypes.c_int32 * 4)(4, 4, 4, 4)
+    info = lqlib.CgInfo()
+    prm = lqlib.CgParams(1e-10, 100, 0, 0.0, 0, 0)
+    call = lambda mode=0, p=prm, ws=P2, wsb=1 << 30, x=P1: L.lq_cg_solve(
+        d, 0.1, mode, vp(P0), vp(0x30000000), vp(x), ctypes.byref(p), vp(ws), ctypes.c_size_t(wsb),
+        ctypes.byref(info), None)
+    assert call(mode=9) == -1
+    assert call(ws=0) == -5
+    assert call(wsb=100) == -5                       # smaller than the workspace query
+    assert info.status == -5
+    assert call(p=lqlib.CgParams(-1.0, 100, 0, 0.0, 0, 0)) == -1
+    assert call(p=lqlib.CgParams(1e-10, 0, 0, 0.0, 0, 0)) == -1
+    assert call(p=lqlib.CgParams(1e-10, 10, 0, 1.5, 0, 0)) == -1
+    assert call(x=0x30000000) == -3                  # x aliases eta
+    assert "alias" in lqlib.last_error() or "overlap" in lqlib.last_error()
+
+
+def test_version(lqlib):
+    assert "sm_103a" in lqlib.version()

@@ -1,0 +1,140 @@
+"""GPU conjugate-gradient solves of D^dag D x = eta against the CPU oracle.
+
+The oracle recomputes the true residual ||eta - D^dag D x|| / ||eta|| of every GPU
+solution in FP64 and its own textbook CG gives the reference solution; D^dag D is
+Hermitian positive definite, so the solution is unique and the two solutions can differ
+only by the tolerance times the condition number.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import dense
+from oracle import formats as F
+from fieldio import to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+RESID_SLACK = 1.001   # FP64 rounding between the GPU's and the oracle's residual evaluation
+
+
+def _solve(lqlib, dims, m, U, eta, mode, x0=None, **kw):
+    Ud = to_dev(F.encode_gauge(U, dims, "f64", 18, "lex"))
+    ed = to_dev(F.encode_spinor(eta, dims, "f64", "lex"))
+    xd = to_dev(F.encode_spinor(x0 if x0 is not None else np.zeros_like(eta), dims, "f64", "lex"))
+    x, info, status = lqlib.cg_solve(dims, m, Ud, ed, x=xd, mode=mode, **kw)
+    return F.decode_spinor(to_host(x), dims, "f64", "lex"), info, status
+
+
+def _true_resid(dims, m, U, eta, x):
+    r = eta - oracle.normal_op(dims, m, U, x)
+    return np.linalg.norm(r.ravel()) / np.linalg.norm(eta.ravel())
+
+
+@pytest.mark.parametrize("mode", ["f64", "mixed_f32", "mixed_f16"])
+def test_cg_2222_against_dense_solve(lqlib, mode):
+    dims = (2, 2, 2, 2)
+    m = 0.1
+    U = synth.gauge_field(dims, seed=1)
+    eta = synth.gaussian_spinor(dims, seed=2)
+    x, info, status = _solve(lqlib, dims, m, U, eta, mode, tol=1e-10)
+    assert status == 0 and info["true_rel_resid"] <= 1e-10
+    Dd = dense.dense_dirac(dims, m, U)
+    A = Dd.conj().T @ Dd
+    xd = np.linalg.solve(A, eta.ravel())
+    assert np.linalg.norm(eta.ravel() - A @ x.ravel()) / np.linalg.norm(eta.ravel()) <= 1e-10 * RESID_SLACK
+    assert oracle.rel_l2(x.ravel(), xd) <= 1e-10 * np.linalg.cond(A)
+
+
+@pytest.mark.parametrize("mode", ["f64", "mixed_f32", "mixed_f16"])
+def test_cg_4444_haar_against_oracle(lqlib, mode):
+    """The small FP64 configuration: 4^4 Haar links, m_q = 0.1, tolerance 1e-10."""
+    dims = (4, 4, 4, 4)
+    m = 0.1
+    U = synth.gauge_field(dims, seed=1)
+    eta = synth.gaussian_spinor(dims, seed=2)
+    x, info, status = _solve(lqlib, dims, m, U, eta, mode, tol=1e-10)
+    assert status == 0
+    assert info["true_rel_resid"] <= 1e-10
+    assert _true_resid(dims, m, U, eta, x) <= 1e-10 * RESID_SLACK
+    xo, it, rel = oracle.cg(dims, m, U, eta, tol=1e-12)
+    assert oracle.rel_l2(x, xo) <= 1e-7
+    if mode == "f64":
+        # plain CG: the same iterations as the oracle's textbook CG (up to rounding)
+        _, it10, _ = oracle.cg(dims, m, U, eta, tol=1e-10)
+        assert abs(info["iters"] - it10) <= 2
+        assert info["cycles"] <= 2
+
+
+@pytest.mark.parametrize("mode", ["f64", "mixed_f32", "mixed_f16"])
+def test_cg_near_identity_ragged(lqlib, mode):
+    """Near-free links, small mass (the ill-conditioned case) on a lattice with a ragged
+    last tile."""
+    dims = (6, 4, 10, 2)
+    m = 0.05
+    U = synth.gauge_field(dims, seed=5, kind="near_identity", eps=0.3)
+    eta = synth.gaussian_spinor(dims, seed=6)
+    x, info, status = _solve(lqlib, dims, m, U, eta, mode, tol=1e-10)
+    assert status == 0
+    assert _true_resid(dims, m, U, eta, x) <= 1e-10 * RESID_SLACK
+    if mode != "f64":
+        assert info["cycles"] >= 2
+
+
+def test_cg_starting_guess_and_resume(lqlib):
+    """A solve started from a previous solution converges at once (resume = call again)."""
+    dims = (4, 4, 4, 4)
+    m = 0.1
+    U = synth.gauge_field(dims, seed=11)
+    eta = synth.gaussian_spinor(dims, seed=12)
+    x1, info1, st1 = _solve(lqlib, dims, m, U, eta, "mixed_f32", tol=1e-8)
+    assert st1 == 0
+    x2, info2, st2 = _solve(lqlib, dims, m, U, eta, "mixed_f32", x0=x1, tol=1e-10)
+    assert st2 == 0 and info2["iters"] < info1["iters"] + 5
+    assert _true_resid(dims, m, U, eta, x2) <= 1e-10 * RESID_SLACK
+
+
+def test_cg_zero_rhs(lqlib):
+    dims = (4, 4, 2, 2)
+    U = synth.gauge_field(dims, seed=13)
+    eta = np.zeros((synth.volume(dims), 4, 3), np.complex128)
+    x0 = synth.gaussian_spinor(dims, seed=14)
+    x, info, status = _solve(lqlib, dims, 0.1, U, eta, "f64", x0=x0)
+    assert status == 0 and info["iters"] == 0 and np.all(x == 0)
+
+
+def test_cg_max_iter_not_converged(lqlib):
+    dims = (4, 4, 4, 4)
+    U = synth.gauge_field(dims, seed=15, kind="near_identity", eps=0.3)
+    eta = synth.gaussian_spinor(dims, seed=16)
+    x, info, status = _solve(lqlib, dims, 0.01, U, eta, "mixed_f32", tol=1e-10, max_iter=3)
+    assert status == 1
+    assert info["iters"] <= 3
+    assert 1e-10 < info["true_rel_resid"] < 1.0
+    # the returned x is the iterate whose FP64 residual was reported
+    assert abs(_true_resid(dims, 0.01, U, eta, x) - info["true_rel_resid"]) < 1e-8
+
+
+def test_cg_workspace_too_small(lqlib):
+    import torch
+    dims = (4, 4, 4, 4)
+    U = to_dev(F.encode_gauge(synth.gauge_field(dims, seed=1), dims))
+    eta = to_dev(F.encode_spinor(synth.gaussian_spinor(dims, seed=2), dims))
+    ws = torch.empty(1024, dtype=torch.uint8, device="cuda")
+    with pytest.raises(ValueError):
+        lqlib.cg_solve(dims, 0.1, U, eta, workspace=ws)
+
+
+@pytest.mark.parametrize("mode", ["mixed_f32", "mixed_f16", "f64"])
+def test_cg_full_size_32(lqlib, mode):
+    """The mixed-precision workload at full size: 32^4, links exp(0.3 i H), m_q = 0.05,
+    tolerance 1e-10; the oracle recomputes the true residual in FP64."""
+    dims = (32, 32, 32, 32)
+    m = 0.05
+    U = synth.gauge_field(dims, seed=3, kind="near_identity", eps=0.3)
+    eta = synth.gaussian_spinor(dims, seed=4)
+    x, info, status = _solve(lqlib, dims, m, U, eta, mode, tol=1e-10)
+    assert status == 0
+    assert info["true_rel_resid"] <= 1e-10
+    assert _true_resid(dims, m, U, eta, x) <= 1e-10 * RESID_SLACK
