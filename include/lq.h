@@ -195,6 +195,28 @@ int lq_cg_solve(const int32_t dims[4], double m_q, int32_t mode, const void *U,
                 const void *eta, void *x, const lq_cg_params *params, void *workspace,
                 size_t ws_bytes, lq_cg_info *info, void *cuda_stream);
 
+/*
+ * lq_cg_solve_noalloc -- lq_cg_solve without a caller workspace.  The paper has no
+ * counterpart; this entry point exists for callers that cannot allocate device memory at
+ * solve time: code under a no-allocation rule after start-up (real-time or reviewed
+ * loops), plugins inside a host program whose allocator owns all device memory, or callers
+ * with no CUDA allocator at hand.  They pass U, eta and x exactly as for lq_cg_solve; the
+ * scratch is a fixed array inside this library (lq_cg_noalloc_max_workspace_bytes() bytes,
+ * 64 MiB), which every GPU that loads the library holds until the process exits.
+ *   - Lattices whose lq_cg_workspace_bytes(dims, mode) exceeds that size are rejected with
+ *     LQ_ERR_WORKSPACE (e.g. 16^4 fits in the mixed modes, 12^4 in LQ_CG_F64).
+ *   - The first call on a device looks up the array's device address (once per device,
+ *     with that device current); make that first call before any stream capture.
+ *   - All calls share the one array, which keeps the previous call's contents; the solver
+ *     re-initialises everything it reads.  Calls that overlap on the GPU (other streams,
+ *     other host threads) race on the array and must not be issued.
+ *   - Nothing is allocated: no cudaMalloc / cudaFree or allocating library routine.
+ */
+int lq_cg_solve_noalloc(const int32_t dims[4], double m_q, int32_t mode, const void *U,
+                        const void *eta, void *x, const lq_cg_params *params, lq_cg_info *info,
+                        void *cuda_stream);
+size_t lq_cg_noalloc_max_workspace_bytes(void);
+
 /* Message of the last error on this host thread ("" if none). */
 const char *lq_last_error(void);
 
