@@ -71,7 +71,7 @@ int check_dims(const int32_t* dims, Geom* g) {
         if (dims[i] < 2 || (dims[i] & 1))
             return fail(LQ_ERR_DIMS, "lattice extent %d is %d: extents must be even and >= 2", i, (int)dims[i]);
         v *= dims[i];
-        if (v > 2147483646LL) return fail(LQ_ERR_DIMS, "lattice volume exceeds 2^31 - 2 sites");
+        if (v > 100000000LL) return fail(LQ_ERR_DIMS, "lattice volume exceeds 10^8 sites");
     }
     *g = make_geom(dims);
     return LQ_OK;

@@ -1,0 +1,106 @@
+// FP32-pair ("double-float") numbers for FP64-class arithmetic on FP32 pipes.
+//
+// A value is hi + lo with two floats.  Sums use Knuth's TwoSum (the rounding error of a
+// float addition is recovered exactly), products Dekker's TwoProduct in its FMA form
+// (e = fma(a, b, -fl(a*b)) is the exact error of the product), following Dekker (1971) and
+// Knuth (TAOCP vol. 2, 4.2.2).  Sums are left unnormalised (lo may grow to a few ulps of
+// hi) and renormalised with FastTwoSum where a result is stored; the relative precision
+// is about 2^-47.
+//
+// All operations use the _rn intrinsics so that the compiler cannot contract a product
+// and a sum into one FMA, which would break the error-free transformations.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#ifndef LQ_HD
+#define LQ_HD __host__ __device__ __forceinline__
+#endif
+
+namespace lq {
+
+struct dd {
+    float hi, lo;
+};
+
+LQ_HD float f_add(float a, float b) {
+#ifdef __CUDA_ARCH__
+    return __fadd_rn(a, b);
+#else
+    volatile float s = a + b;
+    return s;
+#endif
+}
+LQ_HD float f_sub(float a, float b) {
+#ifdef __CUDA_ARCH__
+    return __fsub_rn(a, b);
+#else
+    volatile float s = a - b;
+    return s;
+#endif
+}
+LQ_HD float f_mul(float a, float b) {
+#ifdef __CUDA_ARCH__
+    return __fmul_rn(a, b);
+#else
+    volatile float s = a * b;
+    return s;
+#endif
+}
+LQ_HD float f_fma(float a, float b, float c) {
+#ifdef __CUDA_ARCH__
+    return __fmaf_rn(a, b, c);
+#else
+    return fmaf(a, b, c);
+#endif
+}
+
+// s + e = a + b exactly (TwoSum, 6 operations, no ordering requirement)
+LQ_HD void two_sum(float a, float b, float& s, float& e) {
+    s = f_add(a, b);
+    const float bb = f_sub(s, a);
+    e = f_add(f_sub(a, f_sub(s, bb)), f_sub(b, bb));
+}
+
+// renormalise: |lo| <= ulp(hi)/2 afterwards (FastTwoSum; valid because |lo| << |hi| or hi = 0)
+LQ_HD dd dd_renorm(dd a) {
+    const float s = f_add(a.hi, a.lo);
+    return dd{s, f_sub(a.lo, f_sub(s, a.hi))};
+}
+
+LQ_HD dd operator+(dd a, dd b) {
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    return dd{s, f_add(e, f_add(a.lo, b.lo))};
+}
+LQ_HD dd operator-(dd a) { return dd{-a.hi, -a.lo}; }
+LQ_HD dd operator-(dd a, dd b) { return a + (-b); }
+
+// product: hi*hi exactly as p + e, plus the two cross terms; lo*lo (~2^-48 relative) dropped
+LQ_HD dd operator*(dd a, dd b) {
+    const float p = f_mul(a.hi, b.hi);
+    float e = f_fma(a.hi, b.hi, -p);
+    e = f_fma(a.hi, b.lo, e);
+    e = f_fma(a.lo, b.hi, e);
+    return dd{p, e};
+}
+
+// a*b + c with one TwoSum
+LQ_HD dd fma(dd a, dd b, dd c) {
+    const float p = f_mul(a.hi, b.hi);
+    float e = f_fma(a.hi, b.hi, -p);
+    e = f_fma(a.hi, b.lo, e);
+    e = f_fma(a.lo, b.hi, e);
+    float s, t;
+    two_sum(c.hi, p, s, t);
+    return dd{s, f_add(t, f_add(e, c.lo))};
+}
+
+// FP64 <-> pair (host or set-up code; uses FP64 arithmetic)
+LQ_HD dd dd_from_double(double x) {
+    const float h = (float)x;
+    return dd{h, (float)(x - (double)h)};
+}
+LQ_HD double dd_to_double(dd a) { return (double)a.hi + (double)a.lo; }
+
+}  // namespace lq

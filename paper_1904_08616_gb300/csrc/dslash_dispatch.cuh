@@ -31,7 +31,7 @@ template <int PREC, int FMT, int LAYOUT>
 inline GaugeAcc<PREC, FMT, LAYOUT> make_gauge(const void* buf, const Geom& g) {
     GaugeAcc<PREC, FMT, LAYOUT> a;
     a.ptr = (decltype(a.ptr))buf;
-    a.Vh = g.Vh;
+    a.Vh = (uint32_t)g.Vh;
     return a;
 }
 

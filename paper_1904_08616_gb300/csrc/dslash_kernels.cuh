@@ -23,9 +23,20 @@ template <int S, typename R> LQ_HD cplx<R> pm(cplx<R> a, cplx<R> b) {
     else return csub(a, b);
 }
 
-// acc += U' (1 + S gamma_MU) q,  U' = U (BACK = false) or U^dag (BACK = true)
-template <int MU, int S, bool BACK, typename R>
-LQ_HD void hop_dir(Spinor<R>& acc, const Spinor<R>& q, const Link<R>& U) {
+// acc + S*sc*x  (SCALED) or acc + S*x
+template <int S, bool SCALED, typename R> LQ_HD cplx<R> acc_add(cplx<R> acc, cplx<R> x, R sc) {
+    if constexpr (SCALED) {
+        const R f = S > 0 ? sc : -sc;
+        return {fma(f, x.re, acc.re), fma(f, x.im, acc.im)};
+    } else {
+        return pm<S>(acc, x);
+    }
+}
+
+// acc += sc * U' (1 + S gamma_MU) q,  U' = U (BACK = false) or U^dag (BACK = true);
+// sc is the neighbour's storage scale (1 unless SCALED), folded into the accumulation.
+template <int MU, int S, bool BACK, bool SCALED, typename R>
+LQ_HD void hop_dir(Spinor<R>& acc, const Spinor<R>& q, const Link<R>& U, R sc) {
     cplx<R> h0[3], h1[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -67,21 +78,21 @@ LQ_HD void hop_dir(Spinor<R>& acc, const Spinor<R>& q, const Link<R>& U) {
     }
 #pragma unroll
     for (int A = 0; A < 3; ++A) {
-        acc.v[A] = cadd(acc.v[A], g0[A]);
-        acc.v[3 + A] = cadd(acc.v[3 + A], g1[A]);
+        acc.v[A] = acc_add<1, SCALED>(acc.v[A], g0[A], sc);
+        acc.v[3 + A] = acc_add<1, SCALED>(acc.v[3 + A], g1[A], sc);
         // lower components: S B^dag (g0, g1)
         if constexpr (MU == 0) {          // B^dag g = (i g1, i g0)
-            acc.v[6 + A] = pm<S>(acc.v[6 + A], ctimes_i(g1[A]));
-            acc.v[9 + A] = pm<S>(acc.v[9 + A], ctimes_i(g0[A]));
+            acc.v[6 + A] = acc_add<S, SCALED>(acc.v[6 + A], ctimes_i(g1[A]), sc);
+            acc.v[9 + A] = acc_add<S, SCALED>(acc.v[9 + A], ctimes_i(g0[A]), sc);
         } else if constexpr (MU == 1) {   // B^dag g = (g1, -g0)
-            acc.v[6 + A] = pm<S>(acc.v[6 + A], g1[A]);
-            acc.v[9 + A] = pm<-S>(acc.v[9 + A], g0[A]);
+            acc.v[6 + A] = acc_add<S, SCALED>(acc.v[6 + A], g1[A], sc);
+            acc.v[9 + A] = acc_add<-S, SCALED>(acc.v[9 + A], g0[A], sc);
         } else if constexpr (MU == 2) {   // B^dag g = (i g0, -i g1)
-            acc.v[6 + A] = pm<S>(acc.v[6 + A], ctimes_i(g0[A]));
-            acc.v[9 + A] = pm<S>(acc.v[9 + A], ctimes_mi(g1[A]));
+            acc.v[6 + A] = acc_add<S, SCALED>(acc.v[6 + A], ctimes_i(g0[A]), sc);
+            acc.v[9 + A] = acc_add<S, SCALED>(acc.v[9 + A], ctimes_mi(g1[A]), sc);
         } else {                          // B^dag g = (g0, g1)
-            acc.v[6 + A] = pm<S>(acc.v[6 + A], g0[A]);
-            acc.v[9 + A] = pm<S>(acc.v[9 + A], g1[A]);
+            acc.v[6 + A] = acc_add<S, SCALED>(acc.v[6 + A], g0[A], sc);
+            acc.v[9 + A] = acc_add<S, SCALED>(acc.v[9 + A], g1[A], sc);
         }
     }
 }
@@ -101,14 +112,16 @@ struct Stencil {
         constexpr int SF = DAG ? +1 : -1;
         const Site nf = nb_site(lex_fwd(g, s.lex, c, MU), s.p);
         const Site nb = nb_site(lex_bwd(g, s.lex, c, MU), s.p);
+        constexpr bool SC = SA::kScaled;
         Spinor<Real> q;
         Link<Real> U;
-        sa.load(nf, q);
+        Real sc;
+        sa.load_raw(nf, q, sc);
         ga.load(s, MU, U);
-        hop_dir<MU, SF, false>(acc, q, U);
-        sa.load(nb, q);
+        hop_dir<MU, SF, false, SC>(acc, q, U, sc);
+        sa.load_raw(nb, q, sc);
         ga.load(nb, MU, U);
-        hop_dir<MU, -SF, true>(acc, q, U);
+        hop_dir<MU, -SF, true, SC>(acc, q, U, sc);
     }
 
     LQ_HD void apply(const Site& s, const int c[4], Spinor<Real>& acc) const {
@@ -263,8 +276,8 @@ inline cudaError_t launch_stencil(const Map& map, const Sten& sten, const Epi& e
 }
 
 // EoIdx for a full EO field of K chunks per site, and for a half field of one parity.
-inline EoIdx eo_full(const Geom& g, int K) { return EoIdx{g.Vh, (int64_t)K * g.Vh, g.Vh}; }
-inline EoIdx eo_half(const Geom& g) { return EoIdx{g.Vh, 0, 0}; }
+inline EoIdx eo_full(const Geom& g, int K) { return EoIdx{(uint32_t)g.Vh, (uint32_t)K * (uint32_t)g.Vh, (uint32_t)g.Vh}; }
+inline EoIdx eo_half(const Geom& g) { return EoIdx{(uint32_t)g.Vh, 0u, 0u}; }
 inline EoIdx eo_none() { return EoIdx{0, 0, 0}; }
 
 }  // namespace lq

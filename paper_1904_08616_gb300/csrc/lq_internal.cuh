@@ -64,11 +64,36 @@ template <> struct PrecT<LQ_F16S> { using Real = float; };
 // ------------------------------------------------------------------------------------
 // lattice geometry
 // ------------------------------------------------------------------------------------
+// Division by a run-time constant d >= 1 for 0 <= n < 2^31 with one multiply-high:
+// q = (umulhi(n, mul) + n) >> shift, mul = floor(2^32 (2^shift - d) / d) + 1,
+// shift = ceil(log2 d) (the round-up method of Granlund and Montgomery, 1994).
+struct FastDiv {
+    uint32_t d, mul, shift;
+};
+
+inline FastDiv make_fastdiv(uint32_t d) {
+    uint32_t l = 0;
+    while ((1ull << l) < d) ++l;
+    const uint64_t m = ((1ull << 32) * ((1ull << l) - d)) / d + 1;
+    return FastDiv{d, (uint32_t)m, l};
+}
+
+LQ_HD uint32_t umulhi32(uint32_t a, uint32_t b) {
+#ifdef __CUDA_ARCH__
+    return __umulhi(a, b);
+#else
+    return (uint32_t)(((uint64_t)a * b) >> 32);
+#endif
+}
+
+LQ_HD uint32_t fdiv(uint32_t n, const FastDiv& f) { return (umulhi32(n, f.mul) + n) >> f.shift; }
+
 struct Geom {
     int L[4];       // extents x, y, z, t
     int S[4];       // lexicographic strides 1, Lx, Lx*Ly, Lx*Ly*Lz
     int V, Vh;
     int Lxh;        // Lx / 2
+    FastDiv fLx, fLy, fLz, fLxh;
 };
 
 inline Geom make_geom(const int32_t d[4]) {
@@ -81,6 +106,10 @@ inline Geom make_geom(const int32_t d[4]) {
     g.V = d[0] * d[1] * d[2] * d[3];
     g.Vh = g.V / 2;
     g.Lxh = d[0] / 2;
+    g.fLx = make_fastdiv((uint32_t)d[0]);
+    g.fLy = make_fastdiv((uint32_t)d[1]);
+    g.fLz = make_fastdiv((uint32_t)d[2]);
+    g.fLxh = make_fastdiv((uint32_t)(d[0] / 2));
     return g;
 }
 
@@ -88,11 +117,14 @@ inline Geom make_geom(const int32_t d[4]) {
 struct Site { int lex, p, cb; };
 
 LQ_HD void coords_from_lex(const Geom& g, int lex, int c[4]) {
-    int r = lex;
-    c[0] = r % g.L[0]; r /= g.L[0];
-    c[1] = r % g.L[1]; r /= g.L[1];
-    c[2] = r % g.L[2];
-    c[3] = r / g.L[2];
+    const uint32_t r0 = (uint32_t)lex;
+    const uint32_t r1 = fdiv(r0, g.fLx);
+    const uint32_t r2 = fdiv(r1, g.fLy);
+    const uint32_t r3 = fdiv(r2, g.fLz);
+    c[0] = (int)(r0 - r1 * (uint32_t)g.L[0]);
+    c[1] = (int)(r1 - r2 * (uint32_t)g.L[1]);
+    c[2] = (int)(r2 - r3 * (uint32_t)g.L[2]);
+    c[3] = (int)r3;
 }
 
 LQ_HD Site site_from_lex(const Geom& g, int lex, int c[4]) {
@@ -102,11 +134,14 @@ LQ_HD Site site_from_lex(const Geom& g, int lex, int c[4]) {
 
 // (p, cb) -> coordinates: cb = x/2 + (Lx/2)*(y + Ly*(z + Lz*t)), x's low bit fixed by p.
 LQ_HD Site site_from_eo(const Geom& g, int p, int cb, int c[4]) {
-    int r = cb;
-    const int xh = r % g.Lxh; r /= g.Lxh;
-    c[1] = r % g.L[1]; r /= g.L[1];
-    c[2] = r % g.L[2];
-    c[3] = r / g.L[2];
+    const uint32_t r0 = (uint32_t)cb;
+    const uint32_t r1 = fdiv(r0, g.fLxh);
+    const uint32_t r2 = fdiv(r1, g.fLy);
+    const uint32_t r3 = fdiv(r2, g.fLz);
+    const int xh = (int)(r0 - r1 * (uint32_t)g.Lxh);
+    c[1] = (int)(r1 - r2 * (uint32_t)g.L[1]);
+    c[2] = (int)(r2 - r3 * (uint32_t)g.L[2]);
+    c[3] = (int)r3;
     c[0] = 2 * xh + ((p + c[1] + c[2] + c[3]) & 1);
     const int lex = 2 * cb + (c[0] & 1);
     return Site{lex, p, cb};
@@ -160,30 +195,33 @@ LQ_HD uint32_t f22h2(float a, float b) {
 // ------------------------------------------------------------------------------------
 template <int PREC, int LAYOUT, bool RO> struct SpinorAcc;
 
+// Slot indices are 32-bit: the ABI caps V at 10^8 sites, so every slot index of every
+// field format (at most 36 V for FP64 18-real LEX links) stays below 2^32.
 struct EoIdx {
-    int64_t Vh, pstride, sstride;
+    uint32_t Vh, pstride, sstride;
 };
 
-template <int LAYOUT> LQ_HD int64_t sp_base(const Site& s, int K, const EoIdx& e) {
-    if constexpr (LAYOUT == LQ_LAYOUT_LEX) return (int64_t)s.lex * K;
-    else return (int64_t)s.p * e.pstride + s.cb;
+template <int LAYOUT> LQ_HD uint32_t sp_base(const Site& s, int K, const EoIdx& e) {
+    if constexpr (LAYOUT == LQ_LAYOUT_LEX) return (uint32_t)s.lex * (uint32_t)K;
+    else return (uint32_t)s.p * e.pstride + (uint32_t)s.cb;
 }
-template <int LAYOUT> LQ_HD int64_t sp_kstride(const EoIdx& e) {
-    if constexpr (LAYOUT == LQ_LAYOUT_LEX) return 1;
+template <int LAYOUT> LQ_HD uint32_t sp_kstride(const EoIdx& e) {
+    if constexpr (LAYOUT == LQ_LAYOUT_LEX) return 1u;
     else return e.Vh;
 }
-template <int LAYOUT> LQ_HD int64_t sp_sidx(const Site& s, const EoIdx& e) {
-    if constexpr (LAYOUT == LQ_LAYOUT_LEX) return s.lex;
-    else return (int64_t)s.p * e.sstride + s.cb;
+template <int LAYOUT> LQ_HD uint32_t sp_sidx(const Site& s, const EoIdx& e) {
+    if constexpr (LAYOUT == LQ_LAYOUT_LEX) return (uint32_t)s.lex;
+    else return (uint32_t)s.p * e.sstride + (uint32_t)s.cb;
 }
 
 template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F64, LAYOUT, RO> {
     using Real = double;
     static constexpr int K = 12;
+    static constexpr bool kScaled = false;
     double2* ptr;
     EoIdx e;
     template <typename T> LQ_HD void load(const Site& s, Spinor<T>& out) const {
-        const int64_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
+        const uint32_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
             double2 v = ld<RO>(ptr + b + k * ks);
@@ -191,19 +229,24 @@ template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F64, LAYOUT, RO> {
         }
     }
     template <typename T> LQ_HD void store(const Site& s, const Spinor<T>& in) const {
-        const int64_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
+        const uint32_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
 #pragma unroll
         for (int k = 0; k < 12; ++k) ptr[b + k * ks] = make_double2((double)in.v[k].re, (double)in.v[k].im);
+    }
+    LQ_HD void load_raw(const Site& s, Spinor<double>& out, double& sc) const {
+        load(s, out);
+        sc = 1.0;
     }
 };
 
 template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F32, LAYOUT, RO> {
     using Real = float;
     static constexpr int K = 6;
+    static constexpr bool kScaled = false;
     float4* ptr;
     EoIdx e;
     template <typename T> LQ_HD void load(const Site& s, Spinor<T>& out) const {
-        const int64_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
+        const uint32_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
             float4 v = ld<RO>(ptr + b + k * ks);
@@ -212,11 +255,15 @@ template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F32, LAYOUT, RO> {
         }
     }
     template <typename T> LQ_HD void store(const Site& s, const Spinor<T>& in) const {
-        const int64_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
+        const uint32_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
 #pragma unroll
         for (int k = 0; k < 6; ++k)
             ptr[b + k * ks] = make_float4((float)in.v[2 * k].re, (float)in.v[2 * k].im,
                                           (float)in.v[2 * k + 1].re, (float)in.v[2 * k + 1].im);
+    }
+    LQ_HD void load_raw(const Site& s, Spinor<float>& out, float& sc) const {
+        load(s, out);
+        sc = 1.0f;
     }
 };
 
@@ -226,11 +273,27 @@ template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F32, LAYOUT, RO> {
 template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F16S, LAYOUT, RO> {
     using Real = float;
     static constexpr int K = 3;
+    static constexpr bool kScaled = true;
     uint4* ptr;
     float* scale;
     EoIdx e;
+    // the stored halves as floats, without the site's scale (returned separately)
+    LQ_HD void load_raw(const Site& s, Spinor<float>& out, float& sc) const {
+        const uint32_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
+        sc = ld<RO>(scale + sp_sidx<LAYOUT>(s, e));
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            uint4 w = ld<RO>(ptr + b + k * ks);
+            const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float2 a = h2f2(ww[j]);
+                out.v[4 * k + j] = {a.x, a.y};
+            }
+        }
+    }
     template <typename T> LQ_HD void load(const Site& s, Spinor<T>& out) const {
-        const int64_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
+        const uint32_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
         const T sc = (T)ld<RO>(scale + sp_sidx<LAYOUT>(s, e));
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -244,7 +307,7 @@ template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F16S, LAYOUT, RO> {
         }
     }
     template <typename T> LQ_HD void store(const Site& s, const Spinor<T>& in) const {
-        const int64_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
+        const uint32_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
         float f[24];
 #pragma unroll
         for (int k = 0; k < 12; ++k) { f[2 * k] = (float)in.v[k].re; f[2 * k + 1] = (float)in.v[k].im; }
@@ -252,12 +315,14 @@ template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F16S, LAYOUT, RO> {
 #pragma unroll
         for (int k = 0; k < 24; ++k) m = fmaxf(m, fabsf(f[k]));
         scale[sp_sidx<LAYOUT>(s, e)] = m;
-        const bool z = !(m > 0.f);
+        // one correctly rounded reciprocal per site, then products (kernel outputs; the
+        // bit-exact format conversion in convert.cu divides every component)
+        const float inv = (m > 0.f) ? div_rn(1.0f, m) : 0.f;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             float q[8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) q[j] = z ? 0.f : div_rn(f[8 * k + j], m);
+            for (int j = 0; j < 8; ++j) q[j] = f[8 * k + j] * inv;
             ptr[b + k * ks] = make_uint4(f22h2(q[0], q[1]), f22h2(q[2], q[3]), f22h2(q[4], q[5]), f22h2(q[6], q[7]));
         }
     }
@@ -281,12 +346,12 @@ template <typename R> LQ_HD void reconstruct_row2(Link<R>& U) {
     U.u[2][2] = cconj(c2);
 }
 
-template <int LAYOUT> LQ_HD int64_t lk_base(const Site& s, int mu, int K, int64_t Vh) {
-    if constexpr (LAYOUT == LQ_LAYOUT_LEX) return ((int64_t)s.lex * 4 + mu) * K;
-    else return ((int64_t)(mu * 2 + s.p) * K) * Vh + s.cb;
+template <int LAYOUT> LQ_HD uint32_t lk_base(const Site& s, int mu, int K, uint32_t Vh) {
+    if constexpr (LAYOUT == LQ_LAYOUT_LEX) return ((uint32_t)s.lex * 4u + (uint32_t)mu) * (uint32_t)K;
+    else return ((uint32_t)(mu * 2 + s.p) * (uint32_t)K) * Vh + (uint32_t)s.cb;
 }
-template <int LAYOUT> LQ_HD int64_t lk_kstride(int64_t Vh) {
-    if constexpr (LAYOUT == LQ_LAYOUT_LEX) return 1;
+template <int LAYOUT> LQ_HD uint32_t lk_kstride(uint32_t Vh) {
+    if constexpr (LAYOUT == LQ_LAYOUT_LEX) return 1u;
     else return Vh;
 }
 
@@ -297,9 +362,9 @@ template <int FMT, int LAYOUT> struct GaugeAcc<LQ_F64, FMT, LAYOUT> {
     using Real = double;
     static constexpr int K = FMT / 2;
     const double2* ptr;
-    int64_t Vh;
+    uint32_t Vh;
     LQ_HD void load(const Site& s, int mu, Link<double>& U) const {
-        const int64_t b = lk_base<LAYOUT>(s, mu, K, Vh), ks = lk_kstride<LAYOUT>(Vh);
+        const uint32_t b = lk_base<LAYOUT>(s, mu, K, Vh), ks = lk_kstride<LAYOUT>(Vh);
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             double2 v = ld<true>(ptr + b + k * ks);
@@ -314,9 +379,9 @@ template <int LAYOUT> struct GaugeAcc<LQ_F32, 18, LAYOUT> {
     using Real = float;
     static constexpr int K = 9;
     const float2* ptr;
-    int64_t Vh;
+    uint32_t Vh;
     LQ_HD void load(const Site& s, int mu, Link<float>& U) const {
-        const int64_t b = lk_base<LAYOUT>(s, mu, K, Vh), ks = lk_kstride<LAYOUT>(Vh);
+        const uint32_t b = lk_base<LAYOUT>(s, mu, K, Vh), ks = lk_kstride<LAYOUT>(Vh);
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
             float2 v = ld<true>(ptr + b + k * ks);
@@ -328,9 +393,9 @@ template <int LAYOUT> struct GaugeAcc<LQ_F32, 12, LAYOUT> {
     using Real = float;
     static constexpr int K = 3;
     const float4* ptr;
-    int64_t Vh;
+    uint32_t Vh;
     LQ_HD void load(const Site& s, int mu, Link<float>& U) const {
-        const int64_t b = lk_base<LAYOUT>(s, mu, K, Vh), ks = lk_kstride<LAYOUT>(Vh);
+        const uint32_t b = lk_base<LAYOUT>(s, mu, K, Vh), ks = lk_kstride<LAYOUT>(Vh);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             float4 v = ld<true>(ptr + b + k * ks);
@@ -347,9 +412,9 @@ template <int LAYOUT> struct GaugeAcc<LQ_F16S, 18, LAYOUT> {
     using Real = float;
     static constexpr int K = 9;
     const uint32_t* ptr;
-    int64_t Vh;
+    uint32_t Vh;
     LQ_HD void load(const Site& s, int mu, Link<float>& U) const {
-        const int64_t b = lk_base<LAYOUT>(s, mu, K, Vh), ks = lk_kstride<LAYOUT>(Vh);
+        const uint32_t b = lk_base<LAYOUT>(s, mu, K, Vh), ks = lk_kstride<LAYOUT>(Vh);
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
             float2 v = h2f2(ld<true>(ptr + b + k * ks));
@@ -361,9 +426,9 @@ template <int LAYOUT> struct GaugeAcc<LQ_F16S, 12, LAYOUT> {
     using Real = float;
     static constexpr int K = 3;
     const uint2* ptr;
-    int64_t Vh;
+    uint32_t Vh;
     LQ_HD void load(const Site& s, int mu, Link<float>& U) const {
-        const int64_t b = lk_base<LAYOUT>(s, mu, K, Vh), ks = lk_kstride<LAYOUT>(Vh);
+        const uint32_t b = lk_base<LAYOUT>(s, mu, K, Vh), ks = lk_kstride<LAYOUT>(Vh);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             uint2 w = ld<true>(ptr + b + k * ks);

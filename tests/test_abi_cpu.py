@@ -69,7 +69,8 @@ def test_apply_argument_checks(lqlib):
     assert _apply(L, (4, 4, 4, 3)) == -2
     assert "even" in lqlib.last_error()
     assert _apply(L, (0, 4, 4, 4)) == -2
-    assert _apply(L, (4096, 4096, 4096, 2)) == -2          # volume beyond 2^31 - 2
+    assert _apply(L, (4096, 4096, 4096, 2)) == -2          # volume beyond 10^8 sites
+    assert _apply(L, (100, 100, 100, 102)) == -2
     assert _apply(L, (4, 4, 4, 4), prec=5) == -1
     assert _apply(L, (4, 4, 4, 4), fmt=10) == -1
     assert _apply(L, (4, 4, 4, 4), layout=2) == -1
