@@ -42,8 +42,8 @@ WORKLOAD = "mixed-precision CG to 1e-10 on 32^4, m_q=0.05, links exp(0.3iH)"
 
 # algorithmic bytes per site of the inner-loop kernels (each field read or written once)
 #   K1: p in, 4 links, t out.  K2: t in, 4 links, p, psi, r in, psi, r out.  K3: r, p in, p out.
-SPINOR_B = {"mixed_f16": 52, "mixed_f32": 96, "f64": 192}
-LINK4_B = {"mixed_f16": 96, "mixed_f32": 192, "f64": 576}
+SPINOR_B = {"mixed_f16": 52, "mixed_f32": 96, "f64": 192, "f64x": 192}
+LINK4_B = {"mixed_f16": 96, "mixed_f32": 192, "f64": 576, "f64x": 576}
 
 
 def kernel_bytes(mode):
@@ -199,7 +199,9 @@ def run_ours(args, rank, world, local_rank):
     eta_d = eta_h.to(dev)
     x_d = torch.zeros_like(eta_d)
     mode = args.mode
-    ws = torch.empty(lq.cg_workspace_bytes(DIMS, mode), dtype=torch.uint8, device=dev)
+    # one workspace large enough for every mode this run solves with
+    ws = torch.empty(max(lq.cg_workspace_bytes(DIMS, m) for m in ("f64", "f64x", "mixed_f32", "mixed_f16")),
+                     dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     def solve(m, profile=False):
@@ -260,10 +262,12 @@ def run_ours(args, rank, world, local_rank):
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
     e2e_value = world * upd / (float(te.item()) * 1e-3)
 
-    # plain FP64 CG and the other mixed variant on the same system (one run each after one warm run)
+    # plain FP64 CG (native FP64 and FP32-pair arithmetic) and the other mixed variant on the
+    # same system (one run each after one warm run)
     compare = {}
     if not args.no_compare:
-        for m in ("f64", "mixed_f32" if mode == "mixed_f16" else "mixed_f16"):
+        others = [m for m in ("f64", "f64x", "mixed_f32", "mixed_f16") if m != mode]
+        for m in others:
             solve(m)
             torch.cuda.synchronize()
             c0 = torch.cuda.Event(enable_timing=True)
@@ -306,8 +310,9 @@ def run_ours(args, rank, world, local_rank):
         "metric": "Dslash site-updates/s (whole mixed-precision CG solve to 1e-10)",
         "value": value, "unit": "site-updates/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 (f16s storage) inner / f64 outer" if mode == "mixed_f16"
-        else ("f32 inner / f64 outer" if mode == "mixed_f32" else "f64"),
+        "vs_baseline": None, "dtype": {"mixed_f16": "f32 (f16s storage) inner / f32-pair (fp64-class) outer",
+                                       "mixed_f32": "f32 inner / f32-pair (fp64-class) outer",
+                                       "f64": "f64", "f64x": "f32-pair (fp64-class)"}[mode],
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "lattice": list(DIMS), "m_q": MASS, "links": "exp(0.3iH), 12-real inner",
                    "inner": mode, "tol": TOL, "rhs_per_gpu": 1,
@@ -322,7 +327,8 @@ def run_ours(args, rank, world, local_rank):
         "cg": {"time_to_1e-10_ms": ms_max, "iters": info["iters"], "cycles": info["cycles"],
                "high_applies": info["high_applies"], "true_rel_resid": info["true_rel_resid"],
                "compare": compare,
-               "mixed_vs_fp64_speedup": (compare["f64"]["ms"] / ms_max) if "f64" in compare else None},
+               "mixed_vs_fp64_speedup": (compare["f64"]["ms"] / ms_max) if "f64" in compare else None,
+               "mixed_vs_fp64x_speedup": (compare["f64x"]["ms"] / ms_max) if "f64x" in compare else None},
         "kernels": kern,
     }
     print(json.dumps(line), flush=True)
@@ -334,7 +340,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="mixed_f16", choices=["mixed_f16", "mixed_f32", "f64"])
+    ap.add_argument("--mode", default="mixed_f16", choices=["mixed_f16", "mixed_f32", "f64", "f64x"])
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 / other-mode comparison solves")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     args = ap.parse_args()

@@ -36,7 +36,13 @@
  *           (48 V bytes, in the layout's order) followed by the V float scales (for EO the
  *           scale of (p, cb) is at p*Vh + cb).  The stored value is h * s.
  *           gauge fields: plain halves fl16(fl32(v)), no scale (SU(3) entries are <= 1).
- *   Arithmetic is FP64 for LQ_F64 and FP32 for LQ_F32 / LQ_F16S.
+ *   LQ_F64X FP64-class values as float pairs: hi = fl32(v), lo = fl32(v - hi), stored as the
+ *           LQ_F64 field with every double replaced by (hi, lo) (same size and slots).
+ *           Arithmetic: FP32-pair ("double-float") arithmetic, about 2^-47 relative, run on
+ *           the FP32 pipes (GB300 executes FP64 at 1/63 of its FP32 rate).  LINK18 only.
+ *   Arithmetic is FP64 for LQ_F64, FP32 pairs for LQ_F64X, FP32 for LQ_F32 / LQ_F16S.
+ *   Kernel outputs in LQ_F16S use one reciprocal of the scale per site (h = fl16(v * fl32(1/s)));
+ *   lq_convert_spinor divides every component (h = fl16(fl32(v) / s)) and is bit-exact.
  *
  * Buffers are device pointers owned by the caller, 16-byte aligned; the library neither
  * keeps nor frees them.  Calls that take a cuda_stream (a cudaStream_t, NULL = legacy
@@ -69,7 +75,7 @@ typedef enum lq_status {
     LQ_ERR_BREAKDOWN = -7     /* <p, D^dag D p> <= 0: the operator or the inputs are broken */
 } lq_status;
 
-typedef enum lq_prec { LQ_F64 = 0, LQ_F32 = 1, LQ_F16S = 2 } lq_prec;
+typedef enum lq_prec { LQ_F64 = 0, LQ_F32 = 1, LQ_F16S = 2, LQ_F64X = 3 } lq_prec;
 typedef enum lq_link_fmt { LQ_LINK18 = 18, LQ_LINK12 = 12 } lq_link_fmt;
 typedef enum lq_layout { LQ_LAYOUT_LEX = 0, LQ_LAYOUT_EO = 1 } lq_layout;
 
@@ -135,7 +141,8 @@ int lq_convert_gauge(const int32_t dims[4], int32_t src_prec, int32_t src_layout
 typedef enum lq_cg_mode {
     LQ_CG_F64 = 0,        /* FP64 throughout (plain CG, true residual checked in FP64)     */
     LQ_CG_MIXED_F32 = 1,  /* Algorithm 1: FP32 inner loop (EO layout, 12-real links), FP64 outer */
-    LQ_CG_MIXED_F16 = 2   /* Algorithm 1: scaled-FP16 inner storage, FP32 arithmetic, FP64 outer */
+    LQ_CG_MIXED_F16 = 2,  /* Algorithm 1: scaled-FP16 inner storage, FP32 arithmetic, FP64 outer */
+    LQ_CG_F64X = 3        /* FP64-class CG in FP32-pair arithmetic throughout (LQ_F64X)     */
 } lq_cg_mode;
 
 typedef struct lq_cg_params {
@@ -148,7 +155,11 @@ typedef struct lq_cg_params {
 } lq_cg_params;
 
 /* lq_cg_params.flags */
-#define LQ_CG_PROFILE 1
+#define LQ_CG_PROFILE 1      /* time the solver's kernels with CUDA events (see lq_cg_info)  */
+#define LQ_CG_NATIVE_F64 2   /* outer residual and solution in native FP64 arithmetic instead
+                                of FP32 pairs (mixed modes; slower on GB300)              */
+#define LQ_CG_LINK18 4       /* inner links stored 18-real (no reconstruction) in the mixed
+                                modes; default 12-real                                     */
 
 /* Kernel roles reported in lq_cg_info.kernel_ms / kernel_calls. */
 enum {
@@ -180,6 +191,9 @@ size_t lq_cg_workspace_bytes(const int32_t dims[4], int32_t mode);
  *   eta      right-hand side, LQ_F64 LEX spinor (device).
  *   x        in: starting guess psi_0^high (Algorithm 1 line 1); out: solution (device,
  *            LQ_F64 LEX spinor; must not overlap eta, U or the workspace).
+ *            The outer FP64-class quantities (psi^high, r^high, the residual operator) are held
+ *            and computed as FP32 pairs (LQ_F64X) unless LQ_CG_NATIVE_F64 is set; LQ_CG_F64
+ *            always uses native FP64.
  *   params   tolerances and caps (see lq_cg_params); NULL -> tol 1e-10, max_iter 100000.
  *            With LQ_CG_PROFILE set, CUDA events bracket the solver's kernels on cuda_stream
  *            and info reports their device time per role (inner launches that found the

@@ -5,7 +5,8 @@ for parity tests and the decoders that turn stored fields back into the FP64 num
 oracle computes with.  They follow the format definitions in include/lq.h; the CUDA pack
 kernels implement the same definitions in their own code.
 
-Precisions:  "f64", "f32", "f16s".  Link formats: 18 (full 3x3) or 12 (rows 0 and 1;
+Precisions:  "f64", "f32", "f16s", "f64x" (FP64 values as float pairs hi = fl32(v),
+lo = fl32(v - hi), laid out like "f64" with every double replaced by (hi, lo)).  Link formats: 18 (full 3x3) or 12 (rows 0 and 1;
 row 2 is conj(row0 x row1), an exact identity for SU(3)).  Layouts: "lex" (site-major,
 lexicographic) and "eo" (parity-split, chunked structure of arrays).
 
@@ -20,7 +21,7 @@ import numpy as np
 
 from . import reconstruct12
 
-PRECS = ("f64", "f32", "f16s")
+PRECS = ("f64", "f32", "f16s", "f64x")
 _ELEM = {"f64": np.float64, "f32": np.float32, "f16s": np.float16}
 
 
@@ -41,15 +42,28 @@ def eo_site_map(dims):
     return ((x + y + z + t) % 2).astype(np.int64), n // 2
 
 
-# chunk widths (number of reals per chunk) of the eo layout
+# chunk widths (number of reals per chunk) of the eo layout; f64x uses the f64 slots
 def _spinor_chunk(prec):
-    return {"f64": 2, "f32": 4, "f16s": 8}[prec]
+    return {"f64": 2, "f64x": 2, "f32": 4, "f16s": 8}[prec]
 
 
 def _link_chunk(prec, fmt):
     if fmt == 18:
-        return {"f64": 2, "f32": 2, "f16s": 2}[prec]
-    return {"f64": 2, "f32": 4, "f16s": 4}[prec]
+        return 2
+    return {"f64": 2, "f64x": 2, "f32": 4, "f16s": 4}[prec]
+
+
+def _pairs(v):
+    """float64 array -> float32 array of (hi, lo) pairs, one pair per value."""
+    v = np.asarray(v, dtype=np.float64)
+    hi = v.astype(np.float32)
+    lo = (v - hi.astype(np.float64)).astype(np.float32)
+    return np.stack([hi, lo], axis=-1)
+
+
+def _unpairs(p):
+    p = np.asarray(p, dtype=np.float32)
+    return p[..., 0].astype(np.float64) + p[..., 1].astype(np.float64)
 
 
 def _round(v, prec):
@@ -67,7 +81,7 @@ def _round(v, prec):
 # ------------------------------------------------------------------------------------
 def spinor_bytes(dims, prec) -> int:
     V = _vol(dims)
-    return {"f64": 192 * V, "f32": 96 * V, "f16s": 52 * V}[prec]
+    return {"f64": 192 * V, "f64x": 192 * V, "f32": 96 * V, "f16s": 52 * V}[prec]
 
 
 def _f16s_encode_sites(reals):
@@ -89,6 +103,9 @@ def encode_spinor(psi, dims, prec="f64", layout="lex") -> np.ndarray:
     if prec == "f16s":
         h, s = _f16s_encode_sites(reals)
         data = h
+    elif prec == "f64x":
+        data = reals
+        s = None
     else:
         data = _round(reals, prec)
         s = None
@@ -99,6 +116,8 @@ def encode_spinor(psi, dims, prec="f64", layout="lex") -> np.ndarray:
             s2 = np.empty(V, dtype=np.float32)
             s2[p * (V // 2) + cb] = s
             s = s2
+    if prec == "f64x":
+        data = _pairs(data)
     out = np.ascontiguousarray(data).view(np.uint8).reshape(-1)
     if s is not None:
         out = np.concatenate([out, np.ascontiguousarray(s).view(np.uint8).reshape(-1)])
@@ -111,9 +130,13 @@ def decode_spinor(buf, dims, prec="f64", layout="lex") -> np.ndarray:
     buf = np.ascontiguousarray(np.asarray(buf).view(np.uint8).reshape(-1))
     if buf.size != spinor_bytes(dims, prec):
         raise ValueError("spinor buffer has the wrong size")
-    elem = _ELEM[prec]
-    nb = V * 24 * np.dtype(elem).itemsize
-    data = buf[:nb].view(elem).reshape(V, 24)
+    if prec == "f64x":
+        data = _unpairs(buf.view(np.float32).reshape(-1, 2)).reshape(V, 24)
+        nb = buf.size
+    else:
+        elem = _ELEM[prec]
+        nb = V * 24 * np.dtype(elem).itemsize
+        data = buf[:nb].view(elem).reshape(V, 24)
     s = buf[nb:].view(np.float32) if prec == "f16s" else None
     if layout == "eo":
         data = _from_eo_spinor(data.reshape(-1), dims, _spinor_chunk(prec))
@@ -149,7 +172,7 @@ def _from_eo_spinor(flat, dims, w):
 # ------------------------------------------------------------------------------------
 def gauge_bytes(dims, prec, fmt) -> int:
     V = _vol(dims)
-    per = {"f64": 8, "f32": 4, "f16s": 2}[prec]
+    per = {"f64": 8, "f64x": 8, "f32": 4, "f16s": 2}[prec]
     return V * 4 * fmt * per
 
 
@@ -159,9 +182,11 @@ def encode_gauge(U, dims, prec="f64", fmt=18, layout="lex") -> np.ndarray:
     U = np.ascontiguousarray(U, dtype=np.complex128).reshape(V, 4, 3, 3)
     rows = U if fmt == 18 else U[:, :, :2, :]
     reals = np.ascontiguousarray(rows).view(np.float64).reshape(V, 4, fmt)
-    data = _round(reals, prec)
+    data = reals if prec == "f64x" else _round(reals, prec)
     if layout == "eo":
         data = _to_eo_gauge(data, dims, fmt, _link_chunk(prec, fmt))
+    if prec == "f64x":
+        data = _pairs(data)
     return np.ascontiguousarray(data).view(np.uint8).reshape(-1)
 
 
@@ -171,7 +196,7 @@ def decode_gauge(buf, dims, prec="f64", fmt=18, layout="lex") -> np.ndarray:
     buf = np.ascontiguousarray(np.asarray(buf).view(np.uint8).reshape(-1))
     if buf.size != gauge_bytes(dims, prec, fmt):
         raise ValueError("gauge buffer has the wrong size")
-    data = buf.view(_ELEM[prec])
+    data = _unpairs(buf.view(np.float32).reshape(-1, 2)) if prec == "f64x" else buf.view(_ELEM[prec])
     if layout == "eo":
         data = _from_eo_gauge(data, dims, fmt, _link_chunk(prec, fmt))
     vals = np.ascontiguousarray(data.reshape(V, 4, fmt).astype(np.float64))

@@ -6,8 +6,8 @@ fallback: if liblq.so cannot be built or loaded, every call raises.
 
 Fields are passed as CUDA tensors whose bytes hold the stored field (any dtype; a
 complex128 tensor of shape (V, 4, 3) is exactly an F64 LEX spinor, (V, 4, 3, 3) an F64
-LEX 18-real gauge field).  Precisions: "f64", "f32", "f16s"; layouts: "lex", "eo";
-link formats: 18, 12.
+LEX 18-real gauge field).  Precisions: "f64", "f32", "f16s", "f64x" (FP64-class values as
+FP32 pairs); layouts: "lex", "eo"; link formats: 18, 12.
 """
 from __future__ import annotations
 
@@ -23,9 +23,10 @@ __all__ = [
     "convert_gauge", "cg_workspace_bytes", "cg_solve", "last_error", "version",
 ]
 
-PREC = {"f64": 0, "f32": 1, "f16s": 2}
+PREC = {"f64": 0, "f32": 1, "f16s": 2, "f64x": 3}
 LAYOUT = {"lex": 0, "eo": 1}
-CG_MODE = {"f64": 0, "mixed_f32": 1, "mixed_f16": 2}
+CG_MODE = {"f64": 0, "mixed_f32": 1, "mixed_f16": 2, "f64x": 3}
+CG_PROFILE, CG_NATIVE_F64, CG_LINK18 = 1, 2, 4
 STATUS = {0: "OK", 1: "NOT_CONVERGED", -1: "ERR_ARG", -2: "ERR_DIMS", -3: "ERR_ALIGN",
           -4: "ERR_CUDA", -5: "ERR_WORKSPACE", -6: "ERR_NONFINITE", -7: "ERR_BREAKDOWN"}
 
@@ -216,7 +217,7 @@ def cg_workspace_bytes(dims, mode="f64") -> int:
 
 
 def cg_solve(dims, m_q, U, eta, x=None, mode="f64", tol=1e-10, max_iter=100000, max_cycles=0, delta=0.0,
-             chunk=0, workspace=None, stream=None, profile=False):
+             chunk=0, workspace=None, stream=None, profile=False, native_f64=False, link18=False):
     """Solve D^dag D x = eta (Algorithm 1).  U: F64 LEX 18-real links, eta / x: F64 LEX spinors.
 
     x (if given) is the starting guess and receives the solution.  Returns (x, info, status)
@@ -231,7 +232,8 @@ def cg_solve(dims, m_q, U, eta, x=None, mode="f64", tol=1e-10, max_iter=100000, 
     wb = cg_workspace_bytes(dims, m)
     if workspace is None:
         workspace = _empty_bytes(wb, eta)
-    prm = CgParams(float(tol), int(max_iter), int(max_cycles), float(delta), int(chunk), 1 if profile else 0)
+    flags = (CG_PROFILE if profile else 0) | (CG_NATIVE_F64 if native_f64 else 0) | (CG_LINK18 if link18 else 0)
+    prm = CgParams(float(tol), int(max_iter), int(max_cycles), float(delta), int(chunk), flags)
     info = CgInfo()
     st = load().lq_cg_solve(_dims(dims), float(m_q), m, _ptr(U, gb, "U"), _ptr(eta, sb, "eta"),
                             _ptr(x, sb, "x"), ctypes.byref(prm), _ptr(workspace, wb, "workspace"),

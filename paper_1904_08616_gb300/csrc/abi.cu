@@ -32,7 +32,8 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 size_t spinor_bytes(int64_t nsites, int prec) {
     switch (prec) {
-        case LQ_F64: return (size_t)nsites * 192;
+        case LQ_F64:
+        case LQ_F64X: return (size_t)nsites * 192;
         case LQ_F32: return (size_t)nsites * 96;
         case LQ_F16S: return (size_t)nsites * 52;
         default: return 0;
@@ -42,7 +43,8 @@ size_t spinor_bytes(int64_t nsites, int prec) {
 size_t gauge_bytes(int64_t V, int prec, int fmt) {
     if (fmt != 18 && fmt != 12) return 0;
     switch (prec) {
-        case LQ_F64: return (size_t)V * 4 * fmt * 8;
+        case LQ_F64:
+        case LQ_F64X: return (size_t)V * 4 * fmt * 8;
         case LQ_F32: return (size_t)V * 4 * fmt * 4;
         case LQ_F16S: return (size_t)V * 4 * fmt * 2;
         default: return 0;
@@ -55,7 +57,7 @@ using namespace lq;
 
 namespace {
 
-bool valid_prec(int p) { return p == LQ_F64 || p == LQ_F32 || p == LQ_F16S; }
+bool valid_prec(int p) { return p == LQ_F64 || p == LQ_F32 || p == LQ_F16S || p == LQ_F64X; }
 bool valid_layout(int l) { return l == LQ_LAYOUT_LEX || l == LQ_LAYOUT_EO; }
 bool valid_fmt(int f) { return f == LQ_LINK18 || f == LQ_LINK12; }
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
@@ -91,6 +93,7 @@ int do_apply(const int32_t dims[4], double m_q, int32_t prec, int32_t fmt, int32
     if (!valid_prec(prec)) return fail(LQ_ERR_ARG, "bad precision %d", (int)prec);
     if (!valid_fmt(fmt)) return fail(LQ_ERR_ARG, "bad link format %d", (int)fmt);
     if (!valid_layout(layout)) return fail(LQ_ERR_ARG, "bad layout %d", (int)layout);
+    if (prec == LQ_F64X && fmt != LQ_LINK18) return fail(LQ_ERR_ARG, "LQ_F64X fields use 18-real links");
     if (!isfinite(m_q)) return fail(LQ_ERR_ARG, "m_q is not finite");
     if ((r = check_ptr(U, "U")) || (r = check_ptr(psi, "psi")) || (r = check_ptr(out, "out"))) return r;
     const size_t sb = spinor_bytes(g.V, prec), gb = gauge_bytes(g.V, prec, fmt);
@@ -99,6 +102,7 @@ int do_apply(const int32_t dims[4], double m_q, int32_t prec, int32_t fmt, int32
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e;
     if (prec == LQ_F64) e = apply_f64(g, m_q, fmt, layout, dag, U, psi, out, st);
+    else if (prec == LQ_F64X) e = apply_f64x(g, m_q, fmt, layout, dag, U, psi, out, st);
     else if (prec == LQ_F32) e = apply_f32(g, m_q, fmt, layout, dag, U, psi, out, st);
     else e = apply_f16(g, m_q, fmt, layout, dag, U, psi, out, st);
     if (e != cudaSuccess) return cuda_fail(e, dag ? "dslash_adjoint launch" : "dslash_apply launch");
@@ -136,6 +140,7 @@ int lq_dslash_hop(const int32_t dims[4], int32_t out_parity, int32_t dagger, dou
     if (out_parity != 0 && out_parity != 1) return fail(LQ_ERR_ARG, "out_parity must be 0 or 1");
     if (!valid_prec(prec)) return fail(LQ_ERR_ARG, "bad precision %d", (int)prec);
     if (!valid_fmt(link_fmt)) return fail(LQ_ERR_ARG, "bad link format %d", (int)link_fmt);
+    if (prec == LQ_F64X && link_fmt != LQ_LINK18) return fail(LQ_ERR_ARG, "LQ_F64X fields use 18-real links");
     if (!isfinite(a) || !isfinite(b)) return fail(LQ_ERR_ARG, "a and b must be finite");
     if ((r = check_ptr(U, "U")) || (r = check_ptr(psi_other, "psi_other")) || (r = check_ptr(out, "out"))) return r;
     if (y && (r = check_ptr(y, "y"))) return r;
@@ -147,6 +152,7 @@ int lq_dslash_hop(const int32_t dims[4], int32_t out_parity, int32_t dagger, dou
     cudaError_t e;
     const bool dag = dagger != 0;
     if (prec == LQ_F64) e = hop_f64(g, out_parity, dag, a, b, link_fmt, U, psi_other, y, out, st);
+    else if (prec == LQ_F64X) e = hop_f64x(g, out_parity, dag, a, b, link_fmt, U, psi_other, y, out, st);
     else if (prec == LQ_F32) e = hop_f32(g, out_parity, dag, a, b, link_fmt, U, psi_other, y, out, st);
     else e = hop_f16(g, out_parity, dag, a, b, link_fmt, U, psi_other, y, out, st);
     if (e != cudaSuccess) return cuda_fail(e, "dslash_hop launch");
@@ -176,6 +182,7 @@ int lq_convert_gauge(const int32_t dims[4], int32_t src_prec, int32_t src_layout
     if (!valid_prec(src_prec) || !valid_prec(dst_prec)) return fail(LQ_ERR_ARG, "bad precision");
     if (!valid_layout(src_layout) || !valid_layout(dst_layout)) return fail(LQ_ERR_ARG, "bad layout");
     if (!valid_fmt(dst_fmt)) return fail(LQ_ERR_ARG, "bad link format %d", (int)dst_fmt);
+    if (dst_prec == LQ_F64X && dst_fmt != LQ_LINK18) return fail(LQ_ERR_ARG, "LQ_F64X fields use 18-real links");
     if ((r = check_ptr(src, "src")) || (r = check_ptr(dst, "dst"))) return r;
     if (overlap(src, gauge_bytes(g.V, src_prec, 18), dst, gauge_bytes(g.V, dst_prec, dst_fmt)))
         return fail(LQ_ERR_ALIGN, "dst overlaps src");
@@ -188,7 +195,7 @@ int lq_convert_gauge(const int32_t dims[4], int32_t src_prec, int32_t src_layout
 size_t lq_cg_workspace_bytes(const int32_t dims[4], int32_t mode) {
     Geom g;
     if (check_dims(dims, &g) != LQ_OK) return 0;
-    if (mode != LQ_CG_F64 && mode != LQ_CG_MIXED_F32 && mode != LQ_CG_MIXED_F16) return 0;
+    if (mode != LQ_CG_F64 && mode != LQ_CG_MIXED_F32 && mode != LQ_CG_MIXED_F16 && mode != LQ_CG_F64X) return 0;
     return cg_workspace_bytes(g, mode);
 }
 
@@ -199,7 +206,7 @@ int lq_cg_solve(const int32_t dims[4], double m_q, int32_t mode, const void* U, 
     Geom g;
     int r;
     if ((r = check_dims(dims, &g)) != LQ_OK) return r;
-    if (mode != LQ_CG_F64 && mode != LQ_CG_MIXED_F32 && mode != LQ_CG_MIXED_F16)
+    if (mode != LQ_CG_F64 && mode != LQ_CG_MIXED_F32 && mode != LQ_CG_MIXED_F16 && mode != LQ_CG_F64X)
         return fail(LQ_ERR_ARG, "bad CG mode %d", (int)mode);
     if (!isfinite(m_q)) return fail(LQ_ERR_ARG, "m_q is not finite");
     lq_cg_params prm{1e-10, 100000, 0, 0.0, 0, 0};

@@ -10,8 +10,16 @@ namespace {
 
 constexpr int kConvBS = 256;
 
-__host__ __device__ inline int spinor_chunk(int prec) { return prec == LQ_F64 ? 2 : (prec == LQ_F32 ? 4 : 8); }
-__host__ __device__ inline int link_chunk(int prec, int fmt) { return fmt == 18 ? 2 : (prec == LQ_F64 ? 2 : 4); }
+// LQ_F64X fields use the LQ_F64 slots with each double replaced by a float pair
+__host__ __device__ inline int base_prec(int prec) { return prec == LQ_F64X ? LQ_F64 : prec; }
+__host__ __device__ inline int spinor_chunk(int prec) {
+    prec = base_prec(prec);
+    return prec == LQ_F64 ? 2 : (prec == LQ_F32 ? 4 : 8);
+}
+__host__ __device__ inline int link_chunk(int prec, int fmt) {
+    prec = base_prec(prec);
+    return fmt == 18 ? 2 : (prec == LQ_F64 ? 2 : 4);
+}
 
 struct FieldDesc {
     void* ptr;
@@ -36,8 +44,20 @@ __device__ inline int64_t lk_elem(const FieldDesc& f, const Geom& g, const Site&
 
 __device__ inline double load_real(const void* base, int prec, int64_t i) {
     if (prec == LQ_F64) return ((const double*)base)[i];
+    if (prec == LQ_F64X) return (double)((const float*)base)[2 * i] + (double)((const float*)base)[2 * i + 1];
     if (prec == LQ_F32) return (double)((const float*)base)[i];
     return (double)__half2float(((const __half*)base)[i]);
+}
+
+// F64 or F64X target
+__device__ inline void store_wide(void* base, int prec, int64_t i, double v) {
+    if (prec == LQ_F64) {
+        ((double*)base)[i] = v;
+    } else {
+        const dd p = dd_from_double(v);
+        ((float*)base)[2 * i] = p.hi;
+        ((float*)base)[2 * i + 1] = p.lo;
+    }
 }
 
 __global__ void __launch_bounds__(kConvBS) convert_spinor_kernel(Geom g, FieldDesc src, FieldDesc dst) {
@@ -50,9 +70,9 @@ __global__ void __launch_bounds__(kConvBS) convert_spinor_kernel(Geom g, FieldDe
         if (src.prec == LQ_F16S) sc = (double)((const float*)((const char*)src.ptr + sc_off))[sp_scale_idx(src, g, s)];
 #pragma unroll
         for (int j = 0; j < 24; ++j) v[j] = load_real(src.ptr, src.prec, sp_elem(src, g, s, j)) * sc;
-        if (dst.prec == LQ_F64) {
+        if (dst.prec == LQ_F64 || dst.prec == LQ_F64X) {
 #pragma unroll
-            for (int j = 0; j < 24; ++j) ((double*)dst.ptr)[sp_elem(dst, g, s, j)] = v[j];
+            for (int j = 0; j < 24; ++j) store_wide(dst.ptr, dst.prec, sp_elem(dst, g, s, j), v[j]);
         } else if (dst.prec == LQ_F32) {
 #pragma unroll
             for (int j = 0; j < 24; ++j) ((float*)dst.ptr)[sp_elem(dst, g, s, j)] = (float)v[j];
@@ -78,7 +98,7 @@ __global__ void __launch_bounds__(kConvBS) convert_gauge_kernel(Geom g, FieldDes
             for (int j = 0; j < dst.fmt; ++j) {
                 const double v = load_real(src.ptr, src.prec, lk_elem(src, g, s, mu, j));
                 const int64_t i = lk_elem(dst, g, s, mu, j);
-                if (dst.prec == LQ_F64) ((double*)dst.ptr)[i] = v;
+                if (dst.prec == LQ_F64 || dst.prec == LQ_F64X) store_wide(dst.ptr, dst.prec, i, v);
                 else if (dst.prec == LQ_F32) ((float*)dst.ptr)[i] = (float)v;
                 else ((__half*)dst.ptr)[i] = __float2half_rn((float)v);
             }

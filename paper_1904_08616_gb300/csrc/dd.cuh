@@ -21,6 +21,12 @@ namespace lq {
 
 struct dd {
     float hi, lo;
+    dd() = default;
+    LQ_HD constexpr dd(float h, float l) : hi(h), lo(l) {}
+    LQ_HD constexpr dd(float h) : hi(h), lo(0.f) {}
+    LQ_HD constexpr explicit dd(int h) : hi((float)h), lo(0.f) {}
+    // a double must be split (dd_from_double / from_double<dd>), never truncated to float
+    dd(double) = delete;
 };
 
 LQ_HD float f_add(float a, float b) {
@@ -85,6 +91,11 @@ LQ_HD dd operator*(dd a, dd b) {
     return dd{p, e};
 }
 
+// fused multiply-add for every arithmetic type the kernels use (an overload for dd in this
+// namespace would otherwise hide the float and double ones)
+LQ_HD float fma(float a, float b, float c) { return fmaf(a, b, c); }
+LQ_HD double fma(double a, double b, double c) { return ::fma(a, b, c); }
+
 // a*b + c with one TwoSum
 LQ_HD dd fma(dd a, dd b, dd c) {
     const float p = f_mul(a.hi, b.hi);
@@ -102,5 +113,24 @@ LQ_HD dd dd_from_double(double x) {
     return dd{h, (float)(x - (double)h)};
 }
 LQ_HD double dd_to_double(dd a) { return (double)a.hi + (double)a.lo; }
+
+// Generic conversions used by the type-generic kernels (R = float, double or dd).
+LQ_HD double to_double(float x) { return (double)x; }
+LQ_HD double to_double(double x) { return x; }
+LQ_HD double to_double(dd x) { return dd_to_double(x); }
+
+template <typename R> LQ_HD R from_double(double x) { return (R)x; }
+template <> LQ_HD dd from_double<dd>(double x) { return dd_from_double(x); }
+
+// a value stored as a float pair, read in type T (float: rounded sum; dd: as is)
+template <typename T> LQ_HD T from_pair(float h, float l);
+template <> LQ_HD float from_pair<float>(float h, float l) { return f_add(h, l); }
+template <> LQ_HD double from_pair<double>(float h, float l) { return (double)h + (double)l; }
+template <> LQ_HD dd from_pair<dd>(float h, float l) { return dd{h, l}; }
+
+// a value of type T written as a normalised float pair
+LQ_HD dd to_pair(dd x) { return dd_renorm(x); }
+LQ_HD dd to_pair(float x) { return dd{x, 0.f}; }
+LQ_HD dd to_pair(double x) { return dd_from_double(x); }
 
 }  // namespace lq

@@ -18,7 +18,7 @@ inline SpinorAcc<PREC, LAYOUT, RO> make_spinor(const void* buf, const Geom& g, b
     a.e = (LAYOUT == LQ_LAYOUT_LEX) ? eo_none() : (half ? eo_half(g) : eo_full(g, SpinorAcc<PREC, LAYOUT, RO>::K));
     if constexpr (PREC == LQ_F64) {
         a.ptr = (double2*)buf;
-    } else if constexpr (PREC == LQ_F32) {
+    } else if constexpr (PREC == LQ_F32 || PREC == LQ_F64X) {
         a.ptr = (float4*)buf;
     } else {
         a.ptr = (uint4*)buf;
@@ -46,8 +46,8 @@ cudaError_t run_apply(const Geom& g, double m_q, const void* U, const void* psi,
     EpiAxpby<OutA, InA, true, false> epi;
     epi.out = make_spinor<PREC, LAYOUT, false>(out, g, false);
     epi.y = sten.sa;
-    epi.a = (Real)(m_q + 4.0);
-    epi.b = (Real)0.5;
+    epi.a = from_double<Real>(m_q + 4.0);
+    epi.b = from_double<Real>(0.5);
     epi.rc = RedCtx{nullptr, nullptr};
     epi.slot = 0;
     if constexpr (LAYOUT == LQ_LAYOUT_LEX) return launch_stencil<kApplyBS>(MapLex<kApplyBS>{g}, sten, epi, st);
@@ -67,8 +67,8 @@ cudaError_t run_hop(const Geom& g, int p, double a, double b, const void* U, con
     EpiAxpby<OutA, InA, HASY, false> epi;
     epi.out = make_spinor<PREC, LAYOUT, false>(out, g, true);
     epi.y = make_spinor<PREC, LAYOUT, true>(HASY ? y : psi_other, g, true);
-    epi.a = (Real)a;
-    epi.b = (Real)(0.5 * b);   // the stencil sum excludes the 1/2 of Eq. (1)
+    epi.a = from_double<Real>(a);
+    epi.b = from_double<Real>(0.5 * b);   // the stencil sum excludes the 1/2 of Eq. (1)
     epi.rc = RedCtx{nullptr, nullptr};
     epi.slot = 0;
     return launch_stencil<kApplyBS>(MapEoHalf<kApplyBS>{g, p}, sten, epi, st);
@@ -81,6 +81,8 @@ cudaError_t apply_f16(const Geom& g, double m_q, int fmt, int layout, bool dag, 
 cudaError_t hop_f64(const Geom& g, int p, bool dag, double a, double b, int fmt, const void* U, const void* psi_other, const void* y, void* out, cudaStream_t st);
 cudaError_t hop_f32(const Geom& g, int p, bool dag, double a, double b, int fmt, const void* U, const void* psi_other, const void* y, void* out, cudaStream_t st);
 cudaError_t hop_f16(const Geom& g, int p, bool dag, double a, double b, int fmt, const void* U, const void* psi_other, const void* y, void* out, cudaStream_t st);
+cudaError_t apply_f64x(const Geom& g, double m_q, int fmt, int layout, bool dag, const void* U, const void* psi, void* out, cudaStream_t st);
+cudaError_t hop_f64x(const Geom& g, int p, bool dag, double a, double b, int fmt, const void* U, const void* psi_other, const void* y, void* out, cudaStream_t st);
 
 }  // namespace lq
 

@@ -210,7 +210,7 @@ struct EpiAxpby {
             for (int k = 0; k < 12; ++k) o.v[k] = cscale((R)b, acc.v[k]);
         }
         out.store(s, o);
-        if constexpr (NORM) red[0] += (double)norm2(o);
+        if constexpr (NORM) red[0] += to_double(norm2(o));
     }
     template <int BS> __device__ __forceinline__ void finish(const double (&red)[NRED > 0 ? NRED : 1]) const {
         if constexpr (NORM) {

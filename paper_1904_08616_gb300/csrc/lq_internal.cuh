@@ -12,6 +12,7 @@
 #include <stddef.h>
 
 #include "../../include/lq.h"
+#include "dd.cuh"
 
 // Helpers are callable from host code as well, so the index arithmetic and the stencil
 // algebra can be exercised off the GPU; the library itself only runs them on the device.
@@ -60,6 +61,11 @@ template <int PREC> struct PrecT;
 template <> struct PrecT<LQ_F64> { using Real = double; };
 template <> struct PrecT<LQ_F32> { using Real = float; };
 template <> struct PrecT<LQ_F16S> { using Real = float; };
+template <> struct PrecT<LQ_F64X> { using Real = dd; };
+
+LQ_HD float to_float(float x) { return x; }
+LQ_HD float to_float(double x) { return (float)x; }
+LQ_HD float to_float(dd x) { return f_add(x.hi, x.lo); }
 
 // ------------------------------------------------------------------------------------
 // lattice geometry
@@ -225,13 +231,13 @@ template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F64, LAYOUT, RO> {
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
             double2 v = ld<RO>(ptr + b + k * ks);
-            out.v[k] = {(T)v.x, (T)v.y};
+            out.v[k] = {from_double<T>(v.x), from_double<T>(v.y)};
         }
     }
     template <typename T> LQ_HD void store(const Site& s, const Spinor<T>& in) const {
         const uint32_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) ptr[b + k * ks] = make_double2((double)in.v[k].re, (double)in.v[k].im);
+        for (int k = 0; k < 12; ++k) ptr[b + k * ks] = make_double2(to_double(in.v[k].re), to_double(in.v[k].im));
     }
     LQ_HD void load_raw(const Site& s, Spinor<double>& out, double& sc) const {
         load(s, out);
@@ -258,8 +264,8 @@ template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F32, LAYOUT, RO> {
         const uint32_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
 #pragma unroll
         for (int k = 0; k < 6; ++k)
-            ptr[b + k * ks] = make_float4((float)in.v[2 * k].re, (float)in.v[2 * k].im,
-                                          (float)in.v[2 * k + 1].re, (float)in.v[2 * k + 1].im);
+            ptr[b + k * ks] = make_float4(to_float(in.v[2 * k].re), to_float(in.v[2 * k].im),
+                                          to_float(in.v[2 * k + 1].re), to_float(in.v[2 * k + 1].im));
     }
     LQ_HD void load_raw(const Site& s, Spinor<float>& out, float& sc) const {
         load(s, out);
@@ -310,7 +316,7 @@ template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F16S, LAYOUT, RO> {
         const uint32_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
         float f[24];
 #pragma unroll
-        for (int k = 0; k < 12; ++k) { f[2 * k] = (float)in.v[k].re; f[2 * k + 1] = (float)in.v[k].im; }
+        for (int k = 0; k < 12; ++k) { f[2 * k] = to_float(in.v[k].re); f[2 * k + 1] = to_float(in.v[k].im); }
         float m = 0.f;
 #pragma unroll
         for (int k = 0; k < 24; ++k) m = fmaxf(m, fabsf(f[k]));
@@ -325,6 +331,36 @@ template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F16S, LAYOUT, RO> {
             for (int j = 0; j < 8; ++j) q[j] = f[8 * k + j] * inv;
             ptr[b + k * ks] = make_uint4(f22h2(q[0], q[1]), f22h2(q[2], q[3]), f22h2(q[4], q[5]), f22h2(q[6], q[7]));
         }
+    }
+};
+
+// FP32 pairs: the LQ_F64 layout with every double replaced by (hi, lo); one float4 chunk
+// is one complex number (re.hi, re.lo, im.hi, im.lo).
+template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F64X, LAYOUT, RO> {
+    using Real = dd;
+    static constexpr int K = 12;
+    static constexpr bool kScaled = false;
+    float4* ptr;
+    EoIdx e;
+    template <typename T> LQ_HD void load(const Site& s, Spinor<T>& out) const {
+        const uint32_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            float4 v = ld<RO>(ptr + b + k * ks);
+            out.v[k] = {from_pair<T>(v.x, v.y), from_pair<T>(v.z, v.w)};
+        }
+    }
+    template <typename T> LQ_HD void store(const Site& s, const Spinor<T>& in) const {
+        const uint32_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            const dd re = to_pair(in.v[k].re), im = to_pair(in.v[k].im);
+            ptr[b + k * ks] = make_float4(re.hi, re.lo, im.hi, im.lo);
+        }
+    }
+    LQ_HD void load_raw(const Site& s, Spinor<dd>& out, dd& sc) const {
+        load(s, out);
+        sc = dd(1.0f);
     }
 };
 
@@ -438,6 +474,23 @@ template <int LAYOUT> struct GaugeAcc<LQ_F16S, 12, LAYOUT> {
             U.u[c1 / 3][c1 % 3] = {c.x, c.y};
         }
         reconstruct_row2(U);
+    }
+};
+
+// FP32 pairs: one float4 chunk = one complex entry; 9 (LINK18) or 6 (LINK12) per link
+template <int FMT, int LAYOUT> struct GaugeAcc<LQ_F64X, FMT, LAYOUT> {
+    using Real = dd;
+    static constexpr int K = FMT / 2;
+    const float4* ptr;
+    uint32_t Vh;
+    LQ_HD void load(const Site& s, int mu, Link<dd>& U) const {
+        const uint32_t b = lk_base<LAYOUT>(s, mu, K, Vh), ks = lk_kstride<LAYOUT>(Vh);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            float4 v = ld<true>(ptr + b + k * ks);
+            U.u[k / 3][k % 3] = {dd{v.x, v.y}, dd{v.z, v.w}};
+        }
+        if constexpr (FMT == 12) reconstruct_row2(U);
     }
 };
 

@@ -21,6 +21,12 @@
 // LQ_CG_F64 runs the same driver with an FP64 inner loop on the caller's links and
 // delta = 0, i.e. plain CG followed by an FP64 true-residual check (and, if rounding
 // drift left the true residual above tol, another cycle that continues the direction).
+//
+// The outer (FP64-class) quantities have their own precision HP: native FP64 on the
+// caller's LEX fields, or FP32 pairs (LQ_F64X) in EO copies held in the workspace, which
+// on GB300 run the residual operator about six times faster than native FP64.
+#pragma once
+
 #include <math.h>
 #include <string.h>
 
@@ -32,7 +38,7 @@
 
 namespace lq {
 
-namespace {
+namespace solver_detail {
 
 constexpr int kBS = 128;      // stencil kernels
 constexpr int kSiteBS = 256;  // site-local kernels
@@ -96,7 +102,7 @@ struct EpiK1 {
         for (int k = 0; k < 12; ++k)
             o.v[k] = {fma((R)b, acc.v[k].re, (R)a * pv.v[k].re), fma((R)b, acc.v[k].im, (R)a * pv.v[k].im)};
         t.store(s, o);
-        red[0] += (double)norm2(o);
+        red[0] += to_double(norm2(o));
     }
     template <int BS> __device__ __forceinline__ void finish(const double (&red)[1]) const {
         SolverState* st = rc.st;
@@ -130,7 +136,7 @@ struct EpiK2 {
     Real alpha;
     __device__ __forceinline__ bool init() {
         if (rc.st->stop) return false;
-        alpha = (Real)rc.st->alpha;
+        alpha = from_double<Real>(rc.st->alpha);
         return true;
     }
     template <typename R>
@@ -150,7 +156,7 @@ struct EpiK2 {
         }
         x.store(s, xv);
         r.store(s, rv);
-        red[0] += (double)norm2(rv);
+        red[0] += to_double(norm2(rv));
     }
     template <int BS> __device__ __forceinline__ void finish(const double (&red)[1]) const {
         SolverState* st = rc.st;
@@ -179,7 +185,7 @@ struct OpK3 {
     Real beta;
     __device__ __forceinline__ bool init() {
         if (rc.st->p_iter == rc.st->iter) return false;
-        beta = (Real)rc.st->beta;
+        beta = from_double<Real>(rc.st->beta);
         return true;
     }
     __device__ __forceinline__ void apply(const Site& s, double*) const {
@@ -208,35 +214,35 @@ struct OpRestart {
     RA r;
     PA p;
     XA x;
-    double inv_s, stop_rho;
+    double stop_rho;
     int k_max;
     RedCtx rc;
     __device__ __forceinline__ bool init() { return true; }
+    Real is;   // 1/s in the inner arithmetic
     __device__ __forceinline__ void apply(const Site& s, double* red) const {
-        Spinor<double> v;
-        rh.load(s, v);
         Spinor<Real> w;
+        rh.load(s, w);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) w.v[k] = {(Real)(v.v[k].re * inv_s), (Real)(v.v[k].im * inv_s)};
+        for (int k = 0; k < 12; ++k) w.v[k] = {is * w.v[k].re, is * w.v[k].im};
         r.store(s, w);
         if constexpr (FIRST) {
             p.store(s, w);
             Spinor<Real> z;
             zero(z);
             x.store(s, z);
-            red[0] += (double)norm2(w);
+            red[0] += to_double(norm2(w));
         } else {
             Spinor<Real> pv;
             p.load(s, pv);
-            double re = 0.0, im = 0.0;
+            Real re = Real(0), im = Real(0);
 #pragma unroll
             for (int k = 0; k < 12; ++k) {
-                re += (double)w.v[k].re * pv.v[k].re + (double)w.v[k].im * pv.v[k].im;
-                im += (double)w.v[k].re * pv.v[k].im - (double)w.v[k].im * pv.v[k].re;
+                re = fma(w.v[k].re, pv.v[k].re, fma(w.v[k].im, pv.v[k].im, re));
+                im = fma(w.v[k].re, pv.v[k].im, fma(-w.v[k].im, pv.v[k].re, im));
             }
-            red[0] += re;
-            red[1] += im;
-            red[2] += (double)norm2(w);
+            red[0] += to_double(re);
+            red[1] += to_double(im);
+            red[2] += to_double(norm2(w));
         }
     }
     template <int BS> __device__ __forceinline__ void finish(const double (&red)[NRED]) const {
@@ -268,19 +274,18 @@ struct OpRestartP {
     RA r;
     PA p;
     XA x;
-    double beta0;
+    Real b0;
     RedCtx rc;
     Real cre, cim;
     __device__ __forceinline__ bool init() {
-        cre = (Real)rc.st->red[0];
-        cim = (Real)rc.st->red[1];
+        cre = from_double<Real>(rc.st->red[0]);
+        cim = from_double<Real>(rc.st->red[1]);
         return true;
     }
     __device__ __forceinline__ void apply(const Site& s, double*) const {
         Spinor<Real> rv, pv;
         r.load(s, rv);
         p.load(s, pv);
-        const Real b0 = (Real)beta0;
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
             const cplx<Real> cr = cmul(cplx<Real>{cre, cim}, rv.v[k]);
@@ -294,16 +299,17 @@ struct OpRestartP {
     template <int BS> __device__ __forceinline__ void finish(const double (&)[1]) const {}
 };
 
-// psi^high += s psi  (Algorithm 1 line 22 as read above); FP64
+// psi^high += s psi  (Algorithm 1 line 22 as read above), in the outer arithmetic
 template <class XA, class PsiA>
 struct OpXUpdate {
+    using Real = typename XA::Real;
     static constexpr int NRED = 0;
     XA x;
     PsiA psi;
-    double s;
+    Real s;
     __device__ __forceinline__ bool init() { return true; }
     __device__ __forceinline__ void apply(const Site& st, double*) const {
-        Spinor<double> xv, pv;
+        Spinor<Real> xv, pv;
         x.load(st, xv);
         psi.load(st, pv);
 #pragma unroll
@@ -347,30 +353,29 @@ struct OpZero {
     template <int BS> __device__ __forceinline__ void finish(const double (&)[1]) const {}
 };
 
-// r^high = eta - (a t + b hop^dag(t)), ||r^high||^2 -> st->red[slot]  (FP64)
+// r^high = eta - (a t + b hop^dag(t)), ||r^high||^2 -> st->red[slot]  (outer arithmetic)
 template <class EtaA, class TA, class RA>
 struct EpiResid {
-    using Real = double;
+    using Real = typename RA::Real;
     static constexpr int NRED = 1;
     EtaA eta;
     TA t;
     RA r;
-    double a, b;
+    Real a, b;
     RedCtx rc;
     int slot;
     __device__ __forceinline__ bool init() { return true; }
-    template <typename R>
-    __device__ __forceinline__ void apply(const Site& s, const Spinor<R>& acc, double* red) const {
-        Spinor<double> tv, ev, o;
+    __device__ __forceinline__ void apply(const Site& s, const Spinor<Real>& acc, double* red) const {
+        Spinor<Real> tv, ev, o;
         t.load(s, tv);
         eta.load(s, ev);
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
-            o.v[k].re = ev.v[k].re - fma(b, (double)acc.v[k].re, a * tv.v[k].re);
-            o.v[k].im = ev.v[k].im - fma(b, (double)acc.v[k].im, a * tv.v[k].im);
+            o.v[k].re = ev.v[k].re - fma(b, acc.v[k].re, a * tv.v[k].re);
+            o.v[k].im = ev.v[k].im - fma(b, acc.v[k].im, a * tv.v[k].im);
         }
         r.store(s, o);
-        red[0] += norm2(o);
+        red[0] += to_double(norm2(o));
     }
     template <int BS> __device__ __forceinline__ void finish(const double (&red)[1]) const {
         SolverState* st = rc.st;
@@ -384,72 +389,115 @@ struct EpiResid {
 // ------------------------------------------------------------------------------------
 inline size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
+// Workspace: state record, partial sums, then the outer fields, then the inner fields.
+// With FP32-pair outer arithmetic (HP = LQ_F64X) the outer fields are EO copies of U, eta
+// and x plus r^high and t^high, all as pairs; with native FP64 only r^high and t^high are
+// needed (U, eta, x are the caller's).  The query returns the larger of the two.
 struct WsLayout {
-    size_t state, partials, r_high, t_high, u_low, psi, r, p, t, total;
+    size_t state, partials, r_high, t_high, u_x, eta_x, x_x, u_low, psi, r, p, t, total;
 };
 
-int inner_prec(int mode) { return mode == LQ_CG_MIXED_F32 ? LQ_F32 : (mode == LQ_CG_MIXED_F16 ? LQ_F16S : LQ_F64); }
+inline int inner_prec(int mode) {
+    switch (mode) {
+        case LQ_CG_MIXED_F32: return LQ_F32;
+        case LQ_CG_MIXED_F16: return LQ_F16S;
+        case LQ_CG_F64X: return LQ_F64X;
+        default: return LQ_F64;
+    }
+}
 
-WsLayout ws_layout(const Geom& g, int mode) {
-    WsLayout w;
+inline WsLayout ws_layout(const Geom& g, int mode, bool pair_outer, int inner_fmt) {
+    WsLayout w{};
     size_t o = 0;
-    w.state = o;
-    o += align256(sizeof(SolverState));
-    w.partials = o;
-    o += align256(sizeof(double) * 3 * kMaxPartials);
-    const size_t hi = align256(spinor_bytes(g.V, LQ_F64));
-    w.r_high = o;
-    o += hi;
-    w.t_high = o;
-    o += hi;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o += align256(bytes);
+        return at;
+    };
+    w.state = take(sizeof(SolverState));
+    w.partials = take(sizeof(double) * 3 * kMaxPartials);
+    w.r_high = take(spinor_bytes(g.V, LQ_F64));
+    w.t_high = take(spinor_bytes(g.V, LQ_F64));
+    if (pair_outer) {
+        w.u_x = take(gauge_bytes(g.V, LQ_F64X, 18));
+        w.eta_x = take(spinor_bytes(g.V, LQ_F64X));
+        w.x_x = take(spinor_bytes(g.V, LQ_F64X));
+    }
     const int ip = inner_prec(mode);
-    w.u_low = o;
-    if (mode != LQ_CG_F64) o += align256(gauge_bytes(g.V, ip, 12));
-    const size_t lo = align256(spinor_bytes(g.V, ip));
-    w.psi = o;
-    o += lo;
-    w.r = o;
-    o += lo;
-    w.p = o;
-    o += lo;
-    w.t = o;
-    o += lo;
+    if (mode == LQ_CG_MIXED_F32 || mode == LQ_CG_MIXED_F16) w.u_low = take(gauge_bytes(g.V, ip, inner_fmt));
+    const size_t lo = spinor_bytes(g.V, ip);
+    w.psi = take(lo);
+    w.r = take(lo);
+    w.p = take(lo);
+    w.t = take(lo);
     w.total = o;
     return w;
 }
 
+inline size_t ws_bytes_for_mode(const Geom& g, int mode) {
+    size_t m = 0;
+    // native FP64 CG never uses pair copies; the FP32-pair CG always does; the mixed modes
+    // may use either (LQ_CG_NATIVE_F64)
+    const int pair_lo = (mode == LQ_CG_F64X) ? 1 : 0, pair_hi = (mode == LQ_CG_F64) ? 0 : 1;
+    for (int pair = pair_lo; pair <= pair_hi; ++pair)
+        for (int fmt : {12, 18}) {
+            const size_t t = ws_layout(g, mode, pair != 0, fmt).total;
+            if (t > m) m = t;
+        }
+    return m;
+}
+
 // ------------------------------------------------------------------------------------
-// the driver
+// the driver: inner precision IP / link format IF / layout IL, outer precision HP
 // ------------------------------------------------------------------------------------
-template <int IP, int IF, int IL>
+template <int HP> struct Outer;
+template <> struct Outer<LQ_F64> {      // the caller's FP64 LEX fields
+    static constexpr int L = LQ_LAYOUT_LEX;
+};
+template <> struct Outer<LQ_F64X> {     // FP32-pair EO copies in the workspace
+    static constexpr int L = LQ_LAYOUT_EO;
+};
+
+template <int IP, int IF, int IL, int HP>
 int run_solver(const Geom& g, double m_q, const void* U, const void* eta, void* x, const lq_cg_params& prm,
                double delta, const WsLayout& w, char* ws, lq_cg_info* info, cudaStream_t st) {
     using Real = typename PrecT<IP>::Real;
+    using HReal = typename PrecT<HP>::Real;
+    constexpr int HL = Outer<HP>::L;
     using SpRO = SpinorAcc<IP, IL, true>;
     using SpRW = SpinorAcc<IP, IL, false>;
     using GA = GaugeAcc<IP, IF, IL>;
-    using HiRO = SpinorAcc<LQ_F64, LQ_LAYOUT_LEX, true>;
-    using HiRW = SpinorAcc<LQ_F64, LQ_LAYOUT_LEX, false>;
-    using HiGA = GaugeAcc<LQ_F64, 18, LQ_LAYOUT_LEX>;
+    using HiRO = SpinorAcc<HP, HL, true>;
+    using HiRW = SpinorAcc<HP, HL, false>;
+    using HiGA = GaugeAcc<HP, 18, HL>;
+    using CallerRO = SpinorAcc<LQ_F64, LQ_LAYOUT_LEX, true>;
     using IMap = typename std::conditional<IL == LQ_LAYOUT_LEX, MapLex<kBS>, MapEoFull<kBS>>::type;
     using ISiteMap = typename std::conditional<IL == LQ_LAYOUT_LEX, MapLex<kSiteBS>, MapEoFull<kSiteBS>>::type;
+    using HMap = typename std::conditional<HL == LQ_LAYOUT_LEX, MapLex<kBS>, MapEoFull<kBS>>::type;
+    using HSiteMap = typename std::conditional<HL == LQ_LAYOUT_LEX, MapLex<kSiteBS>, MapEoFull<kSiteBS>>::type;
+    constexpr bool kPairs = (HP == LQ_F64X);
 
     SolverState* dstate = (SolverState*)(ws + w.state);
     const RedCtx rc{dstate, (double*)(ws + w.partials)};
     const double a = m_q + 4.0, b = 0.5;
 
-    // caller fields (FP64, LEX)
-    const HiGA Uh = make_gauge<LQ_F64, 18, LQ_LAYOUT_LEX>(U, g);
-    const HiRO eta_ro = make_spinor<LQ_F64, LQ_LAYOUT_LEX, true>(eta, g, false);
-    const HiRO x_ro = make_spinor<LQ_F64, LQ_LAYOUT_LEX, true>(x, g, false);
-    const HiRW x_rw = make_spinor<LQ_F64, LQ_LAYOUT_LEX, false>(x, g, false);
-    const HiRO rh_ro = make_spinor<LQ_F64, LQ_LAYOUT_LEX, true>(ws + w.r_high, g, false);
-    const HiRW rh_rw = make_spinor<LQ_F64, LQ_LAYOUT_LEX, false>(ws + w.r_high, g, false);
-    const HiRO th_ro = make_spinor<LQ_F64, LQ_LAYOUT_LEX, true>(ws + w.t_high, g, false);
-    const HiRW th_rw = make_spinor<LQ_F64, LQ_LAYOUT_LEX, false>(ws + w.t_high, g, false);
+    // outer fields: the caller's arrays (native FP64) or pair copies in the workspace
+    const void* Uo = kPairs ? (const void*)(ws + w.u_x) : U;
+    const void* etao = kPairs ? (const void*)(ws + w.eta_x) : eta;
+    void* xo = kPairs ? (void*)(ws + w.x_x) : x;
+    const HiGA Uh = make_gauge<HP, 18, HL>(Uo, g);
+    const HiRO eta_ro = make_spinor<HP, HL, true>(etao, g, false);
+    const HiRO x_ro = make_spinor<HP, HL, true>(xo, g, false);
+    const HiRW x_rw = make_spinor<HP, HL, false>(xo, g, false);
+    const HiRO rh_ro = make_spinor<HP, HL, true>(ws + w.r_high, g, false);
+    const HiRW rh_rw = make_spinor<HP, HL, false>(ws + w.r_high, g, false);
+    const HiRO th_ro = make_spinor<HP, HL, true>(ws + w.t_high, g, false);
+    const HiRW th_rw = make_spinor<HP, HL, false>(ws + w.t_high, g, false);
+    const CallerRO eta_caller = make_spinor<LQ_F64, LQ_LAYOUT_LEX, true>(eta, g, false);
+    const SpinorAcc<LQ_F64, LQ_LAYOUT_LEX, false> x_caller = make_spinor<LQ_F64, LQ_LAYOUT_LEX, false>(x, g, false);
 
-    // inner fields
-    const void* Ulow = (IP == LQ_F64) ? U : (const void*)(ws + w.u_low);
+    // inner fields; an FP64-class inner loop shares the outer links
+    const void* Ulow = (IP == LQ_F64) ? U : (IP == LQ_F64X ? Uo : (const void*)(ws + w.u_low));
     const GA Ui = make_gauge<IP, IF, IL>(Ulow, g);
     const SpRO psi_ro = make_spinor<IP, IL, true>(ws + w.psi, g, false);
     const SpRW psi_rw = make_spinor<IP, IL, false>(ws + w.psi, g, false);
@@ -460,8 +508,9 @@ int run_solver(const Geom& g, double m_q, const void* U, const void* eta, void* 
     const SpRO t_ro = make_spinor<IP, IL, true>(ws + w.t, g, false);
     const SpRW t_rw = make_spinor<IP, IL, false>(ws + w.t, g, false);
 
-    const MapLex<kBS> hmap{g};
-    const MapLex<kSiteBS> hsite{g};
+    const MapLex<kSiteBS> lexsite{g};
+    const HMap hmap{g};
+    const HSiteMap hsite{g};
     const IMap imap{g};
     const ISiteMap isite{g};
 
@@ -470,15 +519,17 @@ int run_solver(const Geom& g, double m_q, const void* U, const void* eta, void* 
     lq_cg_info out{};
     const bool prof = (prm.flags & LQ_CG_PROFILE) != 0;
     const int chunk = prm.chunk > 0 ? prm.chunk : (g.V >= (1 << 18) ? 8 : 32);
-    // CUDA events around the inner kernels (3 roles x chunk) and the FP64 residual
+    // CUDA events around the inner kernels (3 roles x chunk) and the outer residual
     struct Events {
         std::vector<cudaEvent_t> ev;
-        ~Events() { for (cudaEvent_t x : ev) cudaEventDestroy(x); }
+        ~Events() {
+            for (cudaEvent_t x : ev) cudaEventDestroy(x);
+        }
     } evs;
     if (prof) {
         evs.ev.resize(6 * chunk + 2);
-        for (auto& x : evs.ev)
-            if ((e = cudaEventCreate(&x)) != cudaSuccess) return cuda_fail(e, "event create");
+        for (auto& ev : evs.ev)
+            if ((e = cudaEventCreate(&ev)) != cudaSuccess) return cuda_fail(e, "event create");
     }
     auto ev_at = [&](int role, int j, int end) { return evs.ev[(role * chunk + j) * 2 + end]; };
     auto elapsed = [&](cudaEvent_t a0, cudaEvent_t a1) {
@@ -498,15 +549,15 @@ int run_solver(const Geom& g, double m_q, const void* U, const void* eta, void* 
         EpiAxpby<HiRW, HiRO, true, false> e1;
         e1.out = th_rw;
         e1.y = x_ro;
-        e1.a = a;
-        e1.b = b;
+        e1.a = from_double<HReal>(a);
+        e1.b = from_double<HReal>(b);
         e1.rc = rc;
         e1.slot = 0;
         if (prof) cudaEventRecord(evs.ev[6 * chunk], st);
         cudaError_t er = launch_stencil<kBS>(hmap, s1, e1, st);
         if (er != cudaSuccess) return er;
         Stencil<HiGA, HiRO, true> s2{g, Uh, th_ro};
-        EpiResid<HiRO, HiRO, HiRW> e2{eta_ro, th_ro, rh_rw, a, b, rc, 2};
+        EpiResid<HiRO, HiRO, HiRW> e2{eta_ro, th_ro, rh_rw, from_double<HReal>(a), from_double<HReal>(b), rc, 2};
         er = launch_stencil<kBS>(hmap, s2, e2, st);
         out.launches += 2;
         if (prof) cudaEventRecord(evs.ev[6 * chunk + 1], st);
@@ -518,21 +569,39 @@ int run_solver(const Geom& g, double m_q, const void* U, const void* eta, void* 
         out.kernel_ms[LQ_K_HIGH] += elapsed(evs.ev[6 * chunk], evs.ev[6 * chunk + 1]);
         out.kernel_calls[LQ_K_HIGH] += 2;
     };
+    // the pair copy of x back into the caller's FP64 x
+    auto write_back_x = [&]() -> cudaError_t {
+        if constexpr (kPairs) {
+            out.launches += 1;
+            return convert_spinor(g, LQ_F64X, LQ_LAYOUT_EO, xo, LQ_F64, LQ_LAYOUT_LEX, x, st);
+        }
+        return cudaSuccess;
+    };
 
     if ((e = cudaMemsetAsync(dstate, 0, sizeof(SolverState), st)) != cudaSuccess) return cuda_fail(e, "state init");
-    if constexpr (IP != LQ_F64) {
+    if constexpr (kPairs) {
+        if ((e = convert_gauge(g, LQ_F64, LQ_LAYOUT_LEX, U, LQ_F64X, 18, LQ_LAYOUT_EO, ws + w.u_x, st)) != cudaSuccess ||
+            (e = convert_spinor(g, LQ_F64, LQ_LAYOUT_LEX, eta, LQ_F64X, LQ_LAYOUT_EO, ws + w.eta_x, st)) != cudaSuccess ||
+            (e = convert_spinor(g, LQ_F64, LQ_LAYOUT_LEX, x, LQ_F64X, LQ_LAYOUT_EO, ws + w.x_x, st)) != cudaSuccess)
+            return cuda_fail(e, "FP32-pair copies");
+        out.launches += 3;
+    }
+    if constexpr (IP == LQ_F32 || IP == LQ_F16S) {
         if ((e = convert_gauge(g, LQ_F64, LQ_LAYOUT_LEX, U, IP, IF, IL, ws + w.u_low, st)) != cudaSuccess)
             return cuda_fail(e, "link pack");
+        out.launches += 1;
     }
-    // ||eta||^2 -> red[3]
-    if ((e = launch_site<kSiteBS>(hsite, OpNorm<HiRO>{eta_ro, rc, 3}, st)) != cudaSuccess) return cuda_fail(e, "norm");
-    out.launches += (IP != LQ_F64) ? 2 : 1;
+    // ||eta||^2 -> red[3], from the caller's FP64 eta
+    if ((e = launch_site<kSiteBS>(lexsite, OpNorm<CallerRO>{eta_caller, rc, 3}, st)) != cudaSuccess)
+        return cuda_fail(e, "norm");
+    out.launches += 1;
     if ((e = read_state()) != cudaSuccess) return cuda_fail(e, "norm");
     const double eta_norm = sqrt(hs.red[3]);
     out.eta_norm = eta_norm;
     if (!isfinite(eta_norm)) return fail(LQ_ERR_NONFINITE, "eta has non-finite entries");
     if (eta_norm == 0.0) {
-        if ((e = launch_site<kSiteBS>(hsite, OpZero<HiRW>{x_rw}, st)) != cudaSuccess) return cuda_fail(e, "zero");
+        if ((e = launch_site<kSiteBS>(lexsite, OpZero<SpinorAcc<LQ_F64, LQ_LAYOUT_LEX, false>>{x_caller}, st)) != cudaSuccess)
+            return cuda_fail(e, "zero");
         out.launches += 1;
         if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "zero");
         out.status = LQ_OK;
@@ -563,20 +632,22 @@ int run_solver(const Geom& g, double m_q, const void* U, const void* eta, void* 
         const double rel_target = target / s;
         const double stop_rho = fmax(delta * delta, rel_target * rel_target);
         const int k_max = prm.max_iter - total;
-        // cycle start
+        // cycle start: both fields of the restart live on the outer map's sites
         if (l == 0) {
-            OpRestart<HiRO, SpRW, SpRW, SpRW, true> op{rh_ro, r_rw, p_rw, psi_rw, 1.0 / s, stop_rho, k_max, rc};
+            OpRestart<HiRO, SpRW, SpRW, SpRW, true> op{rh_ro, r_rw, p_rw, psi_rw, stop_rho, k_max, rc,
+                                                       from_double<Real>(1.0 / s)};
             e = launch_site<kSiteBS>(hsite, op, st);
             out.launches += 1;
         } else {
-            OpRestart<HiRO, SpRW, SpRO, SpRW, false> op{rh_ro, r_rw, p_ro, psi_rw, 1.0 / s, stop_rho, k_max, rc};
+            OpRestart<HiRO, SpRW, SpRO, SpRW, false> op{rh_ro, r_rw, p_ro, psi_rw, stop_rho, k_max, rc,
+                                                        from_double<Real>(1.0 / s)};
             e = launch_site<kSiteBS>(hsite, op, st);
             if (e == cudaSuccess) {
                 OpRestartP<SpRO, SpRW, SpRW> op2;
                 op2.r = r_ro;
                 op2.p = p_rw;
                 op2.x = psi_rw;
-                op2.beta0 = s / (s_prev * rho_k);
+                op2.b0 = from_double<Real>(s / (s_prev * rho_k));
                 op2.rc = rc;
                 e = launch_site<kSiteBS>(isite, op2, st);
             }
@@ -586,10 +657,11 @@ int run_solver(const Geom& g, double m_q, const void* U, const void* eta, void* 
 
         // inner CG: chunks of K1, K2, K3 until the device-side stop flag is set
         Stencil<GA, SpRO, false> sK1{g, Ui, p_ro};
-        EpiK1<SpRW, SpRO> eK1{t_rw, p_ro, (Real)a, (Real)b, rc};
+        EpiK1<SpRW, SpRO> eK1{t_rw, p_ro, from_double<Real>(a), from_double<Real>(b), rc};
         Stencil<GA, SpRO, true> sK2{g, Ui, t_ro};
-        EpiK2<SpRO, SpRO, SpRW, SpRW> eK2{t_ro, p_ro, psi_rw, r_rw, (Real)a, (Real)b, rc, (Real)0};
-        OpK3<SpRW, SpRO> oK3{p_rw, r_ro, rc, (Real)0};
+        EpiK2<SpRO, SpRO, SpRW, SpRW> eK2{t_ro, p_ro, psi_rw, r_rw, from_double<Real>(a), from_double<Real>(b), rc,
+                                          Real(0)};
+        OpK3<SpRW, SpRO> oK3{p_rw, r_ro, rc, Real(0)};
         int guard = 0, iter_before = 0;
         while (true) {
             for (int j = 0; j < chunk; ++j) {
@@ -628,9 +700,11 @@ int run_solver(const Geom& g, double m_q, const void* U, const void* eta, void* 
         }
         total += hs.iter;
         rho_k = hs.rho;
-        // psi^high += s psi_k; then the FP64 residual
-        OpXUpdate<HiRW, SpinorAcc<IP, IL, true>> xu{x_rw, psi_ro, s};
-        if ((e = launch_site<kSiteBS>(hsite, xu, st)) != cudaSuccess) return cuda_fail(e, "x update");
+        // psi^high += s psi_k; then the outer residual
+        OpXUpdate<HiRW, SpinorAcc<IP, IL, true>> xu{x_rw, psi_ro, from_double<HReal>(s)};
+        if constexpr (HL == IL) e = launch_site<kSiteBS>(hsite, xu, st);
+        else e = launch_site<kSiteBS>(lexsite, xu, st);
+        if (e != cudaSuccess) return cuda_fail(e, "x update");
         out.launches += 1;
         if ((e = high_residual()) != cudaSuccess) return cuda_fail(e, "residual");
         if ((e = read_state()) != cudaSuccess) return cuda_fail(e, "residual");
@@ -642,6 +716,8 @@ int run_solver(const Geom& g, double m_q, const void* U, const void* eta, void* 
         s = s_new;
         ++l;
     }
+    if ((e = write_back_x()) != cudaSuccess) return cuda_fail(e, "x write-back");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "x write-back");
     out.iters = total;
     out.cycles = l;
     out.true_rel_resid = s / eta_norm;
@@ -650,30 +726,19 @@ int run_solver(const Geom& g, double m_q, const void* U, const void* eta, void* 
     return status;
 }
 
-}  // namespace
+// Instantiations live in solver_f64.cu (FP64 and FP32-pair inner loops), solver_f32.cu
+// and solver_f16.cu (mixed inner loops with either outer arithmetic and link format).
+int solve_f64(const Geom& g, double m_q, const void* U, const void* eta, void* x, const lq_cg_params& prm,
+              double delta, const WsLayout& w, char* ws, lq_cg_info* info, cudaStream_t st);
+int solve_f64x(const Geom& g, double m_q, const void* U, const void* eta, void* x, const lq_cg_params& prm,
+               double delta, const WsLayout& w, char* ws, lq_cg_info* info, cudaStream_t st);
+int solve_mixed_f32(const Geom& g, double m_q, const void* U, const void* eta, void* x, const lq_cg_params& prm,
+                    double delta, const WsLayout& w, char* ws, lq_cg_info* info, cudaStream_t st, bool pairs,
+                    int fmt);
+int solve_mixed_f16(const Geom& g, double m_q, const void* U, const void* eta, void* x, const lq_cg_params& prm,
+                    double delta, const WsLayout& w, char* ws, lq_cg_info* info, cudaStream_t st, bool pairs,
+                    int fmt);
 
-size_t cg_workspace_bytes(const Geom& g, int mode) { return ws_layout(g, mode).total; }
-
-int cg_solve(const Geom& g, double m_q, int mode, const void* U, const void* eta, void* x, const lq_cg_params& prm,
-             void* ws, size_t ws_bytes, lq_cg_info* info, cudaStream_t st) {
-    const WsLayout w = ws_layout(g, mode);
-    if (ws == nullptr || ws_bytes < w.total)
-        return fail(LQ_ERR_WORKSPACE, "workspace of %zu bytes needed, %zu given", w.total, ws_bytes);
-    char* base = (char*)ws;
-    double delta = prm.delta;
-    switch (mode) {
-        case LQ_CG_F64:
-            if (!(delta > 0.0)) delta = 0.0;
-            return run_solver<LQ_F64, 18, LQ_LAYOUT_LEX>(g, m_q, U, eta, x, prm, delta, w, base, info, st);
-        case LQ_CG_MIXED_F32:
-            if (!(delta > 0.0)) delta = 1e-3;
-            return run_solver<LQ_F32, 12, LQ_LAYOUT_EO>(g, m_q, U, eta, x, prm, delta, w, base, info, st);
-        case LQ_CG_MIXED_F16:
-            if (!(delta > 0.0)) delta = 0.1;
-            return run_solver<LQ_F16S, 12, LQ_LAYOUT_EO>(g, m_q, U, eta, x, prm, delta, w, base, info, st);
-        default:
-            return fail(LQ_ERR_ARG, "unknown CG mode %d", mode);
-    }
-}
+}  // namespace solver_detail
 
 }  // namespace lq

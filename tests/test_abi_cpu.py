@@ -52,6 +52,7 @@ def test_workspace_query(lqlib):
     assert 0 < a < b
     assert lqlib.cg_workspace_bytes((8, 8, 8, 8), "mixed_f16") < lqlib.cg_workspace_bytes((8, 8, 8, 8), "mixed_f32")
     assert lqlib.cg_workspace_bytes((4, 4, 4, 5), "f64") == 0
+    assert lqlib.cg_workspace_bytes((8, 8, 8, 8), "f64x") > lqlib.cg_workspace_bytes((8, 8, 8, 8), "f64")
     assert lqlib.load().lq_cg_workspace_bytes((ctypes.c_int32 * 4)(4, 4, 4, 4), 7) == 0
 
 
@@ -79,6 +80,7 @@ def test_apply_argument_checks(lqlib):
     assert _apply(L, (4, 4, 4, 4), out=P1) == -3              # out aliases psi
     assert _apply(L, (4, 4, 4, 4), out=P1 + 4096) == -3       # partial overlap
     assert _apply(L, (4, 4, 4, 4), m=float("nan")) == -1
+    assert _apply(L, (4, 4, 4, 4), prec=3, fmt=12) == -1       # FP32-pair fields are 18-real
     assert L.lq_dslash_adjoint((ctypes.c_int32 * 4)(4, 4, 4, 3), 0.1, 0, 18, 0, None, None, None, None) == -2
 
 

@@ -32,7 +32,10 @@ def _true_resid(dims, m, U, eta, x):
     return np.linalg.norm(r.ravel()) / np.linalg.norm(eta.ravel())
 
 
-@pytest.mark.parametrize("mode", ["f64", "mixed_f32", "mixed_f16"])
+MODES = ["f64", "f64x", "mixed_f32", "mixed_f16"]
+
+
+@pytest.mark.parametrize("mode", MODES)
 def test_cg_2222_against_dense_solve(lqlib, mode):
     dims = (2, 2, 2, 2)
     m = 0.1
@@ -47,7 +50,7 @@ def test_cg_2222_against_dense_solve(lqlib, mode):
     assert oracle.rel_l2(x.ravel(), xd) <= 1e-10 * np.linalg.cond(A)
 
 
-@pytest.mark.parametrize("mode", ["f64", "mixed_f32", "mixed_f16"])
+@pytest.mark.parametrize("mode", MODES)
 def test_cg_4444_haar_against_oracle(lqlib, mode):
     """The small FP64 configuration: 4^4 Haar links, m_q = 0.1, tolerance 1e-10."""
     dims = (4, 4, 4, 4)
@@ -60,14 +63,14 @@ def test_cg_4444_haar_against_oracle(lqlib, mode):
     assert _true_resid(dims, m, U, eta, x) <= 1e-10 * RESID_SLACK
     xo, it, rel = oracle.cg(dims, m, U, eta, tol=1e-12)
     assert oracle.rel_l2(x, xo) <= 1e-7
-    if mode == "f64":
+    if mode in ("f64", "f64x"):
         # plain CG: the same iterations as the oracle's textbook CG (up to rounding)
         _, it10, _ = oracle.cg(dims, m, U, eta, tol=1e-10)
         assert abs(info["iters"] - it10) <= 2
         assert info["cycles"] <= 2
 
 
-@pytest.mark.parametrize("mode", ["f64", "mixed_f32", "mixed_f16"])
+@pytest.mark.parametrize("mode", MODES)
 def test_cg_near_identity_ragged(lqlib, mode):
     """Near-free links, small mass (the ill-conditioned case) on a lattice with a ragged
     last tile."""
@@ -78,8 +81,22 @@ def test_cg_near_identity_ragged(lqlib, mode):
     x, info, status = _solve(lqlib, dims, m, U, eta, mode, tol=1e-10)
     assert status == 0
     assert _true_resid(dims, m, U, eta, x) <= 1e-10 * RESID_SLACK
-    if mode != "f64":
+    if mode.startswith("mixed"):
         assert info["cycles"] >= 2
+
+
+@pytest.mark.parametrize("mode", ["mixed_f32", "mixed_f16"])
+@pytest.mark.parametrize("native_f64,link18", [(True, False), (False, True), (True, True)])
+def test_cg_outer_arithmetic_and_link_format(lqlib, mode, native_f64, link18):
+    """The solver options: native FP64 outer arithmetic instead of FP32 pairs, and 18-real
+    inner links instead of 12-real."""
+    dims = (4, 6, 4, 4)
+    m = 0.05
+    U = synth.gauge_field(dims, seed=17, kind="near_identity", eps=0.3)
+    eta = synth.gaussian_spinor(dims, seed=18)
+    x, info, status = _solve(lqlib, dims, m, U, eta, mode, tol=1e-10, native_f64=native_f64, link18=link18)
+    assert status == 0
+    assert _true_resid(dims, m, U, eta, x) <= 1e-10 * RESID_SLACK
 
 
 def test_cg_starting_guess_and_resume(lqlib):
@@ -126,7 +143,7 @@ def test_cg_workspace_too_small(lqlib):
         lqlib.cg_solve(dims, 0.1, U, eta, workspace=ws)
 
 
-@pytest.mark.parametrize("mode", ["mixed_f32", "mixed_f16", "f64"])
+@pytest.mark.parametrize("mode", ["mixed_f32", "mixed_f16", "f64", "f64x"])
 def test_cg_full_size_32(lqlib, mode):
     """The mixed-precision workload at full size: 32^4, links exp(0.3 i H), m_q = 0.05,
     tolerance 1e-10; the oracle recomputes the true residual in FP64."""
