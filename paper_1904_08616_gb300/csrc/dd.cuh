@@ -68,10 +68,12 @@ LQ_HD void two_sum(float a, float b, float& s, float& e) {
     e = f_add(f_sub(a, f_sub(s, bb)), f_sub(b, bb));
 }
 
-// renormalise: |lo| <= ulp(hi)/2 afterwards (FastTwoSum; valid because |lo| << |hi| or hi = 0)
+// renormalise: |lo| <= ulp(hi)/2 afterwards.  TwoSum, not FastTwoSum: after a cancellation
+// (a residual eta - A x near convergence) lo can be as large as hi or larger.
 LQ_HD dd dd_renorm(dd a) {
-    const float s = f_add(a.hi, a.lo);
-    return dd{s, f_sub(a.lo, f_sub(s, a.hi))};
+    float s, e;
+    two_sum(a.hi, a.lo, s, e);
+    return dd{s, e};
 }
 
 LQ_HD dd operator+(dd a, dd b) {
@@ -82,7 +84,8 @@ LQ_HD dd operator+(dd a, dd b) {
 LQ_HD dd operator-(dd a) { return dd{-a.hi, -a.lo}; }
 LQ_HD dd operator-(dd a, dd b) { return a + (-b); }
 
-// product: hi*hi exactly as p + e, plus the two cross terms; lo*lo (~2^-48 relative) dropped
+// product: hi*hi exactly as p + e, plus the two cross terms; lo*lo is dropped, which is
+// ~2^-48 relative for normalised operands (normalise cancelled values before squaring)
 LQ_HD dd operator*(dd a, dd b) {
     const float p = f_mul(a.hi, b.hi);
     float e = f_fma(a.hi, b.hi, -p);

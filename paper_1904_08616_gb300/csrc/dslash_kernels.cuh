@@ -177,6 +177,17 @@ template <typename R> LQ_HD R norm2(const Spinor<R>& a) {
     for (int k = 0; k < 12; ++k) s = fma(a.v[k].re, a.v[k].re, fma(a.v[k].im, a.v[k].im, s));
     return s;
 }
+// FP32 pairs: normalise each component first, so that a value whose lo carries most of it
+// (after a cancellation) is squared correctly
+LQ_HD dd norm2(const Spinor<dd>& a) {
+    dd s = dd(0.f);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        const dd re = dd_renorm(a.v[k].re), im = dd_renorm(a.v[k].im);
+        s = fma(re, re, fma(im, im, s));
+    }
+    return s;
+}
 
 // ------------------------------------------------------------------------------------
 // Epilogues.  init() runs once per thread before the site loop and returns false to skip

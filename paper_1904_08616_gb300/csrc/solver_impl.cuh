@@ -43,7 +43,7 @@ namespace solver_detail {
 constexpr int kBS = 128;      // stencil kernels
 constexpr int kSiteBS = 256;  // site-local kernels
 
-template <typename T> __device__ __forceinline__ void zero(Spinor<T>& a) {
+template <typename T> LQ_HD void zero(Spinor<T>& a) {
 #pragma unroll
     for (int k = 0; k < 12; ++k) a.v[k] = {T(0), T(0)};
 }
@@ -93,9 +93,9 @@ struct EpiK1 {
     PA p;
     Real a, b;
     RedCtx rc;
-    __device__ __forceinline__ bool init() { return rc.st->stop == 0; }
+    LQ_HD bool init() { return rc.st->stop == 0; }
     template <typename R>
-    __device__ __forceinline__ void apply(const Site& s, const Spinor<R>& acc, double* red) const {
+    LQ_HD void apply(const Site& s, const Spinor<R>& acc, double* red) const {
         Spinor<R> pv, o;
         p.load(s, pv);
 #pragma unroll
@@ -134,13 +134,13 @@ struct EpiK2 {
     Real a, b;
     RedCtx rc;
     Real alpha;
-    __device__ __forceinline__ bool init() {
+    LQ_HD bool init() {
         if (rc.st->stop) return false;
         alpha = from_double<Real>(rc.st->alpha);
         return true;
     }
     template <typename R>
-    __device__ __forceinline__ void apply(const Site& s, const Spinor<R>& acc, double* red) const {
+    LQ_HD void apply(const Site& s, const Spinor<R>& acc, double* red) const {
         Spinor<R> tv, pv, xv, rv;
         t.load(s, tv);
         p.load(s, pv);
@@ -183,12 +183,12 @@ struct OpK3 {
     RA r;
     RedCtx rc;
     Real beta;
-    __device__ __forceinline__ bool init() {
+    LQ_HD bool init() {
         if (rc.st->p_iter == rc.st->iter) return false;
         beta = from_double<Real>(rc.st->beta);
         return true;
     }
-    __device__ __forceinline__ void apply(const Site& s, double*) const {
+    LQ_HD void apply(const Site& s, double*) const {
         Spinor<Real> pv, rv;
         p.load(s, pv);
         r.load(s, rv);
@@ -217,9 +217,9 @@ struct OpRestart {
     double stop_rho;
     int k_max;
     RedCtx rc;
-    __device__ __forceinline__ bool init() { return true; }
+    LQ_HD bool init() { return true; }
     Real is;   // 1/s in the inner arithmetic
-    __device__ __forceinline__ void apply(const Site& s, double* red) const {
+    LQ_HD void apply(const Site& s, double* red) const {
         Spinor<Real> w;
         rh.load(s, w);
 #pragma unroll
@@ -277,12 +277,12 @@ struct OpRestartP {
     Real b0;
     RedCtx rc;
     Real cre, cim;
-    __device__ __forceinline__ bool init() {
+    LQ_HD bool init() {
         cre = from_double<Real>(rc.st->red[0]);
         cim = from_double<Real>(rc.st->red[1]);
         return true;
     }
-    __device__ __forceinline__ void apply(const Site& s, double*) const {
+    LQ_HD void apply(const Site& s, double*) const {
         Spinor<Real> rv, pv;
         r.load(s, rv);
         p.load(s, pv);
@@ -307,8 +307,8 @@ struct OpXUpdate {
     XA x;
     PsiA psi;
     Real s;
-    __device__ __forceinline__ bool init() { return true; }
-    __device__ __forceinline__ void apply(const Site& st, double*) const {
+    LQ_HD bool init() { return true; }
+    LQ_HD void apply(const Site& st, double*) const {
         Spinor<Real> xv, pv;
         x.load(st, xv);
         psi.load(st, pv);
@@ -326,8 +326,8 @@ struct OpNorm {
     A a;
     RedCtx rc;
     int slot;
-    __device__ __forceinline__ bool init() { return true; }
-    __device__ __forceinline__ void apply(const Site& s, double* red) const {
+    LQ_HD bool init() { return true; }
+    LQ_HD void apply(const Site& s, double* red) const {
         Spinor<double> v;
         a.load(s, v);
         red[0] += norm2(v);
@@ -344,8 +344,8 @@ template <class XA>
 struct OpZero {
     static constexpr int NRED = 0;
     XA x;
-    __device__ __forceinline__ bool init() { return true; }
-    __device__ __forceinline__ void apply(const Site& s, double*) const {
+    LQ_HD bool init() { return true; }
+    LQ_HD void apply(const Site& s, double*) const {
         Spinor<double> z;
         zero(z);
         x.store(s, z);
@@ -364,8 +364,8 @@ struct EpiResid {
     Real a, b;
     RedCtx rc;
     int slot;
-    __device__ __forceinline__ bool init() { return true; }
-    __device__ __forceinline__ void apply(const Site& s, const Spinor<Real>& acc, double* red) const {
+    LQ_HD bool init() { return true; }
+    LQ_HD void apply(const Site& s, const Spinor<Real>& acc, double* red) const {
         Spinor<Real> tv, ev, o;
         t.load(s, tv);
         eta.load(s, ev);
