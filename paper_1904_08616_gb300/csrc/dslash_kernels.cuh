@@ -14,6 +14,8 @@
 // so U P psi = [U h ; S B^dag (U h)] and only the two colour vectors of h need the link.
 #pragma once
 
+#include <type_traits>
+
 #include "lq_internal.cuh"
 
 namespace lq {
@@ -97,12 +99,78 @@ LQ_HD void hop_dir(Spinor<R>& acc, const Spinor<R>& q, const Link<R>& U, R sc) {
     }
 }
 
+// The same hop with the direction MU, the projector sign and the link orientation known
+// only at run time.  Used by the rolled stencil below: one copy of the mat-vec serves all
+// eight hops, which keeps long FP32-pair kernels inside the instruction cache.
+template <typename R> LQ_HD cplx<R> cneg(cplx<R> a) { return {-a.re, -a.im}; }
+template <typename R> LQ_HD cplx<R> csel(bool c, cplx<R> a, cplx<R> b) { return c ? a : b; }
+
+template <bool SCALED, typename R>
+LQ_HD void hop_dir_rt(Spinor<R>& acc, const Spinor<R>& q, const Link<R>& U, R sc, int mu, bool plus, bool back) {
+    cplx<R> h0[3], h1[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const cplx<R> p0 = q.v[c], p1 = q.v[3 + c], p2 = q.v[6 + c], p3 = q.v[9 + c];
+        cplx<R> b0, b1;                       // B_mu psi_dn
+        switch (mu) {
+            case 0: b0 = ctimes_mi(p3); b1 = ctimes_mi(p2); break;
+            case 1: b0 = cneg(p3); b1 = p2; break;
+            case 2: b0 = ctimes_mi(p2); b1 = ctimes_i(p3); break;
+            default: b0 = p2; b1 = p3; break;
+        }
+        h0[c] = cadd(p0, csel(plus, b0, cneg(b0)));
+        h1[c] = cadd(p1, csel(plus, b1, cneg(b1)));
+    }
+    // W = U or U^dag
+    cplx<R> W[3][3];
+#pragma unroll
+    for (int A = 0; A < 3; ++A)
+#pragma unroll
+        for (int B = 0; B < 3; ++B) W[A][B] = csel(back, cconj(U.u[B][A]), U.u[A][B]);
+    cplx<R> g0[3], g1[3];
+#pragma unroll
+    for (int A = 0; A < 3; ++A) {
+        g0[A] = cmul(W[A][0], h0[0]);
+        g1[A] = cmul(W[A][0], h1[0]);
+#pragma unroll
+        for (int B = 1; B < 3; ++B) {
+            g0[A] = cfma(W[A][B], h0[B], g0[A]);
+            g1[A] = cfma(W[A][B], h1[B], g1[A]);
+        }
+    }
+    const R sp = sc, sl = plus ? sc : -sc;    // upper and lower accumulation factors
+#pragma unroll
+    for (int A = 0; A < 3; ++A) {
+        cplx<R> l2, l3;                       // B_mu^dag (g0, g1)
+        switch (mu) {
+            case 0: l2 = ctimes_i(g1[A]); l3 = ctimes_i(g0[A]); break;
+            case 1: l2 = g1[A]; l3 = cneg(g0[A]); break;
+            case 2: l2 = ctimes_i(g0[A]); l3 = ctimes_mi(g1[A]); break;
+            default: l2 = g0[A]; l3 = g1[A]; break;
+        }
+        if constexpr (SCALED) {
+            acc.v[A] = caxpy(sp, g0[A], acc.v[A]);
+            acc.v[3 + A] = caxpy(sp, g1[A], acc.v[3 + A]);
+            acc.v[6 + A] = caxpy(sl, l2, acc.v[6 + A]);
+            acc.v[9 + A] = caxpy(sl, l3, acc.v[9 + A]);
+        } else {
+            acc.v[A] = cadd(acc.v[A], g0[A]);
+            acc.v[3 + A] = cadd(acc.v[3 + A], g1[A]);
+            acc.v[6 + A] = cadd(acc.v[6 + A], csel(plus, l2, cneg(l2)));
+            acc.v[9 + A] = cadd(acc.v[9 + A], csel(plus, l3, cneg(l3)));
+        }
+    }
+}
+
 // The hopping sum  sum_mu [ U_mu(n) P_f psi(n+mu) + U_mu(n-mu)^dag P_b psi(n-mu) ]
 // (without the 1/2), P_f = 1 - gamma (D) or 1 + gamma (D^dag), P_b the other one.
 // GA: gauge accessor (full field), SA: spinor accessor of the neighbours.
 template <class GA, class SA, bool DAG>
 struct Stencil {
     using Real = typename GA::Real;
+    // FP32-pair arithmetic is ~10k instructions per site: roll the eight hops so the
+    // kernel's code fits the instruction cache; the FP32 / FP16 stencils stay unrolled
+    static constexpr bool kRolled = std::is_same<Real, dd>::value;
     Geom g;
     GA ga;
     SA sa;
@@ -127,10 +195,34 @@ struct Stencil {
     LQ_HD void apply(const Site& s, const int c[4], Spinor<Real>& acc) const {
 #pragma unroll
         for (int k = 0; k < 12; ++k) acc.v[k] = {Real(0), Real(0)};
-        dir<0>(s, c, acc);
-        dir<1>(s, c, acc);
-        dir<2>(s, c, acc);
-        dir<3>(s, c, acc);
+        if constexpr (kRolled) {
+            // one hop per trip: forward (h even) and backward (h odd) in each direction
+#pragma unroll 1
+            for (int h = 0; h < 8; ++h) {
+                const int mu = h >> 1;
+                const bool back = (h & 1) != 0;
+                const int cm = mu == 0 ? c[0] : (mu == 1 ? c[1] : (mu == 2 ? c[2] : c[3]));
+                const int L = mu == 0 ? g.L[0] : (mu == 1 ? g.L[1] : (mu == 2 ? g.L[2] : g.L[3]));
+                const int St = mu == 0 ? g.S[0] : (mu == 1 ? g.S[1] : (mu == 2 ? g.S[2] : g.S[3]));
+                int ln;
+                if (!back) ln = (cm == L - 1) ? s.lex - (L - 1) * St : s.lex + St;
+                else ln = (cm == 0) ? s.lex + (L - 1) * St : s.lex - St;
+                const Site nb = nb_site(ln, s.p);
+                Spinor<Real> q;
+                Link<Real> U;
+                Real sc;
+                sa.load_raw(nb, q, sc);
+                ga.load(back ? nb : s, mu, U);
+                // forward hops use 1 + SF gamma, backward hops 1 - SF gamma (SF = +1 for D^dag)
+                const bool plus = back ? !DAG : DAG;
+                hop_dir_rt<SA::kScaled>(acc, q, U, sc, mu, plus, back);
+            }
+        } else {
+            dir<0>(s, c, acc);
+            dir<1>(s, c, acc);
+            dir<2>(s, c, acc);
+            dir<3>(s, c, acc);
+        }
     }
 };
 
