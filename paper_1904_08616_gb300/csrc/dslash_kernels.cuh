@@ -325,9 +325,21 @@ struct EpiAxpby {
     }
 };
 
+// Optional minimum resident blocks per SM requested from the compiler (its register
+// budget) for the FP32-arithmetic and the FP32-pair stencils; 0 leaves the choice to ptxas.
+#ifndef LQ_STENCIL_MINB_F32
+#define LQ_STENCIL_MINB_F32 0
+#endif
+#ifndef LQ_STENCIL_MINB_PAIR
+#define LQ_STENCIL_MINB_PAIR 0
+#endif
+template <class Real> struct StencilMinBlocks { static constexpr int value = 0; };
+template <> struct StencilMinBlocks<float> { static constexpr int value = LQ_STENCIL_MINB_F32; };
+template <> struct StencilMinBlocks<dd> { static constexpr int value = LQ_STENCIL_MINB_PAIR; };
+
 // Generic stencil kernel: grid-stride over tiles, one thread per site.
 template <int BS, class Map, class Sten, class Epi>
-__global__ void __launch_bounds__(BS) stencil_kernel(Map map, Sten sten, Epi epi) {
+__device__ __forceinline__ void stencil_body(const Map& map, const Sten& sten, Epi& epi) {
     if (!epi.init()) return;
     constexpr int NR = Epi::NRED > 0 ? Epi::NRED : 1;
     double red[NR];
@@ -343,6 +355,16 @@ __global__ void __launch_bounds__(BS) stencil_kernel(Map map, Sten sten, Epi epi
         epi.apply(s, acc, red);
     }
     epi.template finish<BS>(red);
+}
+
+template <int BS, class Map, class Sten, class Epi>
+__global__ void __launch_bounds__(BS) stencil_kernel(Map map, Sten sten, Epi epi) {
+    stencil_body<BS>(map, sten, epi);
+}
+
+template <int BS, int MINB, class Map, class Sten, class Epi>
+__global__ void __launch_bounds__(BS, MINB) stencil_kernel_minb(Map map, Sten sten, Epi epi) {
+    stencil_body<BS>(map, sten, epi);
 }
 
 // Grid size for a grid-stride kernel: every SM filled to its occupancy, never more
@@ -363,7 +385,11 @@ inline int grid_for(KernelPtr k, int bs, int ntiles) {
 
 template <int BS, class Map, class Sten, class Epi>
 inline cudaError_t launch_stencil(const Map& map, const Sten& sten, const Epi& epi, cudaStream_t st) {
-    auto k = stencil_kernel<BS, Map, Sten, Epi>;
+    constexpr int MINB = StencilMinBlocks<typename Sten::Real>::value;
+    auto k = [] {
+        if constexpr (MINB > 0) return stencil_kernel_minb<BS, MINB, Map, Sten, Epi>;
+        else return stencil_kernel<BS, Map, Sten, Epi>;
+    }();
     static thread_local int cached_grid_tiles = -1, cached_grid = 0;
     const int nt = map.ntiles();
     int grid;
