@@ -13,7 +13,8 @@
  * Conventions shared by every entry point
  * ----------------------------------------
  * Lattice: dims[4] = {Lx, Ly, Lz, Lt}; every extent must be even and >= 2, and the volume
- *   V = Lx*Ly*Lz*Lt must satisfy V <= 10^8 (the largest volume the paper considers).  Boundaries are periodic in all four
+ *   V = Lx*Ly*Lz*Lt must satisfy V <= 10^8 (the largest volume the paper considers), and
+ *   V * nrhs <= 10^8 for calls on several fields.  Boundaries are periodic in all four
  *   directions.  Direction mu = 0, 1, 2, 3 is x, y, z, t.
  * Gamma matrices: chiral Euclidean basis, P^{-mu} = 1 - gamma_{mu+1}, P^{+mu} = 1 + gamma_{mu+1},
  *   gamma_k = [[0, -i sigma_k], [i sigma_k, 0]] (k = 1, 2, 3), gamma_4 = [[0, 1], [1, 0]],
@@ -43,6 +44,14 @@
  *   Arithmetic is FP64 for LQ_F64, FP32 pairs for LQ_F64X, FP32 for LQ_F32 / LQ_F16S.
  *   Kernel outputs in LQ_F16S use one reciprocal of the scale per site (h = fl16(v * fl32(1/s)));
  *   lq_convert_spinor divides every component (h = fl16(fl32(v) / s)) and is bit-exact.
+ *
+ * Several fields (right-hand sides) at once, nrhs of them:
+ *   LEX: nrhs complete fields one after the other (field r at byte offset r * field size).
+ *   EO : interleaved per site: chunk k of (p, cb) of field r at chunk slot
+ *        ((p*K + k)*Vh + cb)*nrhs + r (F16S: all halves, then the scale of (p, cb, r) at
+ *        (p*Vh + cb)*nrhs + r); for nrhs = 1 this is the single-field EO layout.  The
+ *        fields of one site sit side by side, so a batched kernel reads each link once for
+ *        all of them.  EO multi-field buffers hold a power of two (<= 32) of fields.
  *
  * Buffers are device pointers owned by the caller, 16-byte aligned; the library neither
  * keeps nor frees them.  Calls that take a cuda_stream (a cudaStream_t, NULL = legacy
@@ -109,6 +118,19 @@ int lq_dslash_adjoint(const int32_t dims[4], double m_q, int32_t prec, int32_t l
                       void *cuda_stream);
 
 /*
+ * lq_dslash_apply_multi / lq_dslash_adjoint_multi -- out_r = D psi_r (or D^dag psi_r) for
+ * nrhs fields at once, in the multi-field layouts above; the gauge field is read once per
+ * site for all of them.  The paper applies D to one vector at a time (Eq. 1); batching is
+ * this library's.  EO: nrhs a power of two <= 32, one launch.  LEX: any nrhs >= 1.
+ */
+int lq_dslash_apply_multi(const int32_t dims[4], double m_q, int32_t prec, int32_t link_fmt,
+                          int32_t layout, int32_t nrhs, const void *U, const void *psi, void *out,
+                          void *cuda_stream);
+int lq_dslash_adjoint_multi(const int32_t dims[4], double m_q, int32_t prec, int32_t link_fmt,
+                            int32_t layout, int32_t nrhs, const void *U, const void *psi, void *out,
+                            void *cuda_stream);
+
+/*
  * lq_dslash_hop -- the parity-to-parity hopping term of Eq. (1):
  *   out_p = a * y_p + b * H_{p,1-p} psi_{1-p},   H = 1/2 sum_mu [ ... ] of Eq. (1),
  * on the half lattice of parity out_parity (the even-odd split of Eq. 1; the paper does
@@ -131,6 +153,11 @@ int lq_dslash_hop(const int32_t dims[4], int32_t out_parity, int32_t dagger, dou
 int lq_convert_spinor(const int32_t dims[4], int32_t src_prec, int32_t src_layout,
                       const void *src, int32_t dst_prec, int32_t dst_layout, void *dst,
                       void *cuda_stream);
+/* lq_convert_spinor for nrhs fields in the multi-field layouts (e.g. nrhs stacked FP64 LEX
+ * fields into one interleaved FP32 EO buffer). */
+int lq_convert_spinor_multi(const int32_t dims[4], int32_t nrhs, int32_t src_prec,
+                            int32_t src_layout, const void *src, int32_t dst_prec,
+                            int32_t dst_layout, void *dst, void *cuda_stream);
 int lq_convert_gauge(const int32_t dims[4], int32_t src_prec, int32_t src_layout,
                      const void *src, int32_t dst_prec, int32_t dst_fmt, int32_t dst_layout,
                      void *dst, void *cuda_stream);
@@ -184,6 +211,8 @@ typedef struct lq_cg_info {
 
 /* Workspace bytes lq_cg_solve needs for these dims and mode (0 on bad arguments). */
 size_t lq_cg_workspace_bytes(const int32_t dims[4], int32_t mode);
+/* Workspace bytes lq_cg_solve_multi needs for nrhs right-hand sides. */
+size_t lq_cg_workspace_bytes_multi(const int32_t dims[4], int32_t mode, int32_t nrhs);
 
 /*
  * lq_cg_solve -- solve D^dag D x = eta (Algorithm 1 of the paper, Section 1).
@@ -230,6 +259,20 @@ int lq_cg_solve_noalloc(const int32_t dims[4], double m_q, int32_t mode, const v
                         const void *eta, void *x, const lq_cg_params *params, lq_cg_info *info,
                         void *cuda_stream);
 size_t lq_cg_noalloc_max_workspace_bytes(void);
+
+/*
+ * lq_cg_solve_multi -- nrhs independent solves D^dag D x_r = eta_r (Algorithm 1 for each)
+ * sharing the gauge field.  eta and x hold nrhs stacked FP64 LEX fields; info (optional)
+ * receives nrhs records.  The right-hand sides are processed in batches of a power of two
+ * (<= 8) whose kernels read each link once per site for the whole batch; each right-hand
+ * side keeps its own CG scalars and stops on its own criterion while the batch goes on,
+ * and the reliable updates of a batch are taken together.  Batching is not in the paper.
+ * Returns LQ_OK if every solve converged, LQ_NOT_CONVERGED if some did not, or the most
+ * negative error status.
+ */
+int lq_cg_solve_multi(const int32_t dims[4], double m_q, int32_t mode, int32_t nrhs,
+                      const void *U, const void *eta, void *x, const lq_cg_params *params,
+                      void *workspace, size_t ws_bytes, lq_cg_info *info, void *cuda_stream);
 
 /* Message of the last error on this host thread ("" if none). */
 const char *lq_last_error(void);

@@ -224,3 +224,38 @@ def _from_eo_gauge(flat, dims, fmt, w):
     arr = flat.reshape(4, 2, K, V // 2, w)
     d = arr[:, p, :, cb, :]          # (V, 4, K, w): advanced indices first
     return d.reshape(V, 4, fmt)
+
+
+# ------------------------------------------------------------------------------------
+# several fields: LEX stacks complete fields; EO interleaves the fields of each chunk slot
+# ------------------------------------------------------------------------------------
+def encode_spinor_multi(psis, dims, prec="f64", layout="lex") -> np.ndarray:
+    """A list of complex (V, 4, 3) fields -> one multi-field buffer (uint8)."""
+    n = len(psis)
+    if layout == "lex":
+        return np.concatenate([encode_spinor(p, dims, prec, "lex") for p in psis])
+    V = _vol(dims)
+    singles = [encode_spinor(p, dims, prec, "eo") for p in psis]
+    if prec == "f16s":
+        halves = np.stack([b[:48 * V].view(np.uint8).reshape(-1, 16) for b in singles], axis=1)   # slot, field, 16 B
+        scales = np.stack([b[48 * V:].view(np.float32) for b in singles], axis=1)                 # site, field
+        return np.concatenate([halves.reshape(-1), np.ascontiguousarray(scales).view(np.uint8).reshape(-1)])
+    chunks = np.stack([b.reshape(-1, 16) for b in singles], axis=1)                               # slot, field, 16 B
+    return np.ascontiguousarray(chunks).reshape(-1)
+
+
+def decode_spinor_multi(buf, dims, n, prec="f64", layout="lex"):
+    """A multi-field buffer -> list of n complex (V, 4, 3) fields."""
+    buf = np.asarray(buf).view(np.uint8).reshape(-1)
+    one = spinor_bytes(dims, prec)
+    if layout == "lex":
+        return [decode_spinor(buf[i * one:(i + 1) * one], dims, prec, "lex") for i in range(n)]
+    V = _vol(dims)
+    if prec == "f16s":
+        halves = buf[:48 * V * n].reshape(-1, n, 16)
+        scales = buf[48 * V * n:].view(np.float32).reshape(-1, n)
+        return [decode_spinor(np.concatenate([np.ascontiguousarray(halves[:, i]).reshape(-1),
+                                              np.ascontiguousarray(scales[:, i]).view(np.uint8).reshape(-1)]),
+                              dims, prec, "eo") for i in range(n)]
+    chunks = buf.reshape(-1, n, 16)
+    return [decode_spinor(np.ascontiguousarray(chunks[:, i]).reshape(-1), dims, prec, "eo") for i in range(n)]

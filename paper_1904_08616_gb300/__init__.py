@@ -19,8 +19,9 @@ from . import build as _build
 
 __all__ = [
     "LqError", "load", "lib_path", "PREC", "LAYOUT", "CG_MODE",
-    "field_bytes", "dslash_apply", "dslash_adjoint", "dslash_hop", "convert_spinor",
-    "convert_gauge", "cg_workspace_bytes", "cg_solve", "last_error", "version",
+    "field_bytes", "dslash_apply", "dslash_adjoint", "dslash_apply_multi", "dslash_adjoint_multi",
+    "dslash_hop", "convert_spinor", "convert_spinor_multi", "convert_gauge", "cg_workspace_bytes",
+    "cg_solve", "cg_solve_multi", "last_error", "version",
 ]
 
 PREC = {"f64": 0, "f32": 1, "f16s": 2, "f64x": 3}
@@ -81,6 +82,17 @@ def load(build_if_missing: bool = True):
         L.lq_dslash_hop.restype = ctypes.c_int
         L.lq_convert_spinor.argtypes = [_Dims, i32, i32, _vp, i32, i32, _vp, _vp]
         L.lq_convert_spinor.restype = ctypes.c_int
+        L.lq_convert_spinor_multi.argtypes = [_Dims, i32, i32, i32, _vp, i32, i32, _vp, _vp]
+        L.lq_convert_spinor_multi.restype = ctypes.c_int
+        for name in ("lq_dslash_apply_multi", "lq_dslash_adjoint_multi"):
+            fn = getattr(L, name)
+            fn.argtypes = [_Dims, f64, i32, i32, i32, i32, _vp, _vp, _vp, _vp]
+            fn.restype = ctypes.c_int
+        L.lq_cg_workspace_bytes_multi.argtypes = [_Dims, i32, i32]
+        L.lq_cg_workspace_bytes_multi.restype = ctypes.c_size_t
+        L.lq_cg_solve_multi.argtypes = [_Dims, f64, i32, i32, _vp, _vp, _vp, ctypes.POINTER(CgParams), _vp,
+                                        ctypes.c_size_t, ctypes.POINTER(CgInfo), _vp]
+        L.lq_cg_solve_multi.restype = ctypes.c_int
         L.lq_convert_gauge.argtypes = [_Dims, i32, i32, _vp, i32, i32, i32, _vp, _vp]
         L.lq_convert_gauge.restype = ctypes.c_int
         L.lq_cg_workspace_bytes.argtypes = [_Dims, i32]
@@ -175,6 +187,27 @@ def dslash_adjoint(dims, m_q, U, psi, out=None, prec="f64", link_fmt=18, layout=
     return _apply(load().lq_dslash_adjoint, dims, m_q, U, psi, out, prec, link_fmt, layout, stream)
 
 
+def _apply_multi(fn, dims, m_q, nrhs, U, psi, out, prec, link_fmt, layout, stream):
+    sb = field_bytes(dims, "spinor", prec, link_fmt, layout) * int(nrhs)
+    gb = field_bytes(dims, "gauge", prec, link_fmt, layout)
+    if out is None:
+        out = _empty_bytes(sb, psi)
+    _check(fn(_dims(dims), float(m_q), _prec(prec), int(link_fmt), _layout(layout), int(nrhs),
+              _ptr(U, gb, "U"), _ptr(psi, sb, "psi"), _ptr(out, sb, "out"), _stream(stream)))
+    return out
+
+
+def dslash_apply_multi(dims, m_q, nrhs, U, psi, out=None, prec="f64", link_fmt=18, layout="lex", stream=None):
+    """out_r = D psi_r for nrhs fields (LEX: stacked fields; EO: interleaved per site)."""
+    return _apply_multi(load().lq_dslash_apply_multi, dims, m_q, nrhs, U, psi, out, prec, link_fmt, layout, stream)
+
+
+def dslash_adjoint_multi(dims, m_q, nrhs, U, psi, out=None, prec="f64", link_fmt=18, layout="lex", stream=None):
+    """out_r = D^dag psi_r for nrhs fields."""
+    return _apply_multi(load().lq_dslash_adjoint_multi, dims, m_q, nrhs, U, psi, out, prec, link_fmt, layout,
+                        stream)
+
+
 def dslash_hop(dims, out_parity, U, psi_other, out=None, a=0.0, b=1.0, y=None, dagger=False,
                prec="f64", link_fmt=18, stream=None):
     """out_p = a y_p + b H_{p,1-p} psi_{1-p} on EO half fields, H = the 1/2 sum_mu of Eq. (1)."""
@@ -199,6 +232,18 @@ def convert_spinor(dims, src, src_prec="f64", src_layout="lex", dst=None, dst_pr
     return dst
 
 
+def convert_spinor_multi(dims, nrhs, src, src_prec="f64", src_layout="lex", dst=None, dst_prec="f32",
+                         dst_layout="eo", stream=None):
+    sb = field_bytes(dims, "spinor", src_prec) * int(nrhs)
+    db = field_bytes(dims, "spinor", dst_prec) * int(nrhs)
+    if dst is None:
+        dst = _empty_bytes(db, src)
+    _check(load().lq_convert_spinor_multi(_dims(dims), int(nrhs), _prec(src_prec), _layout(src_layout),
+                                          _ptr(src, sb, "src"), _prec(dst_prec), _layout(dst_layout),
+                                          _ptr(dst, db, "dst"), _stream(stream)))
+    return dst
+
+
 def convert_gauge(dims, src, src_prec="f64", src_layout="lex", dst=None, dst_prec="f32", dst_fmt=12,
                   dst_layout="eo", stream=None):
     sb = field_bytes(dims, "gauge", src_prec, 18)
@@ -211,9 +256,9 @@ def convert_gauge(dims, src, src_prec="f64", src_layout="lex", dst=None, dst_pre
     return dst
 
 
-def cg_workspace_bytes(dims, mode="f64") -> int:
+def cg_workspace_bytes(dims, mode="f64", nrhs=1) -> int:
     m = CG_MODE[mode] if isinstance(mode, str) else int(mode)
-    return int(load().lq_cg_workspace_bytes(_dims(dims), m))
+    return int(load().lq_cg_workspace_bytes_multi(_dims(dims), m, int(nrhs)))
 
 
 def cg_solve(dims, m_q, U, eta, x=None, mode="f64", tol=1e-10, max_iter=100000, max_cycles=0, delta=0.0,
@@ -244,3 +289,34 @@ def cg_solve(dims, m_q, U, eta, x=None, mode="f64", tol=1e-10, max_iter=100000, 
     d["kernel_ms"] = list(d["kernel_ms"])
     d["kernel_calls"] = list(d["kernel_calls"])
     return x, d, st
+
+
+def cg_solve_multi(dims, m_q, nrhs, U, eta, x=None, mode="f64", tol=1e-10, max_iter=100000, max_cycles=0,
+                   delta=0.0, chunk=0, workspace=None, stream=None, profile=False, native_f64=False, link18=False):
+    """nrhs independent solves D^dag D x_r = eta_r sharing the links (eta, x: nrhs stacked FP64
+    LEX fields).  Returns (x, [info per right-hand side], status)."""
+    import torch
+    m = CG_MODE[mode] if isinstance(mode, str) else int(mode)
+    n = int(nrhs)
+    sb = field_bytes(dims, "spinor", "f64") * n
+    gb = field_bytes(dims, "gauge", "f64", 18)
+    if x is None:
+        x = torch.zeros_like(eta)
+    wb = cg_workspace_bytes(dims, m, n)
+    if workspace is None:
+        workspace = _empty_bytes(wb, eta)
+    flags = (CG_PROFILE if profile else 0) | (CG_NATIVE_F64 if native_f64 else 0) | (CG_LINK18 if link18 else 0)
+    prm = CgParams(float(tol), int(max_iter), int(max_cycles), float(delta), int(chunk), flags)
+    infos = (CgInfo * n)()
+    st = load().lq_cg_solve_multi(_dims(dims), float(m_q), m, n, _ptr(U, gb, "U"), _ptr(eta, sb, "eta"),
+                                  _ptr(x, sb, "x"), ctypes.byref(prm), _ptr(workspace, wb, "workspace"),
+                                  ctypes.c_size_t(workspace.numel() * workspace.element_size()), infos,
+                                  _stream(stream))
+    _check(st)
+    out = []
+    for i in range(n):
+        d = {k: getattr(infos[i], k) for k, _ in CgInfo._fields_ if k != "reserved"}
+        d["kernel_ms"] = list(d["kernel_ms"])
+        d["kernel_calls"] = list(d["kernel_calls"])
+        out.append(d)
+    return x, out, st

@@ -86,26 +86,47 @@ int check_ptr(const void* p, const char* name) {
 }
 
 int do_apply(const int32_t dims[4], double m_q, int32_t prec, int32_t fmt, int32_t layout, const void* U,
-             const void* psi, void* out, void* stream, bool dag) {
+             const void* psi, void* out, void* stream, bool dag, int32_t nrhs = 1) {
     Geom g;
     int r;
     if ((r = check_dims(dims, &g)) != LQ_OK) return r;
+    if (nrhs < 1 || (int64_t)nrhs * g.V > 100000000LL)
+        return fail(LQ_ERR_ARG, "nrhs must be >= 1 with nrhs * V <= 10^8");
+    if (layout == LQ_LAYOUT_EO && (nrhs & (nrhs - 1)) != 0)
+        return fail(LQ_ERR_ARG, "EO fields interleave a power-of-two number of right-hand sides (got %d)", (int)nrhs);
+    if (nrhs > 32 && layout == LQ_LAYOUT_EO) return fail(LQ_ERR_ARG, "at most 32 interleaved right-hand sides");
     if (!valid_prec(prec)) return fail(LQ_ERR_ARG, "bad precision %d", (int)prec);
     if (!valid_fmt(fmt)) return fail(LQ_ERR_ARG, "bad link format %d", (int)fmt);
     if (!valid_layout(layout)) return fail(LQ_ERR_ARG, "bad layout %d", (int)layout);
     if (prec == LQ_F64X && fmt != LQ_LINK18) return fail(LQ_ERR_ARG, "LQ_F64X fields use 18-real links");
     if (!isfinite(m_q)) return fail(LQ_ERR_ARG, "m_q is not finite");
     if ((r = check_ptr(U, "U")) || (r = check_ptr(psi, "psi")) || (r = check_ptr(out, "out"))) return r;
-    const size_t sb = spinor_bytes(g.V, prec), gb = gauge_bytes(g.V, prec, fmt);
+    const size_t sb = spinor_bytes((int64_t)g.V * nrhs, prec), gb = gauge_bytes(g.V, prec, fmt);
     if (overlap(out, sb, psi, sb) || overlap(out, sb, U, gb))
         return fail(LQ_ERR_ALIGN, "out overlaps psi or U");
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e;
-    if (prec == LQ_F64) e = apply_f64(g, m_q, fmt, layout, dag, U, psi, out, st);
-    else if (prec == LQ_F64X) e = apply_f64x(g, m_q, fmt, layout, dag, U, psi, out, st);
-    else if (prec == LQ_F32) e = apply_f32(g, m_q, fmt, layout, dag, U, psi, out, st);
-    else e = apply_f16(g, m_q, fmt, layout, dag, U, psi, out, st);
-    if (e != cudaSuccess) return cuda_fail(e, dag ? "dslash_adjoint launch" : "dslash_apply launch");
+    // LEX fields are stacked: any count splits into power-of-two groups of consecutive
+    // fields; EO fields are interleaved and go in one launch
+    const size_t field = spinor_bytes(g.V, prec);
+    for (int first = 0; first < nrhs;) {
+        int lnr = 0;
+        if (layout == LQ_LAYOUT_EO) {
+            while ((1 << (lnr + 1)) <= nrhs) ++lnr;
+        } else {
+            while ((1 << (lnr + 1)) <= nrhs - first && lnr < 5) ++lnr;
+        }
+        // F16S stacked fields keep each field's scales after its halves; batch them one by one
+        if (prec == LQ_F16S && layout == LQ_LAYOUT_LEX) lnr = 0;
+        const void* pin = (const char*)psi + (layout == LQ_LAYOUT_LEX ? field * first : 0);
+        void* pout = (char*)out + (layout == LQ_LAYOUT_LEX ? field * first : 0);
+        cudaError_t e;
+        if (prec == LQ_F64) e = apply_f64(g, m_q, fmt, layout, dag, U, pin, pout, st, lnr);
+        else if (prec == LQ_F64X) e = apply_f64x(g, m_q, fmt, layout, dag, U, pin, pout, st, lnr);
+        else if (prec == LQ_F32) e = apply_f32(g, m_q, fmt, layout, dag, U, pin, pout, st, lnr);
+        else e = apply_f16(g, m_q, fmt, layout, dag, U, pin, pout, st, lnr);
+        if (e != cudaSuccess) return cuda_fail(e, dag ? "dslash_adjoint launch" : "dslash_apply launch");
+        first += 1 << lnr;
+    }
     return LQ_OK;
 }
 
@@ -129,6 +150,16 @@ int lq_dslash_apply(const int32_t dims[4], double m_q, int32_t prec, int32_t lin
 int lq_dslash_adjoint(const int32_t dims[4], double m_q, int32_t prec, int32_t link_fmt, int32_t layout,
                       const void* U, const void* psi, void* out, void* cuda_stream) {
     return do_apply(dims, m_q, prec, link_fmt, layout, U, psi, out, cuda_stream, true);
+}
+
+int lq_dslash_apply_multi(const int32_t dims[4], double m_q, int32_t prec, int32_t link_fmt, int32_t layout,
+                          int32_t nrhs, const void* U, const void* psi, void* out, void* cuda_stream) {
+    return do_apply(dims, m_q, prec, link_fmt, layout, U, psi, out, cuda_stream, false, nrhs);
+}
+
+int lq_dslash_adjoint_multi(const int32_t dims[4], double m_q, int32_t prec, int32_t link_fmt, int32_t layout,
+                            int32_t nrhs, const void* U, const void* psi, void* out, void* cuda_stream) {
+    return do_apply(dims, m_q, prec, link_fmt, layout, U, psi, out, cuda_stream, true, nrhs);
 }
 
 int lq_dslash_hop(const int32_t dims[4], int32_t out_parity, int32_t dagger, double a, double b, int32_t prec,
@@ -174,6 +205,22 @@ int lq_convert_spinor(const int32_t dims[4], int32_t src_prec, int32_t src_layou
     return LQ_OK;
 }
 
+int lq_convert_spinor_multi(const int32_t dims[4], int32_t nrhs, int32_t src_prec, int32_t src_layout,
+                            const void* src, int32_t dst_prec, int32_t dst_layout, void* dst, void* cuda_stream) {
+    Geom g;
+    int r;
+    if ((r = check_dims(dims, &g)) != LQ_OK) return r;
+    if (nrhs < 1 || (int64_t)nrhs * g.V > 100000000LL) return fail(LQ_ERR_ARG, "nrhs must be >= 1 with nrhs * V <= 10^8");
+    if (!valid_prec(src_prec) || !valid_prec(dst_prec)) return fail(LQ_ERR_ARG, "bad precision");
+    if (!valid_layout(src_layout) || !valid_layout(dst_layout)) return fail(LQ_ERR_ARG, "bad layout");
+    if ((r = check_ptr(src, "src")) || (r = check_ptr(dst, "dst"))) return r;
+    const int64_t n = (int64_t)g.V * nrhs;
+    if (overlap(src, spinor_bytes(n, src_prec), dst, spinor_bytes(n, dst_prec))) return fail(LQ_ERR_ALIGN, "dst overlaps src");
+    cudaError_t e = convert_spinor(g, src_prec, src_layout, src, dst_prec, dst_layout, dst, (cudaStream_t)cuda_stream, nrhs);
+    if (e != cudaSuccess) return cuda_fail(e, "convert_spinor launch");
+    return LQ_OK;
+}
+
 int lq_convert_gauge(const int32_t dims[4], int32_t src_prec, int32_t src_layout, const void* src, int32_t dst_prec,
                      int32_t dst_fmt, int32_t dst_layout, void* dst, void* cuda_stream) {
     Geom g;
@@ -192,20 +239,23 @@ int lq_convert_gauge(const int32_t dims[4], int32_t src_prec, int32_t src_layout
     return LQ_OK;
 }
 
-size_t lq_cg_workspace_bytes(const int32_t dims[4], int32_t mode) {
+size_t lq_cg_workspace_bytes_multi(const int32_t dims[4], int32_t mode, int32_t nrhs) {
     Geom g;
-    if (check_dims(dims, &g) != LQ_OK) return 0;
+    if (check_dims(dims, &g) != LQ_OK || nrhs < 1) return 0;
     if (mode != LQ_CG_F64 && mode != LQ_CG_MIXED_F32 && mode != LQ_CG_MIXED_F16 && mode != LQ_CG_F64X) return 0;
-    return cg_workspace_bytes(g, mode);
+    return cg_workspace_bytes(g, mode, nrhs);
 }
 
-int lq_cg_solve(const int32_t dims[4], double m_q, int32_t mode, const void* U, const void* eta, void* x,
-                const lq_cg_params* params, void* workspace, size_t ws_bytes, lq_cg_info* info,
-                void* cuda_stream) {
-    if (info) memset(info, 0, sizeof(*info));
+size_t lq_cg_workspace_bytes(const int32_t dims[4], int32_t mode) { return lq_cg_workspace_bytes_multi(dims, mode, 1); }
+
+int lq_cg_solve_multi(const int32_t dims[4], double m_q, int32_t mode, int32_t nrhs, const void* U, const void* eta,
+                      void* x, const lq_cg_params* params, void* workspace, size_t ws_bytes, lq_cg_info* info,
+                      void* cuda_stream) {
+    if (info && nrhs > 0) memset(info, 0, sizeof(*info) * (size_t)nrhs);
     Geom g;
     int r;
     if ((r = check_dims(dims, &g)) != LQ_OK) return r;
+    if (nrhs < 1 || (int64_t)nrhs * g.V > 100000000LL) return fail(LQ_ERR_ARG, "nrhs must be >= 1 with nrhs * V <= 10^8");
     if (mode != LQ_CG_F64 && mode != LQ_CG_MIXED_F32 && mode != LQ_CG_MIXED_F16 && mode != LQ_CG_F64X)
         return fail(LQ_ERR_ARG, "bad CG mode %d", (int)mode);
     if (!isfinite(m_q)) return fail(LQ_ERR_ARG, "m_q is not finite");
@@ -217,12 +267,20 @@ int lq_cg_solve(const int32_t dims[4], double m_q, int32_t mode, const void* U, 
     if (!(prm.delta < 1.0) || !isfinite(prm.delta)) return fail(LQ_ERR_ARG, "delta must be < 1");
     if ((r = check_ptr(U, "U")) || (r = check_ptr(eta, "eta")) || (r = check_ptr(x, "x"))) return r;
     if ((r = check_ptr(workspace, "workspace"))) return r == LQ_ERR_ARG ? fail(LQ_ERR_WORKSPACE, "workspace is NULL") : r;
-    const size_t sb = spinor_bytes(g.V, LQ_F64), gb = gauge_bytes(g.V, LQ_F64, 18);
+    const size_t sb = spinor_bytes((int64_t)g.V * nrhs, LQ_F64), gb = gauge_bytes(g.V, LQ_F64, 18);
     if (overlap(x, sb, eta, sb) || overlap(x, sb, U, gb) || overlap(x, sb, workspace, ws_bytes))
         return fail(LQ_ERR_ALIGN, "x overlaps eta, U or the workspace");
     if (overlap(workspace, ws_bytes, eta, sb) || overlap(workspace, ws_bytes, U, gb))
         return fail(LQ_ERR_ALIGN, "workspace overlaps eta or U");
-    r = cg_solve(g, m_q, mode, U, eta, x, prm, workspace, ws_bytes, info, (cudaStream_t)cuda_stream);
+    r = cg_solve(g, m_q, mode, nrhs, U, eta, x, prm, workspace, ws_bytes, info, (cudaStream_t)cuda_stream);
+    if (info && r < 0 && info->status == 0) info->status = r;
+    return r;
+}
+
+int lq_cg_solve(const int32_t dims[4], double m_q, int32_t mode, const void* U, const void* eta, void* x,
+                const lq_cg_params* params, void* workspace, size_t ws_bytes, lq_cg_info* info,
+                void* cuda_stream) {
+    const int r = lq_cg_solve_multi(dims, m_q, mode, 1, U, eta, x, params, workspace, ws_bytes, info, cuda_stream);
     if (info) info->status = r;
     return r;
 }

@@ -26,14 +26,22 @@ struct FieldDesc {
     int prec, layout, fmt;
 };
 
-// element index of real j of a spinor site
-__device__ inline int64_t sp_elem(const FieldDesc& f, const Geom& g, const Site& s, int j) {
-    if (f.layout == LQ_LAYOUT_LEX) return (int64_t)s.lex * 24 + j;
+// element index of real j of a spinor site of right-hand side s.rhs among nr (LEX: nr
+// stacked complete fields; EO: right-hand sides interleaved per chunk slot).  A stacked
+// F16S field is 26 V halves (24 V halves, then V float scales), so field r's halves start
+// at 26 V r and its scales at float 13 V r + 12 V.
+__device__ inline int64_t sp_elem(const FieldDesc& f, const Geom& g, const Site& s, int j, int nr) {
+    if (f.layout == LQ_LAYOUT_LEX) {
+        const int64_t field = (f.prec == LQ_F16S) ? 26 * (int64_t)g.V : 24 * (int64_t)g.V;
+        return s.rhs * field + (int64_t)s.lex * 24 + j;
+    }
     const int w = spinor_chunk(f.prec), K = 24 / w;
-    return (((int64_t)s.p * K + j / w) * g.Vh + s.cb) * w + (j % w);
+    return ((((int64_t)s.p * K + j / w) * g.Vh + s.cb) * nr + s.rhs) * w + (j % w);
 }
-__device__ inline int64_t sp_scale_idx(const FieldDesc& f, const Geom& g, const Site& s) {
-    return f.layout == LQ_LAYOUT_LEX ? (int64_t)s.lex : (int64_t)s.p * g.Vh + s.cb;
+// index (in floats from the buffer start) of the scale of a site of an F16S field
+__device__ inline int64_t sp_scale_idx(const FieldDesc& f, const Geom& g, const Site& s, int nr) {
+    if (f.layout == LQ_LAYOUT_LEX) return 13 * (int64_t)g.V * s.rhs + 12 * (int64_t)g.V + s.lex;
+    return 12 * (int64_t)g.V * nr + ((int64_t)s.p * g.Vh + s.cb) * nr + s.rhs;
 }
 // element index of real j of link (s, mu)
 __device__ inline int64_t lk_elem(const FieldDesc& f, const Geom& g, const Site& s, int mu, int j) {
@@ -60,32 +68,33 @@ __device__ inline void store_wide(void* base, int prec, int64_t i, double v) {
     }
 }
 
-__global__ void __launch_bounds__(kConvBS) convert_spinor_kernel(Geom g, FieldDesc src, FieldDesc dst) {
-    const int64_t sc_off = 48 * (int64_t)g.V;   // F16S scales follow the halves
-    for (int lex = blockIdx.x * kConvBS + threadIdx.x; lex < g.V; lex += gridDim.x * kConvBS) {
+__global__ void __launch_bounds__(kConvBS) convert_spinor_kernel(Geom g, FieldDesc src, FieldDesc dst, int nr) {
+    const int64_t n = (int64_t)g.V * nr;
+    for (int64_t f = blockIdx.x * (int64_t)kConvBS + threadIdx.x; f < n; f += (int64_t)gridDim.x * kConvBS) {
         int c[4];
-        const Site s = site_from_lex(g, lex, c);
+        const Site s = site_from_lex(g, (int)(f / nr), c, (int)(f % nr));
         double v[24];
         double sc = 1.0;
-        if (src.prec == LQ_F16S) sc = (double)((const float*)((const char*)src.ptr + sc_off))[sp_scale_idx(src, g, s)];
+        if (src.prec == LQ_F16S)
+            sc = (double)((const float*)src.ptr)[sp_scale_idx(src, g, s, nr)];
 #pragma unroll
-        for (int j = 0; j < 24; ++j) v[j] = load_real(src.ptr, src.prec, sp_elem(src, g, s, j)) * sc;
+        for (int j = 0; j < 24; ++j) v[j] = load_real(src.ptr, src.prec, sp_elem(src, g, s, j, nr)) * sc;
         if (dst.prec == LQ_F64 || dst.prec == LQ_F64X) {
 #pragma unroll
-            for (int j = 0; j < 24; ++j) store_wide(dst.ptr, dst.prec, sp_elem(dst, g, s, j), v[j]);
+            for (int j = 0; j < 24; ++j) store_wide(dst.ptr, dst.prec, sp_elem(dst, g, s, j, nr), v[j]);
         } else if (dst.prec == LQ_F32) {
 #pragma unroll
-            for (int j = 0; j < 24; ++j) ((float*)dst.ptr)[sp_elem(dst, g, s, j)] = (float)v[j];
+            for (int j = 0; j < 24; ++j) ((float*)dst.ptr)[sp_elem(dst, g, s, j, nr)] = (float)v[j];
         } else {
-            float f[24];
+            float fv[24];
             float m = 0.f;
 #pragma unroll
-            for (int j = 0; j < 24; ++j) { f[j] = (float)v[j]; m = fmaxf(m, fabsf(f[j])); }
-            ((float*)((char*)dst.ptr + sc_off))[sp_scale_idx(dst, g, s)] = m;
+            for (int j = 0; j < 24; ++j) { fv[j] = (float)v[j]; m = fmaxf(m, fabsf(fv[j])); }
+            ((float*)dst.ptr)[sp_scale_idx(dst, g, s, nr)] = m;
             const bool z = !(m > 0.f);
 #pragma unroll
             for (int j = 0; j < 24; ++j)
-                ((__half*)dst.ptr)[sp_elem(dst, g, s, j)] = __float2half_rn(z ? 0.f : __fdiv_rn(f[j], m));
+                ((__half*)dst.ptr)[sp_elem(dst, g, s, j, nr)] = __float2half_rn(z ? 0.f : __fdiv_rn(fv[j], m));
         }
     }
 }
@@ -106,20 +115,21 @@ __global__ void __launch_bounds__(kConvBS) convert_gauge_kernel(Geom g, FieldDes
     }
 }
 
-int conv_grid(const Geom& g) {
+int conv_grid(const Geom& g, int nr = 1) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    long long want = ((long long)g.V + kConvBS - 1) / kConvBS;
+    long long want = ((long long)g.V * nr + kConvBS - 1) / kConvBS;
     long long cap = (long long)sms * 8;
     return (int)(want < cap ? (want > 0 ? want : 1) : cap);
 }
 
 }  // namespace
 
-cudaError_t convert_spinor(const Geom& g, int sp, int sl, const void* src, int dp, int dl, void* dst, cudaStream_t st) {
-    convert_spinor_kernel<<<conv_grid(g), kConvBS, 0, st>>>(g, FieldDesc{(void*)src, sp, sl, 0},
-                                                            FieldDesc{dst, dp, dl, 0});
+cudaError_t convert_spinor(const Geom& g, int sp, int sl, const void* src, int dp, int dl, void* dst, cudaStream_t st,
+                           int nr) {
+    convert_spinor_kernel<<<conv_grid(g, nr), kConvBS, 0, st>>>(g, FieldDesc{(void*)src, sp, sl, 0},
+                                                                FieldDesc{dst, dp, dl, 0}, nr);
     return cudaGetLastError();
 }
 

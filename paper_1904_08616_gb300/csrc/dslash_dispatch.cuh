@@ -10,12 +10,14 @@ namespace lq {
 
 constexpr int kApplyBS = 128;
 
-// Spinor accessor over a caller buffer holding nsites sites (V: full field, Vh: half).
+// Spinor accessor over a caller buffer holding nr fields of nsites sites each (V: full
+// fields, Vh: half fields), in the layout's multi-field order.
 template <int PREC, int LAYOUT, bool RO>
-inline SpinorAcc<PREC, LAYOUT, RO> make_spinor(const void* buf, const Geom& g, bool half) {
+inline SpinorAcc<PREC, LAYOUT, RO> make_spinor(const void* buf, const Geom& g, bool half, int nr = 1) {
     SpinorAcc<PREC, LAYOUT, RO> a;
-    const int64_t nsites = half ? g.Vh : g.V;
-    a.e = (LAYOUT == LQ_LAYOUT_LEX) ? eo_none() : (half ? eo_half(g) : eo_full(g, SpinorAcc<PREC, LAYOUT, RO>::K));
+    const int64_t nsites = (int64_t)(half ? g.Vh : g.V) * nr;
+    a.e = (LAYOUT == LQ_LAYOUT_LEX) ? lex_idx(g, nr)
+                                    : (half ? eo_half(g, nr) : eo_full(g, SpinorAcc<PREC, LAYOUT, RO>::K, nr));
     if constexpr (PREC == LQ_F64) {
         a.ptr = (double2*)buf;
     } else if constexpr (PREC == LQ_F32 || PREC == LQ_F64X) {
@@ -35,23 +37,26 @@ inline GaugeAcc<PREC, FMT, LAYOUT> make_gauge(const void* buf, const Geom& g) {
     return a;
 }
 
-// out = D psi (DAG = false) or D^dag psi on the whole lattice
+// out = D psi (DAG = false) or D^dag psi on the whole lattice, for 2^lnr fields at once
+// (LEX: stacked fields; EO: right-hand sides interleaved per site)
 template <int PREC, int FMT, int LAYOUT, bool DAG>
-cudaError_t run_apply(const Geom& g, double m_q, const void* U, const void* psi, void* out, cudaStream_t st) {
+cudaError_t run_apply(const Geom& g, double m_q, const void* U, const void* psi, void* out, cudaStream_t st,
+                      int lnr = 0) {
     using InA = SpinorAcc<PREC, LAYOUT, true>;
     using OutA = SpinorAcc<PREC, LAYOUT, false>;
     using GA = GaugeAcc<PREC, FMT, LAYOUT>;
     using Real = typename GA::Real;
-    Stencil<GA, InA, DAG> sten{g, make_gauge<PREC, FMT, LAYOUT>(U, g), make_spinor<PREC, LAYOUT, true>(psi, g, false)};
+    const int nr = 1 << lnr;
+    Stencil<GA, InA, DAG> sten{g, make_gauge<PREC, FMT, LAYOUT>(U, g), make_spinor<PREC, LAYOUT, true>(psi, g, false, nr)};
     EpiAxpby<OutA, InA, true, false> epi;
-    epi.out = make_spinor<PREC, LAYOUT, false>(out, g, false);
+    epi.out = make_spinor<PREC, LAYOUT, false>(out, g, false, nr);
     epi.y = sten.sa;
     epi.a = from_double<Real>(m_q + 4.0);
     epi.b = from_double<Real>(0.5);
     epi.rc = RedCtx{nullptr, nullptr};
     epi.slot = 0;
-    if constexpr (LAYOUT == LQ_LAYOUT_LEX) return launch_stencil<kApplyBS>(MapLex<kApplyBS>{g}, sten, epi, st);
-    else return launch_stencil<kApplyBS>(MapEoFull<kApplyBS>{g}, sten, epi, st);
+    if constexpr (LAYOUT == LQ_LAYOUT_LEX) return launch_stencil<kApplyBS>(MapLex<kApplyBS>{g, lnr}, sten, epi, st);
+    else return launch_stencil<kApplyBS>(MapEoFull<kApplyBS>{g, lnr}, sten, epi, st);
 }
 
 // out_p = a y_p + b H_{p,1-p} psi_{1-p}  (EO half fields)
@@ -74,14 +79,15 @@ cudaError_t run_hop(const Geom& g, int p, double a, double b, const void* U, con
     return launch_stencil<kApplyBS>(MapEoHalf<kApplyBS>{g, p}, sten, epi, st);
 }
 
-// Dispatch entry points, one set per precision (defined in dslash_f64/f32/f16.cu).
-cudaError_t apply_f64(const Geom& g, double m_q, int fmt, int layout, bool dag, const void* U, const void* psi, void* out, cudaStream_t st);
-cudaError_t apply_f32(const Geom& g, double m_q, int fmt, int layout, bool dag, const void* U, const void* psi, void* out, cudaStream_t st);
-cudaError_t apply_f16(const Geom& g, double m_q, int fmt, int layout, bool dag, const void* U, const void* psi, void* out, cudaStream_t st);
+// Dispatch entry points, one set per precision (defined in dslash_f64/f32/f16/f64x.cu);
+// the applies act on 2^lnr fields.
+cudaError_t apply_f64(const Geom& g, double m_q, int fmt, int layout, bool dag, const void* U, const void* psi, void* out, cudaStream_t st, int lnr);
+cudaError_t apply_f32(const Geom& g, double m_q, int fmt, int layout, bool dag, const void* U, const void* psi, void* out, cudaStream_t st, int lnr);
+cudaError_t apply_f16(const Geom& g, double m_q, int fmt, int layout, bool dag, const void* U, const void* psi, void* out, cudaStream_t st, int lnr);
 cudaError_t hop_f64(const Geom& g, int p, bool dag, double a, double b, int fmt, const void* U, const void* psi_other, const void* y, void* out, cudaStream_t st);
 cudaError_t hop_f32(const Geom& g, int p, bool dag, double a, double b, int fmt, const void* U, const void* psi_other, const void* y, void* out, cudaStream_t st);
 cudaError_t hop_f16(const Geom& g, int p, bool dag, double a, double b, int fmt, const void* U, const void* psi_other, const void* y, void* out, cudaStream_t st);
-cudaError_t apply_f64x(const Geom& g, double m_q, int fmt, int layout, bool dag, const void* U, const void* psi, void* out, cudaStream_t st);
+cudaError_t apply_f64x(const Geom& g, double m_q, int fmt, int layout, bool dag, const void* U, const void* psi, void* out, cudaStream_t st, int lnr);
 cudaError_t hop_f64x(const Geom& g, int p, bool dag, double a, double b, int fmt, const void* U, const void* psi_other, const void* y, void* out, cudaStream_t st);
 
 }  // namespace lq
@@ -90,18 +96,18 @@ cudaError_t hop_f64x(const Geom& g, int p, bool dag, double a, double b, int fmt
 #define LQ_DEFINE_PREC_DISPATCH(NAME, PREC)                                                            \
     namespace lq {                                                                                   \
     cudaError_t apply_##NAME(const Geom& g, double m_q, int fmt, int layout, bool dag, const void* U, \
-                             const void* psi, void* out, cudaStream_t st) {                           \
+                             const void* psi, void* out, cudaStream_t st, int lnr) {                  \
         const bool lex = layout == LQ_LAYOUT_LEX;                                                     \
         if (fmt == 18) {                                                                              \
-            if (lex) return dag ? run_apply<PREC, 18, LQ_LAYOUT_LEX, true>(g, m_q, U, psi, out, st)   \
-                                : run_apply<PREC, 18, LQ_LAYOUT_LEX, false>(g, m_q, U, psi, out, st); \
-            return dag ? run_apply<PREC, 18, LQ_LAYOUT_EO, true>(g, m_q, U, psi, out, st)             \
-                       : run_apply<PREC, 18, LQ_LAYOUT_EO, false>(g, m_q, U, psi, out, st);           \
+            if (lex) return dag ? run_apply<PREC, 18, LQ_LAYOUT_LEX, true>(g, m_q, U, psi, out, st, lnr)   \
+                                : run_apply<PREC, 18, LQ_LAYOUT_LEX, false>(g, m_q, U, psi, out, st, lnr); \
+            return dag ? run_apply<PREC, 18, LQ_LAYOUT_EO, true>(g, m_q, U, psi, out, st, lnr)             \
+                       : run_apply<PREC, 18, LQ_LAYOUT_EO, false>(g, m_q, U, psi, out, st, lnr);           \
         }                                                                                             \
-        if (lex) return dag ? run_apply<PREC, 12, LQ_LAYOUT_LEX, true>(g, m_q, U, psi, out, st)       \
-                            : run_apply<PREC, 12, LQ_LAYOUT_LEX, false>(g, m_q, U, psi, out, st);     \
-        return dag ? run_apply<PREC, 12, LQ_LAYOUT_EO, true>(g, m_q, U, psi, out, st)                 \
-                   : run_apply<PREC, 12, LQ_LAYOUT_EO, false>(g, m_q, U, psi, out, st);               \
+        if (lex) return dag ? run_apply<PREC, 12, LQ_LAYOUT_LEX, true>(g, m_q, U, psi, out, st, lnr)       \
+                            : run_apply<PREC, 12, LQ_LAYOUT_LEX, false>(g, m_q, U, psi, out, st, lnr);     \
+        return dag ? run_apply<PREC, 12, LQ_LAYOUT_EO, true>(g, m_q, U, psi, out, st, lnr)                 \
+                   : run_apply<PREC, 12, LQ_LAYOUT_EO, false>(g, m_q, U, psi, out, st, lnr);               \
     }                                                                                                 \
     cudaError_t hop_##NAME(const Geom& g, int p, bool dag, double a, double b, int fmt, const void* U, \
                            const void* psi_other, const void* y, void* out, cudaStream_t st) {        \

@@ -5,13 +5,13 @@
 namespace lq {
 
 cudaError_t apply_f64x(const Geom& g, double m_q, int fmt, int layout, bool dag, const void* U, const void* psi,
-                       void* out, cudaStream_t st) {
+                       void* out, cudaStream_t st, int lnr) {
     if (fmt != 18) return cudaErrorInvalidValue;
     if (layout == LQ_LAYOUT_LEX)
-        return dag ? run_apply<LQ_F64X, 18, LQ_LAYOUT_LEX, true>(g, m_q, U, psi, out, st)
-                   : run_apply<LQ_F64X, 18, LQ_LAYOUT_LEX, false>(g, m_q, U, psi, out, st);
-    return dag ? run_apply<LQ_F64X, 18, LQ_LAYOUT_EO, true>(g, m_q, U, psi, out, st)
-               : run_apply<LQ_F64X, 18, LQ_LAYOUT_EO, false>(g, m_q, U, psi, out, st);
+        return dag ? run_apply<LQ_F64X, 18, LQ_LAYOUT_LEX, true>(g, m_q, U, psi, out, st, lnr)
+                   : run_apply<LQ_F64X, 18, LQ_LAYOUT_LEX, false>(g, m_q, U, psi, out, st, lnr);
+    return dag ? run_apply<LQ_F64X, 18, LQ_LAYOUT_EO, true>(g, m_q, U, psi, out, st, lnr)
+               : run_apply<LQ_F64X, 18, LQ_LAYOUT_EO, false>(g, m_q, U, psi, out, st, lnr);
 }
 
 cudaError_t hop_f64x(const Geom& g, int p, bool dag, double a, double b, int fmt, const void* U,

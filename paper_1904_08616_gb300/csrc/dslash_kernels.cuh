@@ -178,8 +178,8 @@ struct Stencil {
     template <int MU>
     LQ_HD void dir(const Site& s, const int c[4], Spinor<Real>& acc) const {
         constexpr int SF = DAG ? +1 : -1;
-        const Site nf = nb_site(lex_fwd(g, s.lex, c, MU), s.p);
-        const Site nb = nb_site(lex_bwd(g, s.lex, c, MU), s.p);
+        const Site nf = nb_site(lex_fwd(g, s.lex, c, MU), s.p, s.rhs);
+        const Site nb = nb_site(lex_bwd(g, s.lex, c, MU), s.p, s.rhs);
         constexpr bool SC = SA::kScaled;
         Spinor<Real> q;
         Link<Real> U;
@@ -207,7 +207,7 @@ struct Stencil {
                 int ln;
                 if (!back) ln = (cm == L - 1) ? s.lex - (L - 1) * St : s.lex + St;
                 else ln = (cm == 0) ? s.lex + (L - 1) * St : s.lex - St;
-                const Site nb = nb_site(ln, s.p);
+                const Site nb = nb_site(ln, s.p, s.rhs);
                 Spinor<Real> q;
                 Link<Real> U;
                 Real sc;
@@ -229,24 +229,29 @@ struct Stencil {
 // ------------------------------------------------------------------------------------
 // Site maps: tile -> sites.  A tile is one block's worth of consecutive sites.
 // ------------------------------------------------------------------------------------
+// With nr right-hand sides a map covers (site, rhs) pairs, rhs fastest: the nr threads of
+// one site are adjacent, so their link loads coincide.  nr is a power of two (lnr = log2)
+// dividing BS, so a thread keeps the same rhs = threadIdx.x mod nr in every tile.
 template <int BS> struct MapLex {            // all V sites, lexicographic
     Geom g;
-    __host__ __device__ int ntiles() const { return (g.V + BS - 1) / BS; }
+    int lnr = 0;
+    __host__ __device__ int ntiles() const { return (int)(((int64_t)g.V << lnr) + BS - 1) / BS; }
     __device__ __forceinline__ bool site(int tile, Site& s, int c[4]) const {
-        const int lex = tile * BS + (int)threadIdx.x;
-        if (lex >= g.V) return false;
-        s = site_from_lex(g, lex, c);
+        const int f = tile * BS + (int)threadIdx.x;
+        if (f >= (g.V << lnr)) return false;
+        s = site_from_lex(g, f >> lnr, c, f & ((1 << lnr) - 1));
         return true;
     }
 };
 
 template <int BS> struct MapEoFull {         // all V sites; tiles alternate parity over the same cb range
     Geom g;
-    __host__ __device__ int ntiles() const { return 2 * ((g.Vh + BS - 1) / BS); }
+    int lnr = 0;
+    __host__ __device__ int ntiles() const { return 2 * (int)((((int64_t)g.Vh << lnr) + BS - 1) / BS); }
     __device__ __forceinline__ bool site(int tile, Site& s, int c[4]) const {
-        const int cb = (tile >> 1) * BS + (int)threadIdx.x;
-        if (cb >= g.Vh) return false;
-        s = site_from_eo(g, tile & 1, cb, c);
+        const int f = (tile >> 1) * BS + (int)threadIdx.x;
+        if (f >= (g.Vh << lnr)) return false;
+        s = site_from_eo(g, tile & 1, f >> lnr, c, f & ((1 << lnr) - 1));
         return true;
     }
 };
@@ -254,11 +259,12 @@ template <int BS> struct MapEoFull {         // all V sites; tiles alternate par
 template <int BS> struct MapEoHalf {         // the Vh sites of one parity
     Geom g;
     int p;
-    __host__ __device__ int ntiles() const { return (g.Vh + BS - 1) / BS; }
+    int lnr = 0;
+    __host__ __device__ int ntiles() const { return (int)((((int64_t)g.Vh << lnr) + BS - 1) / BS); }
     __device__ __forceinline__ bool site(int tile, Site& s, int c[4]) const {
-        const int cb = tile * BS + (int)threadIdx.x;
-        if (cb >= g.Vh) return false;
-        s = site_from_eo(g, p, cb, c);
+        const int f = tile * BS + (int)threadIdx.x;
+        if (f >= (g.Vh << lnr)) return false;
+        s = site_from_eo(g, p, f >> lnr, c, f & ((1 << lnr) - 1));
         return true;
     }
 };
@@ -283,8 +289,9 @@ LQ_HD dd norm2(const Spinor<dd>& a) {
 
 // ------------------------------------------------------------------------------------
 // Epilogues.  init() runs once per thread before the site loop and returns false to skip
-// the whole kernel (uniformly); apply() consumes the hopping sum of one site; finish()
-// performs the grid reduction (if NRED > 0).
+// the whole kernel (uniformly); active() says whether this thread's right-hand side has
+// work (its sites are skipped otherwise, but the thread still joins the reduction);
+// apply() consumes the hopping sum of one site; finish() performs the grid reduction.
 // ------------------------------------------------------------------------------------
 
 // out = a * y(n) + b * hop(n)        (y = the centre input for the full operator)
@@ -299,6 +306,7 @@ struct EpiAxpby {
     RedCtx rc;
     int slot;
     LQ_HD bool init() { return true; }
+    LQ_HD bool active() const { return true; }
     template <typename R>
     LQ_HD void apply(const Site& s, const Spinor<R>& acc, double* red) const {
         Spinor<R> o;
@@ -320,7 +328,7 @@ struct EpiAxpby {
             const double v[1] = {red[0]};
             SolverState* st = rc.st;
             const int sl = slot;
-            grid_reduce<BS, 1>(rc, kTicketMisc, v, [st, sl](const double* t) { st->red[sl] = t[0]; });
+            grid_reduce<BS, 1>(rc, kTicketMisc, v, [st, sl](const double* t) { st->red[sl][0] = t[0]; });
         }
     }
 };
@@ -345,7 +353,7 @@ __device__ __forceinline__ void stencil_body(const Map& map, const Sten& sten, E
     double red[NR];
 #pragma unroll
     for (int j = 0; j < NR; ++j) red[j] = 0.0;
-    const int nt = map.ntiles();
+    const int nt = epi.active() ? map.ntiles() : 0;
     for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
         Site s;
         int c[4];
@@ -405,8 +413,10 @@ inline cudaError_t launch_stencil(const Map& map, const Sten& sten, const Epi& e
 }
 
 // EoIdx for a full EO field of K chunks per site, and for a half field of one parity.
-inline EoIdx eo_full(const Geom& g, int K) { return EoIdx{(uint32_t)g.Vh, (uint32_t)K * (uint32_t)g.Vh, (uint32_t)g.Vh}; }
-inline EoIdx eo_half(const Geom& g) { return EoIdx{(uint32_t)g.Vh, 0u, 0u}; }
-inline EoIdx eo_none() { return EoIdx{0, 0, 0}; }
+inline EoIdx eo_full(const Geom& g, int K, int nr = 1) {
+    return EoIdx{(uint32_t)g.Vh, (uint32_t)K * (uint32_t)g.Vh, (uint32_t)g.Vh, (uint32_t)nr, (uint32_t)g.V};
+}
+inline EoIdx eo_half(const Geom& g, int nr = 1) { return EoIdx{(uint32_t)g.Vh, 0u, 0u, (uint32_t)nr, (uint32_t)g.V}; }
+inline EoIdx lex_idx(const Geom& g, int nr = 1) { return EoIdx{0u, 0u, 0u, (uint32_t)nr, (uint32_t)g.V}; }
 
 }  // namespace lq

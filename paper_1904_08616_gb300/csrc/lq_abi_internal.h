@@ -20,12 +20,13 @@ int cuda_fail(cudaError_t e, const char* what);
 size_t spinor_bytes(int64_t nsites, int prec);
 size_t gauge_bytes(int64_t V, int prec, int fmt);
 
-cudaError_t convert_spinor(const Geom& g, int sp, int sl, const void* src, int dp, int dl, void* dst, cudaStream_t st);
+cudaError_t convert_spinor(const Geom& g, int sp, int sl, const void* src, int dp, int dl, void* dst, cudaStream_t st,
+                           int nr = 1);
 cudaError_t convert_gauge(const Geom& g, int sp, int sl, const void* src, int dp, int dfmt, int dl, void* dst,
                           cudaStream_t st);
 
-size_t cg_workspace_bytes(const Geom& g, int mode);
-int cg_solve(const Geom& g, double m_q, int mode, const void* U, const void* eta, void* x, const lq_cg_params& prm,
-             void* ws, size_t ws_bytes, lq_cg_info* info, cudaStream_t st);
+size_t cg_workspace_bytes(const Geom& g, int mode, int nrhs);
+int cg_solve(const Geom& g, double m_q, int mode, int nrhs, const void* U, const void* eta, void* x,
+             const lq_cg_params& prm, void* ws, size_t ws_bytes, lq_cg_info* info, cudaStream_t st);
 
 }  // namespace lq

@@ -119,8 +119,9 @@ inline Geom make_geom(const int32_t d[4]) {
     return g;
 }
 
-// A site seen from every layout: lexicographic index, parity and checkerboard index.
-struct Site { int lex, p, cb; };
+// A site seen from every layout: lexicographic index, parity and checkerboard index, and
+// the right-hand side it is processed for (0 for single-field operations).
+struct Site { int lex, p, cb, rhs; };
 
 LQ_HD void coords_from_lex(const Geom& g, int lex, int c[4]) {
     const uint32_t r0 = (uint32_t)lex;
@@ -133,13 +134,13 @@ LQ_HD void coords_from_lex(const Geom& g, int lex, int c[4]) {
     c[3] = (int)r3;
 }
 
-LQ_HD Site site_from_lex(const Geom& g, int lex, int c[4]) {
+LQ_HD Site site_from_lex(const Geom& g, int lex, int c[4], int rhs = 0) {
     coords_from_lex(g, lex, c);
-    return Site{lex, (c[0] + c[1] + c[2] + c[3]) & 1, lex >> 1};
+    return Site{lex, (c[0] + c[1] + c[2] + c[3]) & 1, lex >> 1, rhs};
 }
 
 // (p, cb) -> coordinates: cb = x/2 + (Lx/2)*(y + Ly*(z + Lz*t)), x's low bit fixed by p.
-LQ_HD Site site_from_eo(const Geom& g, int p, int cb, int c[4]) {
+LQ_HD Site site_from_eo(const Geom& g, int p, int cb, int c[4], int rhs = 0) {
     const uint32_t r0 = (uint32_t)cb;
     const uint32_t r1 = fdiv(r0, g.fLxh);
     const uint32_t r2 = fdiv(r1, g.fLy);
@@ -150,7 +151,7 @@ LQ_HD Site site_from_eo(const Geom& g, int p, int cb, int c[4]) {
     c[3] = (int)r3;
     c[0] = 2 * xh + ((p + c[1] + c[2] + c[3]) & 1);
     const int lex = 2 * cb + (c[0] & 1);
-    return Site{lex, p, cb};
+    return Site{lex, p, cb, rhs};
 }
 
 // lexicographic index of n + mu (fwd) and n - mu (bwd), periodic
@@ -160,7 +161,7 @@ LQ_HD int lex_fwd(const Geom& g, int lex, const int c[4], int mu) {
 LQ_HD int lex_bwd(const Geom& g, int lex, const int c[4], int mu) {
     return (c[mu] == 0) ? lex + (g.L[mu] - 1) * g.S[mu] : lex - g.S[mu];
 }
-LQ_HD Site nb_site(int lexn, int p) { return Site{lexn, p ^ 1, lexn >> 1}; }
+LQ_HD Site nb_site(int lexn, int p, int rhs) { return Site{lexn, p ^ 1, lexn >> 1, rhs}; }
 
 // ------------------------------------------------------------------------------------
 // load helpers (read-only path for fields that are constant during a kernel)
@@ -193,31 +194,36 @@ LQ_HD uint32_t f22h2(float a, float b) {
 }
 
 // ------------------------------------------------------------------------------------
-// Spinor field accessors.
-//   LEX: chunk k of site n at slot n*K + k.
-//   EO : chunk k of (p, cb) at slot p*pstride + k*Vh + cb (pstride = K*Vh for a full
-//        field, 0 for a half field holding one parity).
-// F16S scales: LEX at n, EO at p*sstride + cb (sstride = Vh full, 0 half).
+// Spinor field accessors, for nr right-hand sides (nr = 1 for a single field).
+//   LEX: nr consecutive fields; chunk k of site n of field r at slot (r*V + n)*K + k.
+//   EO : chunk k of (p, cb, r) at slot ((p*K + k)*Vh + cb)*nr + r, i.e. base
+//        (p*pstride + cb)*nr + r and stride Vh*nr per chunk (pstride = K*Vh for a full
+//        field, 0 for a half field holding one parity); the right-hand sides of a site
+//        sit next to each other, so the threads of one site read contiguous memory.
+// F16S scales: LEX at r*V + n, EO at (p*sstride + cb)*nr + r (sstride = Vh full, 0 half).
 // ------------------------------------------------------------------------------------
 template <int PREC, int LAYOUT, bool RO> struct SpinorAcc;
 
-// Slot indices are 32-bit: the ABI caps V at 10^8 sites, so every slot index of every
-// field format (at most 36 V for FP64 18-real LEX links) stays below 2^32.
+// Slot indices are 32-bit: the ABI caps V at 10^8 sites and V * nrhs at 10^8 site-fields
+// per call, so every slot index of every field format (at most 36 V for FP64 18-real LEX
+// links, 12 V nrhs for FP64 spinors) stays below 2^32.
 struct EoIdx {
     uint32_t Vh, pstride, sstride;
+    uint32_t nr;    // right-hand sides interleaved per site (EO) or stacked fields (LEX)
+    uint32_t V;     // sites per field (LEX stacking)
 };
 
 template <int LAYOUT> LQ_HD uint32_t sp_base(const Site& s, int K, const EoIdx& e) {
-    if constexpr (LAYOUT == LQ_LAYOUT_LEX) return (uint32_t)s.lex * (uint32_t)K;
-    else return (uint32_t)s.p * e.pstride + (uint32_t)s.cb;
+    if constexpr (LAYOUT == LQ_LAYOUT_LEX) return ((uint32_t)s.rhs * e.V + (uint32_t)s.lex) * (uint32_t)K;
+    else return ((uint32_t)s.p * e.pstride + (uint32_t)s.cb) * e.nr + (uint32_t)s.rhs;
 }
 template <int LAYOUT> LQ_HD uint32_t sp_kstride(const EoIdx& e) {
     if constexpr (LAYOUT == LQ_LAYOUT_LEX) return 1u;
-    else return e.Vh;
+    else return e.Vh * e.nr;
 }
 template <int LAYOUT> LQ_HD uint32_t sp_sidx(const Site& s, const EoIdx& e) {
-    if constexpr (LAYOUT == LQ_LAYOUT_LEX) return (uint32_t)s.lex;
-    else return (uint32_t)s.p * e.sstride + (uint32_t)s.cb;
+    if constexpr (LAYOUT == LQ_LAYOUT_LEX) return (uint32_t)s.rhs * e.V + (uint32_t)s.lex;
+    else return ((uint32_t)s.p * e.sstride + (uint32_t)s.cb) * e.nr + (uint32_t)s.rhs;
 }
 
 template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F64, LAYOUT, RO> {
@@ -495,28 +501,35 @@ template <int FMT, int LAYOUT> struct GaugeAcc<LQ_F64X, FMT, LAYOUT> {
 };
 
 // ------------------------------------------------------------------------------------
-// Solver state in device memory (part of the caller's workspace).  Written only by the
-// last block of a reducing kernel (the "finisher"), read by later kernels.
+// Solver state in device memory (part of the caller's workspace), one slot per
+// right-hand side of a batch.  Written only by the last block of a reducing kernel (the
+// "finisher"), read by later kernels.
 // ------------------------------------------------------------------------------------
+constexpr int kMaxRhs = 8;         // right-hand sides per solver batch (a power of two)
+
 struct SolverState {
-    double rho;         // ||r||^2 of the inner iterate, in the cycle's units
-    double alpha, beta;
-    double sigma;       // <p, D^dag D p> = ||D p||^2 of the last iteration
-    double stop_rho;    // inner loop stops when rho <= stop_rho
-    double red[4];      // results of standalone reductions
-    int iter;           // inner iterations in the current cycle
-    int k_max;          // inner iteration cap for the current cycle
-    int stop;           // 0 running; 1 criterion met / cap; 2 breakdown; 3 non-finite
-    int p_iter;         // iteration whose search-direction update has been written
+    double rho[kMaxRhs];        // ||r||^2 of the inner iterate, in the cycle's units
+    double alpha[kMaxRhs], beta[kMaxRhs];
+    double sigma[kMaxRhs];      // <p, D^dag D p> = ||D p||^2 of the last iteration
+    double stop_rho[kMaxRhs];   // inner loop stops when rho <= stop_rho
+    double red[4][kMaxRhs];     // results of standalone reductions
+    int iter[kMaxRhs];          // inner iterations in the current cycle
+    int stop[kMaxRhs];          // 0 running; 1 criterion met / cap / idle; 2 breakdown; 3 non-finite
+    int p_iter[kMaxRhs];        // iteration whose search-direction update has been written
+    int k_max;                  // inner iteration cap for the current cycle
+    int nr;                     // right-hand sides in the batch
+    int all_stop;               // every right-hand side has stop != 0
+    int pad;
     unsigned int ticket[4];
 };
 
-constexpr int kMaxPartials = 4096;     // per-block partial sums (x 2 for complex dots)
+constexpr int kMaxPartials = 4096;     // blocks per reducing kernel
+constexpr int kMaxRedValues = 3;       // values reduced per thread
 constexpr int kTicketK1 = 0, kTicketK2 = 1, kTicketK3 = 2, kTicketMisc = 3;
 
 struct RedCtx {
     SolverState* st;
-    double* partials;   // at least 2 * gridDim.x doubles
+    double* partials;   // kMaxRedValues * kMaxRhs * kMaxPartials doubles
 };
 
 // Sum of v over the block (deterministic tree); result valid in thread 0.
@@ -535,41 +548,66 @@ template <int BS> __device__ __forceinline__ double block_sum(double v, double* 
     return t;
 }
 
-// Grid-wide deterministic reduction of NV values per thread.  Every block stores its
-// partials; the block that arrives last sums them in block order and calls fin(total)
-// from thread 0.  Returns nothing; no block waits for another.
+// Grid-wide deterministic reduction of NV values per thread, segmented by right-hand side:
+// thread t contributes to segment t mod nr (nr a power of two, nr <= 8).  Every block
+// stores its per-segment partial sums; the block that arrives last sums them in block
+// order and calls fin(tot) from thread 0 with tot[j * kMaxRhs + r] = the total of value j
+// over segment r.  No block waits for another.
 template <int BS, int NV, class Fin>
-__device__ __forceinline__ void grid_reduce(const RedCtx& rc, int ticket_id, const double (&v)[NV], Fin fin) {
-    __shared__ double sh[BS / 32];
+__device__ __forceinline__ void grid_reduce_seg(const RedCtx& rc, int ticket_id, const double (&v)[NV], int nr,
+                                                Fin fin) {
+    __shared__ double shw[NV][BS / 32][kMaxRhs];
+    __shared__ double shb[BS / 32];
+    __shared__ double tot[NV * kMaxRhs];
     __shared__ bool last;
-    double tot[NV];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int j = 0; j < NV; ++j) {
-        tot[j] = block_sum<BS>(v[j], sh);
-        __syncthreads();
+        double x = v[j];
+        for (int o = 16; o >= nr; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane < nr) shw[j][w][lane] = x;
     }
-    if (threadIdx.x == 0) {
+    __syncthreads();
+    if ((int)threadIdx.x < NV * nr) {
+        const int j = threadIdx.x / nr, r = threadIdx.x % nr;
+        double t = 0.0;
 #pragma unroll
-        for (int j = 0; j < NV; ++j) rc.partials[(size_t)j * gridDim.x + blockIdx.x] = tot[j];
+        for (int i = 0; i < BS / 32; ++i) t += shw[j][i][r];
+        rc.partials[(size_t)(j * kMaxRhs + r) * gridDim.x + blockIdx.x] = t;
         __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
         const unsigned int t = atomicAdd(&rc.st->ticket[ticket_id], 1u);
         last = (t == gridDim.x - 1);
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
-    double fin_v[NV];
-#pragma unroll
-    for (int j = 0; j < NV; ++j) {
-        double s = 0.0;
-        for (int i = threadIdx.x; i < (int)gridDim.x; i += BS) s += __ldcg(rc.partials + (size_t)j * gridDim.x + i);
-        fin_v[j] = block_sum<BS>(s, sh);
+    for (int q = 0; q < NV * nr; ++q) {
+        const int j = q / nr, r = q % nr;
+        double x = 0.0;
+        for (int i = threadIdx.x; i < (int)gridDim.x; i += BS)
+            x += __ldcg(rc.partials + (size_t)(j * kMaxRhs + r) * gridDim.x + i);
+        x = block_sum<BS>(x, shb);
+        if (threadIdx.x == 0) tot[j * kMaxRhs + r] = x;
         __syncthreads();
     }
     if (threadIdx.x == 0) {
         rc.st->ticket[ticket_id] = 0u;
-        fin(fin_v);
+        fin(tot);
     }
+}
+
+// The unsegmented case (one field): tot[j] is the total of value j.
+template <int BS, int NV, class Fin>
+__device__ __forceinline__ void grid_reduce(const RedCtx& rc, int ticket_id, const double (&v)[NV], Fin fin) {
+    grid_reduce_seg<BS, NV>(rc, ticket_id, v, 1, [&](const double* t) {
+        double u[NV];
+#pragma unroll
+        for (int j = 0; j < NV; ++j) u[j] = t[j * kMaxRhs];
+        fin(u);
+    });
 }
 
 }  // namespace lq

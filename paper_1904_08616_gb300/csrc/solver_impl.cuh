@@ -1,15 +1,18 @@
-// Conjugate gradient on A = D^dag D (arXiv 1904.08616, Algorithm 1).
+// Conjugate gradient on A = D^dag D (arXiv 1904.08616, Algorithm 1), for a batch of up to
+// kMaxRhs right-hand sides solved as independent CGs that share every link load.
 //
-// One driver serves all three modes.  The outer loop is Algorithm 1's: FP64 solution
-// psi^high (the caller's x), FP64 residual r^high = eta - A psi^high recomputed with the
-// FP64 operator (lines 2 and 23), s = ||r^high||, and an inner CG (lines 13-20) on the
+// One driver serves all modes.  The outer loop is Algorithm 1's: FP64-class solution
+// psi^high, FP64-class residual r^high = eta - A psi^high recomputed with the FP64-class
+// operator (lines 2 and 23), s = ||r^high||, and an inner CG (lines 13-20) on the
 // unit-norm residual r_0 = r^high / s in the inner precision.  The inner loop uses
 // three fused kernels per iteration:
 //   K1  t = D p                       + ||t||^2 = <p, A p>  -> alpha = rho / <p, A p>
 //   K2  q = D^dag t (in registers); psi += alpha p; r -= alpha q  + ||r||^2 -> beta, stop
 //   K3  p = r + beta p
-// Scalars live in a device-side state record written by the last block of each
-// reducing kernel; the host only reads that record between chunks of iterations.
+// Scalars live in a device-side state record (one slot per right-hand side) written by
+// the last block of each reducing kernel; the host only reads that record between
+// chunks of iterations.  A right-hand side whose inner loop has stopped is skipped by
+// the kernels while the others go on; the cycles (reliable updates) are taken together.
 //
 // Readings of Algorithm 1 (the text has index garbles):
 //   * at the start of cycle l, r_0 = r^high_l / s_l;
@@ -24,7 +27,7 @@
 //
 // The outer (FP64-class) quantities have their own precision HP: native FP64 on the
 // caller's LEX fields, or FP32 pairs (LQ_F64X) in EO copies held in the workspace, which
-// on GB300 run the residual operator about six times faster than native FP64.
+// on GB300 run the residual operator about four times faster than native FP64.
 #pragma once
 
 #include <math.h>
@@ -48,6 +51,16 @@ template <typename T> LQ_HD void zero(Spinor<T>& a) {
     for (int k = 0; k < 12; ++k) a.v[k] = {T(0), T(0)};
 }
 
+// this thread's right-hand side (the maps give every thread a fixed one)
+LQ_HD int thread_rhs(int nr) {
+#ifdef __CUDA_ARCH__
+    return (int)threadIdx.x & (nr - 1);
+#else
+    (void)nr;
+    return 0;
+#endif
+}
+
 // ------------------------------------------------------------------------------------
 // site-local kernel: grid-stride over tiles of a map, op.apply per site
 // ------------------------------------------------------------------------------------
@@ -58,7 +71,7 @@ __global__ void __launch_bounds__(BS) site_kernel(Map map, Op op) {
     double red[NR];
 #pragma unroll
     for (int j = 0; j < NR; ++j) red[j] = 0.0;
-    const int nt = map.ntiles();
+    const int nt = op.active() ? map.ntiles() : 0;
     for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
         Site s;
         int c[4];
@@ -81,6 +94,9 @@ cudaError_t launch_site(const Map& map, const Op& op, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Per-right-hand-side scalars handed to a kernel as a parameter.
+template <typename T> struct PerRhs { T v[kMaxRhs]; };
+
 // ------------------------------------------------------------------------------------
 // inner-loop kernels
 // ------------------------------------------------------------------------------------
@@ -93,7 +109,14 @@ struct EpiK1 {
     PA p;
     Real a, b;
     RedCtx rc;
-    LQ_HD bool init() { return rc.st->stop == 0; }
+    int nr;
+    bool on;
+    LQ_HD bool init() {
+        if (rc.st->all_stop) return false;
+        on = rc.st->stop[thread_rhs(nr)] == 0;
+        return true;
+    }
+    LQ_HD bool active() const { return on; }
     template <typename R>
     LQ_HD void apply(const Site& s, const Spinor<R>& acc, double* red) const {
         Spinor<R> pv, o;
@@ -106,17 +129,21 @@ struct EpiK1 {
     }
     template <int BS> __device__ __forceinline__ void finish(const double (&red)[1]) const {
         SolverState* st = rc.st;
-        grid_reduce<BS, 1>(rc, kTicketK1, red, [st](const double* tot) {
-            const double sg = tot[0];
-            st->sigma = sg;
-            if (!isfinite(sg)) {
-                st->stop = 3;
-                st->alpha = 0.0;
-            } else if (!(sg > 0.0)) {
-                st->stop = 2;
-                st->alpha = 0.0;
-            } else {
-                st->alpha = st->rho / sg;
+        const int n = nr;
+        grid_reduce_seg<BS, 1>(rc, kTicketK1, red, n, [st, n](const double* tot) {
+            for (int j = 0; j < n; ++j) {
+                if (st->stop[j]) continue;
+                const double sg = tot[j];
+                st->sigma[j] = sg;
+                if (!isfinite(sg)) {
+                    st->stop[j] = 3;
+                    st->alpha[j] = 0.0;
+                } else if (!(sg > 0.0)) {
+                    st->stop[j] = 2;
+                    st->alpha[j] = 0.0;
+                } else {
+                    st->alpha[j] = st->rho[j] / sg;
+                }
             }
         });
     }
@@ -133,12 +160,17 @@ struct EpiK2 {
     RA r;
     Real a, b;
     RedCtx rc;
+    int nr;
     Real alpha;
+    bool on;
     LQ_HD bool init() {
-        if (rc.st->stop) return false;
-        alpha = from_double<Real>(rc.st->alpha);
+        if (rc.st->all_stop) return false;
+        const int j = thread_rhs(nr);
+        on = rc.st->stop[j] == 0;
+        alpha = from_double<Real>(rc.st->alpha[j]);
         return true;
     }
+    LQ_HD bool active() const { return on; }
     template <typename R>
     LQ_HD void apply(const Site& s, const Spinor<R>& acc, double* red) const {
         Spinor<R> tv, pv, xv, rv;
@@ -160,21 +192,29 @@ struct EpiK2 {
     }
     template <int BS> __device__ __forceinline__ void finish(const double (&red)[1]) const {
         SolverState* st = rc.st;
-        grid_reduce<BS, 1>(rc, kTicketK2, red, [st](const double* tot) {
-            const double rn = tot[0];
-            st->iter += 1;
-            if (!isfinite(rn)) {
-                st->stop = 3;
-                return;
+        const int n = nr;
+        grid_reduce_seg<BS, 1>(rc, kTicketK2, red, n, [st, n](const double* tot) {
+            int all = 1;
+            for (int j = 0; j < n; ++j) {
+                if (!st->stop[j]) {
+                    const double rn = tot[j];
+                    st->iter[j] += 1;
+                    if (!isfinite(rn)) {
+                        st->stop[j] = 3;
+                    } else {
+                        st->beta[j] = rn / st->rho[j];
+                        st->rho[j] = rn;
+                        if (rn <= st->stop_rho[j] || st->iter[j] >= st->k_max) st->stop[j] = 1;
+                    }
+                }
+                all &= (st->stop[j] != 0);
             }
-            st->beta = rn / st->rho;
-            st->rho = rn;
-            if (rn <= st->stop_rho || st->iter >= st->k_max) st->stop = 1;
+            st->all_stop = all;
         });
     }
 };
 
-// K3: p = r + beta p, once per completed iteration
+// K3: p = r + beta p, once per completed iteration of each right-hand side
 template <class PA, class RA>
 struct OpK3 {
     using Real = typename PA::Real;
@@ -182,12 +222,19 @@ struct OpK3 {
     PA p;
     RA r;
     RedCtx rc;
+    int nr;
     Real beta;
+    bool on;
     LQ_HD bool init() {
-        if (rc.st->p_iter == rc.st->iter) return false;
-        beta = from_double<Real>(rc.st->beta);
+        bool any = false;
+        for (int j = 0; j < nr; ++j) any |= (rc.st->p_iter[j] != rc.st->iter[j]);
+        if (!any) return false;
+        const int j = thread_rhs(nr);
+        on = rc.st->p_iter[j] != rc.st->iter[j];
+        beta = from_double<Real>(rc.st->beta[j]);
         return true;
     }
+    LQ_HD bool active() const { return on; }
     LQ_HD void apply(const Site& s, double*) const {
         Spinor<Real> pv, rv;
         p.load(s, pv);
@@ -198,41 +245,53 @@ struct OpK3 {
     }
     template <int BS> __device__ __forceinline__ void finish(const double (&red)[1]) const {
         SolverState* st = rc.st;
-        grid_reduce<BS, 1>(rc, kTicketK3, red, [st](const double*) { st->p_iter = st->iter; });
+        const int n = nr;
+        grid_reduce_seg<BS, 1>(rc, kTicketK3, red, n, [st, n](const double*) {
+            for (int j = 0; j < n; ++j) st->p_iter[j] = st->iter[j];
+        });
     }
 };
 
 // ------------------------------------------------------------------------------------
-// cycle start (Algorithm 1 lines 8-12)
+// cycle start (Algorithm 1 lines 8-12), per right-hand side that takes part (act)
 // ------------------------------------------------------------------------------------
-// r = fl_low(r^high / s); FIRST: p = r; psi = 0.  Otherwise reduce <r, p> and ||r||^2.
-template <class RHA, class RA, class PA, class XA, bool FIRST>
+// r = fl_low(r^high / s); first cycle: p = r; psi = 0.  Reduces <r, p> and ||r||^2.
+template <class RHA, class RA, class PA, class XA>
 struct OpRestart {
     using Real = typename RA::Real;
-    static constexpr int NRED = FIRST ? 1 : 3;
+    static constexpr int NRED = 3;
     RHA rh;
     RA r;
     PA p;
     XA x;
-    double stop_rho;
-    int k_max;
     RedCtx rc;
-    LQ_HD bool init() { return true; }
-    Real is;   // 1/s in the inner arithmetic
+    int nr, k_max;
+    PerRhs<Real> is;          // 1/s
+    PerRhs<double> stop_rho;
+    PerRhs<int> act, first;
+    Real my_is;
+    bool on, my_first;
+    LQ_HD bool init() {
+        const int j = thread_rhs(nr);
+        on = act.v[j] != 0;
+        my_first = first.v[j] != 0;
+        my_is = is.v[j];
+        return true;
+    }
+    LQ_HD bool active() const { return on; }
     LQ_HD void apply(const Site& s, double* red) const {
         Spinor<Real> w;
         rh.load(s, w);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) w.v[k] = {is * w.v[k].re, is * w.v[k].im};
+        for (int k = 0; k < 12; ++k) w.v[k] = {my_is * w.v[k].re, my_is * w.v[k].im};
         r.store(s, w);
-        if constexpr (FIRST) {
+        Spinor<Real> pv;
+        if (my_first) {
             p.store(s, w);
             Spinor<Real> z;
             zero(z);
             x.store(s, z);
-            red[0] += to_double(norm2(w));
         } else {
-            Spinor<Real> pv;
             p.load(s, pv);
             Real re = Real(0), im = Real(0);
 #pragma unroll
@@ -242,31 +301,37 @@ struct OpRestart {
             }
             red[0] += to_double(re);
             red[1] += to_double(im);
-            red[2] += to_double(norm2(w));
         }
+        red[2] += to_double(norm2(w));
     }
-    template <int BS> __device__ __forceinline__ void finish(const double (&red)[NRED]) const {
+    template <int BS> __device__ __forceinline__ void finish(const double (&red)[3]) const {
         SolverState* st = rc.st;
-        const double sr = stop_rho;
-        const int km = k_max;
-        grid_reduce<BS, NRED>(rc, kTicketMisc, red, [st, sr, km](const double* tot) {
-            if constexpr (FIRST) {
-                st->rho = tot[0];
-            } else {
-                st->red[0] = tot[0];
-                st->red[1] = tot[1];
-                st->rho = tot[2];
+        const int n = nr, km = k_max;
+        const PerRhs<double> sr = stop_rho;
+        const PerRhs<int> ac = act;
+        grid_reduce_seg<BS, 3>(rc, kTicketMisc, red, n, [st, n, km, sr, ac](const double* tot) {
+            int all = 1;
+            for (int j = 0; j < n; ++j) {
+                if (ac.v[j]) {
+                    st->red[0][j] = tot[0 * kMaxRhs + j];
+                    st->red[1][j] = tot[1 * kMaxRhs + j];
+                    st->rho[j] = tot[2 * kMaxRhs + j];
+                    st->stop[j] = 0;
+                    all = 0;
+                } else {
+                    st->stop[j] = 1;    // idle this cycle
+                }
+                st->iter[j] = 0;
+                st->p_iter[j] = 0;
+                st->stop_rho[j] = sr.v[j];
             }
-            st->iter = 0;
-            st->p_iter = 0;
-            st->stop = 0;
-            st->stop_rho = sr;
             st->k_max = km;
+            st->all_stop = all;
         });
     }
 };
 
-// p = r + beta0 (p - c r), c = <r, p> from the previous kernel; psi = 0
+// later cycles: p = r + beta0 (p - c r), c = <r, p> from the previous kernel; psi = 0
 template <class RA, class PA, class XA>
 struct OpRestartP {
     using Real = typename RA::Real;
@@ -274,14 +339,21 @@ struct OpRestartP {
     RA r;
     PA p;
     XA x;
-    Real b0;
     RedCtx rc;
-    Real cre, cim;
+    int nr;
+    PerRhs<Real> b0;
+    PerRhs<int> on_v;     // act and not first
+    Real cre, cim, my_b0;
+    bool on;
     LQ_HD bool init() {
-        cre = from_double<Real>(rc.st->red[0]);
-        cim = from_double<Real>(rc.st->red[1]);
+        const int j = thread_rhs(nr);
+        on = on_v.v[j] != 0;
+        cre = from_double<Real>(rc.st->red[0][j]);
+        cim = from_double<Real>(rc.st->red[1][j]);
+        my_b0 = b0.v[j];
         return true;
     }
+    LQ_HD bool active() const { return on; }
     LQ_HD void apply(const Site& s, double*) const {
         Spinor<Real> rv, pv;
         r.load(s, rv);
@@ -289,7 +361,7 @@ struct OpRestartP {
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
             const cplx<Real> cr = cmul(cplx<Real>{cre, cim}, rv.v[k]);
-            pv.v[k] = {fma(b0, pv.v[k].re - cr.re, rv.v[k].re), fma(b0, pv.v[k].im - cr.im, rv.v[k].im)};
+            pv.v[k] = {fma(my_b0, pv.v[k].re - cr.re, rv.v[k].re), fma(my_b0, pv.v[k].im - cr.im, rv.v[k].im)};
         }
         p.store(s, pv);
         Spinor<Real> z;
@@ -306,27 +378,39 @@ struct OpXUpdate {
     static constexpr int NRED = 0;
     XA x;
     PsiA psi;
-    Real s;
-    LQ_HD bool init() { return true; }
+    int nr;
+    PerRhs<Real> s;
+    PerRhs<int> act;
+    Real my_s;
+    bool on;
+    LQ_HD bool init() {
+        const int j = thread_rhs(nr);
+        on = act.v[j] != 0;
+        my_s = s.v[j];
+        return true;
+    }
+    LQ_HD bool active() const { return on; }
     LQ_HD void apply(const Site& st, double*) const {
         Spinor<Real> xv, pv;
         x.load(st, xv);
         psi.load(st, pv);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) xv.v[k] = {fma(s, pv.v[k].re, xv.v[k].re), fma(s, pv.v[k].im, xv.v[k].im)};
+        for (int k = 0; k < 12; ++k)
+            xv.v[k] = {fma(my_s, pv.v[k].re, xv.v[k].re), fma(my_s, pv.v[k].im, xv.v[k].im)};
         x.store(st, xv);
     }
     template <int BS> __device__ __forceinline__ void finish(const double (&)[1]) const {}
 };
 
-// ||a||^2 -> st->red[slot] (FP64)
+// ||a||^2 -> st->red[slot][rhs] (FP64)
 template <class A>
 struct OpNorm {
     static constexpr int NRED = 1;
     A a;
     RedCtx rc;
-    int slot;
+    int nr, slot;
     LQ_HD bool init() { return true; }
+    LQ_HD bool active() const { return true; }
     LQ_HD void apply(const Site& s, double* red) const {
         Spinor<double> v;
         a.load(s, v);
@@ -334,17 +418,26 @@ struct OpNorm {
     }
     template <int BS> __device__ __forceinline__ void finish(const double (&red)[1]) const {
         SolverState* st = rc.st;
-        const int sl = slot;
-        grid_reduce<BS, 1>(rc, kTicketMisc, red, [st, sl](const double* t) { st->red[sl] = t[0]; });
+        const int n = nr, sl = slot;
+        grid_reduce_seg<BS, 1>(rc, kTicketMisc, red, n, [st, n, sl](const double* t) {
+            for (int j = 0; j < n; ++j) st->red[sl][j] = t[j];
+        });
     }
 };
 
-// x = 0
+// x = 0 for the right-hand sides marked in act
 template <class XA>
 struct OpZero {
     static constexpr int NRED = 0;
     XA x;
-    LQ_HD bool init() { return true; }
+    int nr;
+    PerRhs<int> act;
+    bool on;
+    LQ_HD bool init() {
+        on = act.v[thread_rhs(nr)] != 0;
+        return true;
+    }
+    LQ_HD bool active() const { return on; }
     LQ_HD void apply(const Site& s, double*) const {
         Spinor<double> z;
         zero(z);
@@ -353,7 +446,7 @@ struct OpZero {
     template <int BS> __device__ __forceinline__ void finish(const double (&)[1]) const {}
 };
 
-// r^high = eta - (a t + b hop^dag(t)), ||r^high||^2 -> st->red[slot]  (outer arithmetic)
+// r^high = eta - (a t + b hop^dag(t)), ||r^high||^2 -> st->red[slot][rhs]  (outer arithmetic)
 template <class EtaA, class TA, class RA>
 struct EpiResid {
     using Real = typename RA::Real;
@@ -363,8 +456,9 @@ struct EpiResid {
     RA r;
     Real a, b;
     RedCtx rc;
-    int slot;
+    int nr, slot;
     LQ_HD bool init() { return true; }
+    LQ_HD bool active() const { return true; }
     LQ_HD void apply(const Site& s, const Spinor<Real>& acc, double* red) const {
         Spinor<Real> tv, ev, o;
         t.load(s, tv);
@@ -379,8 +473,10 @@ struct EpiResid {
     }
     template <int BS> __device__ __forceinline__ void finish(const double (&red)[1]) const {
         SolverState* st = rc.st;
-        const int sl = slot;
-        grid_reduce<BS, 1>(rc, kTicketMisc, red, [st, sl](const double* tt) { st->red[sl] = tt[0]; });
+        const int n = nr, sl = slot;
+        grid_reduce_seg<BS, 1>(rc, kTicketMisc, red, n, [st, n, sl](const double* tt) {
+            for (int j = 0; j < n; ++j) st->red[sl][j] = tt[j];
+        });
     }
 };
 
@@ -389,10 +485,11 @@ struct EpiResid {
 // ------------------------------------------------------------------------------------
 inline size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-// Workspace: state record, partial sums, then the outer fields, then the inner fields.
-// With FP32-pair outer arithmetic (HP = LQ_F64X) the outer fields are EO copies of U, eta
-// and x plus r^high and t^high, all as pairs; with native FP64 only r^high and t^high are
-// needed (U, eta, x are the caller's).  The query returns the larger of the two.
+// Workspace for a batch of nb right-hand sides: state record, partial sums, then the
+// outer fields, then the inner fields.  With FP32-pair outer arithmetic (HP = LQ_F64X) the
+// outer fields are EO copies of U, eta and x plus r^high and t^high, all as pairs; with
+// native FP64 only r^high and t^high are needed (U, eta, x are the caller's).  The query
+// returns the largest layout a mode can use.
 struct WsLayout {
     size_t state, partials, r_high, t_high, u_x, eta_x, x_x, u_low, psi, r, p, t, total;
 };
@@ -406,7 +503,7 @@ inline int inner_prec(int mode) {
     }
 }
 
-inline WsLayout ws_layout(const Geom& g, int mode, bool pair_outer, int inner_fmt) {
+inline WsLayout ws_layout(const Geom& g, int mode, bool pair_outer, int inner_fmt, int nb) {
     WsLayout w{};
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -414,18 +511,19 @@ inline WsLayout ws_layout(const Geom& g, int mode, bool pair_outer, int inner_fm
         o += align256(bytes);
         return at;
     };
+    const int64_t Vn = (int64_t)g.V * nb;
     w.state = take(sizeof(SolverState));
-    w.partials = take(sizeof(double) * 3 * kMaxPartials);
-    w.r_high = take(spinor_bytes(g.V, LQ_F64));
-    w.t_high = take(spinor_bytes(g.V, LQ_F64));
+    w.partials = take(sizeof(double) * kMaxRedValues * kMaxRhs * kMaxPartials);
+    w.r_high = take(spinor_bytes(Vn, LQ_F64));
+    w.t_high = take(spinor_bytes(Vn, LQ_F64));
     if (pair_outer) {
         w.u_x = take(gauge_bytes(g.V, LQ_F64X, 18));
-        w.eta_x = take(spinor_bytes(g.V, LQ_F64X));
-        w.x_x = take(spinor_bytes(g.V, LQ_F64X));
+        w.eta_x = take(spinor_bytes(Vn, LQ_F64X));
+        w.x_x = take(spinor_bytes(Vn, LQ_F64X));
     }
     const int ip = inner_prec(mode);
     if (mode == LQ_CG_MIXED_F32 || mode == LQ_CG_MIXED_F16) w.u_low = take(gauge_bytes(g.V, ip, inner_fmt));
-    const size_t lo = spinor_bytes(g.V, ip);
+    const size_t lo = spinor_bytes(Vn, ip);
     w.psi = take(lo);
     w.r = take(lo);
     w.p = take(lo);
@@ -434,21 +532,37 @@ inline WsLayout ws_layout(const Geom& g, int mode, bool pair_outer, int inner_fm
     return w;
 }
 
-inline size_t ws_bytes_for_mode(const Geom& g, int mode) {
+// right-hand sides in the first batch of a multi-field solve (a power of two <= kMaxRhs)
+inline int batch_size(int nrhs) {
+    int b = 1;
+    while (b * 2 <= nrhs && b * 2 <= kMaxRhs) b *= 2;
+    return b;
+}
+
+inline size_t ws_bytes_for_mode(const Geom& g, int mode, int nrhs) {
     size_t m = 0;
+    const int nb = batch_size(nrhs);
     // native FP64 CG never uses pair copies; the FP32-pair CG always does; the mixed modes
     // may use either (LQ_CG_NATIVE_F64)
     const int pair_lo = (mode == LQ_CG_F64X) ? 1 : 0, pair_hi = (mode == LQ_CG_F64) ? 0 : 1;
     for (int pair = pair_lo; pair <= pair_hi; ++pair)
         for (int fmt : {12, 18}) {
-            const size_t t = ws_layout(g, mode, pair != 0, fmt).total;
+            const size_t t = ws_layout(g, mode, pair != 0, fmt, nb).total;
             if (t > m) m = t;
         }
     return m;
 }
 
+inline int log2i(int n) {
+    int l = 0;
+    while ((1 << l) < n) ++l;
+    return l;
+}
+
 // ------------------------------------------------------------------------------------
-// the driver: inner precision IP / link format IF / layout IL, outer precision HP
+// the driver: inner precision IP / link format IF / layout IL, outer precision HP, for a
+// batch of nb right-hand sides (a power of two <= kMaxRhs) given as nb consecutive FP64
+// LEX fields eta[.], x[.]
 // ------------------------------------------------------------------------------------
 template <int HP> struct Outer;
 template <> struct Outer<LQ_F64> {      // the caller's FP64 LEX fields
@@ -459,7 +573,7 @@ template <> struct Outer<LQ_F64X> {     // FP32-pair EO copies in the workspace
 };
 
 template <int IP, int IF, int IL, int HP>
-int run_solver(const Geom& g, double m_q, const void* U, const void* eta, void* x, const lq_cg_params& prm,
+int run_solver(const Geom& g, double m_q, int nb, const void* U, const void* eta, void* x, const lq_cg_params& prm,
                double delta, const WsLayout& w, char* ws, lq_cg_info* info, cudaStream_t st) {
     using Real = typename PrecT<IP>::Real;
     using HReal = typename PrecT<HP>::Real;
@@ -471,11 +585,13 @@ int run_solver(const Geom& g, double m_q, const void* U, const void* eta, void* 
     using HiRW = SpinorAcc<HP, HL, false>;
     using HiGA = GaugeAcc<HP, 18, HL>;
     using CallerRO = SpinorAcc<LQ_F64, LQ_LAYOUT_LEX, true>;
+    using CallerRW = SpinorAcc<LQ_F64, LQ_LAYOUT_LEX, false>;
     using IMap = typename std::conditional<IL == LQ_LAYOUT_LEX, MapLex<kBS>, MapEoFull<kBS>>::type;
     using ISiteMap = typename std::conditional<IL == LQ_LAYOUT_LEX, MapLex<kSiteBS>, MapEoFull<kSiteBS>>::type;
     using HMap = typename std::conditional<HL == LQ_LAYOUT_LEX, MapLex<kBS>, MapEoFull<kBS>>::type;
     using HSiteMap = typename std::conditional<HL == LQ_LAYOUT_LEX, MapLex<kSiteBS>, MapEoFull<kSiteBS>>::type;
     constexpr bool kPairs = (HP == LQ_F64X);
+    const int lnr = log2i(nb);
 
     SolverState* dstate = (SolverState*)(ws + w.state);
     const RedCtx rc{dstate, (double*)(ws + w.partials)};
@@ -486,39 +602,44 @@ int run_solver(const Geom& g, double m_q, const void* U, const void* eta, void* 
     const void* etao = kPairs ? (const void*)(ws + w.eta_x) : eta;
     void* xo = kPairs ? (void*)(ws + w.x_x) : x;
     const HiGA Uh = make_gauge<HP, 18, HL>(Uo, g);
-    const HiRO eta_ro = make_spinor<HP, HL, true>(etao, g, false);
-    const HiRO x_ro = make_spinor<HP, HL, true>(xo, g, false);
-    const HiRW x_rw = make_spinor<HP, HL, false>(xo, g, false);
-    const HiRO rh_ro = make_spinor<HP, HL, true>(ws + w.r_high, g, false);
-    const HiRW rh_rw = make_spinor<HP, HL, false>(ws + w.r_high, g, false);
-    const HiRO th_ro = make_spinor<HP, HL, true>(ws + w.t_high, g, false);
-    const HiRW th_rw = make_spinor<HP, HL, false>(ws + w.t_high, g, false);
-    const CallerRO eta_caller = make_spinor<LQ_F64, LQ_LAYOUT_LEX, true>(eta, g, false);
-    const SpinorAcc<LQ_F64, LQ_LAYOUT_LEX, false> x_caller = make_spinor<LQ_F64, LQ_LAYOUT_LEX, false>(x, g, false);
+    const HiRO eta_ro = make_spinor<HP, HL, true>(etao, g, false, nb);
+    const HiRO x_ro = make_spinor<HP, HL, true>(xo, g, false, nb);
+    const HiRW x_rw = make_spinor<HP, HL, false>(xo, g, false, nb);
+    const HiRO rh_ro = make_spinor<HP, HL, true>(ws + w.r_high, g, false, nb);
+    const HiRW rh_rw = make_spinor<HP, HL, false>(ws + w.r_high, g, false, nb);
+    const HiRO th_ro = make_spinor<HP, HL, true>(ws + w.t_high, g, false, nb);
+    const HiRW th_rw = make_spinor<HP, HL, false>(ws + w.t_high, g, false, nb);
+    const CallerRO eta_caller = make_spinor<LQ_F64, LQ_LAYOUT_LEX, true>(eta, g, false, nb);
+    const CallerRW x_caller = make_spinor<LQ_F64, LQ_LAYOUT_LEX, false>(x, g, false, nb);
 
     // inner fields; an FP64-class inner loop shares the outer links
     const void* Ulow = (IP == LQ_F64) ? U : (IP == LQ_F64X ? Uo : (const void*)(ws + w.u_low));
     const GA Ui = make_gauge<IP, IF, IL>(Ulow, g);
-    const SpRO psi_ro = make_spinor<IP, IL, true>(ws + w.psi, g, false);
-    const SpRW psi_rw = make_spinor<IP, IL, false>(ws + w.psi, g, false);
-    const SpRO r_ro = make_spinor<IP, IL, true>(ws + w.r, g, false);
-    const SpRW r_rw = make_spinor<IP, IL, false>(ws + w.r, g, false);
-    const SpRO p_ro = make_spinor<IP, IL, true>(ws + w.p, g, false);
-    const SpRW p_rw = make_spinor<IP, IL, false>(ws + w.p, g, false);
-    const SpRO t_ro = make_spinor<IP, IL, true>(ws + w.t, g, false);
-    const SpRW t_rw = make_spinor<IP, IL, false>(ws + w.t, g, false);
+    const SpRO psi_ro = make_spinor<IP, IL, true>(ws + w.psi, g, false, nb);
+    const SpRW psi_rw = make_spinor<IP, IL, false>(ws + w.psi, g, false, nb);
+    const SpRO r_ro = make_spinor<IP, IL, true>(ws + w.r, g, false, nb);
+    const SpRW r_rw = make_spinor<IP, IL, false>(ws + w.r, g, false, nb);
+    const SpRO p_ro = make_spinor<IP, IL, true>(ws + w.p, g, false, nb);
+    const SpRW p_rw = make_spinor<IP, IL, false>(ws + w.p, g, false, nb);
+    const SpRO t_ro = make_spinor<IP, IL, true>(ws + w.t, g, false, nb);
+    const SpRW t_rw = make_spinor<IP, IL, false>(ws + w.t, g, false, nb);
 
-    const MapLex<kSiteBS> lexsite{g};
-    const HMap hmap{g};
-    const HSiteMap hsite{g};
-    const IMap imap{g};
-    const ISiteMap isite{g};
+    const MapLex<kSiteBS> lexsite{g, lnr};
+    const HMap hmap{g, lnr};
+    const HSiteMap hsite{g, lnr};
+    const IMap imap{g, lnr};
+    const ISiteMap isite{g, lnr};
 
     cudaError_t e;
     SolverState hs;
-    lq_cg_info out{};
+    lq_cg_info out[kMaxRhs];
+    memset(out, 0, sizeof(out));
     const bool prof = (prm.flags & LQ_CG_PROFILE) != 0;
-    const int chunk = prm.chunk > 0 ? prm.chunk : (g.V >= (1 << 18) ? 8 : 32);
+    const int64_t Vn = (int64_t)g.V * nb;
+    const int chunk = prm.chunk > 0 ? prm.chunk : (Vn >= (1 << 18) ? 8 : 32);
+    int launches = 0;
+    double kms[4] = {0, 0, 0, 0};
+    int kcalls[4] = {0, 0, 0, 0};
     // CUDA events around the inner kernels (3 roles x chunk) and the outer residual
     struct Events {
         std::vector<cudaEvent_t> ev;
@@ -543,7 +664,7 @@ int run_solver(const Geom& g, double m_q, const void* U, const void* eta, void* 
         return cudaStreamSynchronize(st);
     };
 
-    // r^high = eta - A x, s^2 -> red[2]   (Algorithm 1 lines 2 and 23)
+    // r^high = eta - A x, s^2 -> red[2][.]   (Algorithm 1 lines 2 and 23)
     auto high_residual = [&]() -> cudaError_t {
         Stencil<HiGA, HiRO, false> s1{g, Uh, x_ro};
         EpiAxpby<HiRW, HiRO, true, false> e1;
@@ -557,111 +678,146 @@ int run_solver(const Geom& g, double m_q, const void* U, const void* eta, void* 
         cudaError_t er = launch_stencil<kBS>(hmap, s1, e1, st);
         if (er != cudaSuccess) return er;
         Stencil<HiGA, HiRO, true> s2{g, Uh, th_ro};
-        EpiResid<HiRO, HiRO, HiRW> e2{eta_ro, th_ro, rh_rw, from_double<HReal>(a), from_double<HReal>(b), rc, 2};
+        EpiResid<HiRO, HiRO, HiRW> e2{eta_ro, th_ro, rh_rw, from_double<HReal>(a), from_double<HReal>(b), rc, nb, 2};
         er = launch_stencil<kBS>(hmap, s2, e2, st);
-        out.launches += 2;
+        launches += 2;
         if (prof) cudaEventRecord(evs.ev[6 * chunk + 1], st);
         return er;
     };
     // after the stream has been synchronised: add the residual's event time
     auto account_high = [&]() {
         if (!prof) return;
-        out.kernel_ms[LQ_K_HIGH] += elapsed(evs.ev[6 * chunk], evs.ev[6 * chunk + 1]);
-        out.kernel_calls[LQ_K_HIGH] += 2;
-    };
-    // the pair copy of x back into the caller's FP64 x
-    auto write_back_x = [&]() -> cudaError_t {
-        if constexpr (kPairs) {
-            out.launches += 1;
-            return convert_spinor(g, LQ_F64X, LQ_LAYOUT_EO, xo, LQ_F64, LQ_LAYOUT_LEX, x, st);
-        }
-        return cudaSuccess;
+        kms[LQ_K_HIGH] += elapsed(evs.ev[6 * chunk], evs.ev[6 * chunk + 1]);
+        kcalls[LQ_K_HIGH] += 2;
     };
 
     if ((e = cudaMemsetAsync(dstate, 0, sizeof(SolverState), st)) != cudaSuccess) return cuda_fail(e, "state init");
     if constexpr (kPairs) {
         if ((e = convert_gauge(g, LQ_F64, LQ_LAYOUT_LEX, U, LQ_F64X, 18, LQ_LAYOUT_EO, ws + w.u_x, st)) != cudaSuccess ||
-            (e = convert_spinor(g, LQ_F64, LQ_LAYOUT_LEX, eta, LQ_F64X, LQ_LAYOUT_EO, ws + w.eta_x, st)) != cudaSuccess ||
-            (e = convert_spinor(g, LQ_F64, LQ_LAYOUT_LEX, x, LQ_F64X, LQ_LAYOUT_EO, ws + w.x_x, st)) != cudaSuccess)
+            (e = convert_spinor(g, LQ_F64, LQ_LAYOUT_LEX, eta, LQ_F64X, LQ_LAYOUT_EO, ws + w.eta_x, st, nb)) !=
+                cudaSuccess ||
+            (e = convert_spinor(g, LQ_F64, LQ_LAYOUT_LEX, x, LQ_F64X, LQ_LAYOUT_EO, ws + w.x_x, st, nb)) != cudaSuccess)
             return cuda_fail(e, "FP32-pair copies");
-        out.launches += 3;
+        launches += 3;
     }
     if constexpr (IP == LQ_F32 || IP == LQ_F16S) {
         if ((e = convert_gauge(g, LQ_F64, LQ_LAYOUT_LEX, U, IP, IF, IL, ws + w.u_low, st)) != cudaSuccess)
             return cuda_fail(e, "link pack");
-        out.launches += 1;
+        launches += 1;
     }
-    // ||eta||^2 -> red[3], from the caller's FP64 eta
-    if ((e = launch_site<kSiteBS>(lexsite, OpNorm<CallerRO>{eta_caller, rc, 3}, st)) != cudaSuccess)
+    // ||eta||^2 -> red[3][.], from the caller's FP64 eta
+    if ((e = launch_site<kSiteBS>(lexsite, OpNorm<CallerRO>{eta_caller, rc, nb, 3}, st)) != cudaSuccess)
         return cuda_fail(e, "norm");
-    out.launches += 1;
+    launches += 1;
     if ((e = read_state()) != cudaSuccess) return cuda_fail(e, "norm");
-    const double eta_norm = sqrt(hs.red[3]);
-    out.eta_norm = eta_norm;
-    if (!isfinite(eta_norm)) return fail(LQ_ERR_NONFINITE, "eta has non-finite entries");
-    if (eta_norm == 0.0) {
-        if ((e = launch_site<kSiteBS>(lexsite, OpZero<SpinorAcc<LQ_F64, LQ_LAYOUT_LEX, false>>{x_caller}, st)) != cudaSuccess)
+
+    double eta_norm[kMaxRhs], s[kMaxRhs], s_prev[kMaxRhs], rho_k[kMaxRhs], target[kMaxRhs];
+    int done[kMaxRhs], first[kMaxRhs], stagnant[kMaxRhs], status[kMaxRhs], total[kMaxRhs];
+    PerRhs<int> zero_rhs{};
+    bool any_zero = false;
+    for (int j = 0; j < nb; ++j) {
+        eta_norm[j] = sqrt(hs.red[3][j]);
+        out[j].eta_norm = eta_norm[j];
+        done[j] = 0;
+        first[j] = 1;
+        stagnant[j] = 0;
+        status[j] = LQ_OK;
+        total[j] = 0;
+        s_prev[j] = rho_k[j] = 0.0;
+        target[j] = prm.tol * eta_norm[j];
+        if (!isfinite(eta_norm[j])) {
+            status[j] = LQ_ERR_NONFINITE;
+            done[j] = 1;
+        } else if (eta_norm[j] == 0.0) {
+            zero_rhs.v[j] = 1;
+            any_zero = true;
+            done[j] = 1;
+        }
+    }
+    if (any_zero) {
+        if ((e = launch_site<kSiteBS>(lexsite, OpZero<CallerRW>{x_caller, nb, zero_rhs, false}, st)) != cudaSuccess)
             return cuda_fail(e, "zero");
-        out.launches += 1;
-        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "zero");
-        out.status = LQ_OK;
-        if (info) *info = out;
-        return LQ_OK;
+        launches += 1;
+        if constexpr (kPairs) {
+            if ((e = convert_spinor(g, LQ_F64, LQ_LAYOUT_LEX, x, LQ_F64X, LQ_LAYOUT_EO, ws + w.x_x, st, nb)) !=
+                cudaSuccess)
+                return cuda_fail(e, "zero");
+            launches += 1;
+        }
     }
 
     if ((e = high_residual()) != cudaSuccess) return cuda_fail(e, "residual");
     if ((e = read_state()) != cudaSuccess) return cuda_fail(e, "residual");
     account_high();
-    double s = sqrt(hs.red[2]);
-    out.high_applies = 1;
-    const double target = prm.tol * eta_norm;
-    double s_prev = 0.0, rho_k = 0.0;
-    int l = 0, total = 0, stagnant = 0, status = LQ_OK;
+    for (int j = 0; j < nb; ++j) s[j] = sqrt(hs.red[2][j]);
+    int high_applies = 1, l = 0;
     const int max_cycles = prm.max_cycles > 0 ? prm.max_cycles : 1000;
 
     while (true) {
-        if (!isfinite(s)) {
-            status = fail(LQ_ERR_NONFINITE, "FP64 residual became non-finite");
-            break;
-        }
-        if (s <= target) break;
-        if (l >= max_cycles || total >= prm.max_iter || stagnant >= 5) {
-            status = LQ_NOT_CONVERGED;
-            break;
-        }
-        const double rel_target = target / s;
-        const double stop_rho = fmax(delta * delta, rel_target * rel_target);
-        const int k_max = prm.max_iter - total;
-        // cycle start: both fields of the restart live on the outer map's sites
-        if (l == 0) {
-            OpRestart<HiRO, SpRW, SpRW, SpRW, true> op{rh_ro, r_rw, p_rw, psi_rw, stop_rho, k_max, rc,
-                                                       from_double<Real>(1.0 / s)};
-            e = launch_site<kSiteBS>(hsite, op, st);
-            out.launches += 1;
-        } else {
-            OpRestart<HiRO, SpRW, SpRO, SpRW, false> op{rh_ro, r_rw, p_ro, psi_rw, stop_rho, k_max, rc,
-                                                        from_double<Real>(1.0 / s)};
-            e = launch_site<kSiteBS>(hsite, op, st);
-            if (e == cudaSuccess) {
-                OpRestartP<SpRO, SpRW, SpRW> op2;
-                op2.r = r_ro;
-                op2.p = p_rw;
-                op2.x = psi_rw;
-                op2.b0 = from_double<Real>(s / (s_prev * rho_k));
-                op2.rc = rc;
-                e = launch_site<kSiteBS>(isite, op2, st);
+        // convergence and limits, per right-hand side
+        int total_max = 0;
+        bool any = false;
+        for (int j = 0; j < nb; ++j) {
+            if (done[j]) continue;
+            if (!isfinite(s[j])) {
+                status[j] = LQ_ERR_NONFINITE;
+                done[j] = 1;
+            } else if (s[j] <= target[j]) {
+                done[j] = 1;
+            } else if (l >= max_cycles || total[j] >= prm.max_iter || stagnant[j] >= 5) {
+                status[j] = LQ_NOT_CONVERGED;
+                done[j] = 1;
             }
-            out.launches += 2;
+            if (!done[j]) {
+                any = true;
+                if (total[j] > total_max) total_max = total[j];
+            }
+        }
+        if (!any) break;
+        const int k_max = prm.max_iter - total_max;
+
+        // cycle start
+        OpRestart<HiRO, SpRW, SpRW, SpRW> op;
+        op.rh = rh_ro;
+        op.r = r_rw;
+        op.p = p_rw;
+        op.x = psi_rw;
+        op.rc = rc;
+        op.nr = nb;
+        op.k_max = k_max;
+        OpRestartP<SpRO, SpRW, SpRW> op2;
+        op2.r = r_ro;
+        op2.p = p_rw;
+        op2.x = psi_rw;
+        op2.rc = rc;
+        op2.nr = nb;
+        bool any_cont = false;
+        for (int j = 0; j < nb; ++j) {
+            const bool act = !done[j];
+            const double rel_target = target[j] / (s[j] > 0 ? s[j] : 1.0);
+            op.act.v[j] = act;
+            op.first.v[j] = first[j];
+            op.is.v[j] = from_double<Real>(act ? 1.0 / s[j] : 0.0);
+            op.stop_rho.v[j] = fmax(delta * delta, rel_target * rel_target);
+            op2.on_v.v[j] = act && !first[j];
+            op2.b0.v[j] = from_double<Real>(act && !first[j] ? s[j] / (s_prev[j] * rho_k[j]) : 0.0);
+            any_cont |= act && !first[j];
+        }
+        e = launch_site<kSiteBS>(hsite, op, st);
+        launches += 1;
+        if (e == cudaSuccess && any_cont) {
+            e = launch_site<kSiteBS>(isite, op2, st);
+            launches += 1;
         }
         if (e != cudaSuccess) return cuda_fail(e, "cycle start");
 
-        // inner CG: chunks of K1, K2, K3 until the device-side stop flag is set
+        // inner CG: chunks of K1, K2, K3 until every right-hand side has stopped
         Stencil<GA, SpRO, false> sK1{g, Ui, p_ro};
-        EpiK1<SpRW, SpRO> eK1{t_rw, p_ro, from_double<Real>(a), from_double<Real>(b), rc};
+        EpiK1<SpRW, SpRO> eK1{t_rw, p_ro, from_double<Real>(a), from_double<Real>(b), rc, nb, false};
         Stencil<GA, SpRO, true> sK2{g, Ui, t_ro};
-        EpiK2<SpRO, SpRO, SpRW, SpRW> eK2{t_ro, p_ro, psi_rw, r_rw, from_double<Real>(a), from_double<Real>(b), rc,
-                                          Real(0)};
-        OpK3<SpRW, SpRO> oK3{p_rw, r_ro, rc, Real(0)};
+        EpiK2<SpRO, SpRO, SpRW, SpRW> eK2{t_ro, p_ro, psi_rw, r_rw, from_double<Real>(a), from_double<Real>(b), rc, nb,
+                                          Real(0), false};
+        OpK3<SpRW, SpRO> oK3{p_rw, r_ro, rc, nb, Real(0), false};
         int guard = 0, iter_before = 0;
         while (true) {
             for (int j = 0; j < chunk; ++j) {
@@ -673,71 +829,101 @@ int run_solver(const Geom& g, double m_q, const void* U, const void* eta, void* 
                 if ((e = launch_site<kSiteBS>(isite, oK3, st)) != cudaSuccess) return cuda_fail(e, "K3");
                 if (prof) cudaEventRecord(ev_at(2, j, 1), st);
             }
-            out.launches += 3 * chunk;
+            launches += 3 * chunk;
             if ((e = read_state()) != cudaSuccess) return cuda_fail(e, "inner loop");
+            int iter_max = 0;
+            for (int j = 0; j < nb; ++j)
+                if (hs.iter[j] > iter_max) iter_max = hs.iter[j];
             if (prof) {
-                // only the iterations that ran in this chunk; later launches found the stop flag
-                const int ran = hs.iter - iter_before;
+                // only the iterations that ran in this chunk; later launches found the stop flags
+                const int ran = iter_max - iter_before;
                 for (int j = 0; j < ran && j < chunk; ++j) {
-                    out.kernel_ms[LQ_K_APPLY_D] += elapsed(ev_at(0, j, 0), ev_at(0, j, 1));
-                    out.kernel_ms[LQ_K_APPLY_DDAG] += elapsed(ev_at(0, j, 1), ev_at(1, j, 1));
-                    out.kernel_ms[LQ_K_UPDATE_P] += elapsed(ev_at(1, j, 1), ev_at(2, j, 1));
-                    out.kernel_calls[LQ_K_APPLY_D] += 1;
-                    out.kernel_calls[LQ_K_APPLY_DDAG] += 1;
-                    out.kernel_calls[LQ_K_UPDATE_P] += 1;
+                    kms[LQ_K_APPLY_D] += elapsed(ev_at(0, j, 0), ev_at(0, j, 1));
+                    kms[LQ_K_APPLY_DDAG] += elapsed(ev_at(0, j, 1), ev_at(1, j, 1));
+                    kms[LQ_K_UPDATE_P] += elapsed(ev_at(1, j, 1), ev_at(2, j, 1));
+                    kcalls[LQ_K_APPLY_D] += 1;
+                    kcalls[LQ_K_APPLY_DDAG] += 1;
+                    kcalls[LQ_K_UPDATE_P] += 1;
                 }
             }
-            iter_before = hs.iter;
-            if (hs.stop) break;
+            iter_before = iter_max;
+            if (hs.all_stop) break;
             if (++guard > (k_max / chunk) + 2) break;   // cannot happen: K2 stops at k_max
         }
-        if (hs.stop >= 2) {
-            // breakdown or non-finite: keep x as it is (the last reliable iterate)
-            status = fail(hs.stop == 2 ? LQ_ERR_BREAKDOWN : LQ_ERR_NONFINITE,
-                          hs.stop == 2 ? "CG breakdown: <p, D^dag D p> <= 0" : "inner CG produced non-finite values");
-            total += hs.iter;
-            break;
+
+        // outcome of the cycle, per right-hand side
+        PerRhs<HReal> xs{};
+        PerRhs<int> xact{};
+        for (int j = 0; j < nb; ++j) {
+            if (done[j]) continue;
+            total[j] += hs.iter[j];
+            if (hs.stop[j] >= 2) {
+                // breakdown or non-finite: keep x as it is (the last reliable iterate)
+                status[j] = fail(hs.stop[j] == 2 ? LQ_ERR_BREAKDOWN : LQ_ERR_NONFINITE,
+                                 hs.stop[j] == 2 ? "CG breakdown: <p, D^dag D p> <= 0"
+                                                 : "inner CG produced non-finite values");
+                done[j] = 1;
+                continue;
+            }
+            rho_k[j] = hs.rho[j];
+            xact.v[j] = 1;
+            xs.v[j] = from_double<HReal>(s[j]);
         }
-        total += hs.iter;
-        rho_k = hs.rho;
         // psi^high += s psi_k; then the outer residual
-        OpXUpdate<HiRW, SpinorAcc<IP, IL, true>> xu{x_rw, psi_ro, from_double<HReal>(s)};
-        if constexpr (HL == IL) e = launch_site<kSiteBS>(hsite, xu, st);
-        else e = launch_site<kSiteBS>(lexsite, xu, st);
-        if (e != cudaSuccess) return cuda_fail(e, "x update");
-        out.launches += 1;
+        OpXUpdate<HiRW, SpinorAcc<IP, IL, true>> xu{x_rw, psi_ro, nb, xs, xact, HReal(0), false};
+        if ((e = launch_site<kSiteBS>(hsite, xu, st)) != cudaSuccess) return cuda_fail(e, "x update");
+        launches += 1;
         if ((e = high_residual()) != cudaSuccess) return cuda_fail(e, "residual");
         if ((e = read_state()) != cudaSuccess) return cuda_fail(e, "residual");
         account_high();
-        out.high_applies += 1;
-        const double s_new = sqrt(hs.red[2]);
-        stagnant = (s_new > 0.999 * s) ? stagnant + 1 : 0;
-        s_prev = s;
-        s = s_new;
+        high_applies += 1;
+        for (int j = 0; j < nb; ++j) {
+            if (!xact.v[j]) continue;
+            const double s_new = sqrt(hs.red[2][j]);
+            stagnant[j] = (s_new > 0.999 * s[j]) ? stagnant[j] + 1 : 0;
+            s_prev[j] = s[j];
+            s[j] = s_new;
+            first[j] = 0;
+            out[j].cycles += 1;
+        }
         ++l;
     }
-    if ((e = write_back_x()) != cudaSuccess) return cuda_fail(e, "x write-back");
+    if constexpr (kPairs) {
+        if ((e = convert_spinor(g, LQ_F64X, LQ_LAYOUT_EO, xo, LQ_F64, LQ_LAYOUT_LEX, x, st, nb)) != cudaSuccess)
+            return cuda_fail(e, "x write-back");
+        launches += 1;
+    }
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "x write-back");
-    out.iters = total;
-    out.cycles = l;
-    out.true_rel_resid = s / eta_norm;
-    out.status = status;
-    if (info) *info = out;
-    return status;
+    int worst = LQ_OK;
+    for (int j = 0; j < nb; ++j) {
+        out[j].iters = total[j];
+        out[j].high_applies = high_applies;
+        out[j].true_rel_resid = eta_norm[j] > 0 ? s[j] / eta_norm[j] : 0.0;
+        out[j].status = status[j];
+        out[j].launches = launches;
+        for (int q = 0; q < 4; ++q) {
+            out[j].kernel_ms[q] = kms[q];
+            out[j].kernel_calls[q] = kcalls[q];
+        }
+        if (info) info[j] = out[j];
+        if (status[j] < 0 && (worst >= 0 || status[j] < worst)) worst = status[j];
+        if (status[j] == LQ_NOT_CONVERGED && worst == LQ_OK) worst = LQ_NOT_CONVERGED;
+    }
+    return worst;
 }
 
 // Instantiations live in solver_f64.cu (FP64 and FP32-pair inner loops), solver_f32.cu
 // and solver_f16.cu (mixed inner loops with either outer arithmetic and link format).
-int solve_f64(const Geom& g, double m_q, const void* U, const void* eta, void* x, const lq_cg_params& prm,
+int solve_f64(const Geom& g, double m_q, int nb, const void* U, const void* eta, void* x, const lq_cg_params& prm,
               double delta, const WsLayout& w, char* ws, lq_cg_info* info, cudaStream_t st);
-int solve_f64x(const Geom& g, double m_q, const void* U, const void* eta, void* x, const lq_cg_params& prm,
+int solve_f64x(const Geom& g, double m_q, int nb, const void* U, const void* eta, void* x, const lq_cg_params& prm,
                double delta, const WsLayout& w, char* ws, lq_cg_info* info, cudaStream_t st);
-int solve_mixed_f32(const Geom& g, double m_q, const void* U, const void* eta, void* x, const lq_cg_params& prm,
-                    double delta, const WsLayout& w, char* ws, lq_cg_info* info, cudaStream_t st, bool pairs,
-                    int fmt);
-int solve_mixed_f16(const Geom& g, double m_q, const void* U, const void* eta, void* x, const lq_cg_params& prm,
-                    double delta, const WsLayout& w, char* ws, lq_cg_info* info, cudaStream_t st, bool pairs,
-                    int fmt);
+int solve_mixed_f32(const Geom& g, double m_q, int nb, const void* U, const void* eta, void* x,
+                    const lq_cg_params& prm, double delta, const WsLayout& w, char* ws, lq_cg_info* info,
+                    cudaStream_t st, bool pairs, int fmt);
+int solve_mixed_f16(const Geom& g, double m_q, int nb, const void* U, const void* eta, void* x,
+                    const lq_cg_params& prm, double delta, const WsLayout& w, char* ws, lq_cg_info* info,
+                    cudaStream_t st, bool pairs, int fmt);
 
 }  // namespace solver_detail
 
