@@ -236,3 +236,43 @@ def schur_even(dims, m_q: float, U, psi_full, dagger: bool = False) -> np.ndarra
     out = a * src - hop(dims, U, t, 0, dagger)
     out[par == 1] = 0.0
     return out
+
+
+# --------------------------------------------------------------------------------------
+# Gradients (PyTorch convention: grad = dL/dRe + i dL/dIm of a real loss L).
+# --------------------------------------------------------------------------------------
+def link_grad(dims, g, psi) -> np.ndarray:
+    """Gradient with respect to the links of L = Re <g, D psi> (D of Eq. 1), complex (V,4,3,3).
+
+    D depends on U_mu(n) through 1/2 U_mu(n) P^{-mu} psi(n+mu) in row n and, conjugated,
+    through 1/2 U_mu(n)^dag P^{+mu} psi(n) in row n+mu, hence
+        grad U_mu(n) = 1/2 sum_spin [ g(n) (P^{-mu} psi(n+mu))^H + (P^{+mu} psi(n)) g(n+mu)^H ].
+    Written with the full 4x4 projectors and explicit index sums over spin and colour.
+    """
+    from . import dense
+    V = volume(dims)
+    g = np.asarray(g, dtype=np.complex128).reshape(V, 4, 3)
+    psi = np.asarray(psi, dtype=np.complex128).reshape(V, 4, 3)
+    out = np.zeros((V, 4, 3, 3), dtype=np.complex128)
+    one = np.eye(4)
+    for mu in range(4):
+        gm = gamma(mu)
+        fwd = dense.shift_index(dims, mu, +1)
+        w = np.einsum("ab,nbc->nac", one - gm, psi[fwd])      # P^{-mu} psi(n+mu)
+        v = np.einsum("ab,nbc->nac", one + gm, psi)           # P^{+mu} psi(n)
+        out[:, mu] = 0.5 * (np.einsum("naA,naB->nAB", g, w.conj())
+                            + np.einsum("naA,naB->nAB", v, g[fwd].conj()))
+    return out
+
+
+def solve_grads(dims, m_q, U, eta, chi, tol=1e-13):
+    """Gradients of L = Re <chi, (D^dag D)^{-1} eta>: returns (grad_eta, grad_U).
+
+    With x = A^{-1} eta and y = A^{-1} chi (A = D^dag D is Hermitian):
+        grad_eta = y,  grad_U = -[ G(D x, y) + G(D y, x) ],  G(g, psi) = link_grad(g, psi).
+    """
+    x, _, _ = cg(dims, m_q, U, eta, tol=tol)
+    y, _, _ = cg(dims, m_q, U, chi, tol=tol)
+    Dx = dslash(dims, m_q, U, x)
+    Dy = dslash(dims, m_q, U, y)
+    return y, -(link_grad(dims, Dx, y) + link_grad(dims, Dy, x))

@@ -399,3 +399,65 @@ def test_alg1_fp64_restarts_continue_cg(delta):
     assert cycles >= 4
     assert abs(inner - itc) <= 1
     assert rel <= 1e-10
+
+
+# ----------------------------------------------------------------------------- gradients
+def test_link_grad_matches_finite_differences():
+    """L = Re <g, D(U) psi> is linear in U, so a central difference is exact up to
+    rounding; compare every component of a few links."""
+    dims = (2, 4, 2, 2)
+    m = 0.3
+    U = synth.gauge_field(dims, seed=95)
+    psi = synth.gaussian_spinor(dims, seed=96)
+    g = synth.gaussian_spinor(dims, seed=97)
+    G = oracle.link_grad(dims, g, psi)
+    L = lambda UU: np.vdot(g.ravel(), oracle.dslash(dims, m, UU, psi).ravel()).real
+    h = 1e-3
+    rng = np.random.default_rng(98)
+    for _ in range(12):
+        n, mu, A, B = rng.integers(0, synth.volume(dims)), rng.integers(0, 4), rng.integers(0, 3), rng.integers(0, 3)
+        for part in (1.0, 1j):
+            Up = U.copy()
+            Um = U.copy()
+            Up[n, mu, A, B] += h * part
+            Um[n, mu, A, B] -= h * part
+            fd = (L(Up) - L(Um)) / (2 * h)
+            want = G[n, mu, A, B].real if part == 1.0 else G[n, mu, A, B].imag
+            assert abs(fd - want) < 1e-9 * max(1.0, abs(want))
+
+
+def test_solve_grads_match_dense_finite_differences():
+    """L = Re <chi, (D^dag D)^{-1} eta> on 2^4 with dense solves: the oracle's adjoint
+    gradients against central differences of the dense solution."""
+    dims = (2, 2, 2, 2)
+    m = 0.2
+    U = synth.gauge_field(dims, seed=99, kind="near_identity", eps=0.5)
+    eta = synth.gaussian_spinor(dims, seed=100)
+    chi = synth.gaussian_spinor(dims, seed=101)
+    g_eta, g_U = oracle.solve_grads(dims, m, U, eta, chi)
+
+    def L(UU, ee):
+        Dd = dense.dense_dirac(dims, m, UU)
+        x = np.linalg.solve(Dd.conj().T @ Dd, ee.ravel())
+        return np.vdot(chi.ravel(), x).real
+
+    h = 1e-6
+    rng = np.random.default_rng(102)
+    for _ in range(6):
+        n, mu, A, B = rng.integers(0, 16), rng.integers(0, 4), rng.integers(0, 3), rng.integers(0, 3)
+        for part in (1.0, 1j):
+            Up, Um = U.copy(), U.copy()
+            Up[n, mu, A, B] += h * part
+            Um[n, mu, A, B] -= h * part
+            fd = (L(Up, eta) - L(Um, eta)) / (2 * h)
+            want = g_U[n, mu, A, B].real if part == 1.0 else g_U[n, mu, A, B].imag
+            assert abs(fd - want) < 1e-6 * max(1.0, abs(want))
+    for _ in range(4):
+        n, a, A = rng.integers(0, 16), rng.integers(0, 4), rng.integers(0, 3)
+        for part in (1.0, 1j):
+            ep, em = eta.copy(), eta.copy()
+            ep[n, a, A] += h * part
+            em[n, a, A] -= h * part
+            fd = (L(U, ep) - L(U, em)) / (2 * h)
+            want = g_eta[n, a, A].real if part == 1.0 else g_eta[n, a, A].imag
+            assert abs(fd - want) < 1e-6 * max(1.0, abs(want))
