@@ -274,6 +274,24 @@ int lq_cg_solve_multi(const int32_t dims[4], double m_q, int32_t mode, int32_t n
                       const void *U, const void *eta, void *x, const lq_cg_params *params,
                       void *workspace, size_t ws_bytes, lq_cg_info *info, void *cuda_stream);
 
+/*
+ * lq_link_grad -- the gradient of L = Re <g, D psi> with respect to the links of Eq. (1),
+ * for differentiating through the operator (the paper does not; this is the library's
+ * adjoint support).  With the convention grad = dL/dRe U + i dL/dIm U, per link
+ *   G_mu(n) = 1/2 sum_spin [ g(n) ((1 - gamma_mu) psi(n+mu))^H + ((1 + gamma_mu) psi(n)) g(n+mu)^H ],
+ * a 3x3 complex matrix (colour row index from the first factor).  Differentiating through
+ * D^dag uses lq_link_grad(psi, g) with the roles swapped, since Re <g, D^dag psi> =
+ * Re <psi, D g>.  The mass term does not depend on U, so m_q is not an argument.
+ *   g, psi : FP64 LEX spinor fields (V x 12 complex128), read only; the gradient is linear
+ *            in each.
+ *   out    : FP64 LEX 18-real gauge layout (V x 4 x 3 x 3 complex128), written as
+ *            out = scale * G, or out += scale * G when accumulate != 0.  out must not
+ *            overlap g or psi.
+ * One kernel launch, asynchronous on cuda_stream; errors as for the other entry points.
+ */
+int lq_link_grad(const int32_t dims[4], const void *g, const void *psi, double scale,
+                 int32_t accumulate, void *out, void *cuda_stream);
+
 /* Message of the last error on this host thread ("" if none). */
 const char *lq_last_error(void);
 

@@ -20,7 +20,7 @@ from . import build as _build
 __all__ = [
     "LqError", "load", "lib_path", "PREC", "LAYOUT", "CG_MODE",
     "field_bytes", "dslash_apply", "dslash_adjoint", "dslash_apply_multi", "dslash_adjoint_multi",
-    "dslash_hop", "convert_spinor", "convert_spinor_multi", "convert_gauge", "cg_workspace_bytes",
+    "dslash_hop", "link_grad", "convert_spinor", "convert_spinor_multi", "convert_gauge", "cg_workspace_bytes",
     "cg_solve", "cg_solve_multi", "last_error", "version",
 ]
 
@@ -80,6 +80,8 @@ def load(build_if_missing: bool = True):
             fn.restype = ctypes.c_int
         L.lq_dslash_hop.argtypes = [_Dims, i32, i32, f64, f64, i32, i32, _vp, _vp, _vp, _vp, _vp]
         L.lq_dslash_hop.restype = ctypes.c_int
+        L.lq_link_grad.argtypes = [_Dims, _vp, _vp, f64, i32, _vp, _vp]
+        L.lq_link_grad.restype = ctypes.c_int
         L.lq_convert_spinor.argtypes = [_Dims, i32, i32, _vp, i32, i32, _vp, _vp]
         L.lq_convert_spinor.restype = ctypes.c_int
         L.lq_convert_spinor_multi.argtypes = [_Dims, i32, i32, i32, _vp, i32, i32, _vp, _vp]
@@ -218,6 +220,18 @@ def dslash_hop(dims, out_parity, U, psi_other, out=None, a=0.0, b=1.0, y=None, d
     _check(load().lq_dslash_hop(_dims(dims), int(out_parity), int(bool(dagger)), float(a), float(b),
                                 _prec(prec), int(link_fmt), _ptr(U, gb, "U"), _ptr(psi_other, hb, "psi_other"),
                                 _ptr(y, hb, "y"), _ptr(out, hb, "out"), _stream(stream)))
+    return out
+
+
+def link_grad(dims, g, psi, out=None, scale=1.0, accumulate=False, stream=None):
+    """Gradient of Re <g, D psi> with respect to the links (F64 LEX fields; out is an F64 LEX
+    18-real gauge field, written as scale * G or accumulated into)."""
+    sb = field_bytes(dims, "spinor", "f64")
+    gb = field_bytes(dims, "gauge", "f64", 18, "lex")
+    if out is None:
+        out = _empty_bytes(gb, psi)
+    _check(load().lq_link_grad(_dims(dims), _ptr(g, sb, "g"), _ptr(psi, sb, "psi"), float(scale),
+                               int(bool(accumulate)), _ptr(out, gb, "out"), _stream(stream)))
     return out
 
 

@@ -190,6 +190,20 @@ int lq_dslash_hop(const int32_t dims[4], int32_t out_parity, int32_t dagger, dou
     return LQ_OK;
 }
 
+int lq_link_grad(const int32_t dims[4], const void* gfield, const void* psi, double scale, int32_t accumulate,
+                 void* out, void* cuda_stream) {
+    Geom g;
+    int r;
+    if ((r = check_dims(dims, &g)) != LQ_OK) return r;
+    if (!isfinite(scale)) return fail(LQ_ERR_ARG, "scale must be finite");
+    if ((r = check_ptr(gfield, "g")) || (r = check_ptr(psi, "psi")) || (r = check_ptr(out, "out"))) return r;
+    const size_t sb = spinor_bytes(g.V, LQ_F64), ob = gauge_bytes(g.V, LQ_F64, LQ_LINK18);
+    if (overlap(out, ob, gfield, sb) || overlap(out, ob, psi, sb)) return fail(LQ_ERR_ALIGN, "out overlaps g or psi");
+    const cudaError_t e = link_grad(g, gfield, psi, scale, accumulate != 0, out, (cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "link_grad launch");
+    return LQ_OK;
+}
+
 int lq_convert_spinor(const int32_t dims[4], int32_t src_prec, int32_t src_layout, const void* src, int32_t dst_prec,
                       int32_t dst_layout, void* dst, void* cuda_stream) {
     Geom g;

@@ -25,6 +25,9 @@ cudaError_t convert_spinor(const Geom& g, int sp, int sl, const void* src, int d
 cudaError_t convert_gauge(const Geom& g, int sp, int sl, const void* src, int dp, int dfmt, int dl, void* dst,
                           cudaStream_t st);
 
+cudaError_t link_grad(const Geom& g, const void* gf, const void* psi, double scale, bool accumulate, void* out,
+                      cudaStream_t st);
+
 size_t cg_workspace_bytes(const Geom& g, int mode, int nrhs);
 int cg_solve(const Geom& g, double m_q, int mode, int nrhs, const void* U, const void* eta, void* x,
              const lq_cg_params& prm, void* ws, size_t ws_bytes, lq_cg_info* info, cudaStream_t st);
