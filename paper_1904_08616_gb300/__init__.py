@@ -154,6 +154,8 @@ def _ptr(t, nbytes: int | None = None, name: str = "tensor"):
         raise ValueError(f"{name} must be a CUDA tensor")
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
+    if t.is_conj() or t.is_neg():
+        raise ValueError(f"{name} is a lazy conjugate/negative view: call resolve_conj()/resolve_neg() first")
     if nbytes is not None and t.numel() * t.element_size() < nbytes:
         raise ValueError(f"{name} holds {t.numel() * t.element_size()} bytes, {nbytes} needed")
     return _vp(t.data_ptr())

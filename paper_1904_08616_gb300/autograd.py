@@ -35,6 +35,11 @@ def _links(buf, dims):
     return buf.view(torch.complex128).reshape(_volume(dims), 4, 3, 3)
 
 
+def _dense(t):
+    """Materialise lazy conjugate / negative views (autograd hands those out) as plain memory."""
+    return t.resolve_conj().resolve_neg().contiguous()
+
+
 def _check_fields(dims, U, psi):
     V = _volume(dims)
     if U.dtype != torch.complex128 or psi.dtype != torch.complex128:
@@ -46,8 +51,8 @@ def _check_fields(dims, U, psi):
 class _DiracApply(torch.autograd.Function):
     @staticmethod
     def forward(ctx, U, psi, dims, m_q, dagger):
-        U = U.contiguous()
-        psi = psi.contiguous()
+        U = _dense(U)
+        psi = _dense(psi)
         fn = dslash_adjoint if dagger else dslash_apply
         out = _spinor(fn(dims, m_q, U, psi), dims)
         ctx.save_for_backward(U, psi)
@@ -58,7 +63,7 @@ class _DiracApply(torch.autograd.Function):
     def backward(ctx, g):
         U, psi = ctx.saved_tensors
         dims, m_q, dagger = ctx.dims, ctx.m_q, ctx.dagger
-        g = g.contiguous()
+        g = _dense(g)
         grad_U = grad_psi = None
         if ctx.needs_input_grad[1]:
             fn = dslash_apply if dagger else dslash_adjoint
@@ -73,8 +78,8 @@ class _DiracApply(torch.autograd.Function):
 class _DiracSolve(torch.autograd.Function):
     @staticmethod
     def forward(ctx, U, eta, dims, m_q, mode, tol, max_iter):
-        U = U.contiguous()
-        eta = eta.contiguous()
+        U = _dense(U)
+        eta = _dense(eta)
         x, _, st = cg_solve(dims, m_q, U, eta, mode=mode, tol=tol, max_iter=max_iter)
         if st != 0:
             raise RuntimeError(f"forward solve did not converge to {tol} in {max_iter} iterations")
@@ -86,7 +91,7 @@ class _DiracSolve(torch.autograd.Function):
     def backward(ctx, chi):
         U, x = ctx.saved_tensors
         dims, m_q = ctx.dims, ctx.m_q
-        y, _, st = cg_solve(dims, m_q, U, chi.contiguous(), mode=ctx.mode, tol=ctx.tol, max_iter=ctx.max_iter)
+        y, _, st = cg_solve(dims, m_q, U, _dense(chi), mode=ctx.mode, tol=ctx.tol, max_iter=ctx.max_iter)
         if st != 0:
             raise RuntimeError(f"adjoint solve did not converge to {ctx.tol} in {ctx.max_iter} iterations")
         grad_U = None

@@ -53,6 +53,9 @@ def test_link_grad_bad_args(lqlib):
         lqlib.link_grad(dims, out, f, out=out)       # out overlaps g
     with pytest.raises(lqlib.LqError):
         lqlib.link_grad(dims, f, f, scale=float("nan"))
+    c = _cdev(synth.gaussian_spinor(dims, seed=2))
+    with pytest.raises(ValueError):
+        lqlib.link_grad(dims, c.conj(), c)           # a lazy view's memory is not its value
 
 
 @pytest.mark.parametrize("dagger", [False, True])
