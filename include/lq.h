@@ -187,6 +187,13 @@ typedef struct lq_cg_params {
                                 of FP32 pairs (mixed modes; slower on GB300)              */
 #define LQ_CG_LINK18 4       /* inner links stored 18-real (no reconstruction) in the mixed
                                 modes; default 12-real                                     */
+#define LQ_CG_AUTOTUNE 8     /* lq_cg_solve_lattices: pick the inner block size by timing
+                                (cached per lattice set and GPU); default 128 threads      */
+#define LQ_CG_NO_GRAPH 16    /* lq_cg_solve_lattices: launch the inner kernels one by one
+                                instead of replaying a captured CUDA graph                 */
+#define LQ_CG_BLOCK_64 0x100 /* lq_cg_solve_lattices: inner block size 64 / 128 / 256 threads */
+#define LQ_CG_BLOCK_128 0x200 /*   (at most one; overrides LQ_CG_AUTOTUNE)                  */
+#define LQ_CG_BLOCK_256 0x400
 
 /* Kernel roles reported in lq_cg_info.kernel_ms / kernel_calls. */
 enum {
@@ -204,7 +211,7 @@ typedef struct lq_cg_info {
     double true_rel_resid;   /* ||eta - D^dag D x|| / ||eta||, FP64 operator, at return    */
     double eta_norm;         /* ||eta||                                                    */
     int32_t launches;        /* kernels this call launched (all roles, including skips)     */
-    int32_t reserved;
+    int32_t block;           /* threads per block of the inner stencil kernels               */
     double kernel_ms[4];     /* LQ_CG_PROFILE: summed device time per role (events)         */
     int32_t kernel_calls[4]; /* LQ_CG_PROFILE: launches that did work, per role             */
 } lq_cg_info;
@@ -273,6 +280,46 @@ size_t lq_cg_noalloc_max_workspace_bytes(void);
 int lq_cg_solve_multi(const int32_t dims[4], double m_q, int32_t mode, int32_t nrhs,
                       const void *U, const void *eta, void *x, const lq_cg_params *params,
                       void *workspace, size_t ws_bytes, lq_cg_info *info, void *cuda_stream);
+
+/*
+ * lq_cg_solve_lattices -- several independent problems, on lattices of different sizes,
+ * solved together: for each lattice l, D_l^dag D_l x_{l,r} = eta_{l,r} for its nrhs
+ * right-hand sides (Algorithm 1, or plain CG in LQ_CG_F64, per right-hand side as in
+ * lq_cg_solve_multi).  Batching uneven lattices is not in the paper.
+ *   n        number of lattices, 1 <= n <= 8.
+ *   lats     n descriptors: dims, nrhs (1, 2, 4 or 8), m_q, and the caller's FP64 LEX
+ *            fields U (18-real), eta and x (nrhs stacked fields each; x is the starting
+ *            guess and receives the solutions).  No x may overlap another descriptor's
+ *            fields or the workspace.
+ *   mode     any lq_cg_mode; the mixed modes use 12-real inner links and FP32-pair outer
+ *            arithmetic (LQ_CG_NATIVE_F64, LQ_CG_LINK18 and LQ_CG_PROFILE are rejected).
+ *   params   as lq_cg_solve, plus LQ_CG_AUTOTUNE (choose the inner block size from 64, 128,
+ *            256 by timing the first inner kernel over these lattices; the choice is cached
+ *            per GPU, mode and lattice set, and appended to the file named by the
+ *            environment variable LQ_TUNE_CACHE if set), LQ_CG_BLOCK_64/128/256 (a fixed
+ *            inner block size) and LQ_CG_NO_GRAPH.
+ *   workspace at least lq_cg_workspace_bytes_lattices(n, lats, mode) bytes.
+ *   info     optional, sum of nrhs records in lattice order (block = the inner block size).
+ * Each inner-loop kernel is one launch over all lattices (blocks are shared out in
+ * proportion to each lattice's sites); a chunk of inner iterations is captured once as a
+ * CUDA graph and replayed; each lattice takes its reliable updates when its own inner loop
+ * stops.  Returns LQ_OK if every solve converged, LQ_NOT_CONVERGED if some did not, or the
+ * most negative error status.  Returns after the solves have finished.
+ */
+typedef struct lq_lattice {
+    int32_t dims[4];
+    int32_t nrhs;
+    int32_t pad;            /* set to 0 */
+    double m_q;
+    const void *U;
+    const void *eta;
+    void *x;
+} lq_lattice;
+
+size_t lq_cg_workspace_bytes_lattices(int32_t n, const lq_lattice *lats, int32_t mode);
+int lq_cg_solve_lattices(int32_t n, const lq_lattice *lats, int32_t mode,
+                         const lq_cg_params *params, void *workspace, size_t ws_bytes,
+                         lq_cg_info *info, void *cuda_stream);
 
 /*
  * lq_link_grad -- the gradient of L = Re <g, D psi> with respect to the links of Eq. (1),

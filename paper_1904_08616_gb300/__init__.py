@@ -21,13 +21,14 @@ __all__ = [
     "LqError", "load", "lib_path", "PREC", "LAYOUT", "CG_MODE",
     "field_bytes", "dslash_apply", "dslash_adjoint", "dslash_apply_multi", "dslash_adjoint_multi",
     "dslash_hop", "link_grad", "convert_spinor", "convert_spinor_multi", "convert_gauge", "cg_workspace_bytes",
-    "cg_solve", "cg_solve_multi", "last_error", "version",
+    "cg_solve", "cg_solve_multi", "cg_workspace_bytes_lattices", "cg_solve_lattices",
+    "last_error", "version",
 ]
 
 PREC = {"f64": 0, "f32": 1, "f16s": 2, "f64x": 3}
 LAYOUT = {"lex": 0, "eo": 1}
 CG_MODE = {"f64": 0, "mixed_f32": 1, "mixed_f16": 2, "f64x": 3}
-CG_PROFILE, CG_NATIVE_F64, CG_LINK18 = 1, 2, 4
+CG_PROFILE, CG_NATIVE_F64, CG_LINK18, CG_AUTOTUNE, CG_NO_GRAPH = 1, 2, 4, 8, 16
 STATUS = {0: "OK", 1: "NOT_CONVERGED", -1: "ERR_ARG", -2: "ERR_DIMS", -3: "ERR_ALIGN",
           -4: "ERR_CUDA", -5: "ERR_WORKSPACE", -6: "ERR_NONFINITE", -7: "ERR_BREAKDOWN"}
 
@@ -46,8 +47,13 @@ class CgParams(ctypes.Structure):
 class CgInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("cycles", ctypes.c_int32),
                 ("high_applies", ctypes.c_int32), ("true_rel_resid", ctypes.c_double),
-                ("eta_norm", ctypes.c_double), ("launches", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("eta_norm", ctypes.c_double), ("launches", ctypes.c_int32), ("block", ctypes.c_int32),
                 ("kernel_ms", ctypes.c_double * 4), ("kernel_calls", ctypes.c_int32 * 4)]
+
+
+class Lattice(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int32 * 4), ("nrhs", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("m_q", ctypes.c_double), ("U", ctypes.c_void_p), ("eta", ctypes.c_void_p), ("x", ctypes.c_void_p)]
 
 
 _lock = threading.Lock()
@@ -95,6 +101,11 @@ def load(build_if_missing: bool = True):
         L.lq_cg_solve_multi.argtypes = [_Dims, f64, i32, i32, _vp, _vp, _vp, ctypes.POINTER(CgParams), _vp,
                                         ctypes.c_size_t, ctypes.POINTER(CgInfo), _vp]
         L.lq_cg_solve_multi.restype = ctypes.c_int
+        L.lq_cg_workspace_bytes_lattices.argtypes = [i32, ctypes.POINTER(Lattice), i32]
+        L.lq_cg_workspace_bytes_lattices.restype = ctypes.c_size_t
+        L.lq_cg_solve_lattices.argtypes = [i32, ctypes.POINTER(Lattice), i32, ctypes.POINTER(CgParams), _vp,
+                                           ctypes.c_size_t, ctypes.POINTER(CgInfo), _vp]
+        L.lq_cg_solve_lattices.restype = ctypes.c_int
         L.lq_convert_gauge.argtypes = [_Dims, i32, i32, _vp, i32, i32, i32, _vp, _vp]
         L.lq_convert_gauge.restype = ctypes.c_int
         L.lq_cg_workspace_bytes.argtypes = [_Dims, i32]
@@ -301,10 +312,8 @@ def cg_solve(dims, m_q, U, eta, x=None, mode="f64", tol=1e-10, max_iter=100000, 
                             ctypes.c_size_t(workspace.numel() * workspace.element_size()),
                             ctypes.byref(info), _stream(stream))
     _check(st)
-    d = {k: getattr(info, k) for k, _ in CgInfo._fields_ if k != "reserved"}
-    d["kernel_ms"] = list(d["kernel_ms"])
-    d["kernel_calls"] = list(d["kernel_calls"])
-    return x, d, st
+    d = {k: getattr(info, k) for k, _ in CgInfo._fields_ }
+    return x, _info_dict(info), st
 
 
 def cg_solve_multi(dims, m_q, nrhs, U, eta, x=None, mode="f64", tol=1e-10, max_iter=100000, max_cycles=0,
@@ -329,10 +338,71 @@ def cg_solve_multi(dims, m_q, nrhs, U, eta, x=None, mode="f64", tol=1e-10, max_i
                                   ctypes.c_size_t(workspace.numel() * workspace.element_size()), infos,
                                   _stream(stream))
     _check(st)
-    out = []
-    for i in range(n):
-        d = {k: getattr(infos[i], k) for k, _ in CgInfo._fields_ if k != "reserved"}
-        d["kernel_ms"] = list(d["kernel_ms"])
-        d["kernel_calls"] = list(d["kernel_calls"])
-        out.append(d)
-    return x, out, st
+    return x, [_info_dict(infos[i]) for i in range(n)], st
+
+
+def _info_dict(info) -> dict:
+    d = {k: getattr(info, k) for k, _ in CgInfo._fields_}
+    d["kernel_ms"] = list(d["kernel_ms"])
+    d["kernel_calls"] = list(d["kernel_calls"])
+    return d
+
+
+def _lattice_array(problems):
+    arr = (Lattice * len(problems))()
+    for i, p in enumerate(problems):
+        arr[i].dims = _dims(p["dims"])
+        arr[i].nrhs = int(p.get("nrhs", 1))
+        arr[i].pad = 0
+        arr[i].m_q = float(p.get("m_q", 0.0))
+    return arr
+
+
+def cg_workspace_bytes_lattices(problems, mode="mixed_f32") -> int:
+    """Workspace for cg_solve_lattices; problems: dicts with "dims" and "nrhs"."""
+    m = CG_MODE[mode] if isinstance(mode, str) else int(mode)
+    return int(load().lq_cg_workspace_bytes_lattices(len(problems), _lattice_array(problems), m))
+
+
+def cg_solve_lattices(problems, mode="mixed_f32", tol=1e-10, max_iter=100000, max_cycles=0, delta=0.0, chunk=0,
+                      workspace=None, stream=None, autotune=False, graph=True, block=None):
+    """Solve several lattices of different sizes together (lq_cg_solve_lattices).
+
+    problems: list of dicts {"dims", "m_q", "U", "eta", "nrhs" (1, 2, 4 or 8), "x" (optional
+    start guess)}, U an F64 LEX 18-real gauge field, eta / x nrhs stacked F64 LEX spinors.
+    Returns ([x per lattice], [[info per right-hand side] per lattice], status).
+    """
+    import torch
+    m = CG_MODE[mode] if isinstance(mode, str) else int(mode)
+    arr = _lattice_array(problems)
+    xs = []
+    for i, p in enumerate(problems):
+        nr = int(p.get("nrhs", 1))
+        sb = field_bytes(p["dims"], "spinor", "f64") * nr
+        gb = field_bytes(p["dims"], "gauge", "f64", 18)
+        x = p.get("x")
+        if x is None:
+            x = torch.zeros_like(p["eta"])
+        xs.append(x)
+        arr[i].U = _ptr(p["U"], gb, "U")
+        arr[i].eta = _ptr(p["eta"], sb, "eta")
+        arr[i].x = _ptr(x, sb, "x")
+    wb = int(load().lq_cg_workspace_bytes_lattices(len(problems), arr, m))
+    if workspace is None:
+        workspace = _empty_bytes(wb, problems[0]["eta"])
+    flags = (CG_AUTOTUNE if autotune else 0) | (0 if graph else CG_NO_GRAPH)
+    if block is not None:
+        flags |= {64: 0x100, 128: 0x200, 256: 0x400}[int(block)]
+    prm = CgParams(float(tol), int(max_iter), int(max_cycles), float(delta), int(chunk), flags)
+    total = sum(int(p.get("nrhs", 1)) for p in problems)
+    infos = (CgInfo * total)()
+    st = load().lq_cg_solve_lattices(len(problems), arr, m, ctypes.byref(prm), _ptr(workspace, wb, "workspace"),
+                                     ctypes.c_size_t(workspace.numel() * workspace.element_size()), infos,
+                                     _stream(stream))
+    _check(st)
+    out, at = [], 0
+    for p in problems:
+        nr = int(p.get("nrhs", 1))
+        out.append([_info_dict(infos[at + j]) for j in range(nr)])
+        at += nr
+    return xs, out, st

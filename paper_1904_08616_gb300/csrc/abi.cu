@@ -291,6 +291,82 @@ int lq_cg_solve_multi(const int32_t dims[4], double m_q, int32_t mode, int32_t n
     return r;
 }
 
+namespace {
+
+constexpr int kMaxLattices = 8;
+
+bool valid_mode(int mode) {
+    return mode == LQ_CG_F64 || mode == LQ_CG_MIXED_F32 || mode == LQ_CG_MIXED_F16 || mode == LQ_CG_F64X;
+}
+
+// lattice descriptors: counts, dims, nrhs; fills gs and nr
+int check_lattices(int32_t n, const lq_lattice* lats, Geom* gs, int* nr) {
+    if (n < 1 || n > kMaxLattices) return fail(LQ_ERR_ARG, "n must be 1..%d lattices", kMaxLattices);
+    if (!lats) return fail(LQ_ERR_ARG, "lats is NULL");
+    for (int l = 0; l < n; ++l) {
+        int r;
+        if ((r = check_dims(lats[l].dims, &gs[l])) != LQ_OK) return r;
+        const int k = lats[l].nrhs;
+        if (k != 1 && k != 2 && k != 4 && k != 8) return fail(LQ_ERR_ARG, "lattice %d: nrhs must be 1, 2, 4 or 8", l);
+        if ((int64_t)k * gs[l].V > 100000000LL) return fail(LQ_ERR_ARG, "lattice %d: nrhs * V exceeds 10^8", l);
+        nr[l] = k;
+    }
+    return LQ_OK;
+}
+
+}  // namespace
+
+size_t lq_cg_workspace_bytes_lattices(int32_t n, const lq_lattice* lats, int32_t mode) {
+    Geom gs[kMaxLattices];
+    int nr[kMaxLattices];
+    if (!valid_mode(mode) || check_lattices(n, lats, gs, nr) != LQ_OK) return 0;
+    return cg_workspace_bytes_lattices(n, gs, nr, mode);
+}
+
+int lq_cg_solve_lattices(int32_t n, const lq_lattice* lats, int32_t mode, const lq_cg_params* params,
+                         void* workspace, size_t ws_bytes, lq_cg_info* info, void* cuda_stream) {
+    Geom gs[kMaxLattices];
+    int nr[kMaxLattices];
+    int r;
+    if ((r = check_lattices(n, lats, gs, nr)) != LQ_OK) return r;
+    int total = 0;
+    for (int l = 0; l < n; ++l) total += nr[l];
+    if (info) memset(info, 0, sizeof(*info) * (size_t)total);
+    if (!valid_mode(mode)) return fail(LQ_ERR_ARG, "bad CG mode %d", (int)mode);
+    lq_cg_params prm{1e-10, 100000, 0, 0.0, 0, 0};
+    if (params) prm = *params;
+    if (!(prm.tol > 0.0) || !isfinite(prm.tol)) return fail(LQ_ERR_ARG, "tol must be positive and finite");
+    if (prm.max_iter < 1) return fail(LQ_ERR_ARG, "max_iter must be >= 1");
+    if (prm.max_cycles < 0 || prm.chunk < 0) return fail(LQ_ERR_ARG, "max_cycles and chunk must be >= 0");
+    if (!(prm.delta < 1.0) || !isfinite(prm.delta)) return fail(LQ_ERR_ARG, "delta must be < 1");
+    if (prm.flags & (LQ_CG_PROFILE | LQ_CG_NATIVE_F64 | LQ_CG_LINK18))
+        return fail(LQ_ERR_ARG, "LQ_CG_PROFILE, LQ_CG_NATIVE_F64 and LQ_CG_LINK18 do not apply to lattice batches");
+    {
+        const int bsel = prm.flags & (LQ_CG_BLOCK_64 | LQ_CG_BLOCK_128 | LQ_CG_BLOCK_256);
+        if (bsel & (bsel - 1)) return fail(LQ_ERR_ARG, "at most one LQ_CG_BLOCK_* flag");
+    }
+    if ((r = check_ptr(workspace, "workspace"))) return r == LQ_ERR_ARG ? fail(LQ_ERR_WORKSPACE, "workspace is NULL") : r;
+    for (int l = 0; l < n; ++l) {
+        if (!isfinite(lats[l].m_q)) return fail(LQ_ERR_ARG, "lattice %d: m_q is not finite", l);
+        if ((r = check_ptr(lats[l].U, "U")) || (r = check_ptr(lats[l].eta, "eta")) || (r = check_ptr(lats[l].x, "x")))
+            return r;
+    }
+    // no solution field may overlap any input, any other solution or the workspace
+    for (int l = 0; l < n; ++l) {
+        const size_t xb = spinor_bytes((int64_t)gs[l].V * nr[l], LQ_F64);
+        if (overlap(lats[l].x, xb, workspace, ws_bytes)) return fail(LQ_ERR_ALIGN, "lattice %d: x overlaps the workspace", l);
+        for (int k = 0; k < n; ++k) {
+            const size_t sb = spinor_bytes((int64_t)gs[k].V * nr[k], LQ_F64), gb = gauge_bytes(gs[k].V, LQ_F64, 18);
+            if (overlap(lats[l].x, xb, lats[k].eta, sb) || overlap(lats[l].x, xb, lats[k].U, gb) ||
+                (k != l && overlap(lats[l].x, xb, lats[k].x, sb)))
+                return fail(LQ_ERR_ALIGN, "lattice %d: x overlaps the fields of lattice %d", l, k);
+            if (overlap(workspace, ws_bytes, lats[k].eta, sb) || overlap(workspace, ws_bytes, lats[k].U, gb))
+                return fail(LQ_ERR_ALIGN, "workspace overlaps the fields of lattice %d", k);
+        }
+    }
+    return cg_solve_lattices(n, gs, lats, mode, prm, workspace, ws_bytes, info, (cudaStream_t)cuda_stream);
+}
+
 int lq_cg_solve(const int32_t dims[4], double m_q, int32_t mode, const void* U, const void* eta, void* x,
                 const lq_cg_params* params, void* workspace, size_t ws_bytes, lq_cg_info* info,
                 void* cuda_stream) {

@@ -323,12 +323,13 @@ struct EpiAxpby {
         out.store(s, o);
         if constexpr (NORM) red[0] += to_double(norm2(o));
     }
-    template <int BS> __device__ __forceinline__ void finish(const double (&red)[NRED > 0 ? NRED : 1]) const {
+    template <int BS>
+    __device__ __forceinline__ void finish(const double (&red)[NRED > 0 ? NRED : 1], const VGrid& vg) const {
         if constexpr (NORM) {
             const double v[1] = {red[0]};
             SolverState* st = rc.st;
             const int sl = slot;
-            grid_reduce<BS, 1>(rc, kTicketMisc, v, [st, sl](const double* t) { st->red[sl][0] = t[0]; });
+            grid_reduce<BS, 1>(rc, kTicketMisc, v, vg, [st, sl](const double* t) { st->red[sl][0] = t[0]; });
         }
     }
 };
@@ -347,14 +348,14 @@ template <> struct StencilMinBlocks<dd> { static constexpr int value = LQ_STENCI
 
 // Generic stencil kernel: grid-stride over tiles, one thread per site.
 template <int BS, class Map, class Sten, class Epi>
-__device__ __forceinline__ void stencil_body(const Map& map, const Sten& sten, Epi& epi) {
+__device__ __forceinline__ void stencil_body(const Map& map, const Sten& sten, Epi& epi, const VGrid& vg) {
     if (!epi.init()) return;
     constexpr int NR = Epi::NRED > 0 ? Epi::NRED : 1;
     double red[NR];
 #pragma unroll
     for (int j = 0; j < NR; ++j) red[j] = 0.0;
     const int nt = epi.active() ? map.ntiles() : 0;
-    for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+    for (int tile = vg.bid; tile < nt; tile += vg.nblk) {
         Site s;
         int c[4];
         if (!map.site(tile, s, c)) continue;
@@ -362,17 +363,17 @@ __device__ __forceinline__ void stencil_body(const Map& map, const Sten& sten, E
         sten.apply(s, c, acc);
         epi.apply(s, acc, red);
     }
-    epi.template finish<BS>(red);
+    epi.template finish<BS>(red, vg);
 }
 
 template <int BS, class Map, class Sten, class Epi>
 __global__ void __launch_bounds__(BS) stencil_kernel(Map map, Sten sten, Epi epi) {
-    stencil_body<BS>(map, sten, epi);
+    stencil_body<BS>(map, sten, epi, hw_grid());
 }
 
 template <int BS, int MINB, class Map, class Sten, class Epi>
 __global__ void __launch_bounds__(BS, MINB) stencil_kernel_minb(Map map, Sten sten, Epi epi) {
-    stencil_body<BS>(map, sten, epi);
+    stencil_body<BS>(map, sten, epi, hw_grid());
 }
 
 // Grid size for a grid-stride kernel: every SM filled to its occupancy, never more

@@ -527,6 +527,15 @@ constexpr int kMaxPartials = 4096;     // blocks per reducing kernel
 constexpr int kMaxRedValues = 3;       // values reduced per thread
 constexpr int kTicketK1 = 0, kTicketK2 = 1, kTicketK3 = 2, kTicketMisc = 3;
 
+// The blocks a kernel body sees as its grid: the hardware grid, or one lattice's share of
+// a launch that serves several lattices (bid in [0, nblk)).
+struct VGrid {
+    int bid, nblk;
+};
+#ifdef __CUDACC__
+__device__ __forceinline__ VGrid hw_grid() { return VGrid{(int)blockIdx.x, (int)gridDim.x}; }
+#endif
+
 struct RedCtx {
     SolverState* st;
     double* partials;   // kMaxRedValues * kMaxRhs * kMaxPartials doubles
@@ -555,7 +564,7 @@ template <int BS> __device__ __forceinline__ double block_sum(double v, double* 
 // over segment r.  No block waits for another.
 template <int BS, int NV, class Fin>
 __device__ __forceinline__ void grid_reduce_seg(const RedCtx& rc, int ticket_id, const double (&v)[NV], int nr,
-                                                Fin fin) {
+                                                const VGrid& vg, Fin fin) {
     __shared__ double shw[NV][BS / 32][kMaxRhs];
     __shared__ double shb[BS / 32];
     __shared__ double tot[NV * kMaxRhs];
@@ -573,13 +582,13 @@ __device__ __forceinline__ void grid_reduce_seg(const RedCtx& rc, int ticket_id,
         double t = 0.0;
 #pragma unroll
         for (int i = 0; i < BS / 32; ++i) t += shw[j][i][r];
-        rc.partials[(size_t)(j * kMaxRhs + r) * gridDim.x + blockIdx.x] = t;
+        rc.partials[(size_t)(j * kMaxRhs + r) * vg.nblk + vg.bid] = t;
         __threadfence();
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned int t = atomicAdd(&rc.st->ticket[ticket_id], 1u);
-        last = (t == gridDim.x - 1);
+        last = (t == (unsigned int)vg.nblk - 1u);
     }
     __syncthreads();
     if (!last) return;
@@ -587,8 +596,8 @@ __device__ __forceinline__ void grid_reduce_seg(const RedCtx& rc, int ticket_id,
     for (int q = 0; q < NV * nr; ++q) {
         const int j = q / nr, r = q % nr;
         double x = 0.0;
-        for (int i = threadIdx.x; i < (int)gridDim.x; i += BS)
-            x += __ldcg(rc.partials + (size_t)(j * kMaxRhs + r) * gridDim.x + i);
+        for (int i = threadIdx.x; i < vg.nblk; i += BS)
+            x += __ldcg(rc.partials + (size_t)(j * kMaxRhs + r) * vg.nblk + i);
         x = block_sum<BS>(x, shb);
         if (threadIdx.x == 0) tot[j * kMaxRhs + r] = x;
         __syncthreads();
@@ -601,8 +610,9 @@ __device__ __forceinline__ void grid_reduce_seg(const RedCtx& rc, int ticket_id,
 
 // The unsegmented case (one field): tot[j] is the total of value j.
 template <int BS, int NV, class Fin>
-__device__ __forceinline__ void grid_reduce(const RedCtx& rc, int ticket_id, const double (&v)[NV], Fin fin) {
-    grid_reduce_seg<BS, NV>(rc, ticket_id, v, 1, [&](const double* t) {
+__device__ __forceinline__ void grid_reduce(const RedCtx& rc, int ticket_id, const double (&v)[NV], const VGrid& vg,
+                                            Fin fin) {
+    grid_reduce_seg<BS, NV>(rc, ticket_id, v, 1, vg, [&](const double* t) {
         double u[NV];
 #pragma unroll
         for (int j = 0; j < NV; ++j) u[j] = t[j * kMaxRhs];

@@ -65,20 +65,25 @@ LQ_HD int thread_rhs(int nr) {
 // site-local kernel: grid-stride over tiles of a map, op.apply per site
 // ------------------------------------------------------------------------------------
 template <int BS, class Map, class Op>
-__global__ void __launch_bounds__(BS) site_kernel(Map map, Op op) {
+__device__ __forceinline__ void site_body(const Map& map, Op& op, const VGrid& vg) {
     if (!op.init()) return;
     constexpr int NR = Op::NRED > 0 ? Op::NRED : 1;
     double red[NR];
 #pragma unroll
     for (int j = 0; j < NR; ++j) red[j] = 0.0;
     const int nt = op.active() ? map.ntiles() : 0;
-    for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+    for (int tile = vg.bid; tile < nt; tile += vg.nblk) {
         Site s;
         int c[4];
         if (!map.site(tile, s, c)) continue;
         op.apply(s, red);
     }
-    op.template finish<BS>(red);
+    op.template finish<BS>(red, vg);
+}
+
+template <int BS, class Map, class Op>
+__global__ void __launch_bounds__(BS) site_kernel(Map map, Op op) {
+    site_body<BS>(map, op, hw_grid());
 }
 
 template <int BS, class Map, class Op>
@@ -127,10 +132,10 @@ struct EpiK1 {
         t.store(s, o);
         red[0] += to_double(norm2(o));
     }
-    template <int BS> __device__ __forceinline__ void finish(const double (&red)[1]) const {
+    template <int BS> __device__ __forceinline__ void finish(const double (&red)[1], const VGrid& vg) const {
         SolverState* st = rc.st;
         const int n = nr;
-        grid_reduce_seg<BS, 1>(rc, kTicketK1, red, n, [st, n](const double* tot) {
+        grid_reduce_seg<BS, 1>(rc, kTicketK1, red, n, vg, [st, n](const double* tot) {
             for (int j = 0; j < n; ++j) {
                 if (st->stop[j]) continue;
                 const double sg = tot[j];
@@ -190,10 +195,10 @@ struct EpiK2 {
         r.store(s, rv);
         red[0] += to_double(norm2(rv));
     }
-    template <int BS> __device__ __forceinline__ void finish(const double (&red)[1]) const {
+    template <int BS> __device__ __forceinline__ void finish(const double (&red)[1], const VGrid& vg) const {
         SolverState* st = rc.st;
         const int n = nr;
-        grid_reduce_seg<BS, 1>(rc, kTicketK2, red, n, [st, n](const double* tot) {
+        grid_reduce_seg<BS, 1>(rc, kTicketK2, red, n, vg, [st, n](const double* tot) {
             int all = 1;
             for (int j = 0; j < n; ++j) {
                 if (!st->stop[j]) {
@@ -243,10 +248,10 @@ struct OpK3 {
         for (int k = 0; k < 12; ++k) pv.v[k] = {fma(beta, pv.v[k].re, rv.v[k].re), fma(beta, pv.v[k].im, rv.v[k].im)};
         p.store(s, pv);
     }
-    template <int BS> __device__ __forceinline__ void finish(const double (&red)[1]) const {
+    template <int BS> __device__ __forceinline__ void finish(const double (&red)[1], const VGrid& vg) const {
         SolverState* st = rc.st;
         const int n = nr;
-        grid_reduce_seg<BS, 1>(rc, kTicketK3, red, n, [st, n](const double*) {
+        grid_reduce_seg<BS, 1>(rc, kTicketK3, red, n, vg, [st, n](const double*) {
             for (int j = 0; j < n; ++j) st->p_iter[j] = st->iter[j];
         });
     }
@@ -304,12 +309,12 @@ struct OpRestart {
         }
         red[2] += to_double(norm2(w));
     }
-    template <int BS> __device__ __forceinline__ void finish(const double (&red)[3]) const {
+    template <int BS> __device__ __forceinline__ void finish(const double (&red)[3], const VGrid& vg) const {
         SolverState* st = rc.st;
         const int n = nr, km = k_max;
         const PerRhs<double> sr = stop_rho;
         const PerRhs<int> ac = act;
-        grid_reduce_seg<BS, 3>(rc, kTicketMisc, red, n, [st, n, km, sr, ac](const double* tot) {
+        grid_reduce_seg<BS, 3>(rc, kTicketMisc, red, n, vg, [st, n, km, sr, ac](const double* tot) {
             int all = 1;
             for (int j = 0; j < n; ++j) {
                 if (ac.v[j]) {
@@ -368,7 +373,7 @@ struct OpRestartP {
         zero(z);
         x.store(s, z);
     }
-    template <int BS> __device__ __forceinline__ void finish(const double (&)[1]) const {}
+    template <int BS> __device__ __forceinline__ void finish(const double (&)[1], const VGrid& vg) const {}
 };
 
 // psi^high += s psi  (Algorithm 1 line 22 as read above), in the outer arithmetic
@@ -399,7 +404,7 @@ struct OpXUpdate {
             xv.v[k] = {fma(my_s, pv.v[k].re, xv.v[k].re), fma(my_s, pv.v[k].im, xv.v[k].im)};
         x.store(st, xv);
     }
-    template <int BS> __device__ __forceinline__ void finish(const double (&)[1]) const {}
+    template <int BS> __device__ __forceinline__ void finish(const double (&)[1], const VGrid& vg) const {}
 };
 
 // ||a||^2 -> st->red[slot][rhs] (FP64)
@@ -416,10 +421,10 @@ struct OpNorm {
         a.load(s, v);
         red[0] += norm2(v);
     }
-    template <int BS> __device__ __forceinline__ void finish(const double (&red)[1]) const {
+    template <int BS> __device__ __forceinline__ void finish(const double (&red)[1], const VGrid& vg) const {
         SolverState* st = rc.st;
         const int n = nr, sl = slot;
-        grid_reduce_seg<BS, 1>(rc, kTicketMisc, red, n, [st, n, sl](const double* t) {
+        grid_reduce_seg<BS, 1>(rc, kTicketMisc, red, n, vg, [st, n, sl](const double* t) {
             for (int j = 0; j < n; ++j) st->red[sl][j] = t[j];
         });
     }
@@ -443,7 +448,7 @@ struct OpZero {
         zero(z);
         x.store(s, z);
     }
-    template <int BS> __device__ __forceinline__ void finish(const double (&)[1]) const {}
+    template <int BS> __device__ __forceinline__ void finish(const double (&)[1], const VGrid& vg) const {}
 };
 
 // r^high = eta - (a t + b hop^dag(t)), ||r^high||^2 -> st->red[slot][rhs]  (outer arithmetic)
@@ -471,10 +476,10 @@ struct EpiResid {
         r.store(s, o);
         red[0] += to_double(norm2(o));
     }
-    template <int BS> __device__ __forceinline__ void finish(const double (&red)[1]) const {
+    template <int BS> __device__ __forceinline__ void finish(const double (&red)[1], const VGrid& vg) const {
         SolverState* st = rc.st;
         const int n = nr, sl = slot;
-        grid_reduce_seg<BS, 1>(rc, kTicketMisc, red, n, [st, n, sl](const double* tt) {
+        grid_reduce_seg<BS, 1>(rc, kTicketMisc, red, n, vg, [st, n, sl](const double* tt) {
             for (int j = 0; j < n; ++j) st->red[sl][j] = tt[j];
         });
     }
@@ -558,11 +563,12 @@ inline int log2i(int n) {
     while ((1 << l) < n) ++l;
     return l;
 }
-
 // ------------------------------------------------------------------------------------
-// the driver: inner precision IP / link format IF / layout IL, outer precision HP, for a
-// batch of nb right-hand sides (a power of two <= kMaxRhs) given as nb consecutive FP64
-// LEX fields eta[.], x[.]
+// One solve: inner precision IP / link format IF / layout IL, outer precision HP, inner
+// stencil block size IBS, for a batch of nb right-hand sides (a power of two <= kMaxRhs)
+// given as nb consecutive FP64 LEX fields eta[.], x[.].  The steps of Algorithm 1 are
+// methods so that one driver runs a single lattice and another runs several lattices whose
+// inner kernels share launches.
 // ------------------------------------------------------------------------------------
 template <int HP> struct Outer;
 template <> struct Outer<LQ_F64> {      // the caller's FP64 LEX fields
@@ -572,12 +578,21 @@ template <> struct Outer<LQ_F64X> {     // FP32-pair EO copies in the workspace
     static constexpr int L = LQ_LAYOUT_EO;
 };
 
-template <int IP, int IF, int IL, int HP>
-int run_solver(const Geom& g, double m_q, int nb, const void* U, const void* eta, void* x, const lq_cg_params& prm,
-               double delta, const WsLayout& w, char* ws, lq_cg_info* info, cudaStream_t st) {
+struct EventSet {
+    std::vector<cudaEvent_t> ev;
+    EventSet() = default;
+    EventSet(const EventSet&) = delete;
+    EventSet& operator=(const EventSet&) = delete;
+    ~EventSet() {
+        for (cudaEvent_t x : ev) cudaEventDestroy(x);
+    }
+};
+
+template <int IP, int IF, int IL, int HP, int IBS = kBS>
+struct Solve {
     using Real = typename PrecT<IP>::Real;
     using HReal = typename PrecT<HP>::Real;
-    constexpr int HL = Outer<HP>::L;
+    static constexpr int HL = Outer<HP>::L;
     using SpRO = SpinorAcc<IP, IL, true>;
     using SpRW = SpinorAcc<IP, IL, false>;
     using GA = GaugeAcc<IP, IF, IL>;
@@ -586,86 +601,144 @@ int run_solver(const Geom& g, double m_q, int nb, const void* U, const void* eta
     using HiGA = GaugeAcc<HP, 18, HL>;
     using CallerRO = SpinorAcc<LQ_F64, LQ_LAYOUT_LEX, true>;
     using CallerRW = SpinorAcc<LQ_F64, LQ_LAYOUT_LEX, false>;
-    using IMap = typename std::conditional<IL == LQ_LAYOUT_LEX, MapLex<kBS>, MapEoFull<kBS>>::type;
+    using IMap = typename std::conditional<IL == LQ_LAYOUT_LEX, MapLex<IBS>, MapEoFull<IBS>>::type;
     using ISiteMap = typename std::conditional<IL == LQ_LAYOUT_LEX, MapLex<kSiteBS>, MapEoFull<kSiteBS>>::type;
     using HMap = typename std::conditional<HL == LQ_LAYOUT_LEX, MapLex<kBS>, MapEoFull<kBS>>::type;
     using HSiteMap = typename std::conditional<HL == LQ_LAYOUT_LEX, MapLex<kSiteBS>, MapEoFull<kSiteBS>>::type;
-    constexpr bool kPairs = (HP == LQ_F64X);
-    const int lnr = log2i(nb);
+    using K1Sten = Stencil<GA, SpRO, false>;
+    using K1Epi = EpiK1<SpRW, SpRO>;
+    using K2Sten = Stencil<GA, SpRO, true>;
+    using K2Epi = EpiK2<SpRO, SpRO, SpRW, SpRW>;
+    using K3Op = OpK3<SpRW, SpRO>;
+    static constexpr bool kPairs = (HP == LQ_F64X);
+    static constexpr int kBlock = IBS;
 
-    SolverState* dstate = (SolverState*)(ws + w.state);
-    const RedCtx rc{dstate, (double*)(ws + w.partials)};
-    const double a = m_q + 4.0, b = 0.5;
+    // the problem
+    Geom g;
+    double m_q = 0.0, delta = 0.0, a = 4.0, b = 0.5;
+    int nb = 1;
+    const void* U = nullptr;
+    const void* eta = nullptr;
+    void* x = nullptr;
+    lq_cg_params prm{};
+    WsLayout w{};
+    char* ws = nullptr;
+    cudaStream_t st = nullptr;
 
-    // outer fields: the caller's arrays (native FP64) or pair copies in the workspace
-    const void* Uo = kPairs ? (const void*)(ws + w.u_x) : U;
-    const void* etao = kPairs ? (const void*)(ws + w.eta_x) : eta;
-    void* xo = kPairs ? (void*)(ws + w.x_x) : x;
-    const HiGA Uh = make_gauge<HP, 18, HL>(Uo, g);
-    const HiRO eta_ro = make_spinor<HP, HL, true>(etao, g, false, nb);
-    const HiRO x_ro = make_spinor<HP, HL, true>(xo, g, false, nb);
-    const HiRW x_rw = make_spinor<HP, HL, false>(xo, g, false, nb);
-    const HiRO rh_ro = make_spinor<HP, HL, true>(ws + w.r_high, g, false, nb);
-    const HiRW rh_rw = make_spinor<HP, HL, false>(ws + w.r_high, g, false, nb);
-    const HiRO th_ro = make_spinor<HP, HL, true>(ws + w.t_high, g, false, nb);
-    const HiRW th_rw = make_spinor<HP, HL, false>(ws + w.t_high, g, false, nb);
-    const CallerRO eta_caller = make_spinor<LQ_F64, LQ_LAYOUT_LEX, true>(eta, g, false, nb);
-    const CallerRW x_caller = make_spinor<LQ_F64, LQ_LAYOUT_LEX, false>(x, g, false, nb);
+    // device-side objects
+    SolverState* dstate = nullptr;
+    RedCtx rc{};
+    const void* Uo = nullptr;
+    const void* etao = nullptr;
+    void* xo = nullptr;
+    HiGA Uh;
+    HiRO eta_ro, x_ro, rh_ro, th_ro;
+    HiRW x_rw, rh_rw, th_rw;
+    CallerRO eta_caller;
+    CallerRW x_caller;
+    GA Ui;
+    SpRO psi_ro, r_ro, p_ro, t_ro;
+    SpRW psi_rw, r_rw, p_rw, t_rw;
+    MapLex<kSiteBS> lexsite;
+    HMap hmap;
+    HSiteMap hsite;
+    IMap imap;
+    ISiteMap isite;
+    K1Sten sK1;
+    K1Epi eK1;
+    K2Sten sK2;
+    K2Epi eK2;
+    K3Op oK3;
 
-    // inner fields; an FP64-class inner loop shares the outer links
-    const void* Ulow = (IP == LQ_F64) ? U : (IP == LQ_F64X ? Uo : (const void*)(ws + w.u_low));
-    const GA Ui = make_gauge<IP, IF, IL>(Ulow, g);
-    const SpRO psi_ro = make_spinor<IP, IL, true>(ws + w.psi, g, false, nb);
-    const SpRW psi_rw = make_spinor<IP, IL, false>(ws + w.psi, g, false, nb);
-    const SpRO r_ro = make_spinor<IP, IL, true>(ws + w.r, g, false, nb);
-    const SpRW r_rw = make_spinor<IP, IL, false>(ws + w.r, g, false, nb);
-    const SpRO p_ro = make_spinor<IP, IL, true>(ws + w.p, g, false, nb);
-    const SpRW p_rw = make_spinor<IP, IL, false>(ws + w.p, g, false, nb);
-    const SpRO t_ro = make_spinor<IP, IL, true>(ws + w.t, g, false, nb);
-    const SpRW t_rw = make_spinor<IP, IL, false>(ws + w.t, g, false, nb);
-
-    const MapLex<kSiteBS> lexsite{g, lnr};
-    const HMap hmap{g, lnr};
-    const HSiteMap hsite{g, lnr};
-    const IMap imap{g, lnr};
-    const ISiteMap isite{g, lnr};
-
-    cudaError_t e;
-    SolverState hs;
+    // host-side state
+    SolverState hs{};
     lq_cg_info out[kMaxRhs];
-    memset(out, 0, sizeof(out));
-    const bool prof = (prm.flags & LQ_CG_PROFILE) != 0;
-    const int64_t Vn = (int64_t)g.V * nb;
-    const int chunk = prm.chunk > 0 ? prm.chunk : (Vn >= (1 << 18) ? 8 : 32);
-    int launches = 0;
+    bool prof = false;
+    int chunk = 8, launches = 0, high_applies = 0, l = 0, k_max = 0, guard = 0;
     double kms[4] = {0, 0, 0, 0};
     int kcalls[4] = {0, 0, 0, 0};
-    // CUDA events around the inner kernels (3 roles x chunk) and the outer residual
-    struct Events {
-        std::vector<cudaEvent_t> ev;
-        ~Events() {
-            for (cudaEvent_t x : ev) cudaEventDestroy(x);
-        }
-    } evs;
-    if (prof) {
-        evs.ev.resize(6 * chunk + 2);
-        for (auto& ev : evs.ev)
-            if ((e = cudaEventCreate(&ev)) != cudaSuccess) return cuda_fail(e, "event create");
+    EventSet evs;
+    double eta_norm[kMaxRhs], s[kMaxRhs], s_prev[kMaxRhs], rho_k[kMaxRhs], target[kMaxRhs];
+    int done[kMaxRhs], first[kMaxRhs], stagnant[kMaxRhs], status[kMaxRhs], total[kMaxRhs];
+
+    Solve() = default;
+    Solve(const Solve&) = delete;
+    Solve& operator=(const Solve&) = delete;
+
+    void init(const Geom& g_, double m_q_, int nb_, const void* U_, const void* eta_, void* x_,
+              const lq_cg_params& prm_, double delta_, const WsLayout& w_, char* ws_, cudaStream_t st_) {
+        g = g_;
+        m_q = m_q_;
+        nb = nb_;
+        U = U_;
+        eta = eta_;
+        x = x_;
+        prm = prm_;
+        delta = delta_;
+        w = w_;
+        ws = ws_;
+        st = st_;
+        a = m_q + 4.0;
+        b = 0.5;
+        const int lnr = log2i(nb);
+        dstate = (SolverState*)(ws + w.state);
+        rc = RedCtx{dstate, (double*)(ws + w.partials)};
+        // outer fields: the caller's arrays (native FP64) or pair copies in the workspace
+        Uo = kPairs ? (const void*)(ws + w.u_x) : U;
+        etao = kPairs ? (const void*)(ws + w.eta_x) : eta;
+        xo = kPairs ? (void*)(ws + w.x_x) : x;
+        Uh = make_gauge<HP, 18, HL>(Uo, g);
+        eta_ro = make_spinor<HP, HL, true>(etao, g, false, nb);
+        x_ro = make_spinor<HP, HL, true>(xo, g, false, nb);
+        x_rw = make_spinor<HP, HL, false>(xo, g, false, nb);
+        rh_ro = make_spinor<HP, HL, true>(ws + w.r_high, g, false, nb);
+        rh_rw = make_spinor<HP, HL, false>(ws + w.r_high, g, false, nb);
+        th_ro = make_spinor<HP, HL, true>(ws + w.t_high, g, false, nb);
+        th_rw = make_spinor<HP, HL, false>(ws + w.t_high, g, false, nb);
+        eta_caller = make_spinor<LQ_F64, LQ_LAYOUT_LEX, true>(eta, g, false, nb);
+        x_caller = make_spinor<LQ_F64, LQ_LAYOUT_LEX, false>(x, g, false, nb);
+        // inner fields; an FP64-class inner loop shares the outer links
+        const void* Ulow = (IP == LQ_F64) ? U : (IP == LQ_F64X ? Uo : (const void*)(ws + w.u_low));
+        Ui = make_gauge<IP, IF, IL>(Ulow, g);
+        psi_ro = make_spinor<IP, IL, true>(ws + w.psi, g, false, nb);
+        psi_rw = make_spinor<IP, IL, false>(ws + w.psi, g, false, nb);
+        r_ro = make_spinor<IP, IL, true>(ws + w.r, g, false, nb);
+        r_rw = make_spinor<IP, IL, false>(ws + w.r, g, false, nb);
+        p_ro = make_spinor<IP, IL, true>(ws + w.p, g, false, nb);
+        p_rw = make_spinor<IP, IL, false>(ws + w.p, g, false, nb);
+        t_ro = make_spinor<IP, IL, true>(ws + w.t, g, false, nb);
+        t_rw = make_spinor<IP, IL, false>(ws + w.t, g, false, nb);
+        lexsite = MapLex<kSiteBS>{g, lnr};
+        hmap = HMap{g, lnr};
+        hsite = HSiteMap{g, lnr};
+        imap = IMap{g, lnr};
+        isite = ISiteMap{g, lnr};
+        sK1 = K1Sten{g, Ui, p_ro};
+        eK1 = K1Epi{t_rw, p_ro, from_double<Real>(a), from_double<Real>(b), rc, nb, false};
+        sK2 = K2Sten{g, Ui, t_ro};
+        eK2 = K2Epi{t_ro, p_ro, psi_rw, r_rw, from_double<Real>(a), from_double<Real>(b), rc, nb, Real(0), false};
+        oK3 = K3Op{p_rw, r_ro, rc, nb, Real(0), false};
+        memset(out, 0, sizeof(out));
+        prof = (prm.flags & LQ_CG_PROFILE) != 0;
+        const int64_t Vn = (int64_t)g.V * nb;
+        chunk = prm.chunk > 0 ? prm.chunk : (Vn >= (1 << 18) ? 8 : 32);
     }
-    auto ev_at = [&](int role, int j, int end) { return evs.ev[(role * chunk + j) * 2 + end]; };
-    auto elapsed = [&](cudaEvent_t a0, cudaEvent_t a1) {
+
+    cudaEvent_t ev_at(int role, int j, int end) const { return evs.ev[(role * chunk + j) * 2 + end]; }
+    static double elapsed(cudaEvent_t a0, cudaEvent_t a1) {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, a0, a1);
         return (double)ms;
-    };
-    auto read_state = [&]() -> cudaError_t {
-        cudaError_t er = cudaMemcpyAsync(&hs, dstate, sizeof(hs), cudaMemcpyDeviceToHost, st);
+    }
+    cudaError_t read_state_async() { return cudaMemcpyAsync(&hs, dstate, sizeof(hs), cudaMemcpyDeviceToHost, st); }
+    cudaError_t read_state() {
+        const cudaError_t er = read_state_async();
         if (er != cudaSuccess) return er;
         return cudaStreamSynchronize(st);
-    };
+    }
 
     // r^high = eta - A x, s^2 -> red[2][.]   (Algorithm 1 lines 2 and 23)
-    auto high_residual = [&]() -> cudaError_t {
+    cudaError_t high_residual() {
         Stencil<HiGA, HiRO, false> s1{g, Uh, x_ro};
         EpiAxpby<HiRW, HiRO, true, false> e1;
         e1.out = th_rw;
@@ -683,78 +756,94 @@ int run_solver(const Geom& g, double m_q, int nb, const void* U, const void* eta
         launches += 2;
         if (prof) cudaEventRecord(evs.ev[6 * chunk + 1], st);
         return er;
-    };
+    }
     // after the stream has been synchronised: add the residual's event time
-    auto account_high = [&]() {
+    void account_high() {
         if (!prof) return;
         kms[LQ_K_HIGH] += elapsed(evs.ev[6 * chunk], evs.ev[6 * chunk + 1]);
         kcalls[LQ_K_HIGH] += 2;
-    };
-
-    if ((e = cudaMemsetAsync(dstate, 0, sizeof(SolverState), st)) != cudaSuccess) return cuda_fail(e, "state init");
-    if constexpr (kPairs) {
-        if ((e = convert_gauge(g, LQ_F64, LQ_LAYOUT_LEX, U, LQ_F64X, 18, LQ_LAYOUT_EO, ws + w.u_x, st)) != cudaSuccess ||
-            (e = convert_spinor(g, LQ_F64, LQ_LAYOUT_LEX, eta, LQ_F64X, LQ_LAYOUT_EO, ws + w.eta_x, st, nb)) !=
-                cudaSuccess ||
-            (e = convert_spinor(g, LQ_F64, LQ_LAYOUT_LEX, x, LQ_F64X, LQ_LAYOUT_EO, ws + w.x_x, st, nb)) != cudaSuccess)
-            return cuda_fail(e, "FP32-pair copies");
-        launches += 3;
     }
-    if constexpr (IP == LQ_F32 || IP == LQ_F16S) {
-        if ((e = convert_gauge(g, LQ_F64, LQ_LAYOUT_LEX, U, IP, IF, IL, ws + w.u_low, st)) != cudaSuccess)
-            return cuda_fail(e, "link pack");
-        launches += 1;
-    }
-    // ||eta||^2 -> red[3][.], from the caller's FP64 eta
-    if ((e = launch_site<kSiteBS>(lexsite, OpNorm<CallerRO>{eta_caller, rc, nb, 3}, st)) != cudaSuccess)
-        return cuda_fail(e, "norm");
-    launches += 1;
-    if ((e = read_state()) != cudaSuccess) return cuda_fail(e, "norm");
 
-    double eta_norm[kMaxRhs], s[kMaxRhs], s_prev[kMaxRhs], rho_k[kMaxRhs], target[kMaxRhs];
-    int done[kMaxRhs], first[kMaxRhs], stagnant[kMaxRhs], status[kMaxRhs], total[kMaxRhs];
-    PerRhs<int> zero_rhs{};
-    bool any_zero = false;
-    for (int j = 0; j < nb; ++j) {
-        eta_norm[j] = sqrt(hs.red[3][j]);
-        out[j].eta_norm = eta_norm[j];
-        done[j] = 0;
-        first[j] = 1;
-        stagnant[j] = 0;
-        status[j] = LQ_OK;
-        total[j] = 0;
-        s_prev[j] = rho_k[j] = 0.0;
-        target[j] = prm.tol * eta_norm[j];
-        if (!isfinite(eta_norm[j])) {
-            status[j] = LQ_ERR_NONFINITE;
-            done[j] = 1;
-        } else if (eta_norm[j] == 0.0) {
-            zero_rhs.v[j] = 1;
-            any_zero = true;
-            done[j] = 1;
+    // state record, field conversions, ||eta||, x = 0 for zero right-hand sides, and the
+    // first outer residual
+    int begin() {
+        cudaError_t e;
+        if (prof) {
+            evs.ev.resize(6 * chunk + 2);
+            for (auto& ev : evs.ev)
+                if ((e = cudaEventCreate(&ev)) != cudaSuccess) return cuda_fail(e, "event create");
         }
-    }
-    if (any_zero) {
-        if ((e = launch_site<kSiteBS>(lexsite, OpZero<CallerRW>{x_caller, nb, zero_rhs, false}, st)) != cudaSuccess)
-            return cuda_fail(e, "zero");
-        launches += 1;
+        // state zeroed, with the inner loop marked stopped until a cycle starts (inner
+        // launches shared with other lattices then skip this one)
+        if ((e = cudaMemsetAsync(dstate, 0, sizeof(SolverState), st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(&dstate->all_stop, 1, sizeof(dstate->all_stop), st)) != cudaSuccess)
+            return cuda_fail(e, "state init");
         if constexpr (kPairs) {
-            if ((e = convert_spinor(g, LQ_F64, LQ_LAYOUT_LEX, x, LQ_F64X, LQ_LAYOUT_EO, ws + w.x_x, st, nb)) !=
+            if ((e = convert_gauge(g, LQ_F64, LQ_LAYOUT_LEX, U, LQ_F64X, 18, LQ_LAYOUT_EO, ws + w.u_x, st)) !=
+                    cudaSuccess ||
+                (e = convert_spinor(g, LQ_F64, LQ_LAYOUT_LEX, eta, LQ_F64X, LQ_LAYOUT_EO, ws + w.eta_x, st, nb)) !=
+                    cudaSuccess ||
+                (e = convert_spinor(g, LQ_F64, LQ_LAYOUT_LEX, x, LQ_F64X, LQ_LAYOUT_EO, ws + w.x_x, st, nb)) !=
+                    cudaSuccess)
+                return cuda_fail(e, "FP32-pair copies");
+            launches += 3;
+        }
+        if constexpr (IP == LQ_F32 || IP == LQ_F16S) {
+            if ((e = convert_gauge(g, LQ_F64, LQ_LAYOUT_LEX, U, IP, IF, IL, ws + w.u_low, st)) != cudaSuccess)
+                return cuda_fail(e, "link pack");
+            launches += 1;
+        }
+        // ||eta||^2 -> red[3][.], from the caller's FP64 eta
+        if ((e = launch_site<kSiteBS>(lexsite, OpNorm<CallerRO>{eta_caller, rc, nb, 3}, st)) != cudaSuccess)
+            return cuda_fail(e, "norm");
+        launches += 1;
+        if ((e = read_state()) != cudaSuccess) return cuda_fail(e, "norm");
+
+        PerRhs<int> zero_rhs{};
+        bool any_zero = false;
+        for (int j = 0; j < nb; ++j) {
+            eta_norm[j] = sqrt(hs.red[3][j]);
+            out[j].eta_norm = eta_norm[j];
+            done[j] = 0;
+            first[j] = 1;
+            stagnant[j] = 0;
+            status[j] = LQ_OK;
+            total[j] = 0;
+            s_prev[j] = rho_k[j] = 0.0;
+            target[j] = prm.tol * eta_norm[j];
+            if (!isfinite(eta_norm[j])) {
+                status[j] = LQ_ERR_NONFINITE;
+                done[j] = 1;
+            } else if (eta_norm[j] == 0.0) {
+                zero_rhs.v[j] = 1;
+                any_zero = true;
+                done[j] = 1;
+            }
+        }
+        if (any_zero) {
+            if ((e = launch_site<kSiteBS>(lexsite, OpZero<CallerRW>{x_caller, nb, zero_rhs, false}, st)) !=
                 cudaSuccess)
                 return cuda_fail(e, "zero");
             launches += 1;
+            if constexpr (kPairs) {
+                if ((e = convert_spinor(g, LQ_F64, LQ_LAYOUT_LEX, x, LQ_F64X, LQ_LAYOUT_EO, ws + w.x_x, st, nb)) !=
+                    cudaSuccess)
+                    return cuda_fail(e, "zero");
+                launches += 1;
+            }
         }
+        if ((e = high_residual()) != cudaSuccess) return cuda_fail(e, "residual");
+        if ((e = read_state()) != cudaSuccess) return cuda_fail(e, "residual");
+        account_high();
+        for (int j = 0; j < nb; ++j) s[j] = sqrt(hs.red[2][j]);
+        high_applies = 1;
+        l = 0;
+        return LQ_OK;
     }
 
-    if ((e = high_residual()) != cudaSuccess) return cuda_fail(e, "residual");
-    if ((e = read_state()) != cudaSuccess) return cuda_fail(e, "residual");
-    account_high();
-    for (int j = 0; j < nb; ++j) s[j] = sqrt(hs.red[2][j]);
-    int high_applies = 1, l = 0;
-    const int max_cycles = prm.max_cycles > 0 ? prm.max_cycles : 1000;
-
-    while (true) {
-        // convergence and limits, per right-hand side
+    // convergence and limits, per right-hand side; true if some right-hand side needs a cycle
+    bool plan() {
+        const int max_cycles = prm.max_cycles > 0 ? prm.max_cycles : 1000;
         int total_max = 0;
         bool any = false;
         for (int j = 0; j < nb; ++j) {
@@ -773,10 +862,12 @@ int run_solver(const Geom& g, double m_q, int nb, const void* U, const void* eta
                 if (total[j] > total_max) total_max = total[j];
             }
         }
-        if (!any) break;
-        const int k_max = prm.max_iter - total_max;
+        k_max = prm.max_iter - total_max;
+        return any;
+    }
 
-        // cycle start
+    // cycle start (Algorithm 1 lines 8-12)
+    int start_cycle() {
         OpRestart<HiRO, SpRW, SpRW, SpRW> op;
         op.rh = rh_ro;
         op.r = r_rw;
@@ -803,28 +894,28 @@ int run_solver(const Geom& g, double m_q, int nb, const void* U, const void* eta
             op2.b0.v[j] = from_double<Real>(act && !first[j] ? s[j] / (s_prev[j] * rho_k[j]) : 0.0);
             any_cont |= act && !first[j];
         }
-        e = launch_site<kSiteBS>(hsite, op, st);
+        cudaError_t e = launch_site<kSiteBS>(hsite, op, st);
         launches += 1;
         if (e == cudaSuccess && any_cont) {
             e = launch_site<kSiteBS>(isite, op2, st);
             launches += 1;
         }
         if (e != cudaSuccess) return cuda_fail(e, "cycle start");
+        guard = 0;
+        return LQ_OK;
+    }
 
-        // inner CG: chunks of K1, K2, K3 until every right-hand side has stopped
-        Stencil<GA, SpRO, false> sK1{g, Ui, p_ro};
-        EpiK1<SpRW, SpRO> eK1{t_rw, p_ro, from_double<Real>(a), from_double<Real>(b), rc, nb, false};
-        Stencil<GA, SpRO, true> sK2{g, Ui, t_ro};
-        EpiK2<SpRO, SpRO, SpRW, SpRW> eK2{t_ro, p_ro, psi_rw, r_rw, from_double<Real>(a), from_double<Real>(b), rc, nb,
-                                          Real(0), false};
-        OpK3<SpRW, SpRO> oK3{p_rw, r_ro, rc, nb, Real(0), false};
-        int guard = 0, iter_before = 0;
+    // the inner CG of one lattice: chunks of K1, K2, K3 until every right-hand side has
+    // stopped; leaves the final state record in hs
+    int inner_single() {
+        cudaError_t e;
+        int iter_before = 0;
         while (true) {
             for (int j = 0; j < chunk; ++j) {
                 if (prof) cudaEventRecord(ev_at(0, j, 0), st);
-                if ((e = launch_stencil<kBS>(imap, sK1, eK1, st)) != cudaSuccess) return cuda_fail(e, "K1");
+                if ((e = launch_stencil<IBS>(imap, sK1, eK1, st)) != cudaSuccess) return cuda_fail(e, "K1");
                 if (prof) cudaEventRecord(ev_at(0, j, 1), st);
-                if ((e = launch_stencil<kBS>(imap, sK2, eK2, st)) != cudaSuccess) return cuda_fail(e, "K2");
+                if ((e = launch_stencil<IBS>(imap, sK2, eK2, st)) != cudaSuccess) return cuda_fail(e, "K2");
                 if (prof) cudaEventRecord(ev_at(1, j, 1), st);
                 if ((e = launch_site<kSiteBS>(isite, oK3, st)) != cudaSuccess) return cuda_fail(e, "K3");
                 if (prof) cudaEventRecord(ev_at(2, j, 1), st);
@@ -850,8 +941,13 @@ int run_solver(const Geom& g, double m_q, int nb, const void* U, const void* eta
             if (hs.all_stop) break;
             if (++guard > (k_max / chunk) + 2) break;   // cannot happen: K2 stops at k_max
         }
+        return LQ_OK;
+    }
 
-        // outcome of the cycle, per right-hand side
+    // outcome of the cycle (hs holds the final inner state), psi^high += s psi_k, and the
+    // outer residual
+    int end_cycle() {
+        cudaError_t e;
         PerRhs<HReal> xs{};
         PerRhs<int> xact{};
         for (int j = 0; j < nb; ++j) {
@@ -869,7 +965,6 @@ int run_solver(const Geom& g, double m_q, int nb, const void* U, const void* eta
             xact.v[j] = 1;
             xs.v[j] = from_double<HReal>(s[j]);
         }
-        // psi^high += s psi_k; then the outer residual
         OpXUpdate<HiRW, SpinorAcc<IP, IL, true>> xu{x_rw, psi_ro, nb, xs, xact, HReal(0), false};
         if ((e = launch_site<kSiteBS>(hsite, xu, st)) != cudaSuccess) return cuda_fail(e, "x update");
         launches += 1;
@@ -887,29 +982,52 @@ int run_solver(const Geom& g, double m_q, int nb, const void* U, const void* eta
             out[j].cycles += 1;
         }
         ++l;
+        return LQ_OK;
     }
-    if constexpr (kPairs) {
-        if ((e = convert_spinor(g, LQ_F64X, LQ_LAYOUT_EO, xo, LQ_F64, LQ_LAYOUT_LEX, x, st, nb)) != cudaSuccess)
-            return cuda_fail(e, "x write-back");
-        launches += 1;
-    }
-    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "x write-back");
-    int worst = LQ_OK;
-    for (int j = 0; j < nb; ++j) {
-        out[j].iters = total[j];
-        out[j].high_applies = high_applies;
-        out[j].true_rel_resid = eta_norm[j] > 0 ? s[j] / eta_norm[j] : 0.0;
-        out[j].status = status[j];
-        out[j].launches = launches;
-        for (int q = 0; q < 4; ++q) {
-            out[j].kernel_ms[q] = kms[q];
-            out[j].kernel_calls[q] = kcalls[q];
+
+    // write-back, per-right-hand-side records; returns the worst status
+    int finish(lq_cg_info* info) {
+        cudaError_t e;
+        if constexpr (kPairs) {
+            if ((e = convert_spinor(g, LQ_F64X, LQ_LAYOUT_EO, xo, LQ_F64, LQ_LAYOUT_LEX, x, st, nb)) != cudaSuccess)
+                return cuda_fail(e, "x write-back");
+            launches += 1;
         }
-        if (info) info[j] = out[j];
-        if (status[j] < 0 && (worst >= 0 || status[j] < worst)) worst = status[j];
-        if (status[j] == LQ_NOT_CONVERGED && worst == LQ_OK) worst = LQ_NOT_CONVERGED;
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "x write-back");
+        int worst = LQ_OK;
+        for (int j = 0; j < nb; ++j) {
+            out[j].iters = total[j];
+            out[j].high_applies = high_applies;
+            out[j].true_rel_resid = eta_norm[j] > 0 ? s[j] / eta_norm[j] : 0.0;
+            out[j].status = status[j];
+            out[j].launches = launches;
+            out[j].block = IBS;
+            for (int q = 0; q < 4; ++q) {
+                out[j].kernel_ms[q] = kms[q];
+                out[j].kernel_calls[q] = kcalls[q];
+            }
+            if (info) info[j] = out[j];
+            if (status[j] < 0 && (worst >= 0 || status[j] < worst)) worst = status[j];
+            if (status[j] == LQ_NOT_CONVERGED && worst == LQ_OK) worst = LQ_NOT_CONVERGED;
+        }
+        return worst;
     }
-    return worst;
+};
+
+// The single-lattice driver: one batch of nb right-hand sides.
+template <int IP, int IF, int IL, int HP>
+int run_solver(const Geom& g, double m_q, int nb, const void* U, const void* eta, void* x, const lq_cg_params& prm,
+               double delta, const WsLayout& w, char* ws, lq_cg_info* info, cudaStream_t st) {
+    Solve<IP, IF, IL, HP> sv;
+    sv.init(g, m_q, nb, U, eta, x, prm, delta, w, ws, st);
+    int r;
+    if ((r = sv.begin()) != LQ_OK) return r;
+    while (sv.plan()) {
+        if ((r = sv.start_cycle()) != LQ_OK) return r;
+        if ((r = sv.inner_single()) != LQ_OK) return r;
+        if ((r = sv.end_cycle()) != LQ_OK) return r;
+    }
+    return sv.finish(info);
 }
 
 // Instantiations live in solver_f64.cu (FP64 and FP32-pair inner loops), solver_f32.cu

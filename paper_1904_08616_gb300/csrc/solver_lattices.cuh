@@ -1,0 +1,332 @@
+// Several lattices of different sizes solved together (Algorithm 1 for each), with the
+// inner CG kernels of all lattices sharing launches.  The paper solves one system at a
+// time; this is the library's batching of uneven problems.
+//
+// Each inner kernel (K1, K2, K3 of solver_impl.cuh) runs as ONE launch over every lattice:
+// the launch carries a table of per-lattice work descriptors (map, stencil, epilogue, all
+// holding that lattice's geometry, fields and state record) and the block ranges that serve
+// each lattice; a block finds its lattice, then runs the ordinary kernel body with that
+// lattice's share of the grid as its virtual grid, so reductions and tickets stay per
+// lattice.  Lattices whose inner loop has stopped leave their blocks idle.  A chunk of
+// iterations (chunk x {K1, K2, K3}) is captured once into a CUDA graph and replayed; the
+// host reads the state records between chunks and runs the outer steps (reliable update,
+// restart) of the lattices whose cycle ended, on the same stream.
+//
+// The inner block size (threads per block of K1/K2) is a template parameter; the tuner
+// times K1 over the actual lattices for each candidate and caches the winner by a JSON key
+// (GPU, mode, lattice shapes and right-hand-side counts), in memory and, when the
+// environment variable LQ_TUNE_CACHE names a file, on disk.
+#pragma once
+
+#include <memory>
+#include <string>
+
+#include "solver_impl.cuh"
+
+namespace lq {
+
+namespace solver_detail {
+
+constexpr int kMaxLat = 8;
+
+template <class Map, class Sten, class Epi> struct StencilJob {
+    Map map;
+    Sten sten;
+    Epi epi;
+};
+template <class Map, class Op> struct SiteJob {
+    Map map;
+    Op op;
+};
+template <class Job> struct JobTable {
+    Job job[kMaxLat];
+    int boff[kMaxLat + 1];   // blocks [boff[l], boff[l+1]) serve lattice l
+    int n;
+};
+
+template <class Table> __device__ __forceinline__ int job_of_block(const Table& t) {
+    int l = 0;
+    while (l + 1 < t.n && (int)blockIdx.x >= t.boff[l + 1]) ++l;
+    return l;
+}
+
+template <int BS, class Map, class Sten, class Epi>
+__global__ void __launch_bounds__(BS) multi_stencil_kernel(const __grid_constant__ JobTable<StencilJob<Map, Sten, Epi>> t) {
+    const int l = job_of_block(t);
+    const VGrid vg{(int)blockIdx.x - t.boff[l], t.boff[l + 1] - t.boff[l]};
+    Epi epi = t.job[l].epi;
+    stencil_body<BS>(t.job[l].map, t.job[l].sten, epi, vg);
+}
+
+template <int BS, class Map, class Op>
+__global__ void __launch_bounds__(BS) multi_site_kernel(const __grid_constant__ JobTable<SiteJob<Map, Op>> t) {
+    const int l = job_of_block(t);
+    const VGrid vg{(int)blockIdx.x - t.boff[l], t.boff[l + 1] - t.boff[l]};
+    Op op = t.job[l].op;
+    site_body<BS>(t.job[l].map, op, vg);
+}
+
+// Blocks per lattice: the kernel's full-occupancy grid shared in proportion to the tiles,
+// at least one block and at most one per tile (and kMaxPartials) for each lattice.
+template <class KernelPtr, class Table>
+inline void split_blocks(KernelPtr k, int bs, const int* ntiles, int n, Table& t) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, bs, 0);
+    if (per_sm < 1) per_sm = 1;
+    const long long G = (long long)sms * per_sm;
+    long long T = 0;
+    for (int l = 0; l < n; ++l) T += ntiles[l];
+    t.n = n;
+    t.boff[0] = 0;
+    for (int l = 0; l < n; ++l) {
+        long long b = (G * ntiles[l] + T - 1) / T;
+        if (b > ntiles[l]) b = ntiles[l];
+        if (b > kMaxPartials) b = kMaxPartials;
+        if (b < 1) b = 1;
+        t.boff[l + 1] = t.boff[l] + (int)b;
+    }
+}
+
+// The three inner launches over all lattices of one solve.
+template <class S> struct InnerLaunches {
+    using T1 = JobTable<StencilJob<typename S::IMap, typename S::K1Sten, typename S::K1Epi>>;
+    using T2 = JobTable<StencilJob<typename S::IMap, typename S::K2Sten, typename S::K2Epi>>;
+    using T3 = JobTable<SiteJob<typename S::ISiteMap, typename S::K3Op>>;
+    static constexpr int BS = S::kBlock;
+    T1 t1;
+    T2 t2;
+    T3 t3;
+
+    static constexpr auto k1() { return multi_stencil_kernel<BS, typename S::IMap, typename S::K1Sten, typename S::K1Epi>; }
+    static constexpr auto k2() { return multi_stencil_kernel<BS, typename S::IMap, typename S::K2Sten, typename S::K2Epi>; }
+    static constexpr auto k3() { return multi_site_kernel<kSiteBS, typename S::ISiteMap, typename S::K3Op>; }
+
+    void build(const S* sv, int n) {
+        int nt[kMaxLat], ns[kMaxLat];
+        for (int l = 0; l < n; ++l) {
+            t1.job[l] = {sv[l].imap, sv[l].sK1, sv[l].eK1};
+            t2.job[l] = {sv[l].imap, sv[l].sK2, sv[l].eK2};
+            t3.job[l] = {sv[l].isite, sv[l].oK3};
+            nt[l] = sv[l].imap.ntiles();
+            ns[l] = sv[l].isite.ntiles();
+        }
+        split_blocks(k1(), BS, nt, n, t1);
+        split_blocks(k2(), BS, nt, n, t2);
+        split_blocks(k3(), kSiteBS, ns, n, t3);
+    }
+    cudaError_t k1_only(cudaStream_t s) const {
+        k1()<<<t1.boff[t1.n], BS, 0, s>>>(t1);
+        return cudaGetLastError();
+    }
+    cudaError_t iteration(cudaStream_t s) const {
+        k1()<<<t1.boff[t1.n], BS, 0, s>>>(t1);
+        k2()<<<t2.boff[t2.n], BS, 0, s>>>(t2);
+        k3()<<<t3.boff[t3.n], kSiteBS, 0, s>>>(t3);
+        return cudaGetLastError();
+    }
+};
+
+// One lattice of a multi-lattice solve as the drivers see it.
+struct LatticeJob {
+    Geom g;
+    double m_q;
+    int nb;
+    const void* U;
+    const void* eta;
+    void* x;
+    WsLayout w;
+    size_t off;   // byte offset of its workspace
+};
+
+// chunk x {K1, K2, K3} captured on a private stream, replayed on the caller's stream
+struct ChunkGraph {
+    cudaStream_t cs = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    ChunkGraph() = default;
+    ChunkGraph(const ChunkGraph&) = delete;
+    ChunkGraph& operator=(const ChunkGraph&) = delete;
+    ~ChunkGraph() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (cs) cudaStreamDestroy(cs);
+    }
+    template <class IL>
+    cudaError_t capture(const IL& il, int chunk) {
+        cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return e;
+        if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+        cudaError_t le = cudaSuccess;
+        for (int j = 0; j < chunk && le == cudaSuccess; ++j) le = il.iteration(cs);
+        e = cudaStreamEndCapture(cs, &graph);
+        if (le != cudaSuccess) return le;
+        if (e != cudaSuccess) return e;
+        return cudaGraphInstantiate(&exec, graph, 0);
+    }
+};
+
+template <int IP, int IF, int IL, int HP, int IBS>
+int run_lattices_bs(int n, const LatticeJob* jobs, const lq_cg_params& prm, double delta, char* ws,
+                    lq_cg_info* info, cudaStream_t st) {
+    using S = Solve<IP, IF, IL, HP, IBS>;
+    std::unique_ptr<S[]> sv(new S[n]);
+    int64_t sites = 0;
+    for (int l = 0; l < n; ++l) {
+        const LatticeJob& j = jobs[l];
+        sv[l].init(j.g, j.m_q, j.nb, j.U, j.eta, j.x, prm, delta, j.w, ws + j.off, st);
+        sites += (int64_t)j.g.V * j.nb;
+    }
+    const int chunk = prm.chunk > 0 ? prm.chunk : (sites >= (1 << 18) ? 8 : 32);
+    int r;
+    for (int l = 0; l < n; ++l)
+        if ((r = sv[l].begin()) != LQ_OK) return r;
+
+    InnerLaunches<S> il;
+    il.build(sv.get(), n);
+    const bool use_graph = (prm.flags & LQ_CG_NO_GRAPH) == 0;
+    ChunkGraph cg;
+    cudaError_t e;
+    if (use_graph && (e = cg.capture(il, chunk)) != cudaSuccess) return cuda_fail(e, "inner-loop graph capture");
+
+    bool in_cycle[kMaxLat] = {}, finished[kMaxLat] = {};
+    int chunks = 0;
+    while (true) {
+        bool any = false;
+        for (int l = 0; l < n; ++l) {
+            if (!in_cycle[l] && !finished[l]) {
+                if (sv[l].plan()) {
+                    if ((r = sv[l].start_cycle()) != LQ_OK) return r;
+                    in_cycle[l] = true;
+                } else {
+                    finished[l] = true;
+                }
+            }
+            any |= in_cycle[l];
+        }
+        if (!any) break;
+        if (use_graph) {
+            if ((e = cudaGraphLaunch(cg.exec, st)) != cudaSuccess) return cuda_fail(e, "inner-loop graph");
+        } else {
+            for (int j = 0; j < chunk; ++j)
+                if ((e = il.iteration(st)) != cudaSuccess) return cuda_fail(e, "inner loop");
+        }
+        ++chunks;
+        for (int l = 0; l < n; ++l) {
+            sv[l].launches += 3 * chunk;
+            if (in_cycle[l] && (e = sv[l].read_state_async()) != cudaSuccess) return cuda_fail(e, "inner loop");
+        }
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "inner loop");
+        for (int l = 0; l < n; ++l) {
+            if (!in_cycle[l]) continue;
+            // K2 stops every right-hand side at k_max, so the guard never decides
+            if (sv[l].hs.all_stop || ++sv[l].guard > (sv[l].k_max / chunk) + 2) {
+                if ((r = sv[l].end_cycle()) != LQ_OK) return r;
+                in_cycle[l] = false;
+            }
+        }
+    }
+    int worst = LQ_OK, at = 0;
+    for (int l = 0; l < n; ++l) {
+        const int s = sv[l].finish(info ? info + at : nullptr);
+        at += jobs[l].nb;
+        if (s < 0 && (worst >= 0 || s < worst)) worst = s;
+        if (s == LQ_NOT_CONVERGED && worst == LQ_OK) worst = LQ_NOT_CONVERGED;
+    }
+    return worst;
+}
+
+// Mean device time of the all-lattice K1 launch with block size IBS, on a p filled with a
+// small constant (every state slot running, so every block works); ms, or < 0 on error.
+template <int IP, int IF, int IL, int HP, int IBS>
+double time_k1(int n, const LatticeJob* jobs, char* ws, cudaStream_t st) {
+    using S = Solve<IP, IF, IL, HP, IBS>;
+    std::unique_ptr<S[]> sv(new S[n]);
+    lq_cg_params prm{};
+    prm.tol = 1e-10;
+    prm.max_iter = 1;
+    for (int l = 0; l < n; ++l) {
+        const LatticeJob& j = jobs[l];
+        sv[l].init(j.g, j.m_q, j.nb, j.U, j.eta, j.x, prm, 0.0, j.w, ws + j.off, st);
+        if (cudaMemsetAsync(sv[l].dstate, 0, sizeof(SolverState), st) != cudaSuccess ||
+            cudaMemsetAsync(ws + j.off + j.w.p, 0x3c, spinor_bytes((int64_t)j.g.V * j.nb, IP), st) != cudaSuccess)
+            return -1.0;
+        if constexpr (IP == LQ_F32 || IP == LQ_F16S) {
+            if (convert_gauge(j.g, LQ_F64, LQ_LAYOUT_LEX, j.U, IP, IF, IL, ws + j.off + j.w.u_low, st) != cudaSuccess)
+                return -1.0;
+        } else if constexpr (IP == LQ_F64X) {
+            if (convert_gauge(j.g, LQ_F64, LQ_LAYOUT_LEX, j.U, LQ_F64X, 18, LQ_LAYOUT_EO, ws + j.off + j.w.u_x, st) !=
+                cudaSuccess)
+                return -1.0;
+        }
+    }
+    InnerLaunches<S> il;
+    il.build(sv.get(), n);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return -1.0;
+    constexpr int kWarm = 2, kReps = 6;
+    bool ok = true;
+    for (int i = 0; i < kWarm; ++i) ok &= il.k1_only(st) == cudaSuccess;
+    ok &= cudaEventRecord(e0, st) == cudaSuccess;
+    for (int i = 0; i < kReps; ++i) ok &= il.k1_only(st) == cudaSuccess;
+    ok &= cudaEventRecord(e1, st) == cudaSuccess;
+    ok &= cudaEventSynchronize(e1) == cudaSuccess;
+    float ms = 0.f;
+    ok &= cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ok ? ms / kReps : -1.0;
+}
+
+// the tuning cache (lattices.cu)
+bool tune_lookup(const std::string& key, int* block);
+void tune_store(const std::string& key, int block);
+std::string tune_key(int mode, int n, const LatticeJob* jobs);
+
+constexpr int kTuneBlocks[3] = {64, 128, 256};
+
+template <int IP, int IF, int IL, int HP>
+int run_lattices(int mode, int n, const LatticeJob* jobs, const lq_cg_params& prm, double delta, char* ws,
+                 lq_cg_info* info, cudaStream_t st) {
+    int bs = kBS;
+    if (prm.flags & LQ_CG_BLOCK_64) {
+        bs = 64;
+    } else if (prm.flags & LQ_CG_BLOCK_128) {
+        bs = 128;
+    } else if (prm.flags & LQ_CG_BLOCK_256) {
+        bs = 256;
+    } else if (prm.flags & LQ_CG_AUTOTUNE) {
+        const std::string key = tune_key(mode, n, jobs);
+        if (!tune_lookup(key, &bs)) {
+            const double t[3] = {time_k1<IP, IF, IL, HP, 64>(n, jobs, ws, st),
+                                 time_k1<IP, IF, IL, HP, 128>(n, jobs, ws, st),
+                                 time_k1<IP, IF, IL, HP, 256>(n, jobs, ws, st)};
+            int best = -1;
+            for (int i = 0; i < 3; ++i)
+                if (t[i] >= 0.0 && (best < 0 || t[i] < t[best])) best = i;
+            if (best < 0) return fail(LQ_ERR_CUDA, "block-size tuning failed: %s", cudaGetErrorString(cudaGetLastError()));
+            bs = kTuneBlocks[best];
+            tune_store(key, bs);
+        }
+    }
+    switch (bs) {
+        case 64: return run_lattices_bs<IP, IF, IL, HP, 64>(n, jobs, prm, delta, ws, info, st);
+        case 256: return run_lattices_bs<IP, IF, IL, HP, 256>(n, jobs, prm, delta, ws, info, st);
+        default: return run_lattices_bs<IP, IF, IL, HP, 128>(n, jobs, prm, delta, ws, info, st);
+    }
+}
+
+// per-mode instantiations (solver_lat_*.cu)
+int lattices_f64(int n, const LatticeJob* jobs, const lq_cg_params& prm, double delta, char* ws, lq_cg_info* info,
+                 cudaStream_t st);
+int lattices_f64x(int n, const LatticeJob* jobs, const lq_cg_params& prm, double delta, char* ws, lq_cg_info* info,
+                  cudaStream_t st);
+int lattices_mixed_f32(int n, const LatticeJob* jobs, const lq_cg_params& prm, double delta, char* ws,
+                       lq_cg_info* info, cudaStream_t st);
+int lattices_mixed_f16(int n, const LatticeJob* jobs, const lq_cg_params& prm, double delta, char* ws,
+                       lq_cg_info* info, cudaStream_t st);
+
+}  // namespace solver_detail
+
+}  // namespace lq

@@ -117,3 +117,66 @@ def test_cg_argument_checks(lqlib):
 
 def test_version(lqlib):
     assert "sm_103a" in lqlib.version()
+
+
+def _lattices(lqlib, specs):
+    """Descriptors with fake, well-separated device addresses (nothing is dereferenced)."""
+    arr = (lqlib.Lattice * len(specs))()
+    base = 0x100000000
+    for i, (dims, nrhs) in enumerate(specs):
+        arr[i].dims = (ctypes.c_int32 * 4)(*dims)
+        arr[i].nrhs = nrhs
+        arr[i].m_q = 0.1
+        arr[i].U = base + 0x30000000 * (3 * i)
+        arr[i].eta = base + 0x30000000 * (3 * i + 1)
+        arr[i].x = base + 0x30000000 * (3 * i + 2)
+    return arr
+
+
+def test_lattices_workspace_query(lqlib):
+    L = lqlib.load()
+    specs = [((8, 8, 8, 8), 4), ((12, 12, 12, 12), 4), ((16, 16, 16, 32), 4)]
+    both = L.lq_cg_workspace_bytes_lattices(3, _lattices(lqlib, specs), 1)
+    parts = [L.lq_cg_workspace_bytes_lattices(1, _lattices(lqlib, [s]), 1) for s in specs]
+    assert both == sum(parts) and all(p > 0 for p in parts)
+    assert L.lq_cg_workspace_bytes_lattices(0, _lattices(lqlib, specs), 1) == 0
+    assert L.lq_cg_workspace_bytes_lattices(1, _lattices(lqlib, [((8, 8, 8, 8), 3)]), 1) == 0
+    assert L.lq_cg_workspace_bytes_lattices(1, _lattices(lqlib, specs), 9) == 0
+    # a lattice costs what the single-lattice solver needs for the same batch, or less
+    assert parts[0] <= lqlib.cg_workspace_bytes((8, 8, 8, 8), "mixed_f32", 4)
+
+
+def test_lattices_argument_checks(lqlib):
+    L = lqlib.load()
+    vp = ctypes.c_void_p
+    specs = [((8, 8, 8, 8), 4), ((12, 12, 12, 12), 2)]
+    info = (lqlib.CgInfo * 8)()
+    ws = 0x4000000000
+
+    def call(arr, n=None, mode=1, flags=0, wsb=64):
+        prm = lqlib.CgParams(1e-10, 100, 0, 0.0, 0, flags)
+        return L.lq_cg_solve_lattices(len(arr) if n is None else n, arr, mode, ctypes.byref(prm), vp(ws),
+                                      ctypes.c_size_t(wsb), info, None)
+
+    good = _lattices(lqlib, specs)
+    assert call(good) == -5                          # workspace smaller than the query
+    assert call(good, n=0) == -1
+    assert call(good, n=9) == -1
+    assert call(good, mode=7) == -1
+    assert call(good, flags=lqlib.CG_PROFILE) == -1
+    assert call(good, flags=lqlib.CG_NATIVE_F64) == -1
+    assert call(good, flags=0x100 | 0x400) == -1     # two block sizes
+    assert call(_lattices(lqlib, [((8, 8, 8, 8), 3)])) == -1
+    assert call(_lattices(lqlib, [((8, 8, 7, 8), 1)])) == -2
+    bad = _lattices(lqlib, specs)
+    bad[1].x = bad[0].eta                            # a solution over another lattice's input
+    assert call(bad) == -3
+    bad = _lattices(lqlib, specs)
+    bad[1].x = bad[0].x                              # two solutions in one buffer
+    assert call(bad) == -3
+    bad = _lattices(lqlib, specs)
+    bad[0].U = 0
+    assert call(bad) == -1
+    bad = _lattices(lqlib, specs)
+    bad[0].m_q = float("inf")
+    assert call(bad) == -1
