@@ -61,13 +61,17 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+# the files the inner-loop kernels (K1, K2, K3 of the single-lattice solver) are built from
+KERNEL_SOURCES = ("lq_internal.cuh", "dd.cuh", "dslash_kernels.cuh", "dslash_dispatch.cuh", "solver_impl.cuh",
+                  "solver_f16.cu", "solver_f32.cu", "solver_f64.cu")
+
+
 def source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1904_08616_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, fn), "rb") as f:
-                h.update(fn.encode() + f.read())
+    for fn in KERNEL_SOURCES:
+        with open(os.path.join(csrc, fn), "rb") as f:
+            h.update(fn.encode() + f.read())
     return h.hexdigest()[:16]
 
 
@@ -334,6 +338,126 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------------------------
+# measurement legs for the other workloads (not the default line): uneven lattices in one
+# solve, 12 right-hand sides batched, and the large volume; each prints one JSON line
+# ------------------------------------------------------------------------------------
+def _timed(fn, steps, warmup):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts), out
+
+
+def _updates(dims, infos):
+    V = int(__import__("numpy").prod(dims))
+    return sum(2 * V * (i["iters"] + i["high_applies"]) for i in infos)
+
+
+def run_workload(args):
+    import numpy as np
+    import torch
+    import paper_1904_08616_gb300 as lq
+    import synth
+    lq.load()
+    dev = torch.device("cuda", 0)
+
+    def field(a):
+        return torch.from_numpy(a.view(np.uint8).reshape(-1)).to(dev)
+
+    def spinors(dims, seeds):
+        sb = lq.field_bytes(dims, "spinor", "f64")
+        out = torch.empty(len(seeds) * sb, dtype=torch.uint8, device=dev)
+        for r, sd in enumerate(seeds):
+            out[r * sb:(r + 1) * sb].copy_(torch.from_numpy(synth.gaussian_spinor(dims, seed=sd).view(np.uint8).reshape(-1)))
+        return out
+
+    line = {"workload": args.workload, "unit": "site-updates/s", "data": "synthetic", "steps": args.steps,
+            "warmup": args.warmup, "mode": args.mode}
+    if args.workload == "lattices":
+        specs = [((8, 8, 8, 8), 4), ((12, 12, 12, 12), 4), ((16, 16, 16, 32), 4)]
+        probs = []
+        for i, (dims, nr) in enumerate(specs):
+            probs.append({"dims": dims, "m_q": 0.1, "nrhs": nr, "U": field(synth.gauge_field(dims, seed=960 + 100 * i)),
+                          "eta": spinors(dims, [961 + 100 * i + r for r in range(nr)])})
+
+        def one():
+            xs, infos, st = lq.cg_solve_lattices(probs, mode=args.mode, tol=TOL, autotune=True)
+            assert st == 0
+            return infos
+
+        def seq():
+            allinf = []
+            for p in probs:
+                _, infos, st = lq.cg_solve_multi(p["dims"], 0.1, p["nrhs"], p["U"], p["eta"], mode=args.mode, tol=TOL)
+                assert st == 0
+                allinf.append(infos)
+            return allinf
+
+        ms, infos = _timed(one, args.steps, args.warmup)
+        ms_seq, _ = _timed(seq, args.steps, args.warmup)
+        upd = sum(_updates(p["dims"], inf) for p, inf in zip(probs, infos))
+        line.update({"config": {"lattices": [list(d) + [n] for d, n in specs], "m_q": 0.1, "links": "haar",
+                                "tol": TOL},
+                     "value": upd / (ms * 1e-3), "ms_per_solve": ms, "ms_sequential_multi": ms_seq,
+                     "block": infos[0][0]["block"], "iters": [max(i["iters"] for i in li) for li in infos]})
+    elif args.workload == "batched":
+        dims, nr = (24, 24, 24, 48), 12
+        U_d = field(synth.gauge_field(dims, seed=5))
+        eta_d = spinors(dims, [500 + r for r in range(nr)])
+        sb = lq.field_bytes(dims, "spinor", "f64")
+
+        def multi():
+            _, infos, st = lq.cg_solve_multi(dims, 0.1, nr, U_d, eta_d, mode=args.mode, tol=TOL)
+            assert st == 0
+            return infos
+
+        def single():
+            out = []
+            for r in range(nr):
+                _, info, st = lq.cg_solve(dims, 0.1, U_d, eta_d[r * sb:(r + 1) * sb], mode=args.mode, tol=TOL)
+                assert st == 0
+                out.append(info)
+            return out
+
+        ms, infos = _timed(multi, args.steps, args.warmup)
+        ms_single, _ = _timed(single, args.steps, args.warmup)
+        line.update({"config": {"lattice": list(dims), "nrhs": nr, "m_q": 0.1, "links": "haar", "tol": TOL},
+                     "value": _updates(dims, infos) / (ms * 1e-3), "ms_per_solve": ms,
+                     "ms_one_by_one": ms_single, "iters": max(i["iters"] for i in infos)})
+    elif args.workload == "large":
+        dims, nr = (64, 64, 64, 128), 4
+        U_d = field(synth.gauge_field(dims, seed=70, kind="haar"))
+        eta_d = spinors(dims, [72 + r for r in range(nr)])
+        res = {}
+        for m in (args.mode, "f64"):
+            torch.cuda.empty_cache()
+
+            def run(m=m):
+                _, infos, st = lq.cg_solve_multi(dims, 0.02, nr, U_d, eta_d, mode=m, tol=TOL)
+                assert st == 0
+                return infos
+
+            ms, infos = _timed(run, args.steps if m == args.mode else 1, args.warmup if m == args.mode else 0)
+            res[m] = {"ms": ms, "iters": max(i["iters"] for i in infos), "cycles": infos[0]["cycles"],
+                      "true_rel_resid": max(i["true_rel_resid"] for i in infos),
+                      "site_updates_per_s": _updates(dims, infos) / (ms * 1e-3)}
+        line.update({"config": {"lattice": list(dims), "nrhs": nr, "m_q": 0.02, "links": "haar", "tol": TOL},
+                     "value": res[args.mode]["site_updates_per_s"], "ms_per_solve": res[args.mode]["ms"],
+                     "solvers": res, "mixed_vs_fp64_speedup": res["f64"]["ms"] / res[args.mode]["ms"]})
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -343,7 +467,13 @@ def main():
     ap.add_argument("--mode", default="mixed_f16", choices=["mixed_f16", "mixed_f32", "f64", "f64x"])
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 / other-mode comparison solves")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--workload", default="cg32", choices=["cg32", "lattices", "batched", "large"],
+                    help="cg32: the 32^4 mixed-precision solve (the bench line); the others print a "
+                         "measurement line for the uneven-lattice, 12-RHS and 64^3x128 workloads")
     args = ap.parse_args()
+    if args.workload != "cg32":
+        run_workload(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

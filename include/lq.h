@@ -14,7 +14,7 @@
  * ----------------------------------------
  * Lattice: dims[4] = {Lx, Ly, Lz, Lt}; every extent must be even and >= 2, and the volume
  *   V = Lx*Ly*Lz*Lt must satisfy V <= 10^8 (the largest volume the paper considers), and
- *   V * nrhs <= 10^8 for calls on several fields.  Boundaries are periodic in all four
+ *   V * nrhs <= 2^28 (268,435,456) for calls on several fields.  Boundaries are periodic in all four
  *   directions.  Direction mu = 0, 1, 2, 3 is x, y, z, t.
  * Gamma matrices: chiral Euclidean basis, P^{-mu} = 1 - gamma_{mu+1}, P^{+mu} = 1 + gamma_{mu+1},
  *   gamma_k = [[0, -i sigma_k], [i sigma_k, 0]] (k = 1, 2, 3), gamma_4 = [[0, 1], [1, 0]],

@@ -57,6 +57,10 @@ using namespace lq;
 
 namespace {
 
+// site-fields per call: every 32-bit slot index of a multi-field spinor (at most 12 per
+// site-field) stays below 2^32
+constexpr int64_t kMaxSiteFields = int64_t(1) << 28;
+
 bool valid_prec(int p) { return p == LQ_F64 || p == LQ_F32 || p == LQ_F16S || p == LQ_F64X; }
 bool valid_layout(int l) { return l == LQ_LAYOUT_LEX || l == LQ_LAYOUT_EO; }
 bool valid_fmt(int f) { return f == LQ_LINK18 || f == LQ_LINK12; }
@@ -90,8 +94,8 @@ int do_apply(const int32_t dims[4], double m_q, int32_t prec, int32_t fmt, int32
     Geom g;
     int r;
     if ((r = check_dims(dims, &g)) != LQ_OK) return r;
-    if (nrhs < 1 || (int64_t)nrhs * g.V > 100000000LL)
-        return fail(LQ_ERR_ARG, "nrhs must be >= 1 with nrhs * V <= 10^8");
+    if (nrhs < 1 || (int64_t)nrhs * g.V > kMaxSiteFields)
+        return fail(LQ_ERR_ARG, "nrhs must be >= 1 with nrhs * V <= 2^28");
     if (layout == LQ_LAYOUT_EO && (nrhs & (nrhs - 1)) != 0)
         return fail(LQ_ERR_ARG, "EO fields interleave a power-of-two number of right-hand sides (got %d)", (int)nrhs);
     if (nrhs > 32 && layout == LQ_LAYOUT_EO) return fail(LQ_ERR_ARG, "at most 32 interleaved right-hand sides");
@@ -224,7 +228,8 @@ int lq_convert_spinor_multi(const int32_t dims[4], int32_t nrhs, int32_t src_pre
     Geom g;
     int r;
     if ((r = check_dims(dims, &g)) != LQ_OK) return r;
-    if (nrhs < 1 || (int64_t)nrhs * g.V > 100000000LL) return fail(LQ_ERR_ARG, "nrhs must be >= 1 with nrhs * V <= 10^8");
+    if (nrhs < 1 || (int64_t)nrhs * g.V > kMaxSiteFields)
+        return fail(LQ_ERR_ARG, "nrhs must be >= 1 with nrhs * V <= 2^28");
     if (!valid_prec(src_prec) || !valid_prec(dst_prec)) return fail(LQ_ERR_ARG, "bad precision");
     if (!valid_layout(src_layout) || !valid_layout(dst_layout)) return fail(LQ_ERR_ARG, "bad layout");
     if ((r = check_ptr(src, "src")) || (r = check_ptr(dst, "dst"))) return r;
@@ -269,7 +274,8 @@ int lq_cg_solve_multi(const int32_t dims[4], double m_q, int32_t mode, int32_t n
     Geom g;
     int r;
     if ((r = check_dims(dims, &g)) != LQ_OK) return r;
-    if (nrhs < 1 || (int64_t)nrhs * g.V > 100000000LL) return fail(LQ_ERR_ARG, "nrhs must be >= 1 with nrhs * V <= 10^8");
+    if (nrhs < 1 || (int64_t)nrhs * g.V > kMaxSiteFields)
+        return fail(LQ_ERR_ARG, "nrhs must be >= 1 with nrhs * V <= 2^28");
     if (mode != LQ_CG_F64 && mode != LQ_CG_MIXED_F32 && mode != LQ_CG_MIXED_F16 && mode != LQ_CG_F64X)
         return fail(LQ_ERR_ARG, "bad CG mode %d", (int)mode);
     if (!isfinite(m_q)) return fail(LQ_ERR_ARG, "m_q is not finite");
@@ -308,7 +314,7 @@ int check_lattices(int32_t n, const lq_lattice* lats, Geom* gs, int* nr) {
         if ((r = check_dims(lats[l].dims, &gs[l])) != LQ_OK) return r;
         const int k = lats[l].nrhs;
         if (k != 1 && k != 2 && k != 4 && k != 8) return fail(LQ_ERR_ARG, "lattice %d: nrhs must be 1, 2, 4 or 8", l);
-        if ((int64_t)k * gs[l].V > 100000000LL) return fail(LQ_ERR_ARG, "lattice %d: nrhs * V exceeds 10^8", l);
+        if ((int64_t)k * gs[l].V > kMaxSiteFields) return fail(LQ_ERR_ARG, "lattice %d: nrhs * V exceeds 2^28", l);
         nr[l] = k;
     }
     return LQ_OK;

@@ -204,7 +204,7 @@ LQ_HD uint32_t f22h2(float a, float b) {
 // ------------------------------------------------------------------------------------
 template <int PREC, int LAYOUT, bool RO> struct SpinorAcc;
 
-// Slot indices are 32-bit: the ABI caps V at 10^8 sites and V * nrhs at 10^8 site-fields
+// Slot indices are 32-bit: the ABI caps V at 10^8 sites and V * nrhs at 2^28 site-fields
 // per call, so every slot index of every field format (at most 36 V for FP64 18-real LEX
 // links, 12 V nrhs for FP64 spinors) stays below 2^32.
 struct EoIdx {

@@ -17,6 +17,8 @@ so these seeded fields stand in for them.
 """
 from __future__ import annotations
 
+import os
+
 import numpy as np
 
 __all__ = [
@@ -81,21 +83,55 @@ def near_identity_su3(rng: np.random.Generator, n: int, eps: float) -> np.ndarra
     return np.einsum("nij,nj,nkj->nik", v, ph, np.conj(v))
 
 
-def gauge_field(dims, seed: int, kind: str = "haar", eps: float = 0.3) -> np.ndarray:
+# Links drawn in one piece up to this many; larger fields are drawn in chunks of this size,
+# chunk k from the PCG64 stream of the seed jumped k times (chunk 0 is the plain stream), so
+# every field up to 32^4 sites is the one-piece draw and larger ones can be drawn in parallel.
+LINK_CHUNK = 1 << 22
+
+
+def _links(kind: str, eps: float, seed: int, k: int, n: int) -> np.ndarray:
+    bitgen = np.random.PCG64(int(seed))
+    rng = np.random.Generator(bitgen if k == 0 else bitgen.jumped(k))
+    if kind == "haar":
+        return haar_su3(rng, n)
+    if kind == "near_identity":
+        return near_identity_su3(rng, n, eps)
+    raise ValueError(f"unknown gauge kind {kind!r}")
+
+
+def _links_task(args):
+    return args[3], _links(*args)
+
+
+def gauge_field(dims, seed: int, kind: str = "haar", eps: float = 0.3, chunk: int = LINK_CHUNK,
+                workers: int | None = None) -> np.ndarray:
     """A seeded gauge field, complex128 (V, 4, 3, 3).
 
     kind = "haar": Haar-random SU(3) on every link (maximally rough, strong coupling).
     kind = "near_identity": exp(i*eps*H) on every link (close to the free field).
+    Fields of more than ``chunk`` links are drawn chunk by chunk (see LINK_CHUNK), on a pool
+    of ``workers`` spawned processes (default: the CPU count, at most 16).
     """
     v = volume(dims)
-    rng = make_rng(seed)
-    if kind == "haar":
-        u = haar_su3(rng, 4 * v)
-    elif kind == "near_identity":
-        u = near_identity_su3(rng, 4 * v, eps)
-    else:
+    if kind not in ("haar", "near_identity"):
         raise ValueError(f"unknown gauge kind {kind!r}")
-    return np.ascontiguousarray(u.reshape(v, 4, 3, 3))
+    n = 4 * v
+    if n <= chunk:
+        u = _links(kind, eps, seed, 0, n)
+        return np.ascontiguousarray(u.reshape(v, 4, 3, 3))
+    out = np.empty((n, 3, 3), dtype=np.complex128)
+    nchunks = (n + chunk - 1) // chunk
+    tasks = [(kind, eps, seed, k, min(chunk, n - k * chunk)) for k in range(nchunks)]
+    nw = workers if workers is not None else min(16, os.cpu_count() or 1)
+    if nw <= 1:
+        for t in tasks:
+            out[t[3] * chunk:t[3] * chunk + t[4]] = _links(*t)
+    else:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(nw) as pool:
+            for k, u in pool.imap_unordered(_links_task, tasks):
+                out[k * chunk:k * chunk + len(u)] = u
+    return out.reshape(v, 4, 3, 3)
 
 
 def unit_gauge_field(dims) -> np.ndarray:

@@ -84,6 +84,17 @@ def test_apply_argument_checks(lqlib):
     assert L.lq_dslash_adjoint((ctypes.c_int32 * 4)(4, 4, 4, 3), 0.1, 0, 18, 0, None, None, None, None) == -2
 
 
+def test_site_field_bound(lqlib):
+    """nrhs * V <= 2^28 per call (32-bit slot indices): 64^3 x 128 takes 8 fields, not 9."""
+    L = lqlib.load()
+    vp = ctypes.c_void_p
+    d = (ctypes.c_int32 * 4)(64, 64, 64, 128)
+    apply = lambda n: L.lq_dslash_apply_multi(d, 0.1, 0, 18, 0, n, vp(0), vp(0), vp(0), None)
+    assert apply(9) == -1 and "2^28" in lqlib.last_error()
+    assert apply(8) == -1 and "NULL" in lqlib.last_error()          # past the bound, stopped at U
+    assert lqlib.cg_workspace_bytes((64, 64, 64, 128), "mixed_f32", 4) > 0
+
+
 def test_hop_and_convert_argument_checks(lqlib):
     L = lqlib.load()
     vp = ctypes.c_void_p
