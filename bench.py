@@ -42,8 +42,8 @@ WORKLOAD = "mixed-precision CG to 1e-10 on 32^4, m_q=0.05, links exp(0.3iH)"
 
 # algorithmic bytes per site of the inner-loop kernels (each field read or written once)
 #   K1: p in, 4 links, t out.  K2: t in, 4 links, p, psi, r in, psi, r out.  K3: r, p in, p out.
-SPINOR_B = {"mixed_f16": 52, "mixed_f32": 96, "f64": 192, "f64x": 192}
-LINK4_B = {"mixed_f16": 96, "mixed_f32": 192, "f64": 576, "f64x": 576}
+SPINOR_B = {"mixed_f16": 52, "mixed_f32": 96, "f64": 192, "f64x": 192, "mixed_i32": 100}
+LINK4_B = {"mixed_f16": 96, "mixed_f32": 192, "f64": 576, "f64x": 576, "mixed_i32": 192}
 
 
 def kernel_bytes(mode):
@@ -204,7 +204,7 @@ def run_ours(args, rank, world, local_rank):
     x_d = torch.zeros_like(eta_d)
     mode = args.mode
     # one workspace large enough for every mode this run solves with
-    ws = torch.empty(max(lq.cg_workspace_bytes(DIMS, m) for m in ("f64", "f64x", "mixed_f32", "mixed_f16")),
+    ws = torch.empty(max(lq.cg_workspace_bytes(DIMS, m) for m in ("f64", "f64x", "mixed_f32", "mixed_f16", "mixed_i32")),
                      dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -270,7 +270,7 @@ def run_ours(args, rank, world, local_rank):
     # same system (one run each after one warm run)
     compare = {}
     if not args.no_compare:
-        others = [m for m in ("f64", "f64x", "mixed_f32", "mixed_f16") if m != mode]
+        others = [m for m in ("f64", "f64x", "mixed_f32", "mixed_f16", "mixed_i32") if m != mode]
         for m in others:
             solve(m)
             torch.cuda.synchronize()
@@ -316,7 +316,8 @@ def run_ours(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"mixed_f16": "f32 (f16s storage) inner / f32-pair (fp64-class) outer",
                                        "mixed_f32": "f32 inner / f32-pair (fp64-class) outer",
-                                       "f64": "f64", "f64x": "f32-pair (fp64-class)"}[mode],
+                                       "f64": "f64", "f64x": "f32-pair (fp64-class)",
+                                       "mixed_i32": "f32 (i32 fixed-point storage) inner / f32-pair outer"}[mode],
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "lattice": list(DIMS), "m_q": MASS, "links": "exp(0.3iH), 12-real inner",
                    "inner": mode, "tol": TOL, "rhs_per_gpu": 1,
@@ -464,7 +465,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="mixed_f16", choices=["mixed_f16", "mixed_f32", "f64", "f64x"])
+    ap.add_argument("--mode", default="mixed_f16", choices=["mixed_f16", "mixed_f32", "f64", "f64x", "mixed_i32"])
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 / other-mode comparison solves")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--workload", default="cg32", choices=["cg32", "lattices", "batched", "large"],

@@ -28,8 +28,9 @@
  *   into fixed-width chunks per site; chunk k of site (p, cb) is stored at chunk slot
  *     spinor:  (p*K + k)*Vh + cb
  *     gauge :  ((mu*2 + p)*K + k)*Vh + cb
- *   chunk widths in reals: spinor F64 2, F32 4, F16S 8; gauge LINK18 2 (all precisions),
- *   LINK12 F64 2, F32 4, F16S 4; K = reals per site (24) or per link (18/12) / width.
+ *   chunk widths in reals: spinor F64 2, F32 4, F16S 8, I32S 4; gauge LINK18 2 (all
+ *   precisions), LINK12 F64 2, F32 4, F16S 4, I32S 4; K = reals per site (24) or per link
+ *   (18/12) / width.
  * Precisions (element types of the stored fields):
  *   LQ_F64  double; LQ_F32 float;
  *   LQ_F16S spinors: per site s = max |fl32(v)| over its 24 reals (float) and 24 halves
@@ -41,15 +42,27 @@
  *           LQ_F64 field with every double replaced by (hi, lo) (same size and slots).
  *           Arithmetic: FP32-pair ("double-float") arithmetic, about 2^-47 relative, run on
  *           the FP32 pipes (GB300 executes FP64 at 1/63 of its FP32 rate).  LINK18 only.
- *   Arithmetic is FP64 for LQ_F64, FP32 pairs for LQ_F64X, FP32 for LQ_F32 / LQ_F16S.
+ *   LQ_I32S 32-bit fixed point (Q1.30), the paper's FPGA-friendly format (Section 2.2):
+ *           spinors: per site s = max |fl32(v)| over its 24 reals (float) and 24 int32
+ *           q = RN(v / s * 2^30) (computed in FP64, ties to even; q = 0 if s = 0); all
+ *           integers first (96 V bytes, in the layout's order), then the V float scales
+ *           (EO: scale of (p, cb) at p*Vh + cb).  The stored value is q * s * 2^-30.
+ *           gauge fields: int32 q = RN(u * 2^30) with no scale (entries must satisfy
+ *           |u| < 2, as unitary links do).
+ *   Arithmetic is FP64 for LQ_F64, FP32 pairs for LQ_F64X, FP32 for LQ_F32 / LQ_F16S /
+ *   LQ_I32S.
  *   Kernel outputs in LQ_F16S use one reciprocal of the scale per site (h = fl16(v * fl32(1/s)));
  *   lq_convert_spinor divides every component (h = fl16(fl32(v) / s)) and is bit-exact.
+ *   Kernel outputs in LQ_I32S use q = RN(fl32(v) * fl32(2^30 / s)) in FP32; lq_convert_spinor
+ *   uses the FP64 definition above and is bit-exact.
  *
  * Several fields (right-hand sides) at once, nrhs of them:
  *   LEX: nrhs complete fields one after the other (field r at byte offset r * field size).
  *   EO : interleaved per site: chunk k of (p, cb) of field r at chunk slot
- *        ((p*K + k)*Vh + cb)*nrhs + r (F16S: all halves, then the scale of (p, cb, r) at
- *        (p*Vh + cb)*nrhs + r); for nrhs = 1 this is the single-field EO layout.  The
+ *        ((p*K + k)*Vh + cb)*nrhs + r (F16S / I32S: all elements, then the scale of
+ *        (p, cb, r) at (p*Vh + cb)*nrhs + r); for nrhs = 1 this is the single-field EO
+ *        layout.  LEX stacks complete fields (F16S / I32S: each field's elements, then its
+ *        scales).  The
  *        fields of one site sit side by side, so a batched kernel reads each link once for
  *        all of them.  EO multi-field buffers hold a power of two (<= 32) of fields.
  *
@@ -84,7 +97,7 @@ typedef enum lq_status {
     LQ_ERR_BREAKDOWN = -7     /* <p, D^dag D p> <= 0: the operator or the inputs are broken */
 } lq_status;
 
-typedef enum lq_prec { LQ_F64 = 0, LQ_F32 = 1, LQ_F16S = 2, LQ_F64X = 3 } lq_prec;
+typedef enum lq_prec { LQ_F64 = 0, LQ_F32 = 1, LQ_F16S = 2, LQ_F64X = 3, LQ_I32S = 4 } lq_prec;
 typedef enum lq_link_fmt { LQ_LINK18 = 18, LQ_LINK12 = 12 } lq_link_fmt;
 typedef enum lq_layout { LQ_LAYOUT_LEX = 0, LQ_LAYOUT_EO = 1 } lq_layout;
 
@@ -135,7 +148,7 @@ int lq_dslash_adjoint_multi(const int32_t dims[4], double m_q, int32_t prec, int
  *   out_p = a * y_p + b * H_{p,1-p} psi_{1-p},   H = 1/2 sum_mu [ ... ] of Eq. (1),
  * on the half lattice of parity out_parity (the even-odd split of Eq. 1; the paper does
  * not use it, it is this library's fast layout).  LQ_LAYOUT_EO only.  psi_other, y and out
- * are half fields: Vh sites of one parity, chunk slot k*Vh + cb (F16S: halves then the Vh
+ * are half fields: Vh sites of one parity, chunk slot k*Vh + cb (F16S / I32S: elements then the Vh
  * scales).  y may be NULL (then a is ignored); y may equal out.  dagger != 0 uses the
  * hopping term of D^dag.  One kernel launch.
  */
@@ -169,7 +182,9 @@ typedef enum lq_cg_mode {
     LQ_CG_F64 = 0,        /* FP64 throughout (plain CG, true residual checked in FP64)     */
     LQ_CG_MIXED_F32 = 1,  /* Algorithm 1: FP32 inner loop (EO layout, 12-real links), FP64 outer */
     LQ_CG_MIXED_F16 = 2,  /* Algorithm 1: scaled-FP16 inner storage, FP32 arithmetic, FP64 outer */
-    LQ_CG_F64X = 3        /* FP64-class CG in FP32-pair arithmetic throughout (LQ_F64X)     */
+    LQ_CG_F64X = 3,       /* FP64-class CG in FP32-pair arithmetic throughout (LQ_F64X)     */
+    LQ_CG_MIXED_I32 = 4   /* Algorithm 1: 32-bit fixed-point inner storage (LQ_I32S), FP32
+                             arithmetic, FP64 outer (not offered for lattice batches)      */
 } lq_cg_mode;
 
 typedef struct lq_cg_params {

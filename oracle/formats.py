@@ -14,6 +14,11 @@ Scaled FP16 spinors ("f16s"): per site, s = max over the 24 reals of |fl32(v)| (
 number) and h = fl16(fl32(v) / s), the division in FP32 with round-to-nearest-even and the
 conversion to FP16 round-to-nearest-even (h = 0 when s = 0).  The stored value of a
 component is the exact product h * s.  FP16 links are fl16(fl32(v)) with no scale.
+
+32-bit fixed-point spinors ("i32s", Q1.30): per site the same FP32 scale s and the integers
+q = RN(v / s * 2^30) computed in FP64 (ties to even; q = 0 when s = 0); the stored value is
+q * s * 2^-30.  Fixed-point links are q = RN(v * 2^30) with no scale.  Scaled formats keep
+all elements first and the per-site scales after them.
 """
 from __future__ import annotations
 
@@ -21,8 +26,10 @@ import numpy as np
 
 from . import reconstruct12
 
-PRECS = ("f64", "f32", "f16s", "f64x")
-_ELEM = {"f64": np.float64, "f32": np.float32, "f16s": np.float16}
+PRECS = ("f64", "f32", "f16s", "f64x", "i32s")
+_ELEM = {"f64": np.float64, "f32": np.float32, "f16s": np.float16, "i32s": np.int32}
+_SCALED = ("f16s", "i32s")
+Q30 = float(2 ** 30)
 
 
 def _vol(dims) -> int:
@@ -44,13 +51,13 @@ def eo_site_map(dims):
 
 # chunk widths (number of reals per chunk) of the eo layout; f64x uses the f64 slots
 def _spinor_chunk(prec):
-    return {"f64": 2, "f64x": 2, "f32": 4, "f16s": 8}[prec]
+    return {"f64": 2, "f64x": 2, "f32": 4, "f16s": 8, "i32s": 4}[prec]
 
 
 def _link_chunk(prec, fmt):
     if fmt == 18:
         return 2
-    return {"f64": 2, "f64x": 2, "f32": 4, "f16s": 4}[prec]
+    return {"f64": 2, "f64x": 2, "f32": 4, "f16s": 4, "i32s": 4}[prec]
 
 
 def _pairs(v):
@@ -73,6 +80,8 @@ def _round(v, prec):
         return v.copy()
     if prec == "f32":
         return v.astype(np.float32)
+    if prec == "i32s":
+        return np.rint(v * Q30).astype(np.int32)
     return v.astype(np.float32).astype(np.float16)
 
 
@@ -81,7 +90,7 @@ def _round(v, prec):
 # ------------------------------------------------------------------------------------
 def spinor_bytes(dims, prec) -> int:
     V = _vol(dims)
-    return {"f64": 192 * V, "f64x": 192 * V, "f32": 96 * V, "f16s": 52 * V}[prec]
+    return {"f64": 192 * V, "f64x": 192 * V, "f32": 96 * V, "f16s": 52 * V, "i32s": 100 * V}[prec]
 
 
 def _f16s_encode_sites(reals):
@@ -95,6 +104,16 @@ def _f16s_encode_sites(reals):
     return h, s
 
 
+def _i32s_encode_sites(reals):
+    """reals: float64 (V, 24) -> (integers (V, 24) int32, scales (V,) float32)."""
+    v = np.asarray(reals, dtype=np.float64)
+    s = np.max(np.abs(v.astype(np.float32)), axis=1).astype(np.float32)
+    safe = np.where(s > 0, s, np.float32(1.0)).astype(np.float64)
+    q = np.rint(v / safe[:, None] * Q30).astype(np.int32)
+    q[s == 0] = 0
+    return q, s
+
+
 def encode_spinor(psi, dims, prec="f64", layout="lex") -> np.ndarray:
     """complex (V, 4, 3) -> the stored buffer as a flat uint8 array."""
     V = _vol(dims)
@@ -103,6 +122,8 @@ def encode_spinor(psi, dims, prec="f64", layout="lex") -> np.ndarray:
     if prec == "f16s":
         h, s = _f16s_encode_sites(reals)
         data = h
+    elif prec == "i32s":
+        data, s = _i32s_encode_sites(reals)
     elif prec == "f64x":
         data = reals
         s = None
@@ -137,7 +158,7 @@ def decode_spinor(buf, dims, prec="f64", layout="lex") -> np.ndarray:
         elem = _ELEM[prec]
         nb = V * 24 * np.dtype(elem).itemsize
         data = buf[:nb].view(elem).reshape(V, 24)
-    s = buf[nb:].view(np.float32) if prec == "f16s" else None
+    s = buf[nb:].view(np.float32) if prec in _SCALED else None
     if layout == "eo":
         data = _from_eo_spinor(data.reshape(-1), dims, _spinor_chunk(prec))
         if s is not None:
@@ -145,7 +166,8 @@ def decode_spinor(buf, dims, prec="f64", layout="lex") -> np.ndarray:
             s = s[p * (V // 2) + cb]
     vals = data.astype(np.float64)
     if s is not None:
-        vals = vals * s.astype(np.float64)[:, None]
+        sc = s.astype(np.float64) * (1.0 / Q30 if prec == "i32s" else 1.0)
+        vals = vals * sc[:, None]
     return np.ascontiguousarray(vals).view(np.complex128).reshape(V, 4, 3)
 
 
@@ -172,7 +194,7 @@ def _from_eo_spinor(flat, dims, w):
 # ------------------------------------------------------------------------------------
 def gauge_bytes(dims, prec, fmt) -> int:
     V = _vol(dims)
-    per = {"f64": 8, "f64x": 8, "f32": 4, "f16s": 2}[prec]
+    per = {"f64": 8, "f64x": 8, "f32": 4, "f16s": 2, "i32s": 4}[prec]
     return V * 4 * fmt * per
 
 
@@ -200,6 +222,8 @@ def decode_gauge(buf, dims, prec="f64", fmt=18, layout="lex") -> np.ndarray:
     if layout == "eo":
         data = _from_eo_gauge(data, dims, fmt, _link_chunk(prec, fmt))
     vals = np.ascontiguousarray(data.reshape(V, 4, fmt).astype(np.float64))
+    if prec == "i32s":
+        vals = vals / Q30
     c = vals.view(np.complex128).reshape(V, 4, fmt // 6, 3)
     if fmt == 12:
         c = reconstruct12(c)
@@ -236,10 +260,11 @@ def encode_spinor_multi(psis, dims, prec="f64", layout="lex") -> np.ndarray:
         return np.concatenate([encode_spinor(p, dims, prec, "lex") for p in psis])
     V = _vol(dims)
     singles = [encode_spinor(p, dims, prec, "eo") for p in psis]
-    if prec == "f16s":
-        halves = np.stack([b[:48 * V].view(np.uint8).reshape(-1, 16) for b in singles], axis=1)   # slot, field, 16 B
-        scales = np.stack([b[48 * V:].view(np.float32) for b in singles], axis=1)                 # site, field
-        return np.concatenate([halves.reshape(-1), np.ascontiguousarray(scales).view(np.uint8).reshape(-1)])
+    if prec in _SCALED:
+        nd = (48 if prec == "f16s" else 96) * V
+        elems = np.stack([b[:nd].view(np.uint8).reshape(-1, 16) for b in singles], axis=1)        # slot, field, 16 B
+        scales = np.stack([b[nd:].view(np.float32) for b in singles], axis=1)                    # site, field
+        return np.concatenate([elems.reshape(-1), np.ascontiguousarray(scales).view(np.uint8).reshape(-1)])
     chunks = np.stack([b.reshape(-1, 16) for b in singles], axis=1)                               # slot, field, 16 B
     return np.ascontiguousarray(chunks).reshape(-1)
 
@@ -251,10 +276,11 @@ def decode_spinor_multi(buf, dims, n, prec="f64", layout="lex"):
     if layout == "lex":
         return [decode_spinor(buf[i * one:(i + 1) * one], dims, prec, "lex") for i in range(n)]
     V = _vol(dims)
-    if prec == "f16s":
-        halves = buf[:48 * V * n].reshape(-1, n, 16)
-        scales = buf[48 * V * n:].view(np.float32).reshape(-1, n)
-        return [decode_spinor(np.concatenate([np.ascontiguousarray(halves[:, i]).reshape(-1),
+    if prec in _SCALED:
+        nd = (48 if prec == "f16s" else 96) * V
+        elems = buf[:nd * n].reshape(-1, n, 16)
+        scales = buf[nd * n:].view(np.float32).reshape(-1, n)
+        return [decode_spinor(np.concatenate([np.ascontiguousarray(elems[:, i]).reshape(-1),
                                               np.ascontiguousarray(scales[:, i]).view(np.uint8).reshape(-1)]),
                               dims, prec, "eo") for i in range(n)]
     chunks = buf.reshape(-1, n, 16)

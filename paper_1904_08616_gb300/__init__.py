@@ -25,9 +25,9 @@ __all__ = [
     "last_error", "version",
 ]
 
-PREC = {"f64": 0, "f32": 1, "f16s": 2, "f64x": 3}
+PREC = {"f64": 0, "f32": 1, "f16s": 2, "f64x": 3, "i32s": 4}
 LAYOUT = {"lex": 0, "eo": 1}
-CG_MODE = {"f64": 0, "mixed_f32": 1, "mixed_f16": 2, "f64x": 3}
+CG_MODE = {"f64": 0, "mixed_f32": 1, "mixed_f16": 2, "f64x": 3, "mixed_i32": 4}
 CG_PROFILE, CG_NATIVE_F64, CG_LINK18, CG_AUTOTUNE, CG_NO_GRAPH = 1, 2, 4, 8, 16
 STATUS = {0: "OK", 1: "NOT_CONVERGED", -1: "ERR_ARG", -2: "ERR_DIMS", -3: "ERR_ALIGN",
           -4: "ERR_CUDA", -5: "ERR_WORKSPACE", -6: "ERR_NONFINITE", -7: "ERR_BREAKDOWN"}

@@ -36,6 +36,7 @@ size_t spinor_bytes(int64_t nsites, int prec) {
         case LQ_F64X: return (size_t)nsites * 192;
         case LQ_F32: return (size_t)nsites * 96;
         case LQ_F16S: return (size_t)nsites * 52;
+        case LQ_I32S: return (size_t)nsites * 100;
         default: return 0;
     }
 }
@@ -45,7 +46,8 @@ size_t gauge_bytes(int64_t V, int prec, int fmt) {
     switch (prec) {
         case LQ_F64:
         case LQ_F64X: return (size_t)V * 4 * fmt * 8;
-        case LQ_F32: return (size_t)V * 4 * fmt * 4;
+        case LQ_F32:
+        case LQ_I32S: return (size_t)V * 4 * fmt * 4;
         case LQ_F16S: return (size_t)V * 4 * fmt * 2;
         default: return 0;
     }
@@ -61,9 +63,12 @@ namespace {
 // site-field) stays below 2^32
 constexpr int64_t kMaxSiteFields = int64_t(1) << 28;
 
-bool valid_prec(int p) { return p == LQ_F64 || p == LQ_F32 || p == LQ_F16S || p == LQ_F64X; }
+bool valid_prec(int p) { return p == LQ_F64 || p == LQ_F32 || p == LQ_F16S || p == LQ_F64X || p == LQ_I32S; }
 bool valid_layout(int l) { return l == LQ_LAYOUT_LEX || l == LQ_LAYOUT_EO; }
 bool valid_fmt(int f) { return f == LQ_LINK18 || f == LQ_LINK12; }
+bool valid_cg_mode(int m) {
+    return m == LQ_CG_F64 || m == LQ_CG_MIXED_F32 || m == LQ_CG_MIXED_F16 || m == LQ_CG_F64X || m == LQ_CG_MIXED_I32;
+}
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 bool overlap(const void* a, size_t na, const void* b, size_t nb) {
     const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
@@ -119,14 +124,15 @@ int do_apply(const int32_t dims[4], double m_q, int32_t prec, int32_t fmt, int32
         } else {
             while ((1 << (lnr + 1)) <= nrhs - first && lnr < 5) ++lnr;
         }
-        // F16S stacked fields keep each field's scales after its halves; batch them one by one
-        if (prec == LQ_F16S && layout == LQ_LAYOUT_LEX) lnr = 0;
+        // scaled stacked fields keep each field's scales after its elements; batch them one by one
+        if ((prec == LQ_F16S || prec == LQ_I32S) && layout == LQ_LAYOUT_LEX) lnr = 0;
         const void* pin = (const char*)psi + (layout == LQ_LAYOUT_LEX ? field * first : 0);
         void* pout = (char*)out + (layout == LQ_LAYOUT_LEX ? field * first : 0);
         cudaError_t e;
         if (prec == LQ_F64) e = apply_f64(g, m_q, fmt, layout, dag, U, pin, pout, st, lnr);
         else if (prec == LQ_F64X) e = apply_f64x(g, m_q, fmt, layout, dag, U, pin, pout, st, lnr);
         else if (prec == LQ_F32) e = apply_f32(g, m_q, fmt, layout, dag, U, pin, pout, st, lnr);
+        else if (prec == LQ_I32S) e = apply_i32(g, m_q, fmt, layout, dag, U, pin, pout, st, lnr);
         else e = apply_f16(g, m_q, fmt, layout, dag, U, pin, pout, st, lnr);
         if (e != cudaSuccess) return cuda_fail(e, dag ? "dslash_adjoint launch" : "dslash_apply launch");
         first += 1 << lnr;
@@ -189,6 +195,7 @@ int lq_dslash_hop(const int32_t dims[4], int32_t out_parity, int32_t dagger, dou
     if (prec == LQ_F64) e = hop_f64(g, out_parity, dag, a, b, link_fmt, U, psi_other, y, out, st);
     else if (prec == LQ_F64X) e = hop_f64x(g, out_parity, dag, a, b, link_fmt, U, psi_other, y, out, st);
     else if (prec == LQ_F32) e = hop_f32(g, out_parity, dag, a, b, link_fmt, U, psi_other, y, out, st);
+    else if (prec == LQ_I32S) e = hop_i32(g, out_parity, dag, a, b, link_fmt, U, psi_other, y, out, st);
     else e = hop_f16(g, out_parity, dag, a, b, link_fmt, U, psi_other, y, out, st);
     if (e != cudaSuccess) return cuda_fail(e, "dslash_hop launch");
     return LQ_OK;
@@ -261,7 +268,7 @@ int lq_convert_gauge(const int32_t dims[4], int32_t src_prec, int32_t src_layout
 size_t lq_cg_workspace_bytes_multi(const int32_t dims[4], int32_t mode, int32_t nrhs) {
     Geom g;
     if (check_dims(dims, &g) != LQ_OK || nrhs < 1) return 0;
-    if (mode != LQ_CG_F64 && mode != LQ_CG_MIXED_F32 && mode != LQ_CG_MIXED_F16 && mode != LQ_CG_F64X) return 0;
+    if (!valid_cg_mode(mode)) return 0;
     return cg_workspace_bytes(g, mode, nrhs);
 }
 
@@ -276,8 +283,7 @@ int lq_cg_solve_multi(const int32_t dims[4], double m_q, int32_t mode, int32_t n
     if ((r = check_dims(dims, &g)) != LQ_OK) return r;
     if (nrhs < 1 || (int64_t)nrhs * g.V > kMaxSiteFields)
         return fail(LQ_ERR_ARG, "nrhs must be >= 1 with nrhs * V <= 2^28");
-    if (mode != LQ_CG_F64 && mode != LQ_CG_MIXED_F32 && mode != LQ_CG_MIXED_F16 && mode != LQ_CG_F64X)
-        return fail(LQ_ERR_ARG, "bad CG mode %d", (int)mode);
+    if (!valid_cg_mode(mode)) return fail(LQ_ERR_ARG, "bad CG mode %d", (int)mode);
     if (!isfinite(m_q)) return fail(LQ_ERR_ARG, "m_q is not finite");
     lq_cg_params prm{1e-10, 100000, 0, 0.0, 0, 0};
     if (params) prm = *params;
@@ -301,6 +307,7 @@ namespace {
 
 constexpr int kMaxLattices = 8;
 
+// lattice batches: every mode but LQ_CG_MIXED_I32
 bool valid_mode(int mode) {
     return mode == LQ_CG_F64 || mode == LQ_CG_MIXED_F32 || mode == LQ_CG_MIXED_F16 || mode == LQ_CG_F64X;
 }

@@ -14,7 +14,7 @@ constexpr int kConvBS = 256;
 __host__ __device__ inline int base_prec(int prec) { return prec == LQ_F64X ? LQ_F64 : prec; }
 __host__ __device__ inline int spinor_chunk(int prec) {
     prec = base_prec(prec);
-    return prec == LQ_F64 ? 2 : (prec == LQ_F32 ? 4 : 8);
+    return prec == LQ_F64 ? 2 : (prec == LQ_F16S ? 8 : 4);
 }
 __host__ __device__ inline int link_chunk(int prec, int fmt) {
     prec = base_prec(prec);
@@ -28,18 +28,22 @@ struct FieldDesc {
 
 // element index of real j of a spinor site of right-hand side s.rhs among nr (LEX: nr
 // stacked complete fields; EO: right-hand sides interleaved per chunk slot).  A stacked
-// F16S field is 26 V halves (24 V halves, then V float scales), so field r's halves start
-// at 26 V r and its scales at float 13 V r + 12 V.
+// scaled field is its 24 V elements followed by its V float scales: 26 V halves (F16S)
+// or 25 V 4-byte words (I32S) per field.
 __device__ inline int64_t sp_elem(const FieldDesc& f, const Geom& g, const Site& s, int j, int nr) {
     if (f.layout == LQ_LAYOUT_LEX) {
-        const int64_t field = (f.prec == LQ_F16S) ? 26 * (int64_t)g.V : 24 * (int64_t)g.V;
+        const int64_t field = (f.prec == LQ_F16S ? 26 : (f.prec == LQ_I32S ? 25 : 24)) * (int64_t)g.V;
         return s.rhs * field + (int64_t)s.lex * 24 + j;
     }
     const int w = spinor_chunk(f.prec), K = 24 / w;
     return ((((int64_t)s.p * K + j / w) * g.Vh + s.cb) * nr + s.rhs) * w + (j % w);
 }
-// index (in floats from the buffer start) of the scale of a site of an F16S field
+// index (in floats from the buffer start) of the scale of a site of a scaled field
 __device__ inline int64_t sp_scale_idx(const FieldDesc& f, const Geom& g, const Site& s, int nr) {
+    if (f.prec == LQ_I32S) {
+        if (f.layout == LQ_LAYOUT_LEX) return 25 * (int64_t)g.V * s.rhs + 24 * (int64_t)g.V + s.lex;
+        return 24 * (int64_t)g.V * nr + ((int64_t)s.p * g.Vh + s.cb) * nr + s.rhs;
+    }
     if (f.layout == LQ_LAYOUT_LEX) return 13 * (int64_t)g.V * s.rhs + 12 * (int64_t)g.V + s.lex;
     return 12 * (int64_t)g.V * nr + ((int64_t)s.p * g.Vh + s.cb) * nr + s.rhs;
 }
@@ -54,6 +58,7 @@ __device__ inline double load_real(const void* base, int prec, int64_t i) {
     if (prec == LQ_F64) return ((const double*)base)[i];
     if (prec == LQ_F64X) return (double)((const float*)base)[2 * i] + (double)((const float*)base)[2 * i + 1];
     if (prec == LQ_F32) return (double)((const float*)base)[i];
+    if (prec == LQ_I32S) return (double)((const int*)base)[i];      // the integer; callers scale it
     return (double)__half2float(((const __half*)base)[i]);
 }
 
@@ -77,6 +82,8 @@ __global__ void __launch_bounds__(kConvBS) convert_spinor_kernel(Geom g, FieldDe
         double sc = 1.0;
         if (src.prec == LQ_F16S)
             sc = (double)((const float*)src.ptr)[sp_scale_idx(src, g, s, nr)];
+        else if (src.prec == LQ_I32S)
+            sc = (double)((const float*)src.ptr)[sp_scale_idx(src, g, s, nr)] * 0x1p-30;
 #pragma unroll
         for (int j = 0; j < 24; ++j) v[j] = load_real(src.ptr, src.prec, sp_elem(src, g, s, j, nr)) * sc;
         if (dst.prec == LQ_F64 || dst.prec == LQ_F64X) {
@@ -85,6 +92,16 @@ __global__ void __launch_bounds__(kConvBS) convert_spinor_kernel(Geom g, FieldDe
         } else if (dst.prec == LQ_F32) {
 #pragma unroll
             for (int j = 0; j < 24; ++j) ((float*)dst.ptr)[sp_elem(dst, g, s, j, nr)] = (float)v[j];
+        } else if (dst.prec == LQ_I32S) {
+            // s = max |fl32(v)|, q = RN(v / s * 2^30) in FP64, ties to even
+            float m = 0.f;
+#pragma unroll
+            for (int j = 0; j < 24; ++j) m = fmaxf(m, fabsf((float)v[j]));
+            ((float*)dst.ptr)[sp_scale_idx(dst, g, s, nr)] = m;
+            const bool z = !(m > 0.f);
+#pragma unroll
+            for (int j = 0; j < 24; ++j)
+                ((int*)dst.ptr)[sp_elem(dst, g, s, j, nr)] = z ? 0 : __double2int_rn(v[j] / (double)m * 0x1p30);
         } else {
             float fv[24];
             float m = 0.f;
@@ -105,10 +122,12 @@ __global__ void __launch_bounds__(kConvBS) convert_gauge_kernel(Geom g, FieldDes
         const Site s = site_from_lex(g, lex, c);
         for (int mu = 0; mu < 4; ++mu) {
             for (int j = 0; j < dst.fmt; ++j) {
-                const double v = load_real(src.ptr, src.prec, lk_elem(src, g, s, mu, j));
+                double v = load_real(src.ptr, src.prec, lk_elem(src, g, s, mu, j));
+                if (src.prec == LQ_I32S) v *= 0x1p-30;
                 const int64_t i = lk_elem(dst, g, s, mu, j);
                 if (dst.prec == LQ_F64 || dst.prec == LQ_F64X) store_wide(dst.ptr, dst.prec, i, v);
                 else if (dst.prec == LQ_F32) ((float*)dst.ptr)[i] = (float)v;
+                else if (dst.prec == LQ_I32S) ((int*)dst.ptr)[i] = __double2int_rn(v * 0x1p30);   // Q1.30
                 else ((__half*)dst.ptr)[i] = __float2half_rn((float)v);
             }
         }

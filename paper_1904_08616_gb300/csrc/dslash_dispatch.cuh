@@ -22,6 +22,9 @@ inline SpinorAcc<PREC, LAYOUT, RO> make_spinor(const void* buf, const Geom& g, b
         a.ptr = (double2*)buf;
     } else if constexpr (PREC == LQ_F32 || PREC == LQ_F64X) {
         a.ptr = (float4*)buf;
+    } else if constexpr (PREC == LQ_I32S) {
+        a.ptr = (int4*)buf;
+        a.scale = (float*)((char*)buf + 96 * nsites);
     } else {
         a.ptr = (uint4*)buf;
         a.scale = (float*)((char*)buf + 48 * nsites);
@@ -79,7 +82,7 @@ cudaError_t run_hop(const Geom& g, int p, double a, double b, const void* U, con
     return launch_stencil<kApplyBS>(MapEoHalf<kApplyBS>{g, p}, sten, epi, st);
 }
 
-// Dispatch entry points, one set per precision (defined in dslash_f64/f32/f16/f64x.cu);
+// Dispatch entry points, one set per precision (defined in dslash_f64/f32/f16/f64x/i32.cu);
 // the applies act on 2^lnr fields.
 cudaError_t apply_f64(const Geom& g, double m_q, int fmt, int layout, bool dag, const void* U, const void* psi, void* out, cudaStream_t st, int lnr);
 cudaError_t apply_f32(const Geom& g, double m_q, int fmt, int layout, bool dag, const void* U, const void* psi, void* out, cudaStream_t st, int lnr);
@@ -89,6 +92,8 @@ cudaError_t hop_f32(const Geom& g, int p, bool dag, double a, double b, int fmt,
 cudaError_t hop_f16(const Geom& g, int p, bool dag, double a, double b, int fmt, const void* U, const void* psi_other, const void* y, void* out, cudaStream_t st);
 cudaError_t apply_f64x(const Geom& g, double m_q, int fmt, int layout, bool dag, const void* U, const void* psi, void* out, cudaStream_t st, int lnr);
 cudaError_t hop_f64x(const Geom& g, int p, bool dag, double a, double b, int fmt, const void* U, const void* psi_other, const void* y, void* out, cudaStream_t st);
+cudaError_t apply_i32(const Geom& g, double m_q, int fmt, int layout, bool dag, const void* U, const void* psi, void* out, cudaStream_t st, int lnr);
+cudaError_t hop_i32(const Geom& g, int p, bool dag, double a, double b, int fmt, const void* U, const void* psi_other, const void* y, void* out, cudaStream_t st);
 
 }  // namespace lq
 

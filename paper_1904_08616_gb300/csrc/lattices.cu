@@ -130,7 +130,7 @@ int cg_solve_lattices(int n, const Geom* gs, const lq_lattice* lats, int mode, c
         jobs[l].x = lats[l].x;
     }
     double delta = prm.delta;
-    if (!(delta > 0.0)) delta = (mode == LQ_CG_MIXED_F32) ? 1e-4 : (mode == LQ_CG_MIXED_F16 ? 0.1 : 0.0);
+    if (!(delta > 0.0)) delta = default_delta(mode);
     char* w = (char*)ws;
     switch (mode) {
         case LQ_CG_F64: return lattices_f64(n, jobs, prm, delta, w, info, st);

@@ -62,6 +62,7 @@ template <> struct PrecT<LQ_F64> { using Real = double; };
 template <> struct PrecT<LQ_F32> { using Real = float; };
 template <> struct PrecT<LQ_F16S> { using Real = float; };
 template <> struct PrecT<LQ_F64X> { using Real = dd; };
+template <> struct PrecT<LQ_I32S> { using Real = float; };
 
 LQ_HD float to_float(float x) { return x; }
 LQ_HD float to_float(double x) { return (float)x; }
@@ -340,6 +341,66 @@ template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F16S, LAYOUT, RO> {
     }
 };
 
+// 32-bit fixed point (Q1.30): an integer q stands for q * 2^-30, times the site's FP32
+// scale s = max |fl32(v)| for spinors.  Loads convert q to FP32 (rounding to 24 bits) and
+// fold s * 2^-30 into the caller's accumulation; stores scale by the correctly rounded
+// 2^30 / s and round to the nearest integer (ties to even).
+constexpr float kQ30 = 1073741824.0f;           // 2^30
+constexpr float kInvQ30 = 9.31322574615478515625e-10f;   // 2^-30
+
+LQ_HD int f2i_rn(float x) {
+#ifdef __CUDA_ARCH__
+    return __float2int_rn(x);
+#else
+    return (int)nearbyintf(x);
+#endif
+}
+
+template <int LAYOUT, bool RO> struct SpinorAcc<LQ_I32S, LAYOUT, RO> {
+    using Real = float;
+    static constexpr int K = 6;
+    static constexpr bool kScaled = true;
+    int4* ptr;
+    float* scale;
+    EoIdx e;
+    // the stored integers as floats, and s * 2^-30 separately
+    LQ_HD void load_raw(const Site& s, Spinor<float>& out, float& sc) const {
+        const uint32_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
+        sc = ld<RO>(scale + sp_sidx<LAYOUT>(s, e)) * kInvQ30;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const int4 w = ld<RO>(ptr + b + k * ks);
+            out.v[2 * k] = {(float)w.x, (float)w.y};
+            out.v[2 * k + 1] = {(float)w.z, (float)w.w};
+        }
+    }
+    template <typename T> LQ_HD void load(const Site& s, Spinor<T>& out) const {
+        const uint32_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
+        const T sc = (T)ld<RO>(scale + sp_sidx<LAYOUT>(s, e)) * (T)kInvQ30;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const int4 w = ld<RO>(ptr + b + k * ks);
+            out.v[2 * k] = {(T)w.x * sc, (T)w.y * sc};
+            out.v[2 * k + 1] = {(T)w.z * sc, (T)w.w * sc};
+        }
+    }
+    template <typename T> LQ_HD void store(const Site& s, const Spinor<T>& in) const {
+        const uint32_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
+        float f[24];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) { f[2 * k] = to_float(in.v[k].re); f[2 * k + 1] = to_float(in.v[k].im); }
+        float m = 0.f;
+#pragma unroll
+        for (int k = 0; k < 24; ++k) m = fmaxf(m, fabsf(f[k]));
+        scale[sp_sidx<LAYOUT>(s, e)] = m;
+        const float inv = (m > 0.f) ? div_rn(kQ30, m) : 0.f;
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            ptr[b + k * ks] = make_int4(f2i_rn(f[4 * k] * inv), f2i_rn(f[4 * k + 1] * inv), f2i_rn(f[4 * k + 2] * inv),
+                                        f2i_rn(f[4 * k + 3] * inv));
+    }
+};
+
 // FP32 pairs: the LQ_F64 layout with every double replaced by (hi, lo); one float4 chunk
 // is one complex number (re.hi, re.lo, im.hi, im.lo).
 template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F64X, LAYOUT, RO> {
@@ -478,6 +539,39 @@ template <int LAYOUT> struct GaugeAcc<LQ_F16S, 12, LAYOUT> {
             const int c0 = 2 * k, c1 = 2 * k + 1;
             U.u[c0 / 3][c0 % 3] = {a.x, a.y};
             U.u[c1 / 3][c1 % 3] = {c.x, c.y};
+        }
+        reconstruct_row2(U);
+    }
+};
+
+// Q1.30 links (no scale; |entries| < 2): int2 chunks (LINK18) or int4 chunks (LINK12)
+template <int LAYOUT> struct GaugeAcc<LQ_I32S, 18, LAYOUT> {
+    using Real = float;
+    static constexpr int K = 9;
+    const int2* ptr;
+    uint32_t Vh;
+    LQ_HD void load(const Site& s, int mu, Link<float>& U) const {
+        const uint32_t b = lk_base<LAYOUT>(s, mu, K, Vh), ks = lk_kstride<LAYOUT>(Vh);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const int2 v = ld<true>(ptr + b + k * ks);
+            U.u[k / 3][k % 3] = {(float)v.x * kInvQ30, (float)v.y * kInvQ30};
+        }
+    }
+};
+template <int LAYOUT> struct GaugeAcc<LQ_I32S, 12, LAYOUT> {
+    using Real = float;
+    static constexpr int K = 3;
+    const int4* ptr;
+    uint32_t Vh;
+    LQ_HD void load(const Site& s, int mu, Link<float>& U) const {
+        const uint32_t b = lk_base<LAYOUT>(s, mu, K, Vh), ks = lk_kstride<LAYOUT>(Vh);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int4 w = ld<true>(ptr + b + k * ks);
+            const int c0 = 2 * k, c1 = 2 * k + 1;
+            U.u[c0 / 3][c0 % 3] = {(float)w.x * kInvQ30, (float)w.y * kInvQ30};
+            U.u[c1 / 3][c1 % 3] = {(float)w.z * kInvQ30, (float)w.w * kInvQ30};
         }
         reconstruct_row2(U);
     }

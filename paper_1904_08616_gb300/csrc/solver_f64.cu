@@ -25,7 +25,8 @@ int cg_solve(const Geom& g, double m_q, int mode, int nrhs, const void* U, const
     using namespace solver_detail;
     const bool native = (prm.flags & LQ_CG_NATIVE_F64) != 0;
     if (mode == LQ_CG_F64X && native) return fail(LQ_ERR_ARG, "LQ_CG_NATIVE_F64 does not apply to LQ_CG_F64X");
-    const bool pairs = (mode == LQ_CG_F64X) || ((mode == LQ_CG_MIXED_F32 || mode == LQ_CG_MIXED_F16) && !native);
+    const bool mixed = mode == LQ_CG_MIXED_F32 || mode == LQ_CG_MIXED_F16 || mode == LQ_CG_MIXED_I32;
+    const bool pairs = (mode == LQ_CG_F64X) || (mixed && !native);
     const int fmt = (prm.flags & LQ_CG_LINK18) ? 18 : 12;
     {
         const WsLayout w = ws_layout(g, mode, pairs, fmt, batch_size(nrhs));
@@ -33,7 +34,7 @@ int cg_solve(const Geom& g, double m_q, int mode, int nrhs, const void* U, const
             return fail(LQ_ERR_WORKSPACE, "workspace of %zu bytes needed, %zu given", w.total, ws_bytes);
     }
     double delta = prm.delta;
-    if (!(delta > 0.0)) delta = (mode == LQ_CG_MIXED_F32) ? 1e-4 : (mode == LQ_CG_MIXED_F16 ? 0.1 : 0.0);
+    if (!(delta > 0.0)) delta = default_delta(mode);
     // batches of a power of two <= kMaxRhs right-hand sides, each sharing the link loads
     const size_t field = spinor_bytes(g.V, LQ_F64);
     int worst = LQ_OK;
@@ -52,6 +53,9 @@ int cg_solve(const Geom& g, double m_q, int mode, int nrhs, const void* U, const
                 break;
             case LQ_CG_MIXED_F16:
                 r = solve_mixed_f16(g, m_q, nb, U, eb, xb, prm, delta, w, (char*)ws, ib, st, pairs, fmt);
+                break;
+            case LQ_CG_MIXED_I32:
+                r = solve_mixed_i32(g, m_q, nb, U, eb, xb, prm, delta, w, (char*)ws, ib, st, pairs, fmt);
                 break;
             default: return fail(LQ_ERR_ARG, "unknown CG mode %d", mode);
         }

@@ -503,8 +503,21 @@ inline int inner_prec(int mode) {
     switch (mode) {
         case LQ_CG_MIXED_F32: return LQ_F32;
         case LQ_CG_MIXED_F16: return LQ_F16S;
+        case LQ_CG_MIXED_I32: return LQ_I32S;
         case LQ_CG_F64X: return LQ_F64X;
         default: return LQ_F64;
+    }
+}
+
+// default inner reduction delta of Algorithm 1 per mode (the paper gives none): FP32-class
+// inner arithmetic and storage 1e-4, scaled-FP16 storage 0.1, FP64-class inner 0 (run to
+// the target)
+inline double default_delta(int mode) {
+    switch (mode) {
+        case LQ_CG_MIXED_F32:
+        case LQ_CG_MIXED_I32: return 1e-4;
+        case LQ_CG_MIXED_F16: return 0.1;
+        default: return 0.0;
     }
 }
 
@@ -527,7 +540,8 @@ inline WsLayout ws_layout(const Geom& g, int mode, bool pair_outer, int inner_fm
         w.x_x = take(spinor_bytes(Vn, LQ_F64X));
     }
     const int ip = inner_prec(mode);
-    if (mode == LQ_CG_MIXED_F32 || mode == LQ_CG_MIXED_F16) w.u_low = take(gauge_bytes(g.V, ip, inner_fmt));
+    if (mode == LQ_CG_MIXED_F32 || mode == LQ_CG_MIXED_F16 || mode == LQ_CG_MIXED_I32)
+        w.u_low = take(gauge_bytes(g.V, ip, inner_fmt));
     const size_t lo = spinor_bytes(Vn, ip);
     w.psi = take(lo);
     w.r = take(lo);
@@ -788,7 +802,7 @@ struct Solve {
                 return cuda_fail(e, "FP32-pair copies");
             launches += 3;
         }
-        if constexpr (IP == LQ_F32 || IP == LQ_F16S) {
+        if constexpr (IP != LQ_F64 && IP != LQ_F64X) {   // reduced-precision inner links
             if ((e = convert_gauge(g, LQ_F64, LQ_LAYOUT_LEX, U, IP, IF, IL, ws + w.u_low, st)) != cudaSuccess)
                 return cuda_fail(e, "link pack");
             launches += 1;
@@ -1030,8 +1044,9 @@ int run_solver(const Geom& g, double m_q, int nb, const void* U, const void* eta
     return sv.finish(info);
 }
 
-// Instantiations live in solver_f64.cu (FP64 and FP32-pair inner loops), solver_f32.cu
-// and solver_f16.cu (mixed inner loops with either outer arithmetic and link format).
+// Instantiations live in solver_f64.cu (FP64 and FP32-pair inner loops), solver_f32.cu,
+// solver_f16.cu and solver_i32.cu (mixed inner loops with either outer arithmetic and link
+// format).
 int solve_f64(const Geom& g, double m_q, int nb, const void* U, const void* eta, void* x, const lq_cg_params& prm,
               double delta, const WsLayout& w, char* ws, lq_cg_info* info, cudaStream_t st);
 int solve_f64x(const Geom& g, double m_q, int nb, const void* U, const void* eta, void* x, const lq_cg_params& prm,
@@ -1040,6 +1055,9 @@ int solve_mixed_f32(const Geom& g, double m_q, int nb, const void* U, const void
                     const lq_cg_params& prm, double delta, const WsLayout& w, char* ws, lq_cg_info* info,
                     cudaStream_t st, bool pairs, int fmt);
 int solve_mixed_f16(const Geom& g, double m_q, int nb, const void* U, const void* eta, void* x,
+                    const lq_cg_params& prm, double delta, const WsLayout& w, char* ws, lq_cg_info* info,
+                    cudaStream_t st, bool pairs, int fmt);
+int solve_mixed_i32(const Geom& g, double m_q, int nb, const void* U, const void* eta, void* x,
                     const lq_cg_params& prm, double delta, const WsLayout& w, char* ws, lq_cg_info* info,
                     cudaStream_t st, bool pairs, int fmt);
 

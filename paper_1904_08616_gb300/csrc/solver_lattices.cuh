@@ -252,7 +252,7 @@ double time_k1(int n, const LatticeJob* jobs, char* ws, cudaStream_t st) {
         if (cudaMemsetAsync(sv[l].dstate, 0, sizeof(SolverState), st) != cudaSuccess ||
             cudaMemsetAsync(ws + j.off + j.w.p, 0x3c, spinor_bytes((int64_t)j.g.V * j.nb, IP), st) != cudaSuccess)
             return -1.0;
-        if constexpr (IP == LQ_F32 || IP == LQ_F16S) {
+        if constexpr (IP != LQ_F64 && IP != LQ_F64X) {
             if (convert_gauge(j.g, LQ_F64, LQ_LAYOUT_LEX, j.U, IP, IF, IL, ws + j.off + j.w.u_low, st) != cudaSuccess)
                 return -1.0;
         } else if constexpr (IP == LQ_F64X) {

@@ -32,7 +32,7 @@ def _true_resid(dims, m, U, eta, x):
     return np.linalg.norm(r.ravel()) / np.linalg.norm(eta.ravel())
 
 
-MODES = ["f64", "f64x", "mixed_f32", "mixed_f16"]
+MODES = ["f64", "f64x", "mixed_f32", "mixed_f16", "mixed_i32"]
 
 
 @pytest.mark.parametrize("mode", MODES)
@@ -85,7 +85,7 @@ def test_cg_near_identity_ragged(lqlib, mode):
         assert info["cycles"] >= 2
 
 
-@pytest.mark.parametrize("mode", ["mixed_f32", "mixed_f16"])
+@pytest.mark.parametrize("mode", ["mixed_f32", "mixed_f16", "mixed_i32"])
 @pytest.mark.parametrize("native_f64,link18", [(True, False), (False, True), (True, True)])
 def test_cg_outer_arithmetic_and_link_format(lqlib, mode, native_f64, link18):
     """The solver options: native FP64 outer arithmetic instead of FP32 pairs, and 18-real
@@ -143,7 +143,7 @@ def test_cg_workspace_too_small(lqlib):
         lqlib.cg_solve(dims, 0.1, U, eta, workspace=ws)
 
 
-@pytest.mark.parametrize("mode", ["mixed_f32", "mixed_f16", "f64", "f64x"])
+@pytest.mark.parametrize("mode", ["mixed_f32", "mixed_f16", "f64", "f64x", "mixed_i32"])
 def test_cg_full_size_32(lqlib, mode):
     """The mixed-precision workload at full size: 32^4, links exp(0.3 i H), m_q = 0.05,
     tolerance 1e-10; the oracle recomputes the true residual in FP64."""

@@ -19,7 +19,7 @@ from fieldio import eo_embed, eo_half, to_dev, to_host
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-13, "f64x": 1e-13, "f32": 1e-6, "f16s": 1e-3}
+TOL = {"f64": 1e-13, "f64x": 1e-13, "f32": 1e-6, "f16s": 1e-3, "i32s": 1e-6}
 # 2^4 aliases n+mu and n-mu; (6, 4, 10, 2) has V = 480, a ragged last tile for 128 threads
 LATTICES = [(2, 2, 2, 2), (4, 4, 4, 4), (4, 6, 2, 8), (6, 4, 10, 2)]
 
@@ -33,7 +33,7 @@ def _fields(dims, seed, kind="haar"):
 @pytest.mark.parametrize("dims", LATTICES)
 @pytest.mark.parametrize("layout", ["lex", "eo"])
 @pytest.mark.parametrize("fmt", [18, 12])
-@pytest.mark.parametrize("prec", ["f64", "f64x", "f32", "f16s"])
+@pytest.mark.parametrize("prec", ["f64", "f64x", "f32", "f16s", "i32s"])
 @pytest.mark.parametrize("dagger", [False, True])
 def test_dslash_matches_oracle(lqlib, dims, layout, fmt, prec, dagger):
     if prec == "f64x" and fmt == 12:
@@ -51,7 +51,7 @@ def test_dslash_matches_oracle(lqlib, dims, layout, fmt, prec, dagger):
 
 
 @pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 10, 2)])
-@pytest.mark.parametrize("prec", ["f32", "f16s", "f64x"])
+@pytest.mark.parametrize("prec", ["f32", "f16s", "f64x", "i32s"])
 @pytest.mark.parametrize("layout", ["lex", "eo"])
 def test_convert_spinor_bit_exact(lqlib, dims, prec, layout):
     psi = synth.gaussian_spinor(dims, seed=7) * np.exp(np.linspace(-8, 8, synth.volume(dims)))[:, None, None]
@@ -66,7 +66,7 @@ def test_convert_spinor_bit_exact(lqlib, dims, prec, layout):
 
 
 @pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 10, 2)])
-@pytest.mark.parametrize("prec", ["f64", "f32", "f16s", "f64x"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16s", "f64x", "i32s"])
 @pytest.mark.parametrize("fmt", [18, 12])
 @pytest.mark.parametrize("layout", ["lex", "eo"])
 def test_convert_gauge_bit_exact(lqlib, dims, prec, fmt, layout):
@@ -79,7 +79,7 @@ def test_convert_gauge_bit_exact(lqlib, dims, prec, fmt, layout):
 
 
 @pytest.mark.parametrize("dims", [(4, 4, 4, 4), (2, 2, 2, 2), (6, 4, 10, 2)])
-@pytest.mark.parametrize("prec", ["f64", "f64x", "f32", "f16s"])
+@pytest.mark.parametrize("prec", ["f64", "f64x", "f32", "f16s", "i32s"])
 @pytest.mark.parametrize("fmt", [18, 12])
 @pytest.mark.parametrize("dagger", [False, True])
 def test_hop_matches_oracle(lqlib, dims, prec, fmt, dagger):
@@ -151,7 +151,8 @@ def big_fields():
 
 
 @pytest.mark.parametrize("prec,fmt,layout", [("f32", 12, "eo"), ("f16s", 12, "eo"), ("f64", 18, "lex"),
-                                             ("f64x", 18, "eo"), ("f32", 18, "eo"), ("f16s", 18, "eo")])
+                                             ("f64x", 18, "eo"), ("f32", 18, "eo"), ("f16s", 18, "eo"),
+                                             ("i32s", 12, "eo")])
 @pytest.mark.parametrize("dagger", [False, True])
 def test_full_size_sampled_sites(lqlib, big_fields, prec, fmt, layout, dagger):
     """32^4 (the mixed-precision workload), in the launch configuration of the solver's

@@ -10,11 +10,11 @@ from fieldio import to_dev, to_host
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-13, "f64x": 1e-13, "f32": 1e-6, "f16s": 1e-3}
+TOL = {"f64": 1e-13, "f64x": 1e-13, "f32": 1e-6, "f16s": 1e-3, "i32s": 1e-6}
 RESID_SLACK = 1.001
 
 
-@pytest.mark.parametrize("prec,fmt", [("f64", 18), ("f32", 12), ("f16s", 12), ("f64x", 18)])
+@pytest.mark.parametrize("prec,fmt", [("f64", 18), ("f32", 12), ("f16s", 12), ("f64x", 18), ("i32s", 12)])
 @pytest.mark.parametrize("layout,nrhs", [("eo", 2), ("eo", 4), ("eo", 8), ("lex", 3), ("lex", 5)])
 @pytest.mark.parametrize("dagger", [False, True])
 def test_multi_apply_matches_oracle(lqlib, prec, fmt, layout, nrhs, dagger):
@@ -51,7 +51,7 @@ def test_multi_apply_equals_single_applies(lqlib, prec):
         assert np.array_equal(got[i], F.decode_spinor(to_host(single), dims, prec, "eo"))
 
 
-@pytest.mark.parametrize("prec", ["f32", "f16s", "f64x"])
+@pytest.mark.parametrize("prec", ["f32", "f16s", "f64x", "i32s"])
 @pytest.mark.parametrize("nrhs", [2, 4])
 def test_multi_convert_bit_exact(lqlib, prec, nrhs):
     dims = (4, 4, 2, 6)
@@ -79,7 +79,7 @@ def _true_resid(dims, m, U, eta, x):
     return np.linalg.norm(r.ravel()) / np.linalg.norm(eta.ravel())
 
 
-@pytest.mark.parametrize("mode", ["mixed_f32", "mixed_f16", "f64x", "f64"])
+@pytest.mark.parametrize("mode", ["mixed_f32", "mixed_f16", "f64x", "f64", "mixed_i32"])
 @pytest.mark.parametrize("nrhs", [1, 3, 4, 12])
 def test_cg_multi_against_oracle(lqlib, mode, nrhs):
     """nrhs = 3 runs as batches 2 + 1, 12 as 8 + 4; every solve meets the tolerance and

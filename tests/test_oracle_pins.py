@@ -351,6 +351,33 @@ def test_f16s_encoding_pins():
     assert oracle.rel_l2(dec, psi) < 1e-3
 
 
+def test_i32s_encoding_pins():
+    """32-bit fixed point (Q1.30 with a per-site scale): zero sites encode to zero; the
+    largest component of a site encodes to 2^30 up to the FP32 rounding of the scale; every
+    stored value is within half a quantum (s 2^-31) of the input."""
+    from oracle import formats as F
+    dims = (2, 2, 2, 2)
+    psi = synth.gaussian_spinor(dims, seed=94) * np.exp(np.linspace(-20, 20, 16))[:, None, None]
+    psi[5] = 0.0
+    buf = F.encode_spinor(psi, dims, "i32s", "lex")
+    V = synth.volume(dims)
+    assert buf.size == 100 * V
+    q = buf[:96 * V].view(np.int32).reshape(V, 24)
+    s = buf[96 * V:].view(np.float32).astype(np.float64)
+    assert s[5] == 0 and np.all(q[5] == 0)
+    qmax = np.max(np.abs(q.astype(np.int64)), axis=1)
+    nz = s > 0
+    assert np.all(np.abs(qmax[nz] - 2 ** 30) <= 2 ** 7)
+    reals = np.ascontiguousarray(psi).view(np.float64).reshape(V, 24)
+    dec = F.decode_spinor(buf, dims, "i32s", "lex")
+    err = np.abs(np.ascontiguousarray(dec).view(np.float64).reshape(V, 24) - reals)
+    assert np.all(err <= (s * 2.0 ** -31)[:, None] * (1 + 1e-9))
+    # links: Q1.30 without a scale, error <= 2^-31 per entry
+    U = synth.gauge_field(dims, seed=95)
+    Ud = F.decode_gauge(F.encode_gauge(U, dims, "i32s", 18, "lex"), dims, "i32s", 18, "lex")
+    assert np.abs(Ud - U).max() <= 2.0 ** -31 * np.sqrt(2) * (1 + 1e-9)
+
+
 def test_eo_layout_roundtrip_and_parity_blocks():
     from oracle import formats as F
     dims = (4, 2, 2, 6)
