@@ -436,6 +436,25 @@ def run_workload(args):
         line.update({"config": {"lattice": list(dims), "nrhs": nr, "m_q": 0.1, "links": "haar", "tol": TOL},
                      "value": _updates(dims, infos) / (ms * 1e-3), "ms_per_solve": ms,
                      "ms_one_by_one": ms_single, "iters": max(i["iters"] for i in infos)})
+    elif args.workload == "schur":
+        # D x = b on the 32^4 workload: the even-odd Schur solve against solving D^dag D x = D^dag b
+        U, b = make_inputs()
+        U_d, b_d = field(U), field(b)
+        eta_d = lq.dslash_adjoint(DIMS, MASS, U_d, b_d)
+        res = {}
+        for name, fn in (("schur", lambda: lq.cg_solve_schur(DIMS, MASS, U_d, b_d, mode=args.mode, tol=TOL)),
+                         ("normal_equations", lambda: lq.cg_solve(DIMS, MASS, U_d, eta_d, mode=args.mode, tol=TOL))):
+            def run(fn=fn):
+                out = fn()
+                assert out[2] == 0
+                return out[1][0] if isinstance(out[1], list) else out[1]
+            ms, info = _timed(run, args.steps, args.warmup)
+            res[name] = {"ms": ms, "iters": info["iters"], "cycles": info["cycles"],
+                         "true_rel_resid": info["true_rel_resid"]}
+        line.update({"config": {"lattice": list(DIMS), "m_q": MASS, "links": "exp(0.3iH)", "tol": TOL,
+                                "system": "D x = b"},
+                     "value": None, "unit": "ms", "solvers": res,
+                     "schur_speedup": res["normal_equations"]["ms"] / res["schur"]["ms"]})
     elif args.workload == "large":
         dims, nr = (64, 64, 64, 128), 4
         U_d = field(synth.gauge_field(dims, seed=70, kind="haar"))
@@ -468,7 +487,7 @@ def main():
     ap.add_argument("--mode", default="mixed_f16", choices=["mixed_f16", "mixed_f32", "f64", "f64x", "mixed_i32"])
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 / other-mode comparison solves")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--workload", default="cg32", choices=["cg32", "lattices", "batched", "large"],
+    ap.add_argument("--workload", default="cg32", choices=["cg32", "lattices", "batched", "large", "schur"],
                     help="cg32: the 32^4 mixed-precision solve (the bench line); the others print a "
                          "measurement line for the uneven-lattice, 12-RHS and 64^3x128 workloads")
     args = ap.parse_args()

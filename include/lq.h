@@ -297,6 +297,30 @@ int lq_cg_solve_multi(const int32_t dims[4], double m_q, int32_t mode, int32_t n
                       void *workspace, size_t ws_bytes, lq_cg_info *info, void *cuda_stream);
 
 /*
+ * lq_cg_solve_schur -- solves D x_r = b_r (not D^dag D) for nrhs right-hand sides with the
+ * even-odd Schur complement (not in the paper, which inverts D^dag D; the even-odd split of
+ * Eq. 1 is this library's): with A = m_q + 4 and H the hopping term of Eq. (1),
+ *   Mhat = A - H_eo H_oe / A on the even sites,  bhat_e = b_e - H_eo b_o / A,
+ *   Mhat^dag Mhat x_e = Mhat^dag bhat_e by CG (Algorithm 1 in the mixed modes),
+ *   x_o = (b_o - H_oe x_e) / A.
+ * Every operator application is two half-lattice hops, the vectors are half fields, and
+ * Mhat^dag Mhat is better conditioned than D^dag D.
+ *   mode     LQ_CG_F64X, LQ_CG_MIXED_F32, LQ_CG_MIXED_F16 or LQ_CG_MIXED_I32 (the outer loop
+ *            runs in FP32 pairs; LQ_CG_F64 and LQ_CG_NATIVE_F64 are rejected).
+ *   b, x     nrhs stacked FP64 LEX fields; x holds the starting guess (its even half is used)
+ *            and receives the solution.
+ *   tol      relative to the normal equations: stop when
+ *            ||Mhat^dag (bhat - Mhat x_e)|| <= tol ||Mhat^dag bhat||; info->true_rel_resid
+ *            reports that ratio.
+ *   workspace at least lq_cg_workspace_bytes_schur(dims, mode, nrhs) bytes.
+ * Other arguments and the return value as lq_cg_solve_multi.
+ */
+size_t lq_cg_workspace_bytes_schur(const int32_t dims[4], int32_t mode, int32_t nrhs);
+int lq_cg_solve_schur(const int32_t dims[4], double m_q, int32_t mode, int32_t nrhs,
+                      const void *U, const void *b, void *x, const lq_cg_params *params,
+                      void *workspace, size_t ws_bytes, lq_cg_info *info, void *cuda_stream);
+
+/*
  * lq_cg_solve_lattices -- several independent problems, on lattices of different sizes,
  * solved together: for each lattice l, D_l^dag D_l x_{l,r} = eta_{l,r} for its nrhs
  * right-hand sides (Algorithm 1, or plain CG in LQ_CG_F64, per right-hand side as in

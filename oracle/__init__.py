@@ -276,3 +276,9 @@ def solve_grads(dims, m_q, U, eta, chi, tol=1e-13):
     Dx = dslash(dims, m_q, U, x)
     Dy = dslash(dims, m_q, U, y)
     return y, -(link_grad(dims, Dx, y) + link_grad(dims, Dy, x))
+
+
+def solve_d(dims, m_q, U, b, tol: float = 1e-13):
+    """x with D x = b (Eq. 1), through the textbook CG on D^dag D x = D^dag b.
+    Returns (x, iterations, true relative residual of the normal equations)."""
+    return cg(dims, m_q, U, dslash(dims, m_q, U, b, dagger=True), tol=tol)

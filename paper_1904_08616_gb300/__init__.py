@@ -22,6 +22,7 @@ __all__ = [
     "field_bytes", "dslash_apply", "dslash_adjoint", "dslash_apply_multi", "dslash_adjoint_multi",
     "dslash_hop", "link_grad", "convert_spinor", "convert_spinor_multi", "convert_gauge", "cg_workspace_bytes",
     "cg_solve", "cg_solve_multi", "cg_workspace_bytes_lattices", "cg_solve_lattices",
+    "cg_workspace_bytes_schur", "cg_solve_schur",
     "last_error", "version",
 ]
 
@@ -101,6 +102,11 @@ def load(build_if_missing: bool = True):
         L.lq_cg_solve_multi.argtypes = [_Dims, f64, i32, i32, _vp, _vp, _vp, ctypes.POINTER(CgParams), _vp,
                                         ctypes.c_size_t, ctypes.POINTER(CgInfo), _vp]
         L.lq_cg_solve_multi.restype = ctypes.c_int
+        L.lq_cg_workspace_bytes_schur.argtypes = [_Dims, i32, i32]
+        L.lq_cg_workspace_bytes_schur.restype = ctypes.c_size_t
+        L.lq_cg_solve_schur.argtypes = [_Dims, f64, i32, i32, _vp, _vp, _vp, ctypes.POINTER(CgParams), _vp,
+                                        ctypes.c_size_t, ctypes.POINTER(CgInfo), _vp]
+        L.lq_cg_solve_schur.restype = ctypes.c_int
         L.lq_cg_workspace_bytes_lattices.argtypes = [i32, ctypes.POINTER(Lattice), i32]
         L.lq_cg_workspace_bytes_lattices.restype = ctypes.c_size_t
         L.lq_cg_solve_lattices.argtypes = [i32, ctypes.POINTER(Lattice), i32, ctypes.POINTER(CgParams), _vp,
@@ -334,6 +340,36 @@ def cg_solve_multi(dims, m_q, nrhs, U, eta, x=None, mode="f64", tol=1e-10, max_i
     prm = CgParams(float(tol), int(max_iter), int(max_cycles), float(delta), int(chunk), flags)
     infos = (CgInfo * n)()
     st = load().lq_cg_solve_multi(_dims(dims), float(m_q), m, n, _ptr(U, gb, "U"), _ptr(eta, sb, "eta"),
+                                  _ptr(x, sb, "x"), ctypes.byref(prm), _ptr(workspace, wb, "workspace"),
+                                  ctypes.c_size_t(workspace.numel() * workspace.element_size()), infos,
+                                  _stream(stream))
+    _check(st)
+    return x, [_info_dict(infos[i]) for i in range(n)], st
+
+
+def cg_workspace_bytes_schur(dims, mode="mixed_f32", nrhs=1) -> int:
+    m = CG_MODE[mode] if isinstance(mode, str) else int(mode)
+    return int(load().lq_cg_workspace_bytes_schur(_dims(dims), m, int(nrhs)))
+
+
+def cg_solve_schur(dims, m_q, U, b, x=None, nrhs=1, mode="mixed_f32", tol=1e-10, max_iter=100000, max_cycles=0,
+                   delta=0.0, chunk=0, workspace=None, stream=None, profile=False, link18=False):
+    """Solve D x = b (nrhs stacked FP64 LEX fields) by the even-odd Schur complement.
+    Returns (x, [info per right-hand side], status)."""
+    import torch
+    m = CG_MODE[mode] if isinstance(mode, str) else int(mode)
+    n = int(nrhs)
+    sb = field_bytes(dims, "spinor", "f64") * n
+    gb = field_bytes(dims, "gauge", "f64", 18)
+    if x is None:
+        x = torch.zeros_like(b)
+    wb = cg_workspace_bytes_schur(dims, m, n)
+    if workspace is None:
+        workspace = _empty_bytes(wb, b)
+    flags = (CG_PROFILE if profile else 0) | (CG_LINK18 if link18 else 0)
+    prm = CgParams(float(tol), int(max_iter), int(max_cycles), float(delta), int(chunk), flags)
+    infos = (CgInfo * n)()
+    st = load().lq_cg_solve_schur(_dims(dims), float(m_q), m, n, _ptr(U, gb, "U"), _ptr(b, sb, "b"),
                                   _ptr(x, sb, "x"), ctypes.byref(prm), _ptr(workspace, wb, "workspace"),
                                   ctypes.c_size_t(workspace.numel() * workspace.element_size()), infos,
                                   _stream(stream))

@@ -380,6 +380,42 @@ int lq_cg_solve_lattices(int32_t n, const lq_lattice* lats, int32_t mode, const 
     return cg_solve_lattices(n, gs, lats, mode, prm, workspace, ws_bytes, info, (cudaStream_t)cuda_stream);
 }
 
+size_t lq_cg_workspace_bytes_schur(const int32_t dims[4], int32_t mode, int32_t nrhs) {
+    Geom g;
+    if (check_dims(dims, &g) != LQ_OK || nrhs < 1 || (int64_t)nrhs * g.V > kMaxSiteFields) return 0;
+    if (!valid_cg_mode(mode) || mode == LQ_CG_F64) return 0;
+    return cg_workspace_bytes_schur(g, mode, nrhs);
+}
+
+int lq_cg_solve_schur(const int32_t dims[4], double m_q, int32_t mode, int32_t nrhs, const void* U, const void* b,
+                      void* x, const lq_cg_params* params, void* workspace, size_t ws_bytes, lq_cg_info* info,
+                      void* cuda_stream) {
+    if (info && nrhs > 0) memset(info, 0, sizeof(*info) * (size_t)nrhs);
+    Geom g;
+    int r;
+    if ((r = check_dims(dims, &g)) != LQ_OK) return r;
+    if (nrhs < 1 || (int64_t)nrhs * g.V > kMaxSiteFields)
+        return fail(LQ_ERR_ARG, "nrhs must be >= 1 with nrhs * V <= 2^28");
+    if (!valid_cg_mode(mode)) return fail(LQ_ERR_ARG, "bad CG mode %d", (int)mode);
+    if (!isfinite(m_q)) return fail(LQ_ERR_ARG, "m_q is not finite");
+    lq_cg_params prm{1e-10, 100000, 0, 0.0, 0, 0};
+    if (params) prm = *params;
+    if (!(prm.tol > 0.0) || !isfinite(prm.tol)) return fail(LQ_ERR_ARG, "tol must be positive and finite");
+    if (prm.max_iter < 1) return fail(LQ_ERR_ARG, "max_iter must be >= 1");
+    if (prm.max_cycles < 0 || prm.chunk < 0) return fail(LQ_ERR_ARG, "max_cycles and chunk must be >= 0");
+    if (!(prm.delta < 1.0) || !isfinite(prm.delta)) return fail(LQ_ERR_ARG, "delta must be < 1");
+    if ((r = check_ptr(U, "U")) || (r = check_ptr(b, "b")) || (r = check_ptr(x, "x"))) return r;
+    if ((r = check_ptr(workspace, "workspace"))) return r == LQ_ERR_ARG ? fail(LQ_ERR_WORKSPACE, "workspace is NULL") : r;
+    const size_t sb = spinor_bytes((int64_t)g.V * nrhs, LQ_F64), gb = gauge_bytes(g.V, LQ_F64, 18);
+    if (overlap(x, sb, b, sb) || overlap(x, sb, U, gb) || overlap(x, sb, workspace, ws_bytes))
+        return fail(LQ_ERR_ALIGN, "x overlaps b, U or the workspace");
+    if (overlap(workspace, ws_bytes, b, sb) || overlap(workspace, ws_bytes, U, gb))
+        return fail(LQ_ERR_ALIGN, "workspace overlaps b or U");
+    r = cg_solve_schur(g, m_q, mode, nrhs, U, b, x, prm, workspace, ws_bytes, info, (cudaStream_t)cuda_stream);
+    if (info && r < 0 && info->status == 0) info->status = r;
+    return r;
+}
+
 int lq_cg_solve(const int32_t dims[4], double m_q, int32_t mode, const void* U, const void* eta, void* x,
                 const lq_cg_params* params, void* workspace, size_t ws_bytes, lq_cg_info* info,
                 void* cuda_stream) {

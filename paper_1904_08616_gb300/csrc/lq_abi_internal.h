@@ -32,6 +32,10 @@ size_t cg_workspace_bytes(const Geom& g, int mode, int nrhs);
 int cg_solve(const Geom& g, double m_q, int mode, int nrhs, const void* U, const void* eta, void* x,
              const lq_cg_params& prm, void* ws, size_t ws_bytes, lq_cg_info* info, cudaStream_t st);
 
+size_t cg_workspace_bytes_schur(const Geom& g, int mode, int nrhs);
+int cg_solve_schur(const Geom& g, double m_q, int mode, int nrhs, const void* U, const void* b, void* x,
+                   const lq_cg_params& prm, void* ws, size_t ws_bytes, lq_cg_info* info, cudaStream_t st);
+
 size_t cg_workspace_bytes_lattices(int n, const Geom* gs, const int* nrhs, int mode);
 int cg_solve_lattices(int n, const Geom* gs, const lq_lattice* lats, int mode, const lq_cg_params& prm, void* ws,
                       size_t ws_bytes, lq_cg_info* info, cudaStream_t st);

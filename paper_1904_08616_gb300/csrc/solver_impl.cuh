@@ -485,6 +485,33 @@ struct EpiResid {
     }
 };
 
+// out = b hop(in) on the other parity: the first half of the Schur operator inside the
+// inner loop, skipped like K1/K2 for right-hand sides (and whole launches) that have stopped
+template <class OutA>
+struct EpiPreHop {
+    using Real = typename OutA::Real;
+    static constexpr int NRED = 0;
+    OutA out;
+    Real b;
+    RedCtx rc;
+    int nr;
+    bool on;
+    LQ_HD bool init() {
+        if (rc.st->all_stop) return false;
+        on = rc.st->stop[thread_rhs(nr)] == 0;
+        return true;
+    }
+    LQ_HD bool active() const { return on; }
+    template <typename R>
+    LQ_HD void apply(const Site& s, const Spinor<R>& acc, double*) const {
+        Spinor<R> o;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) o.v[k] = cscale((R)b, acc.v[k]);
+        out.store(s, o);
+    }
+    template <int BS> __device__ __forceinline__ void finish(const double (&)[1], const VGrid&) const {}
+};
+
 // ------------------------------------------------------------------------------------
 // workspace layout
 // ------------------------------------------------------------------------------------
@@ -497,6 +524,7 @@ inline size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 // returns the largest layout a mode can use.
 struct WsLayout {
     size_t state, partials, r_high, t_high, u_x, eta_x, x_x, u_low, psi, r, p, t, total;
+    size_t tmp_high, b_x, tmp;   // even-odd Schur solve only
 };
 
 inline int inner_prec(int mode) {
@@ -547,6 +575,39 @@ inline WsLayout ws_layout(const Geom& g, int mode, bool pair_outer, int inner_fm
     w.r = take(lo);
     w.p = take(lo);
     w.t = take(lo);
+    w.total = o;
+    return w;
+}
+
+// Even-odd Schur solve (D x = b through CG on Mhat^dag Mhat over the even sites): FP32-pair
+// outer fields (full U, b and x; half r^high, t^high, eta-hat and an odd scratch), then the
+// inner links and half inner fields with an odd scratch.
+inline WsLayout ws_layout_schur(const Geom& g, int mode, int inner_fmt, int nb) {
+    WsLayout w{};
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o += align256(bytes);
+        return at;
+    };
+    const int64_t Vn = (int64_t)g.V * nb, Hn = (int64_t)g.Vh * nb;
+    w.state = take(sizeof(SolverState));
+    w.partials = take(sizeof(double) * kMaxRedValues * kMaxRhs * kMaxPartials);
+    w.r_high = take(spinor_bytes(Hn, LQ_F64X));
+    w.t_high = take(spinor_bytes(Hn, LQ_F64X));
+    w.tmp_high = take(spinor_bytes(Hn, LQ_F64X));
+    w.u_x = take(gauge_bytes(g.V, LQ_F64X, 18));
+    w.eta_x = take(spinor_bytes(Hn, LQ_F64X));
+    w.x_x = take(spinor_bytes(Vn, LQ_F64X));
+    w.b_x = take(spinor_bytes(Vn, LQ_F64X));
+    const int ip = inner_prec(mode);
+    if (ip != LQ_F64X) w.u_low = take(gauge_bytes(g.V, ip, inner_fmt));
+    const size_t lo = spinor_bytes(Hn, ip);
+    w.psi = take(lo);
+    w.r = take(lo);
+    w.p = take(lo);
+    w.t = take(lo);
+    w.tmp = take(lo);
     w.total = o;
     return w;
 }
@@ -602,8 +663,12 @@ struct EventSet {
     }
 };
 
-template <int IP, int IF, int IL, int HP, int IBS = kBS>
+// SCHUR: the even-odd Schur solve of D x = b (FP32-pair outer arithmetic, EO layout):
+// CG on Mhat^dag Mhat over the even sites, Mhat = A - H_eo H_oe / A with A = m_q + 4 and
+// H the hopping term of Eq. (1); each operator is a hop to the odd sites and a hop back.
+template <int IP, int IF, int IL, int HP, int IBS = kBS, bool SCHUR = false>
 struct Solve {
+    static_assert(!SCHUR || (HP == LQ_F64X && IL == LQ_LAYOUT_EO), "the Schur solve runs on FP32-pair EO fields");
     using Real = typename PrecT<IP>::Real;
     using HReal = typename PrecT<HP>::Real;
     static constexpr int HL = Outer<HP>::L;
@@ -615,15 +680,20 @@ struct Solve {
     using HiGA = GaugeAcc<HP, 18, HL>;
     using CallerRO = SpinorAcc<LQ_F64, LQ_LAYOUT_LEX, true>;
     using CallerRW = SpinorAcc<LQ_F64, LQ_LAYOUT_LEX, false>;
-    using IMap = typename std::conditional<IL == LQ_LAYOUT_LEX, MapLex<IBS>, MapEoFull<IBS>>::type;
-    using ISiteMap = typename std::conditional<IL == LQ_LAYOUT_LEX, MapLex<kSiteBS>, MapEoFull<kSiteBS>>::type;
-    using HMap = typename std::conditional<HL == LQ_LAYOUT_LEX, MapLex<kBS>, MapEoFull<kBS>>::type;
-    using HSiteMap = typename std::conditional<HL == LQ_LAYOUT_LEX, MapLex<kSiteBS>, MapEoFull<kSiteBS>>::type;
+    template <int B>
+    using FullMap = typename std::conditional<IL == LQ_LAYOUT_LEX, MapLex<B>, MapEoFull<B>>::type;
+    template <int B>
+    using FullHMap = typename std::conditional<HL == LQ_LAYOUT_LEX, MapLex<B>, MapEoFull<B>>::type;
+    using IMap = typename std::conditional<SCHUR, MapEoHalf<IBS>, FullMap<IBS>>::type;
+    using ISiteMap = typename std::conditional<SCHUR, MapEoHalf<kSiteBS>, FullMap<kSiteBS>>::type;
+    using HMap = typename std::conditional<SCHUR, MapEoHalf<kBS>, FullHMap<kBS>>::type;
+    using HSiteMap = typename std::conditional<SCHUR, MapEoHalf<kSiteBS>, FullHMap<kSiteBS>>::type;
     using K1Sten = Stencil<GA, SpRO, false>;
     using K1Epi = EpiK1<SpRW, SpRO>;
     using K2Sten = Stencil<GA, SpRO, true>;
     using K2Epi = EpiK2<SpRO, SpRO, SpRW, SpRW>;
     using K3Op = OpK3<SpRW, SpRO>;
+    using PreEpi = EpiPreHop<SpRW>;
     static constexpr bool kPairs = (HP == LQ_F64X);
     static constexpr int kBlock = IBS;
 
@@ -663,6 +733,16 @@ struct Solve {
     K2Sten sK2;
     K2Epi eK2;
     K3Op oK3;
+    // Schur solve: odd-site maps, odd scratch fields, the pre-hops and the FP32-pair b
+    IMap omap;
+    HMap hmap_odd;
+    SpRO tmp_ro;
+    SpRW tmp_rw;
+    HiRO tmh_ro, b_ro;
+    HiRW tmh_rw;
+    K1Sten sPre1;
+    K2Sten sPre2;
+    PreEpi ePre;
 
     // host-side state
     SolverState hs{};
@@ -701,36 +781,60 @@ struct Solve {
         Uo = kPairs ? (const void*)(ws + w.u_x) : U;
         etao = kPairs ? (const void*)(ws + w.eta_x) : eta;
         xo = kPairs ? (void*)(ws + w.x_x) : x;
+        // Schur: eta-hat, r^high, t^high and the inner fields are even half fields; x stays full
+        constexpr bool H = SCHUR;
         Uh = make_gauge<HP, 18, HL>(Uo, g);
-        eta_ro = make_spinor<HP, HL, true>(etao, g, false, nb);
+        eta_ro = make_spinor<HP, HL, true>(etao, g, H, nb);
         x_ro = make_spinor<HP, HL, true>(xo, g, false, nb);
         x_rw = make_spinor<HP, HL, false>(xo, g, false, nb);
-        rh_ro = make_spinor<HP, HL, true>(ws + w.r_high, g, false, nb);
-        rh_rw = make_spinor<HP, HL, false>(ws + w.r_high, g, false, nb);
-        th_ro = make_spinor<HP, HL, true>(ws + w.t_high, g, false, nb);
-        th_rw = make_spinor<HP, HL, false>(ws + w.t_high, g, false, nb);
+        rh_ro = make_spinor<HP, HL, true>(ws + w.r_high, g, H, nb);
+        rh_rw = make_spinor<HP, HL, false>(ws + w.r_high, g, H, nb);
+        th_ro = make_spinor<HP, HL, true>(ws + w.t_high, g, H, nb);
+        th_rw = make_spinor<HP, HL, false>(ws + w.t_high, g, H, nb);
         eta_caller = make_spinor<LQ_F64, LQ_LAYOUT_LEX, true>(eta, g, false, nb);
         x_caller = make_spinor<LQ_F64, LQ_LAYOUT_LEX, false>(x, g, false, nb);
         // inner fields; an FP64-class inner loop shares the outer links
         const void* Ulow = (IP == LQ_F64) ? U : (IP == LQ_F64X ? Uo : (const void*)(ws + w.u_low));
         Ui = make_gauge<IP, IF, IL>(Ulow, g);
-        psi_ro = make_spinor<IP, IL, true>(ws + w.psi, g, false, nb);
-        psi_rw = make_spinor<IP, IL, false>(ws + w.psi, g, false, nb);
-        r_ro = make_spinor<IP, IL, true>(ws + w.r, g, false, nb);
-        r_rw = make_spinor<IP, IL, false>(ws + w.r, g, false, nb);
-        p_ro = make_spinor<IP, IL, true>(ws + w.p, g, false, nb);
-        p_rw = make_spinor<IP, IL, false>(ws + w.p, g, false, nb);
-        t_ro = make_spinor<IP, IL, true>(ws + w.t, g, false, nb);
-        t_rw = make_spinor<IP, IL, false>(ws + w.t, g, false, nb);
+        psi_ro = make_spinor<IP, IL, true>(ws + w.psi, g, H, nb);
+        psi_rw = make_spinor<IP, IL, false>(ws + w.psi, g, H, nb);
+        r_ro = make_spinor<IP, IL, true>(ws + w.r, g, H, nb);
+        r_rw = make_spinor<IP, IL, false>(ws + w.r, g, H, nb);
+        p_ro = make_spinor<IP, IL, true>(ws + w.p, g, H, nb);
+        p_rw = make_spinor<IP, IL, false>(ws + w.p, g, H, nb);
+        t_ro = make_spinor<IP, IL, true>(ws + w.t, g, H, nb);
+        t_rw = make_spinor<IP, IL, false>(ws + w.t, g, H, nb);
         lexsite = MapLex<kSiteBS>{g, lnr};
-        hmap = HMap{g, lnr};
-        hsite = HSiteMap{g, lnr};
-        imap = IMap{g, lnr};
-        isite = ISiteMap{g, lnr};
-        sK1 = K1Sten{g, Ui, p_ro};
-        eK1 = K1Epi{t_rw, p_ro, from_double<Real>(a), from_double<Real>(b), rc, nb, false};
-        sK2 = K2Sten{g, Ui, t_ro};
-        eK2 = K2Epi{t_ro, p_ro, psi_rw, r_rw, from_double<Real>(a), from_double<Real>(b), rc, nb, Real(0), false};
+        // the inner and outer operators: a t + b hop(t) with (a, b) = (m_q + 4, 1/2) for
+        // D^dag D, (A, -1/(2A)) for the second hop of the Schur operator
+        const double ka = a, kb = SCHUR ? -0.5 / a : b;
+        if constexpr (SCHUR) {
+            hmap = HMap{g, 0, lnr};
+            hmap_odd = HMap{g, 1, lnr};
+            hsite = HSiteMap{g, 0, lnr};
+            imap = IMap{g, 0, lnr};
+            omap = IMap{g, 1, lnr};
+            isite = ISiteMap{g, 0, lnr};
+            tmp_ro = make_spinor<IP, IL, true>(ws + w.tmp, g, true, nb);
+            tmp_rw = make_spinor<IP, IL, false>(ws + w.tmp, g, true, nb);
+            tmh_ro = make_spinor<HP, HL, true>(ws + w.tmp_high, g, true, nb);
+            tmh_rw = make_spinor<HP, HL, false>(ws + w.tmp_high, g, true, nb);
+            b_ro = make_spinor<HP, HL, true>(ws + w.b_x, g, false, nb);
+            sPre1 = K1Sten{g, Ui, p_ro};
+            sPre2 = K2Sten{g, Ui, t_ro};
+            ePre = PreEpi{tmp_rw, from_double<Real>(0.5), rc, nb, false};
+            sK1 = K1Sten{g, Ui, tmp_ro};
+            sK2 = K2Sten{g, Ui, tmp_ro};
+        } else {
+            hmap = HMap{g, lnr};
+            hsite = HSiteMap{g, lnr};
+            imap = IMap{g, lnr};
+            isite = ISiteMap{g, lnr};
+            sK1 = K1Sten{g, Ui, p_ro};
+            sK2 = K2Sten{g, Ui, t_ro};
+        }
+        eK1 = K1Epi{t_rw, p_ro, from_double<Real>(ka), from_double<Real>(kb), rc, nb, false};
+        eK2 = K2Epi{t_ro, p_ro, psi_rw, r_rw, from_double<Real>(ka), from_double<Real>(kb), rc, nb, Real(0), false};
         oK3 = K3Op{p_rw, r_ro, rc, nb, Real(0), false};
         memset(out, 0, sizeof(out));
         prof = (prm.flags & LQ_CG_PROFILE) != 0;
@@ -751,8 +855,43 @@ struct Solve {
         return cudaStreamSynchronize(st);
     }
 
+    // out = ya y + hb hop(in) over the sites of map, in the outer arithmetic (Schur set-up,
+    // residual and reconstruction steps)
+    template <class Map, class OutA, class InA, class YA, bool DAG, bool HASY>
+    cudaError_t outer_hop(const Map& map, const OutA& out, const InA& in, const YA& y, double ya, double hb) {
+        Stencil<HiGA, InA, DAG> sten{g, Uh, in};
+        EpiAxpby<OutA, YA, HASY, false> e;
+        e.out = out;
+        e.y = y;
+        e.a = from_double<HReal>(ya);
+        e.b = from_double<HReal>(hb);
+        e.rc = rc;
+        e.slot = 0;
+        launches += 1;
+        return launch_stencil<kBS>(map, sten, e, st);
+    }
+
     // r^high = eta - A x, s^2 -> red[2][.]   (Algorithm 1 lines 2 and 23)
     cudaError_t high_residual() {
+        if constexpr (SCHUR) {
+            // tmp_o = H_oe x_e;  t_e = A x_e - H_eo tmp_o / A;  tmp_o = H^dag_oe t_e;
+            // r_e = eta-hat - (A t_e - H^dag_eo tmp_o / A)
+            if (prof) cudaEventRecord(evs.ev[6 * chunk], st);
+            cudaError_t er;
+            if ((er = outer_hop<HMap, HiRW, HiRO, HiRO, false, false>(hmap_odd, tmh_rw, x_ro, x_ro, 0.0, 0.5)) !=
+                    cudaSuccess ||
+                (er = outer_hop<HMap, HiRW, HiRO, HiRO, false, true>(hmap, th_rw, tmh_ro, x_ro, a, -0.5 / a)) !=
+                    cudaSuccess ||
+                (er = outer_hop<HMap, HiRW, HiRO, HiRO, true, false>(hmap_odd, tmh_rw, th_ro, th_ro, 0.0, 0.5)) !=
+                    cudaSuccess)
+                return er;
+            Stencil<HiGA, HiRO, true> s4{g, Uh, tmh_ro};
+            EpiResid<HiRO, HiRO, HiRW> e4{eta_ro, th_ro, rh_rw, from_double<HReal>(a), from_double<HReal>(-0.5 / a), rc, nb, 2};
+            er = launch_stencil<kBS>(hmap, s4, e4, st);
+            launches += 1;
+            if (prof) cudaEventRecord(evs.ev[6 * chunk + 1], st);
+            return er;
+        }
         Stencil<HiGA, HiRO, false> s1{g, Uh, x_ro};
         EpiAxpby<HiRW, HiRO, true, false> e1;
         e1.out = th_rw;
@@ -775,7 +914,7 @@ struct Solve {
     void account_high() {
         if (!prof) return;
         kms[LQ_K_HIGH] += elapsed(evs.ev[6 * chunk], evs.ev[6 * chunk + 1]);
-        kcalls[LQ_K_HIGH] += 2;
+        kcalls[LQ_K_HIGH] += SCHUR ? 4 : 2;
     }
 
     // state record, field conversions, ||eta||, x = 0 for zero right-hand sides, and the
@@ -793,10 +932,12 @@ struct Solve {
             (e = cudaMemsetAsync(&dstate->all_stop, 1, sizeof(dstate->all_stop), st)) != cudaSuccess)
             return cuda_fail(e, "state init");
         if constexpr (kPairs) {
+            // Schur: the caller's right-hand side is b (full, kept as pairs in b_x); eta-hat is
+            // built from it below
             if ((e = convert_gauge(g, LQ_F64, LQ_LAYOUT_LEX, U, LQ_F64X, 18, LQ_LAYOUT_EO, ws + w.u_x, st)) !=
                     cudaSuccess ||
-                (e = convert_spinor(g, LQ_F64, LQ_LAYOUT_LEX, eta, LQ_F64X, LQ_LAYOUT_EO, ws + w.eta_x, st, nb)) !=
-                    cudaSuccess ||
+                (e = convert_spinor(g, LQ_F64, LQ_LAYOUT_LEX, eta, LQ_F64X, LQ_LAYOUT_EO,
+                                    ws + (SCHUR ? w.b_x : w.eta_x), st, nb)) != cudaSuccess ||
                 (e = convert_spinor(g, LQ_F64, LQ_LAYOUT_LEX, x, LQ_F64X, LQ_LAYOUT_EO, ws + w.x_x, st, nb)) !=
                     cudaSuccess)
                 return cuda_fail(e, "FP32-pair copies");
@@ -807,10 +948,24 @@ struct Solve {
                 return cuda_fail(e, "link pack");
             launches += 1;
         }
-        // ||eta||^2 -> red[3][.], from the caller's FP64 eta
-        if ((e = launch_site<kSiteBS>(lexsite, OpNorm<CallerRO>{eta_caller, rc, nb, 3}, st)) != cudaSuccess)
-            return cuda_fail(e, "norm");
-        launches += 1;
+        if constexpr (SCHUR) {
+            // bhat_e = b_e - H_eo b_o / A (in t^high);  tmp_o = H^dag_oe bhat_e;
+            // eta-hat = Mhat^dag bhat_e = A bhat_e - H^dag_eo tmp_o / A;  ||eta-hat||^2 -> red[3]
+            if ((e = outer_hop<HMap, HiRW, HiRO, HiRO, false, true>(hmap, th_rw, b_ro, b_ro, 1.0, -0.5 / a)) !=
+                    cudaSuccess ||
+                (e = outer_hop<HMap, HiRW, HiRO, HiRO, true, false>(hmap_odd, tmh_rw, th_ro, th_ro, 0.0, 0.5)) !=
+                    cudaSuccess ||
+                (e = outer_hop<HMap, HiRW, HiRO, HiRO, true, true>(hmap, make_spinor<HP, HL, false>(etao, g, true, nb),
+                                                                   tmh_ro, th_ro, a, -0.5 / a)) != cudaSuccess ||
+                (e = launch_site<kSiteBS>(hsite, OpNorm<HiRO>{eta_ro, rc, nb, 3}, st)) != cudaSuccess)
+                return cuda_fail(e, "Schur right-hand side");
+            launches += 1;
+        } else {
+            // ||eta||^2 -> red[3][.], from the caller's FP64 eta
+            if ((e = launch_site<kSiteBS>(lexsite, OpNorm<CallerRO>{eta_caller, rc, nb, 3}, st)) != cudaSuccess)
+                return cuda_fail(e, "norm");
+            launches += 1;
+        }
         if ((e = read_state()) != cudaSuccess) return cuda_fail(e, "norm");
 
         PerRhs<int> zero_rhs{};
@@ -927,14 +1082,18 @@ struct Solve {
         while (true) {
             for (int j = 0; j < chunk; ++j) {
                 if (prof) cudaEventRecord(ev_at(0, j, 0), st);
+                if constexpr (SCHUR)
+                    if ((e = launch_stencil<IBS>(omap, sPre1, ePre, st)) != cudaSuccess) return cuda_fail(e, "K1 hop");
                 if ((e = launch_stencil<IBS>(imap, sK1, eK1, st)) != cudaSuccess) return cuda_fail(e, "K1");
                 if (prof) cudaEventRecord(ev_at(0, j, 1), st);
+                if constexpr (SCHUR)
+                    if ((e = launch_stencil<IBS>(omap, sPre2, ePre, st)) != cudaSuccess) return cuda_fail(e, "K2 hop");
                 if ((e = launch_stencil<IBS>(imap, sK2, eK2, st)) != cudaSuccess) return cuda_fail(e, "K2");
                 if (prof) cudaEventRecord(ev_at(1, j, 1), st);
                 if ((e = launch_site<kSiteBS>(isite, oK3, st)) != cudaSuccess) return cuda_fail(e, "K3");
                 if (prof) cudaEventRecord(ev_at(2, j, 1), st);
             }
-            launches += 3 * chunk;
+            launches += (SCHUR ? 5 : 3) * chunk;
             if ((e = read_state()) != cudaSuccess) return cuda_fail(e, "inner loop");
             int iter_max = 0;
             for (int j = 0; j < nb; ++j)
@@ -1002,6 +1161,12 @@ struct Solve {
     // write-back, per-right-hand-side records; returns the worst status
     int finish(lq_cg_info* info) {
         cudaError_t e;
+        if constexpr (SCHUR) {
+            // x_o = (b_o - H_oe x_e) / A
+            if ((e = outer_hop<HMap, HiRW, HiRO, HiRO, false, true>(hmap_odd, x_rw, x_ro, b_ro, 1.0 / a, -0.5 / a)) !=
+                cudaSuccess)
+                return cuda_fail(e, "odd-site solution");
+        }
         if constexpr (kPairs) {
             if ((e = convert_spinor(g, LQ_F64X, LQ_LAYOUT_EO, xo, LQ_F64, LQ_LAYOUT_LEX, x, st, nb)) != cudaSuccess)
                 return cuda_fail(e, "x write-back");
@@ -1028,11 +1193,11 @@ struct Solve {
     }
 };
 
-// The single-lattice driver: one batch of nb right-hand sides.
-template <int IP, int IF, int IL, int HP>
+// The single-lattice driver: one batch of nb right-hand sides (SCHUR: eta is b of D x = b).
+template <int IP, int IF, int IL, int HP, bool SCHUR = false>
 int run_solver(const Geom& g, double m_q, int nb, const void* U, const void* eta, void* x, const lq_cg_params& prm,
                double delta, const WsLayout& w, char* ws, lq_cg_info* info, cudaStream_t st) {
-    Solve<IP, IF, IL, HP> sv;
+    Solve<IP, IF, IL, HP, kBS, SCHUR> sv;
     sv.init(g, m_q, nb, U, eta, x, prm, delta, w, ws, st);
     int r;
     if ((r = sv.begin()) != LQ_OK) return r;
@@ -1060,6 +1225,15 @@ int solve_mixed_f16(const Geom& g, double m_q, int nb, const void* U, const void
 int solve_mixed_i32(const Geom& g, double m_q, int nb, const void* U, const void* eta, void* x,
                     const lq_cg_params& prm, double delta, const WsLayout& w, char* ws, lq_cg_info* info,
                     cudaStream_t st, bool pairs, int fmt);
+// even-odd Schur solves of D x = b (solver_schur_a.cu, solver_schur_b.cu)
+int schur_f64x(const Geom& g, double m_q, int nb, const void* U, const void* b, void* x, const lq_cg_params& prm,
+               double delta, const WsLayout& w, char* ws, lq_cg_info* info, cudaStream_t st, int fmt);
+int schur_f32(const Geom& g, double m_q, int nb, const void* U, const void* b, void* x, const lq_cg_params& prm,
+              double delta, const WsLayout& w, char* ws, lq_cg_info* info, cudaStream_t st, int fmt);
+int schur_f16(const Geom& g, double m_q, int nb, const void* U, const void* b, void* x, const lq_cg_params& prm,
+              double delta, const WsLayout& w, char* ws, lq_cg_info* info, cudaStream_t st, int fmt);
+int schur_i32(const Geom& g, double m_q, int nb, const void* U, const void* b, void* x, const lq_cg_params& prm,
+              double delta, const WsLayout& w, char* ws, lq_cg_info* info, cudaStream_t st, int fmt);
 
 }  // namespace solver_detail
 

@@ -488,3 +488,16 @@ def test_solve_grads_match_dense_finite_differences():
             fd = (L(U, ep) - L(U, em)) / (2 * h)
             want = g_eta[n, a, A].real if part == 1.0 else g_eta[n, a, A].imag
             assert abs(fd - want) < 1e-6 * max(1.0, abs(want))
+
+
+def test_solve_d_matches_dense_solve():
+    """The oracle's D x = b solve (CG on D^dag D x = D^dag b) against numpy's dense solve of
+    D itself on 2^4 (a mistake in the dagger or the normal-equation right-hand side fails)."""
+    dims = (2, 2, 2, 2)
+    m = 0.1
+    U = synth.gauge_field(dims, seed=97)
+    b = synth.gaussian_spinor(dims, seed=98)
+    x, _, _ = oracle.solve_d(dims, m, U, b, tol=1e-14)
+    Dd = dense.dense_dirac(dims, m, U)
+    xd = np.linalg.solve(Dd, dense.flat(b))
+    assert np.linalg.norm(dense.flat(x) - xd) / np.linalg.norm(xd) < 1e-11
