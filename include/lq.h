@@ -361,6 +361,32 @@ int lq_cg_solve_lattices(int32_t n, const lq_lattice *lats, int32_t mode,
                          lq_cg_info *info, void *cuda_stream);
 
 /*
+ * Domain decomposition in t (the paper's multi-FPGA layout exchanges boundary data over
+ * transceivers; Section 3): a lattice is cut into t-slabs, one per domain (rank), each
+ * holding its own FP64 LEX 18-real links and spinors with local dims {Lx, Ly, Lz, Lt_local}
+ * (Lx, Ly, Lz even >= 2, Lt_local >= 1).  Applying D on a domain needs two faces from its
+ * neighbours in t, each Lx*Ly*Lz half spinors of 6 complex FP64 numbers
+ * (lq_halo_face_bytes bytes):
+ *   lq_halo_pack fills, from this domain's psi (and links),
+ *     to_prev = (1 + S gamma_4) psi at t = 0, upper spin half (h0, h1), S = -1 for D and +1
+ *               for D^dag: what the previous domain's forward t-hop needs;
+ *     to_next = U_t^dag (1 - S gamma_4) psi at t = Lt_local - 1, upper half: what the next
+ *               domain's backward t-hop needs (its link lives here).
+ *     Face site s = x + Lx*(y + Ly*z).
+ *   The caller delivers to_prev of domain r+1 as from_next of domain r and to_next of domain
+ *   r-1 as from_prev of domain r (periodic in r).
+ *   lq_halo_dslash then writes out = D psi (or D^dag psi, the same dagger as the pack) on the
+ *   domain.  The result equals the single-domain lq_dslash_apply bit for bit.
+ * Faces must not overlap out; one launch each.
+ */
+size_t lq_halo_face_bytes(const int32_t dims_local[4]);
+int lq_halo_pack(const int32_t dims_local[4], int32_t dagger, const void *U, const void *psi,
+                 void *to_prev, void *to_next, void *cuda_stream);
+int lq_halo_dslash(const int32_t dims_local[4], double m_q, int32_t dagger, const void *U,
+                   const void *psi, const void *from_next, const void *from_prev, void *out,
+                   void *cuda_stream);
+
+/*
  * lq_link_grad -- the gradient of L = Re <g, D psi> with respect to the links of Eq. (1),
  * for differentiating through the operator (the paper does not; this is the library's
  * adjoint support).  With the convention grad = dL/dRe U + i dL/dIm U, per link

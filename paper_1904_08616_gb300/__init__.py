@@ -87,6 +87,12 @@ def load(build_if_missing: bool = True):
             fn.restype = ctypes.c_int
         L.lq_dslash_hop.argtypes = [_Dims, i32, i32, f64, f64, i32, i32, _vp, _vp, _vp, _vp, _vp]
         L.lq_dslash_hop.restype = ctypes.c_int
+        L.lq_halo_face_bytes.argtypes = [_Dims]
+        L.lq_halo_face_bytes.restype = ctypes.c_size_t
+        L.lq_halo_pack.argtypes = [_Dims, i32, _vp, _vp, _vp, _vp, _vp]
+        L.lq_halo_pack.restype = ctypes.c_int
+        L.lq_halo_dslash.argtypes = [_Dims, f64, i32, _vp, _vp, _vp, _vp, _vp, _vp]
+        L.lq_halo_dslash.restype = ctypes.c_int
         L.lq_link_grad.argtypes = [_Dims, _vp, _vp, f64, i32, _vp, _vp]
         L.lq_link_grad.restype = ctypes.c_int
         L.lq_convert_spinor.argtypes = [_Dims, i32, i32, _vp, i32, i32, _vp, _vp]

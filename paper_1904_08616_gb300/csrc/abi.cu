@@ -88,6 +88,20 @@ int check_dims(const int32_t* dims, Geom* g) {
     return LQ_OK;
 }
 
+// a t-slab of a decomposed lattice: x, y, z even >= 2, Lt_local >= 1
+int check_slab(const int32_t* dims, Geom* g) {
+    if (!dims) return fail(LQ_ERR_ARG, "dims is NULL");
+    long long v = 1;
+    for (int i = 0; i < 4; ++i) {
+        const bool ok = (i < 3) ? (dims[i] >= 2 && !(dims[i] & 1)) : (dims[i] >= 1);
+        if (!ok) return fail(LQ_ERR_DIMS, "slab extent %d is %d: x, y, z even and >= 2, t >= 1", i, (int)dims[i]);
+        v *= dims[i];
+        if (v > 100000000LL) return fail(LQ_ERR_DIMS, "slab volume exceeds 10^8 sites");
+    }
+    *g = make_geom(dims);
+    return LQ_OK;
+}
+
 int check_ptr(const void* p, const char* name) {
     if (!p) return fail(LQ_ERR_ARG, "%s is NULL", name);
     if (!aligned16(p)) return fail(LQ_ERR_ALIGN, "%s is not 16-byte aligned", name);
@@ -198,6 +212,48 @@ int lq_dslash_hop(const int32_t dims[4], int32_t out_parity, int32_t dagger, dou
     else if (prec == LQ_I32S) e = hop_i32(g, out_parity, dag, a, b, link_fmt, U, psi_other, y, out, st);
     else e = hop_f16(g, out_parity, dag, a, b, link_fmt, U, psi_other, y, out, st);
     if (e != cudaSuccess) return cuda_fail(e, "dslash_hop launch");
+    return LQ_OK;
+}
+
+size_t lq_halo_face_bytes(const int32_t dims_local[4]) {
+    Geom g;
+    if (check_slab(dims_local, &g) != LQ_OK) return 0;
+    return (size_t)g.S[3] * 96;
+}
+
+int lq_halo_pack(const int32_t dims_local[4], int32_t dagger, const void* U, const void* psi, void* to_prev,
+                 void* to_next, void* cuda_stream) {
+    Geom g;
+    int r;
+    if ((r = check_slab(dims_local, &g)) != LQ_OK) return r;
+    if ((r = check_ptr(U, "U")) || (r = check_ptr(psi, "psi")) || (r = check_ptr(to_prev, "to_prev")) ||
+        (r = check_ptr(to_next, "to_next")))
+        return r;
+    const size_t fb = (size_t)g.S[3] * 96, sb = spinor_bytes(g.V, LQ_F64), gb = gauge_bytes(g.V, LQ_F64, 18);
+    if (overlap(to_prev, fb, to_next, fb) || overlap(to_prev, fb, psi, sb) || overlap(to_next, fb, psi, sb) ||
+        overlap(to_prev, fb, U, gb) || overlap(to_next, fb, U, gb))
+        return fail(LQ_ERR_ALIGN, "face buffers overlap each other or the fields");
+    const cudaError_t e = halo_pack(g, dagger != 0, U, psi, to_prev, to_next, (cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "halo_pack launch");
+    return LQ_OK;
+}
+
+int lq_halo_dslash(const int32_t dims_local[4], double m_q, int32_t dagger, const void* U, const void* psi,
+                   const void* from_next, const void* from_prev, void* out, void* cuda_stream) {
+    Geom g;
+    int r;
+    if ((r = check_slab(dims_local, &g)) != LQ_OK) return r;
+    if (!isfinite(m_q)) return fail(LQ_ERR_ARG, "m_q is not finite");
+    if ((r = check_ptr(U, "U")) || (r = check_ptr(psi, "psi")) || (r = check_ptr(from_next, "from_next")) ||
+        (r = check_ptr(from_prev, "from_prev")) || (r = check_ptr(out, "out")))
+        return r;
+    const size_t fb = (size_t)g.S[3] * 96, sb = spinor_bytes(g.V, LQ_F64), gb = gauge_bytes(g.V, LQ_F64, 18);
+    if (overlap(out, sb, psi, sb) || overlap(out, sb, U, gb) || overlap(out, sb, from_next, fb) ||
+        overlap(out, sb, from_prev, fb))
+        return fail(LQ_ERR_ALIGN, "out overlaps psi, U or a face");
+    const cudaError_t e =
+        halo_dslash(g, m_q, dagger != 0, U, psi, from_next, from_prev, out, (cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "halo_dslash launch");
     return LQ_OK;
 }
 

@@ -35,11 +35,11 @@ template <int S, bool SCALED, typename R> LQ_HD cplx<R> acc_add(cplx<R> acc, cpl
     }
 }
 
-// acc += sc * U' (1 + S gamma_MU) q,  U' = U (BACK = false) or U^dag (BACK = true);
-// sc is the neighbour's storage scale (1 unless SCALED), folded into the accumulation.
-template <int MU, int S, bool BACK, bool SCALED, typename R>
-LQ_HD void hop_dir(Spinor<R>& acc, const Spinor<R>& q, const Link<R>& U, R sc) {
-    cplx<R> h0[3], h1[3];
+// One hop in three stages: the rank-2 spin projection h = (1 + S gamma_MU) q reduced to its
+// upper half (h0, h1 = up + S B_MU dn), the colour mat-vec g = U' h with U' = U (BACK = false)
+// or U^dag (BACK = true), and the accumulation acc += sc * (g0, g1, S B_MU^dag (g0, g1)).
+template <int MU, int S, typename R>
+LQ_HD void hop_project(const Spinor<R>& q, cplx<R> h0[3], cplx<R> h1[3]) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const cplx<R> p0 = q.v[c], p1 = q.v[3 + c], p2 = q.v[6 + c], p3 = q.v[9 + c];
@@ -57,7 +57,10 @@ LQ_HD void hop_dir(Spinor<R>& acc, const Spinor<R>& q, const Link<R>& U, R sc) {
             h1[c] = pm<S>(p1, p3);
         }
     }
-    cplx<R> g0[3], g1[3];
+}
+
+template <bool BACK, typename R>
+LQ_HD void hop_matvec(const Link<R>& U, const cplx<R> h0[3], const cplx<R> h1[3], cplx<R> g0[3], cplx<R> g1[3]) {
 #pragma unroll
     for (int A = 0; A < 3; ++A) {
         if constexpr (!BACK) {
@@ -78,6 +81,10 @@ LQ_HD void hop_dir(Spinor<R>& acc, const Spinor<R>& q, const Link<R>& U, R sc) {
             }
         }
     }
+}
+
+template <int MU, int S, bool SCALED, typename R>
+LQ_HD void hop_accumulate(Spinor<R>& acc, const cplx<R> g0[3], const cplx<R> g1[3], R sc) {
 #pragma unroll
     for (int A = 0; A < 3; ++A) {
         acc.v[A] = acc_add<1, SCALED>(acc.v[A], g0[A], sc);
@@ -97,6 +104,17 @@ LQ_HD void hop_dir(Spinor<R>& acc, const Spinor<R>& q, const Link<R>& U, R sc) {
             acc.v[9 + A] = acc_add<S, SCALED>(acc.v[9 + A], g1[A], sc);
         }
     }
+}
+
+// acc += sc * U' (1 + S gamma_MU) q,  U' = U (BACK = false) or U^dag (BACK = true);
+// sc is the neighbour's storage scale (1 unless SCALED), folded into the accumulation.
+template <int MU, int S, bool BACK, bool SCALED, typename R>
+LQ_HD void hop_dir(Spinor<R>& acc, const Spinor<R>& q, const Link<R>& U, R sc) {
+    cplx<R> h0[3], h1[3];
+    hop_project<MU, S>(q, h0, h1);
+    cplx<R> g0[3], g1[3];
+    hop_matvec<BACK>(U, h0, h1, g0, g1);
+    hop_accumulate<MU, S, SCALED>(acc, g0, g1, sc);
 }
 
 // The same hop with the direction MU, the projector sign and the link orientation known

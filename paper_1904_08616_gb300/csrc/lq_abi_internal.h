@@ -28,6 +28,11 @@ cudaError_t convert_gauge(const Geom& g, int sp, int sl, const void* src, int dp
 cudaError_t link_grad(const Geom& g, const void* gf, const void* psi, double scale, bool accumulate, void* out,
                       cudaStream_t st);
 
+cudaError_t halo_pack(const Geom& g, bool dag, const void* U, const void* psi, void* to_prev, void* to_next,
+                      cudaStream_t st);
+cudaError_t halo_dslash(const Geom& g, double m_q, bool dag, const void* U, const void* psi, const void* from_next,
+                        const void* from_prev, void* out, cudaStream_t st);
+
 size_t cg_workspace_bytes(const Geom& g, int mode, int nrhs);
 int cg_solve(const Geom& g, double m_q, int mode, int nrhs, const void* U, const void* eta, void* x,
              const lq_cg_params& prm, void* ws, size_t ws_bytes, lq_cg_info* info, cudaStream_t st);
