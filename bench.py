@@ -436,6 +436,46 @@ def run_workload(args):
         line.update({"config": {"lattice": list(dims), "nrhs": nr, "m_q": 0.1, "links": "haar", "tol": TOL},
                      "value": _updates(dims, infos) / (ms * 1e-3), "ms_per_solve": ms,
                      "ms_one_by_one": ms_single, "iters": max(i["iters"] for i in infos)})
+    elif args.workload == "dslash":
+        # the operator alone on the 32^4 fields, every stored format: site-updates/s, GB/s
+        # against the measured copy peak and the 8 TB/s nominal, GFLOP/s at 1464 flops/site
+        U, psi = make_inputs()
+        U_d, p_d = field(U), field(psi)
+        peak, peak_kind = measured_peaks()
+        V = int(np.prod(DIMS))
+        spinor_b = {"f64": 192, "f64x": 192, "f32": 96, "f16s": 52, "i32s": 100}
+        link_b = {"f64": 8, "f64x": 8, "f32": 4, "f16s": 2, "i32s": 4}
+        rows = {}
+        for prec, fmt, layout in (("f64", 18, "lex"), ("f64", 18, "eo"), ("f64x", 18, "eo"), ("f32", 18, "eo"),
+                                  ("f32", 12, "eo"), ("f16s", 12, "eo"), ("f16s", 18, "eo"), ("i32s", 12, "eo")):
+            Ub = lq.convert_gauge(DIMS, U_d, "f64", "lex", dst_prec=prec, dst_fmt=fmt, dst_layout=layout)
+            pb = lq.convert_spinor(DIMS, p_d, "f64", "lex", dst_prec=prec, dst_layout=layout)
+            out = torch.empty_like(pb)
+            for _ in range(max(args.warmup, 3)):
+                lq.dslash_apply(DIMS, MASS, Ub, pb, out=out, prec=prec, link_fmt=fmt, layout=layout)
+            torch.cuda.synchronize()
+            reps = 20
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                lq.dslash_apply(DIMS, MASS, Ub, pb, out=out, prec=prec, link_fmt=fmt, layout=layout)
+            e1.record()
+            torch.cuda.synchronize()
+            us = e0.elapsed_time(e1) / reps * 1e3
+            bytes_site = 2 * spinor_b[prec] + 4 * fmt * link_b[prec]
+            rate = V / (us * 1e-6)
+            gbs = bytes_site * rate / 1e9
+            row = {"us": us, "site_updates_per_s": rate, "bytes_per_site": bytes_site, "gbs": gbs,
+                   "frac_measured_hbm": gbs / peak, "frac_nominal_8tbs": gbs / 8000.0,
+                   "gflops_1464": rate * FLOPS_PER_SITE / 1e9}
+            if prec == "f64":
+                row["frac_fp64_pipe_nominal_1.25tf"] = rate * FLOPS_PER_SITE / 1.25e12
+            rows[f"{prec}/{fmt}/{layout}"] = row
+        line.update({"config": {"lattice": list(DIMS), "m_q": MASS, "links": "exp(0.3iH)",
+                                "l2": "every variant streams more than the 126 MB L2 (smallest: 210 MB, f16s/12)",
+                                "peak_kind": peak_kind, "peak_gbs": peak},
+                     "value": rows["f16s/12/eo"]["site_updates_per_s"], "variants": rows})
     elif args.workload == "schur":
         # D x = b on the 32^4 workload: the even-odd Schur solve against solving D^dag D x = D^dag b
         U, b = make_inputs()
@@ -487,7 +527,7 @@ def main():
     ap.add_argument("--mode", default="mixed_f16", choices=["mixed_f16", "mixed_f32", "f64", "f64x", "mixed_i32"])
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 / other-mode comparison solves")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--workload", default="cg32", choices=["cg32", "lattices", "batched", "large", "schur"],
+    ap.add_argument("--workload", default="cg32", choices=["cg32", "lattices", "batched", "large", "schur", "dslash"],
                     help="cg32: the 32^4 mixed-precision solve (the bench line); the others print a "
                          "measurement line for the uneven-lattice, 12-RHS and 64^3x128 workloads")
     args = ap.parse_args()
