@@ -181,6 +181,21 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def whole_job_rate(ms, updates, device):
+    """(slowest rank's ms, units all ranks processed per second over that time); one rank
+    without an initialised process group returns its own figures."""
+    import torch
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        tm = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+        tu = torch.tensor([float(updates)], dtype=torch.float64, device=device)
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tu, op=dist.ReduceOp.SUM)
+        ms_max = float(tm.item())
+        return ms_max, float(tu.item()) / (ms_max * 1e-3)
+    return float(ms), float(updates) / (float(ms) * 1e-3)
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -239,11 +254,7 @@ def run_ours(args, rank, world, local_rank):
     clocks = clk.summary()
     info = infos[-1]
     upd = 2 * V * (info["iters"] + info["high_applies"])
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * upd / (ms_max * 1e-3)
+    ms_max, value = whole_job_rate(ms, upd, dev)
     launches = sum(i["launches"] for i in infos)
 
     # end to end through the public API with pinned host buffers
@@ -261,10 +272,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     barrier()
     e2e_ms = h0.elapsed_time(h1) / args.steps
-    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * upd / (float(te.item()) * 1e-3)
+    _, e2e_value = whole_job_rate(e2e_ms, upd, dev)
 
     # plain FP64 CG (native FP64 and FP32-pair arithmetic) and the other mixed variant on the
     # same system (one run each after one warm run)
@@ -393,7 +401,8 @@ def run_workload(args):
                           "eta": spinors(dims, [961 + 100 * i + r for r in range(nr)])})
 
         def one():
-            xs, infos, st = lq.cg_solve_lattices(probs, mode=args.mode, tol=TOL, autotune=True)
+            kw = {"block": args.lattice_block} if args.lattice_block else {"autotune": True}
+            xs, infos, st = lq.cg_solve_lattices(probs, mode=args.mode, tol=TOL, **kw)
             assert st == 0
             return infos
 
@@ -406,7 +415,7 @@ def run_workload(args):
             return allinf
 
         ms, infos = _timed(one, args.steps, args.warmup)
-        ms_seq, _ = _timed(seq, args.steps, args.warmup)
+        ms_seq = None if args.no_compare else _timed(seq, args.steps, args.warmup)[0]
         upd = sum(_updates(p["dims"], inf) for p, inf in zip(probs, infos))
         line.update({"config": {"lattices": [list(d) + [n] for d, n in specs], "m_q": 0.1, "links": "haar",
                                 "tol": TOL},
@@ -530,6 +539,8 @@ def main():
     ap.add_argument("--workload", default="cg32", choices=["cg32", "lattices", "batched", "large", "schur", "dslash"],
                     help="cg32: the 32^4 mixed-precision solve (the bench line); the others print a "
                          "measurement line for the uneven-lattice, 12-RHS and 64^3x128 workloads")
+    ap.add_argument("--lattice-block", type=int, default=0, choices=[0, 64, 128, 256],
+                    help="lattices workload: inner block size (0: tuned)")
     args = ap.parse_args()
     if args.workload != "cg32":
         run_workload(args)

@@ -1,0 +1,52 @@
+"""bench.py's whole-job figure on host ranks (gloo, 127.0.0.1): the slowest rank's time and
+the units of all ranks; one rank without a process group reports its own."""
+import json
+import os
+import socket
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, outdir):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    ms, rate = bench.whole_job_rate(10.0 * (rank + 1), 1000 * (rank + 1), "cpu")
+    with open(os.path.join(outdir, f"r{rank}.json"), "w") as f:
+        json.dump({"ms": ms, "rate": rate}, f)
+    dist.destroy_process_group()
+
+
+def test_whole_job_rate_two_ranks(tmp_path):
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, str(tmp_path))) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(60)
+        assert p.exitcode == 0
+    for r in range(2):
+        d = json.load(open(tmp_path / f"r{r}.json"))
+        assert d["ms"] == 20.0                      # the slowest rank
+        assert abs(d["rate"] - 3000 / 0.020) < 1e-6  # both ranks' units over that time
+
+
+def test_whole_job_rate_one_rank():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.whole_job_rate(4.0, 8000, "cpu") == (4.0, 8000 / 0.004)
