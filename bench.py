@@ -258,7 +258,6 @@ def run_ours(args, rank, world, local_rank):
     ms = e0.elapsed_time(e1) / args.steps
     clocks = clk.summary()
     info = infos[-1]
-    pinfo = pinfos[-1]
     upd = 2 * V * (info["iters"] + info["high_applies"])
     ms_max, value = whole_job_rate(ms, upd, dev)
     launches = sum(i["launches"] for i in infos)
