@@ -204,8 +204,10 @@ typedef struct lq_cg_params {
                                 modes; default 12-real                                     */
 #define LQ_CG_AUTOTUNE 8     /* lq_cg_solve_lattices: pick the inner block size by timing
                                 (cached per lattice set and GPU); default 128 threads      */
-#define LQ_CG_NO_GRAPH 16    /* lq_cg_solve_lattices: launch the inner kernels one by one
-                                instead of replaying a captured CUDA graph                 */
+#define LQ_CG_NO_GRAPH 16    /* launch the inner kernels one by one from the host instead of
+                                a CUDA graph (single lattices: a conditional WHILE graph runs
+                                a cycle's inner loop on the device; lattice batches: chunks
+                                of iterations are replayed from a captured graph)          */
 #define LQ_CG_BLOCK_64 0x100 /* lq_cg_solve_lattices: inner block size 64 / 128 / 256 threads */
 #define LQ_CG_BLOCK_128 0x200 /*   (at most one; overrides LQ_CG_AUTOTUNE)                  */
 #define LQ_CG_BLOCK_256 0x400
@@ -215,7 +217,8 @@ enum {
     LQ_K_APPLY_D = 0,        /* inner t = D p with ||t||^2                                  */
     LQ_K_APPLY_DDAG = 1,     /* inner q = D^dag t fused with the psi / r updates and ||r||^2 */
     LQ_K_UPDATE_P = 2,       /* inner p = r + beta p                                        */
-    LQ_K_HIGH = 3            /* FP64 residual eta - D^dag D x (two operator kernels)        */
+    LQ_K_HIGH = 3            /* FP64 residual eta - D^dag D x (two operator kernels; four in
+                                the Schur solve)                                           */
 };
 
 typedef struct lq_cg_info {
@@ -252,8 +255,11 @@ size_t lq_cg_workspace_bytes_multi(const int32_t dims[4], int32_t mode, int32_t 
  *   workspace, ws_bytes  device scratch of at least lq_cg_workspace_bytes(dims, mode),
  *            16-byte aligned; its contents on entry are ignored.
  *   info     optional (host) statistics.
- * Kernels run on cuda_stream; the call returns after the solve has finished (it reads
- * small convergence records back to the host between chunks of iterations).
+ * Kernels run on cuda_stream; the call returns after the solve has finished.  Each cycle's
+ * inner loop runs as one CUDA graph launch (a conditional WHILE node, the loop condition set
+ * on the device from the solver's state record); the host reads the state record back once
+ * per cycle.  With LQ_CG_PROFILE or LQ_CG_NO_GRAPH the host launches the inner kernels itself
+ * and polls the record between chunks of iterations.
  * Returns LQ_OK when the FP64 true residual meets tol, LQ_NOT_CONVERGED otherwise.
  */
 int lq_cg_solve(const int32_t dims[4], double m_q, int32_t mode, const void *U,

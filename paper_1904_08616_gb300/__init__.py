@@ -301,7 +301,7 @@ def cg_workspace_bytes(dims, mode="f64", nrhs=1) -> int:
 
 
 def cg_solve(dims, m_q, U, eta, x=None, mode="f64", tol=1e-10, max_iter=100000, max_cycles=0, delta=0.0,
-             chunk=0, workspace=None, stream=None, profile=False, native_f64=False, link18=False):
+             chunk=0, workspace=None, stream=None, profile=False, native_f64=False, link18=False, graph=True):
     """Solve D^dag D x = eta (Algorithm 1).  U: F64 LEX 18-real links, eta / x: F64 LEX spinors.
 
     x (if given) is the starting guess and receives the solution.  Returns (x, info, status)
@@ -316,7 +316,8 @@ def cg_solve(dims, m_q, U, eta, x=None, mode="f64", tol=1e-10, max_iter=100000, 
     wb = cg_workspace_bytes(dims, m)
     if workspace is None:
         workspace = _empty_bytes(wb, eta)
-    flags = (CG_PROFILE if profile else 0) | (CG_NATIVE_F64 if native_f64 else 0) | (CG_LINK18 if link18 else 0)
+    flags = (CG_PROFILE if profile else 0) | (CG_NATIVE_F64 if native_f64 else 0) | (CG_LINK18 if link18 else 0) \
+        | (0 if graph else CG_NO_GRAPH)
     prm = CgParams(float(tol), int(max_iter), int(max_cycles), float(delta), int(chunk), flags)
     info = CgInfo()
     st = load().lq_cg_solve(_dims(dims), float(m_q), m, _ptr(U, gb, "U"), _ptr(eta, sb, "eta"),
@@ -329,7 +330,8 @@ def cg_solve(dims, m_q, U, eta, x=None, mode="f64", tol=1e-10, max_iter=100000, 
 
 
 def cg_solve_multi(dims, m_q, nrhs, U, eta, x=None, mode="f64", tol=1e-10, max_iter=100000, max_cycles=0,
-                   delta=0.0, chunk=0, workspace=None, stream=None, profile=False, native_f64=False, link18=False):
+                   delta=0.0, chunk=0, workspace=None, stream=None, profile=False, native_f64=False, link18=False,
+                   graph=True):
     """nrhs independent solves D^dag D x_r = eta_r sharing the links (eta, x: nrhs stacked FP64
     LEX fields).  Returns (x, [info per right-hand side], status)."""
     import torch
@@ -342,7 +344,8 @@ def cg_solve_multi(dims, m_q, nrhs, U, eta, x=None, mode="f64", tol=1e-10, max_i
     wb = cg_workspace_bytes(dims, m, n)
     if workspace is None:
         workspace = _empty_bytes(wb, eta)
-    flags = (CG_PROFILE if profile else 0) | (CG_NATIVE_F64 if native_f64 else 0) | (CG_LINK18 if link18 else 0)
+    flags = (CG_PROFILE if profile else 0) | (CG_NATIVE_F64 if native_f64 else 0) | (CG_LINK18 if link18 else 0) \
+        | (0 if graph else CG_NO_GRAPH)
     prm = CgParams(float(tol), int(max_iter), int(max_cycles), float(delta), int(chunk), flags)
     infos = (CgInfo * n)()
     st = load().lq_cg_solve_multi(_dims(dims), float(m_q), m, n, _ptr(U, gb, "U"), _ptr(eta, sb, "eta"),
@@ -359,7 +362,7 @@ def cg_workspace_bytes_schur(dims, mode="mixed_f32", nrhs=1) -> int:
 
 
 def cg_solve_schur(dims, m_q, U, b, x=None, nrhs=1, mode="mixed_f32", tol=1e-10, max_iter=100000, max_cycles=0,
-                   delta=0.0, chunk=0, workspace=None, stream=None, profile=False, link18=False):
+                   delta=0.0, chunk=0, workspace=None, stream=None, profile=False, link18=False, graph=True):
     """Solve D x = b (nrhs stacked FP64 LEX fields) by the even-odd Schur complement.
     Returns (x, [info per right-hand side], status)."""
     import torch
@@ -372,7 +375,7 @@ def cg_solve_schur(dims, m_q, U, b, x=None, nrhs=1, mode="mixed_f32", tol=1e-10,
     wb = cg_workspace_bytes_schur(dims, m, n)
     if workspace is None:
         workspace = _empty_bytes(wb, b)
-    flags = (CG_PROFILE if profile else 0) | (CG_LINK18 if link18 else 0)
+    flags = (CG_PROFILE if profile else 0) | (CG_LINK18 if link18 else 0) | (0 if graph else CG_NO_GRAPH)
     prm = CgParams(float(tol), int(max_iter), int(max_cycles), float(delta), int(chunk), flags)
     infos = (CgInfo * n)()
     st = load().lq_cg_solve_schur(_dims(dims), float(m_q), m, n, _ptr(U, gb, "U"), _ptr(b, sb, "b"),

@@ -613,7 +613,7 @@ struct SolverState {
     int k_max;                  // inner iteration cap for the current cycle
     int nr;                     // right-hand sides in the batch
     int all_stop;               // every right-hand side has stop != 0
-    int pad;
+    int trips;                  // inner-loop graph trips in the current cycle
     unsigned int ticket[4];
 };
 

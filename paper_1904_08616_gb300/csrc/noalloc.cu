@@ -66,6 +66,10 @@ extern "C" int lq_cg_solve_noalloc(const int32_t dims[4], double m_q, int32_t mo
         return r;
     }
     // The solver initialises every part of the scratch it reads (state record, partial
-    // sums, vectors), so the previous call's contents need no clearing here.
-    return lq_cg_solve(dims, m_q, mode, U, eta, x, params, ws, kNoAllocScratchBytes, info, cuda_stream);
+    // sums, vectors), so the previous call's contents need no clearing here.  The inner loop
+    // runs host-driven: building a CUDA graph would allocate.
+    lq_cg_params prm{1e-10, 100000, 0, 0.0, 0, 0};
+    if (params) prm = *params;
+    prm.flags |= LQ_CG_NO_GRAPH;
+    return lq_cg_solve(dims, m_q, mode, U, eta, x, &prm, ws, kNoAllocScratchBytes, info, cuda_stream);
 }

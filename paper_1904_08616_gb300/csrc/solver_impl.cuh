@@ -331,6 +331,7 @@ struct OpRestart {
                 st->stop_rho[j] = sr.v[j];
             }
             st->k_max = km;
+            st->trips = 0;
             st->all_stop = all;
         });
     }
@@ -653,6 +654,61 @@ template <> struct Outer<LQ_F64X> {     // FP32-pair EO copies in the workspace
     static constexpr int L = LQ_LAYOUT_EO;
 };
 
+// The last node of the inner-loop graph: another trip while some right-hand side is running
+// and the cycle has not used k_max + 2 trips (K2 stops every right-hand side at k_max, so the
+// trip bound only matters if that ever failed; it keeps the loop finite).
+static __global__ void inner_loop_cond(cudaGraphConditionalHandle h, SolverState* st) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const int t = ++st->trips;
+        cudaGraphSetConditional(h, (st->all_stop == 0 && t < st->k_max + 2) ? 1u : 0u);
+    }
+}
+
+// One cycle's inner CG as a CUDA graph: a conditional WHILE node whose body is K1, K2, K3 and
+// inner_loop_cond, captured once per solve and launched once per cycle.
+struct InnerGraph {
+    cudaStream_t cs = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    InnerGraph() = default;
+    InnerGraph(const InnerGraph&) = delete;
+    InnerGraph& operator=(const InnerGraph&) = delete;
+    ~InnerGraph() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (cs) cudaStreamDestroy(cs);
+    }
+    // body(stream) enqueues one iteration's kernels
+    template <class Body>
+    cudaError_t build(SolverState* st, Body body) {
+        cudaError_t e;
+        if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) return e;
+        if ((e = cudaGraphCreate(&graph, 0)) != cudaSuccess) return e;
+        cudaGraphConditionalHandle h;
+        if ((e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault)) != cudaSuccess) return e;
+        cudaGraphNodeParams p = {};
+        p.type = cudaGraphNodeTypeConditional;
+        p.conditional.handle = h;
+        p.conditional.type = cudaGraphCondTypeWhile;
+        p.conditional.size = 1;
+        cudaGraphNode_t node;
+        if ((e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &p)) != cudaSuccess) return e;
+        cudaGraph_t bodyg = p.conditional.phGraph_out[0];
+        if ((e = cudaStreamBeginCaptureToGraph(cs, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+            cudaSuccess)
+            return e;
+        cudaError_t le = body(cs);
+        if (le == cudaSuccess) {
+            inner_loop_cond<<<1, 32, 0, cs>>>(h, st);
+            le = cudaGetLastError();
+        }
+        e = cudaStreamEndCapture(cs, &bodyg);
+        if (le != cudaSuccess) return le;
+        if (e != cudaSuccess) return e;
+        return cudaGraphInstantiate(&exec, graph, 0);
+    }
+};
+
 struct EventSet {
     std::vector<cudaEvent_t> ev;
     EventSet() = default;
@@ -752,6 +808,7 @@ struct Solve {
     double kms[4] = {0, 0, 0, 0};
     int kcalls[4] = {0, 0, 0, 0};
     EventSet evs;
+    InnerGraph igraph;
     double eta_norm[kMaxRhs], s[kMaxRhs], s_prev[kMaxRhs], rho_k[kMaxRhs], target[kMaxRhs];
     int done[kMaxRhs], first[kMaxRhs], stagnant[kMaxRhs], status[kMaxRhs], total[kMaxRhs];
 
@@ -1078,6 +1135,26 @@ struct Solve {
     // stopped; leaves the final state record in hs
     int inner_single() {
         cudaError_t e;
+        if (!prof && (prm.flags & LQ_CG_NO_GRAPH) == 0) {
+            // the whole inner loop on the device: one graph launch, one read-back
+            if (!igraph.exec) {
+                e = igraph.build(dstate, [&](cudaStream_t s) -> cudaError_t {
+                    cudaError_t r;
+                    if constexpr (SCHUR)
+                        if ((r = launch_stencil<IBS>(omap, sPre1, ePre, s)) != cudaSuccess) return r;
+                    if ((r = launch_stencil<IBS>(imap, sK1, eK1, s)) != cudaSuccess) return r;
+                    if constexpr (SCHUR)
+                        if ((r = launch_stencil<IBS>(omap, sPre2, ePre, s)) != cudaSuccess) return r;
+                    if ((r = launch_stencil<IBS>(imap, sK2, eK2, s)) != cudaSuccess) return r;
+                    return launch_site<kSiteBS>(isite, oK3, s);
+                });
+                if (e != cudaSuccess) return cuda_fail(e, "inner-loop graph");
+            }
+            if ((e = cudaGraphLaunch(igraph.exec, st)) != cudaSuccess) return cuda_fail(e, "inner-loop graph");
+            if ((e = read_state()) != cudaSuccess) return cuda_fail(e, "inner loop");
+            launches += ((SCHUR ? 5 : 3) + 1) * hs.trips;
+            return LQ_OK;
+        }
         int iter_before = 0;
         while (true) {
             for (int j = 0; j < chunk; ++j) {

@@ -155,3 +155,21 @@ def test_cg_full_size_32(lqlib, mode):
     assert status == 0
     assert info["true_rel_resid"] <= 1e-10
     assert _true_resid(dims, m, U, eta, x) <= 1e-10 * RESID_SLACK
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("max_iter", [100000, 7])
+def test_cg_device_loop_equals_host_loop(lqlib, mode, max_iter):
+    """The inner loop run on the device (a conditional CUDA graph) takes the same steps as the
+    host-driven loop: the kernels and their order are the same, so the solution is
+    bit-identical, with the same iteration and cycle counts (also when max_iter cuts a cycle)."""
+    dims = (4, 6, 4, 4)
+    m = 0.05
+    U = synth.gauge_field(dims, seed=19, kind="near_identity", eps=0.3)
+    eta = synth.gaussian_spinor(dims, seed=20)
+    xg, ig, sg = _solve(lqlib, dims, m, U, eta, mode, tol=1e-10, max_iter=max_iter)
+    xh, ih, sh = _solve(lqlib, dims, m, U, eta, mode, tol=1e-10, max_iter=max_iter, graph=False)
+    assert sg == sh
+    assert ig["iters"] == ih["iters"] and ig["cycles"] == ih["cycles"]
+    assert np.array_equal(xg, xh)
+    assert ig["true_rel_resid"] == ih["true_rel_resid"]

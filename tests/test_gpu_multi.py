@@ -137,3 +137,19 @@ def test_cg_multi_full_size_24x24x24x48(lqlib):
     assert all(i["true_rel_resid"] <= 1e-10 for i in infos)
     for i in (0, 11):
         assert _true_resid(dims, m, U, etas[i], xs[i]) <= 1e-10 * RESID_SLACK
+
+
+def test_cg_multi_device_loop_equals_host_loop(lqlib):
+    """A batch whose right-hand sides stop at different iterations: the device-driven inner
+    loop (conditional CUDA graph) and the host-driven one give the same bits and counts."""
+    dims = (4, 4, 2, 4)
+    m = 0.05
+    U = synth.gauge_field(dims, seed=66, kind="near_identity", eps=0.3)
+    etas = [synth.gaussian_spinor(dims, seed=67 + i) for i in range(3)]
+    etas[1] *= 1e-3
+    for mode in ("f64x", "mixed_f16"):
+        xg, ig, sg = _solve_multi(lqlib, dims, m, U, etas, mode, tol=1e-10)
+        xh, ih, sh = _solve_multi(lqlib, dims, m, U, etas, mode, tol=1e-10, graph=False)
+        assert sg == sh == 0
+        assert [i["iters"] for i in ig] == [i["iters"] for i in ih]
+        assert np.array_equal(xg, xh)

@@ -89,3 +89,19 @@ def test_schur_argument_checks(lqlib):
         lqlib.cg_solve_schur(dims, 0.1, U, b, mode="f64", workspace=to_dev(np.zeros(1 << 20, np.uint8)))
     assert lqlib.cg_workspace_bytes_schur(dims, "f64") == 0
     assert 0 < lqlib.cg_workspace_bytes_schur(dims, "mixed_f16") < lqlib.cg_workspace_bytes(dims, "mixed_f16")
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_schur_device_loop_equals_host_loop(lqlib, mode):
+    """The Schur inner loop (with its extra hop kernels) run as a conditional CUDA graph and
+    run from the host take the same steps: bit-identical solutions and the same counts."""
+    dims = (4, 4, 2, 4)
+    m = 0.1
+    U = synth.gauge_field(dims, seed=86, kind="near_identity", eps=0.5)
+    bs = [synth.gaussian_spinor(dims, seed=87), synth.gaussian_spinor(dims, seed=88)]
+    xg, ig, sg = _solve(lqlib, dims, m, U, bs, mode, tol=1e-12)
+    xh, ih, sh = _solve(lqlib, dims, m, U, bs, mode, tol=1e-12, graph=False)
+    assert sg == sh == 0
+    for a, b in zip(ig, ih):
+        assert a["iters"] == b["iters"] and a["cycles"] == b["cycles"]
+    assert np.array_equal(xg, xh)
