@@ -224,8 +224,9 @@ enum {
 typedef struct lq_cg_info {
     int32_t status;          /* same value as returned                                     */
     int32_t iters;           /* inner iterations, all cycles                               */
-    int32_t cycles;          /* outer cycles (Algorithm 1 line 10 loop trips)              */
-    int32_t high_applies;    /* applications of the FP64 D^dag D (Algorithm 1 lines 2, 23) */
+    int32_t cycles;          /* outer cycles of Algorithm 1                                */
+    int32_t high_applies;    /* applications of the FP64 D^dag D (Algorithm 1's residuals);
+                                the first is skipped when the starting guess is zero      */
     double true_rel_resid;   /* ||eta - D^dag D x|| / ||eta||, FP64 operator, at return    */
     double eta_norm;         /* ||eta||                                                    */
     int32_t launches;        /* kernels this call launched (all roles, including skips)     */
@@ -243,7 +244,7 @@ size_t lq_cg_workspace_bytes_multi(const int32_t dims[4], int32_t mode, int32_t 
  * lq_cg_solve -- solve D^dag D x = eta (Algorithm 1 of the paper, Section 1).
  *   U        gauge field, LQ_F64, LQ_LINK18, LQ_LAYOUT_LEX (device).
  *   eta      right-hand side, LQ_F64 LEX spinor (device).
- *   x        in: starting guess psi_0^high (Algorithm 1 line 1); out: solution (device,
+ *   x        in: starting guess psi_0^high (Algorithm 1); out: solution (device,
  *            LQ_F64 LEX spinor; must not overlap eta, U or the workspace).
  *            The outer FP64-class quantities (psi^high, r^high, the residual operator) are held
  *            and computed as FP32 pairs (LQ_F64X) unless LQ_CG_NATIVE_F64 is set; LQ_CG_F64

@@ -1,6 +1,6 @@
 // Field re-encoding between precisions, link formats and layouts (the pack/convert
 // step: the paper streams links in a reduced form prepared beforehand, Section 2.2).
-// One thread per site; formats are the ones documented in include/lq.h.
+// One thread per spinor site or per link; formats are the ones documented in include/lq.h.
 #include "lq_abi_internal.h"
 #include "dslash_kernels.cuh"
 
@@ -8,7 +8,7 @@ namespace lq {
 
 namespace {
 
-constexpr int kConvBS = 256;
+constexpr int kConvBS = 128;
 
 // LQ_F64X fields use the LQ_F64 slots with each double replaced by a float pair
 __host__ __device__ inline int base_prec(int prec) { return prec == LQ_F64X ? LQ_F64 : prec; }
@@ -62,84 +62,247 @@ __device__ inline double load_real(const void* base, int prec, int64_t i) {
     return (double)__half2float(((const __half*)base)[i]);
 }
 
+// x as an FP32 pair, hi = RN32(x) and lo = RN32(x - hi), from integer and FP32 operations:
+// the FP64 conversions and subtraction of dd_from_double run on the FP64 units, which are a
+// small fraction of the FP32 rate on this GPU and would bound the conversion.  The 53-bit
+// significand is cut after 24 bits with round-to-nearest-even (a carry moves into the
+// exponent field); the remainder r (|r| <= 2^28) is x - hi in units of 2^(E-52), and is rounded
+// once to 24 bits by an FMA of its two exact 16-bit halves.  Values whose pair is not two
+// normal floats (zero, |x| < 2^-74, |x| >= 2^127, subnormals, Inf, NaN) take the FP64 route.
+__device__ inline dd split_double(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int E = (int)((b >> 52) & 0x7ffull) - 1023;
+    if (E < -74 || E > 126) return dd_from_double(x);
+    const unsigned long long M = (b & 0xfffffffffffffull) | (1ull << 52);
+    unsigned int keep = (unsigned int)(M >> 29);
+    int rem = (int)(M & 0x1fffffffull);
+    if (rem > 0x10000000 || (rem == 0x10000000 && (keep & 1u))) {
+        keep += 1u;
+        rem -= 0x20000000;
+    }
+    const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+    const float hi = __uint_as_float(sign | (((unsigned int)(E + 127) << 23) + (keep - 0x800000u)));
+    float lo = 0.f;
+    if (rem != 0) {
+        const unsigned int ar = rem < 0 ? (unsigned int)(-rem) : (unsigned int)rem;
+        const float a = __fsub_rn(__uint_as_float(0x4B000000u | (ar >> 16)), 8388608.f);
+        const float c = __fsub_rn(__uint_as_float(0x4B000000u | (ar & 0xffffu)), 8388608.f);
+        const float mag = __fmaf_rn(a, 65536.f, c);
+        const float scale = __uint_as_float((unsigned int)(E - 52 + 127) << 23);
+        lo = __uint_as_float(__float_as_uint(__fmul_rn(mag, scale)) ^ sign ^ (rem < 0 ? 0x80000000u : 0u));
+    }
+    return dd{hi, lo};
+}
+
 // F64 or F64X target
 __device__ inline void store_wide(void* base, int prec, int64_t i, double v) {
     if (prec == LQ_F64) {
         ((double*)base)[i] = v;
     } else {
-        const dd p = dd_from_double(v);
+        const dd p = split_double(v);
         ((float*)base)[2 * i] = p.hi;
         ((float*)base)[2 * i + 1] = p.lo;
     }
 }
 
-__global__ void __launch_bounds__(kConvBS) convert_spinor_kernel(Geom g, FieldDesc src, FieldDesc dst, int nr) {
-    const int64_t n = (int64_t)g.V * nr;
-    for (int64_t f = blockIdx.x * (int64_t)kConvBS + threadIdx.x; f < n; f += (int64_t)gridDim.x * kConvBS) {
-        int c[4];
-        const Site s = site_from_lex(g, (int)(f / nr), c, (int)(f % nr));
-        double v[24];
-        double sc = 1.0;
-        if (src.prec == LQ_F16S)
-            sc = (double)((const float*)src.ptr)[sp_scale_idx(src, g, s, nr)];
-        else if (src.prec == LQ_I32S)
-            sc = (double)((const float*)src.ptr)[sp_scale_idx(src, g, s, nr)] * 0x1p-30;
+// FP64 LEX fields are read and written through a per-warp shared-memory tile, so that a
+// warp moves contiguous 16-byte words; the other side of the conversion is addressed per
+// site.  Stacked LEX fields are contiguous in the field-site index f = rhs V + lex.
+__device__ inline bool wide_lex(const FieldDesc& f) { return f.prec == LQ_F64 && f.layout == LQ_LAYOUT_LEX; }
+
+constexpr int kSpStride = 13;   // staged spinor: 12 double2 + 1 pad (conflict-free 16-byte reads)
+
+// the 24 reals of a spinor site from a non-staged source (scale applied)
+__device__ inline void load_site(const FieldDesc& src, const Geom& g, const Site& s, int nr, double v[24]) {
+    if (src.prec == LQ_F64X && src.layout == LQ_LAYOUT_EO) {
 #pragma unroll
-        for (int j = 0; j < 24; ++j) v[j] = load_real(src.ptr, src.prec, sp_elem(src, g, s, j, nr)) * sc;
-        if (dst.prec == LQ_F64 || dst.prec == LQ_F64X) {
-#pragma unroll
-            for (int j = 0; j < 24; ++j) store_wide(dst.ptr, dst.prec, sp_elem(dst, g, s, j, nr), v[j]);
-        } else if (dst.prec == LQ_F32) {
-#pragma unroll
-            for (int j = 0; j < 24; ++j) ((float*)dst.ptr)[sp_elem(dst, g, s, j, nr)] = (float)v[j];
-        } else if (dst.prec == LQ_I32S) {
-            // s = max |fl32(v)|, q = RN(v / s * 2^30) in FP64, ties to even
-            float m = 0.f;
-#pragma unroll
-            for (int j = 0; j < 24; ++j) m = fmaxf(m, fabsf((float)v[j]));
-            ((float*)dst.ptr)[sp_scale_idx(dst, g, s, nr)] = m;
-            const bool z = !(m > 0.f);
-#pragma unroll
-            for (int j = 0; j < 24; ++j)
-                ((int*)dst.ptr)[sp_elem(dst, g, s, j, nr)] = z ? 0 : __double2int_rn(v[j] / (double)m * 0x1p30);
-        } else {
-            float fv[24];
-            float m = 0.f;
-#pragma unroll
-            for (int j = 0; j < 24; ++j) { fv[j] = (float)v[j]; m = fmaxf(m, fabsf(fv[j])); }
-            ((float*)dst.ptr)[sp_scale_idx(dst, g, s, nr)] = m;
-            const bool z = !(m > 0.f);
-#pragma unroll
-            for (int j = 0; j < 24; ++j)
-                ((__half*)dst.ptr)[sp_elem(dst, g, s, j, nr)] = __float2half_rn(z ? 0.f : __fdiv_rn(fv[j], m));
+        for (int k = 0; k < 12; ++k) {
+            const float4 q = ((const float4*)src.ptr)[sp_elem(src, g, s, 2 * k, nr) / 2];
+            v[2 * k] = (double)q.x + (double)q.y;
+            v[2 * k + 1] = (double)q.z + (double)q.w;
         }
+        return;
+    }
+    double sc = 1.0;
+    if (src.prec == LQ_F16S)
+        sc = (double)((const float*)src.ptr)[sp_scale_idx(src, g, s, nr)];
+    else if (src.prec == LQ_I32S)
+        sc = (double)((const float*)src.ptr)[sp_scale_idx(src, g, s, nr)] * 0x1p-30;
+#pragma unroll
+    for (int j = 0; j < 24; ++j) v[j] = load_real(src.ptr, src.prec, sp_elem(src, g, s, j, nr)) * sc;
+}
+
+// the 24 reals of a spinor site to a non-staged destination
+__device__ inline void store_site(const FieldDesc& dst, const Geom& g, const Site& s, int nr, const double v[24]) {
+    if (dst.prec == LQ_F64X && dst.layout == LQ_LAYOUT_EO) {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            const dd a = split_double(v[2 * k]), b = split_double(v[2 * k + 1]);
+            ((float4*)dst.ptr)[sp_elem(dst, g, s, 2 * k, nr) / 2] = make_float4(a.hi, a.lo, b.hi, b.lo);
+        }
+    } else if (dst.prec == LQ_F64 || dst.prec == LQ_F64X) {
+#pragma unroll
+        for (int j = 0; j < 24; ++j) store_wide(dst.ptr, dst.prec, sp_elem(dst, g, s, j, nr), v[j]);
+    } else if (dst.prec == LQ_F32) {
+#pragma unroll
+        for (int j = 0; j < 24; ++j) ((float*)dst.ptr)[sp_elem(dst, g, s, j, nr)] = (float)v[j];
+    } else if (dst.prec == LQ_I32S) {
+        // s = max |fl32(v)|, q = RN(v / s * 2^30) in FP64, ties to even
+        float m = 0.f;
+#pragma unroll
+        for (int j = 0; j < 24; ++j) m = fmaxf(m, fabsf((float)v[j]));
+        ((float*)dst.ptr)[sp_scale_idx(dst, g, s, nr)] = m;
+        const bool z = !(m > 0.f);
+#pragma unroll
+        for (int j = 0; j < 24; ++j)
+            ((int*)dst.ptr)[sp_elem(dst, g, s, j, nr)] = z ? 0 : __double2int_rn(v[j] / (double)m * 0x1p30);
+    } else {
+        float fv[24];
+        float m = 0.f;
+#pragma unroll
+        for (int j = 0; j < 24; ++j) { fv[j] = (float)v[j]; m = fmaxf(m, fabsf(fv[j])); }
+        ((float*)dst.ptr)[sp_scale_idx(dst, g, s, nr)] = m;
+        const bool z = !(m > 0.f);
+#pragma unroll
+        for (int j = 0; j < 24; ++j)
+            ((__half*)dst.ptr)[sp_elem(dst, g, s, j, nr)] = __float2half_rn(z ? 0.f : __fdiv_rn(fv[j], m));
     }
 }
 
-__global__ void __launch_bounds__(kConvBS) convert_gauge_kernel(Geom g, FieldDesc src, FieldDesc dst) {
-    for (int lex = blockIdx.x * kConvBS + threadIdx.x; lex < g.V; lex += gridDim.x * kConvBS) {
-        int c[4];
-        const Site s = site_from_lex(g, lex, c);
-        for (int mu = 0; mu < 4; ++mu) {
-            for (int j = 0; j < dst.fmt; ++j) {
-                double v = load_real(src.ptr, src.prec, lk_elem(src, g, s, mu, j));
-                if (src.prec == LQ_I32S) v *= 0x1p-30;
-                const int64_t i = lk_elem(dst, g, s, mu, j);
-                if (dst.prec == LQ_F64 || dst.prec == LQ_F64X) store_wide(dst.ptr, dst.prec, i, v);
-                else if (dst.prec == LQ_F32) ((float*)dst.ptr)[i] = (float)v;
-                else if (dst.prec == LQ_I32S) ((int*)dst.ptr)[i] = __double2int_rn(v * 0x1p30);   // Q1.30
-                else ((__half*)dst.ptr)[i] = __float2half_rn((float)v);
+__global__ void __launch_bounds__(kConvBS) convert_spinor_kernel(Geom g, FieldDesc src, FieldDesc dst, int nr) {
+    __shared__ double2 stage[kConvBS / 32][32 * kSpStride];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    double2* sw = stage[wib];
+    const int64_t n = (int64_t)g.V * nr, tiles = (n + 31) / 32;
+    const bool lex_src = wide_lex(src), lex_dst = wide_lex(dst);
+    // the loop bound is the same for every lane of a warp, so the warp barriers are uniform
+    for (int64_t t = (int64_t)blockIdx.x * (kConvBS / 32) + wib; t < tiles; t += (int64_t)gridDim.x * (kConvBS / 32)) {
+        const int64_t f0 = t * 32, f = f0 + lane;
+        const int nv = (int)(n - f0 < 32 ? n - f0 : 32);
+        const bool ok = lane < nv;
+        __syncwarp();
+        if (lex_src) {
+            const double2* s2 = (const double2*)src.ptr + f0 * 12;
+            for (int i = lane; i < nv * 12; i += 32) sw[(i / 12) * kSpStride + i % 12] = __ldg(s2 + i);
+            __syncwarp();
+        }
+        double v[24];
+        Site s{};
+        if (ok) {
+            int c[4];
+            s = site_from_lex(g, (int)(f % g.V), c, (int)(f / g.V));
+            if (lex_src) {
+#pragma unroll
+                for (int k = 0; k < 12; ++k) {
+                    const double2 q = sw[lane * kSpStride + k];
+                    v[2 * k] = q.x;
+                    v[2 * k + 1] = q.y;
+                }
+            } else {
+                load_site(src, g, s, nr, v);
             }
         }
+        if (lex_dst) {
+            __syncwarp();
+            if (ok) {
+#pragma unroll
+                for (int k = 0; k < 12; ++k) sw[lane * kSpStride + k] = make_double2(v[2 * k], v[2 * k + 1]);
+            }
+            __syncwarp();
+            double2* d2 = (double2*)dst.ptr + f0 * 12;
+            for (int i = lane; i < nv * 12; i += 32) d2[i] = sw[(i / 12) * kSpStride + i % 12];
+        } else if (ok) {
+            store_site(dst, g, s, nr, v);
+        }
     }
 }
 
-int conv_grid(const Geom& g, int nr = 1) {
+// the reals of link (s, mu) in a destination format: elements j < dst.fmt of the 18-real link
+__device__ inline void store_link(const FieldDesc& dst, const Geom& g, const Site& s, int mu, const double v[18]) {
+    if (dst.prec == LQ_F64X && dst.layout == LQ_LAYOUT_EO && dst.fmt == 18) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const dd a = split_double(v[2 * k]), b = split_double(v[2 * k + 1]);
+            ((float4*)dst.ptr)[lk_elem(dst, g, s, mu, 2 * k) / 2] = make_float4(a.hi, a.lo, b.hi, b.lo);
+        }
+        return;
+    }
+    if (dst.prec == LQ_F16S && dst.layout == LQ_LAYOUT_EO && dst.fmt == 12) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const __half2 a = __halves2half2(__float2half_rn((float)v[4 * k]), __float2half_rn((float)v[4 * k + 1]));
+            const __half2 b = __halves2half2(__float2half_rn((float)v[4 * k + 2]), __float2half_rn((float)v[4 * k + 3]));
+            ((uint2*)dst.ptr)[lk_elem(dst, g, s, mu, 4 * k) / 4] =
+                make_uint2(*(const uint32_t*)&a, *(const uint32_t*)&b);
+        }
+        return;
+    }
+    if (dst.prec == LQ_F32 && dst.layout == LQ_LAYOUT_EO && dst.fmt == 12) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            ((float4*)dst.ptr)[lk_elem(dst, g, s, mu, 4 * k) / 4] =
+                make_float4((float)v[4 * k], (float)v[4 * k + 1], (float)v[4 * k + 2], (float)v[4 * k + 3]);
+        return;
+    }
+#pragma unroll
+    for (int j = 0; j < 18; ++j) {
+        if (j >= dst.fmt) break;
+        const int64_t i = lk_elem(dst, g, s, mu, j);
+        if (dst.prec == LQ_F64 || dst.prec == LQ_F64X) store_wide(dst.ptr, dst.prec, i, v[j]);
+        else if (dst.prec == LQ_F32) ((float*)dst.ptr)[i] = (float)v[j];
+        else if (dst.prec == LQ_I32S) ((int*)dst.ptr)[i] = __double2int_rn(v[j] * 0x1p30);   // Q1.30
+        else ((__half*)dst.ptr)[i] = __float2half_rn((float)v[j]);
+    }
+}
+
+// one thread per link (site lex, direction mu), link index L = 4 lex + mu; dst2.ptr, if set,
+// receives a second encoding of the same links
+__global__ void __launch_bounds__(kConvBS) convert_gauge_kernel(Geom g, FieldDesc src, FieldDesc dst, FieldDesc dst2) {
+    __shared__ double2 stage[kConvBS / 32][32 * 9];   // lane stride 144 bytes: conflict-free 16-byte reads
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    double2* sw = stage[wib];
+    const int64_t n = (int64_t)g.V * 4, tiles = (n + 31) / 32;
+    const bool lex_src = wide_lex(src) && src.fmt == 18;
+    for (int64_t t = (int64_t)blockIdx.x * (kConvBS / 32) + wib; t < tiles; t += (int64_t)gridDim.x * (kConvBS / 32)) {
+        const int64_t L0 = t * 32, L = L0 + lane;
+        const int nv = (int)(n - L0 < 32 ? n - L0 : 32);
+        __syncwarp();
+        if (lex_src) {
+            const double2* s2 = (const double2*)src.ptr + L0 * 9;
+            for (int i = lane; i < nv * 9; i += 32) sw[i] = __ldg(s2 + i);
+            __syncwarp();
+        }
+        if (lane < nv) {
+            int c[4];
+            const Site s = site_from_lex(g, (int)(L >> 2), c);
+            const int mu = (int)(L & 3);
+            double v[18];
+            if (lex_src) {
+#pragma unroll
+                for (int k = 0; k < 9; ++k) {
+                    const double2 q = sw[lane * 9 + k];
+                    v[2 * k] = q.x;
+                    v[2 * k + 1] = q.y;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 18; ++j) {
+                    v[j] = load_real(src.ptr, src.prec, lk_elem(src, g, s, mu, j));
+                    if (src.prec == LQ_I32S) v[j] *= 0x1p-30;
+                }
+            }
+            store_link(dst, g, s, mu, v);
+            if (dst2.ptr) store_link(dst2, g, s, mu, v);
+        }
+    }
+}
+
+int conv_grid(int64_t items) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    long long want = ((long long)g.V * nr + kConvBS - 1) / kConvBS;
-    long long cap = (long long)sms * 8;
+    const int64_t per_block = kConvBS;   // one item per thread
+    const int64_t want = (items + per_block - 1) / per_block, cap = (int64_t)sms * 16;
     return (int)(want < cap ? (want > 0 ? want : 1) : cap);
 }
 
@@ -147,15 +310,16 @@ int conv_grid(const Geom& g, int nr = 1) {
 
 cudaError_t convert_spinor(const Geom& g, int sp, int sl, const void* src, int dp, int dl, void* dst, cudaStream_t st,
                            int nr) {
-    convert_spinor_kernel<<<conv_grid(g, nr), kConvBS, 0, st>>>(g, FieldDesc{(void*)src, sp, sl, 0},
-                                                                FieldDesc{dst, dp, dl, 0}, nr);
+    convert_spinor_kernel<<<conv_grid((int64_t)g.V * nr), kConvBS, 0, st>>>(g, FieldDesc{(void*)src, sp, sl, 0},
+                                                                          FieldDesc{dst, dp, dl, 0}, nr);
     return cudaGetLastError();
 }
 
 cudaError_t convert_gauge(const Geom& g, int sp, int sl, const void* src, int dp, int dfmt, int dl, void* dst,
-                          cudaStream_t st) {
-    convert_gauge_kernel<<<conv_grid(g), kConvBS, 0, st>>>(g, FieldDesc{(void*)src, sp, sl, 18},
-                                                           FieldDesc{dst, dp, dl, dfmt});
+                          cudaStream_t st, int dp2, int dfmt2, int dl2, void* dst2) {
+    const FieldDesc second = dst2 ? FieldDesc{dst2, dp2, dl2, dfmt2} : FieldDesc{nullptr, 0, 0, 0};
+    convert_gauge_kernel<<<conv_grid((int64_t)g.V * 4), kConvBS, 0, st>>>(g, FieldDesc{(void*)src, sp, sl, 18},
+                                                                       FieldDesc{dst, dp, dl, dfmt}, second);
     return cudaGetLastError();
 }
 

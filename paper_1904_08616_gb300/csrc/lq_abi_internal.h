@@ -22,8 +22,9 @@ size_t gauge_bytes(int64_t V, int prec, int fmt);
 
 cudaError_t convert_spinor(const Geom& g, int sp, int sl, const void* src, int dp, int dl, void* dst, cudaStream_t st,
                            int nr = 1);
+// dst2 (optional): a second encoding (dp2, dfmt2, dl2) of the same links from the same pass
 cudaError_t convert_gauge(const Geom& g, int sp, int sl, const void* src, int dp, int dfmt, int dl, void* dst,
-                          cudaStream_t st);
+                          cudaStream_t st, int dp2 = 0, int dfmt2 = 0, int dl2 = 0, void* dst2 = nullptr);
 
 cudaError_t link_grad(const Geom& g, const void* gf, const void* psi, double scale, bool accumulate, void* out,
                       cudaStream_t st);

@@ -3,15 +3,15 @@
 //
 // One driver serves all modes.  The outer loop is Algorithm 1's: FP64-class solution
 // psi^high, FP64-class residual r^high = eta - A psi^high recomputed with the FP64-class
-// operator (lines 2 and 23), s = ||r^high||, and an inner CG (lines 13-20) on the
+// operator at the start and after every cycle, s = ||r^high||, and an inner CG on the
 // unit-norm residual r_0 = r^high / s in the inner precision.  The inner loop uses
 // three fused kernels per iteration:
 //   K1  t = D p                       + ||t||^2 = <p, A p>  -> alpha = rho / <p, A p>
 //   K2  q = D^dag t (in registers); psi += alpha p; r -= alpha q  + ||r||^2 -> beta, stop
 //   K3  p = r + beta p
 // Scalars live in a device-side state record (one slot per right-hand side) written by
-// the last block of each reducing kernel; the host only reads that record between
-// chunks of iterations.  A right-hand side whose inner loop has stopped is skipped by
+// the last block of each reducing kernel; the host reads that record once per cycle (or
+// between chunks of iterations when it drives the inner loop itself).  A right-hand side whose inner loop has stopped is skipped by
 // the kernels while the others go on; the cycles (reliable updates) are taken together.
 //
 // Readings of Algorithm 1 (the text has index garbles):
@@ -258,7 +258,7 @@ struct OpK3 {
 };
 
 // ------------------------------------------------------------------------------------
-// cycle start (Algorithm 1 lines 8-12), per right-hand side that takes part (act)
+// cycle start (Algorithm 1), per right-hand side that takes part (act)
 // ------------------------------------------------------------------------------------
 // r = fl_low(r^high / s); first cycle: p = r; psi = 0.  Reduces <r, p> and ||r||^2.
 template <class RHA, class RA, class PA, class XA>
@@ -377,7 +377,7 @@ struct OpRestartP {
     template <int BS> __device__ __forceinline__ void finish(const double (&)[1], const VGrid& vg) const {}
 };
 
-// psi^high += s psi  (Algorithm 1 line 22 as read above), in the outer arithmetic
+// psi^high += s psi  (the cycle's update of Algorithm 1 as read above), in the outer arithmetic
 template <class XA, class PsiA>
 struct OpXUpdate {
     using Real = typename XA::Real;
@@ -427,6 +427,38 @@ struct OpNorm {
         const int n = nr, sl = slot;
         grid_reduce_seg<BS, 1>(rc, kTicketMisc, red, n, vg, [st, n, sl](const double* t) {
             for (int j = 0; j < n; ++j) st->red[sl][j] = t[j];
+        });
+    }
+};
+
+// ||eta||^2 -> st->red[3][rhs] and the number of nonzero components of x -> st->red[1][rhs]:
+// for a zero starting guess the first outer residual is eta itself
+template <class A>
+struct OpNormEtaX {
+    static constexpr int NRED = 2;
+    A eta, x;
+    RedCtx rc;
+    int nr;
+    LQ_HD bool init() { return true; }
+    LQ_HD bool active() const { return true; }
+    LQ_HD void apply(const Site& s, double* red) const {
+        Spinor<double> v;
+        eta.load(s, v);
+        red[0] += norm2(v);
+        x.load(s, v);
+        double nz = 0.0;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) nz += (v.v[k].re != 0.0 ? 1.0 : 0.0) + (v.v[k].im != 0.0 ? 1.0 : 0.0);
+        red[1] += nz;
+    }
+    template <int BS> __device__ __forceinline__ void finish(const double (&red)[2], const VGrid& vg) const {
+        SolverState* st = rc.st;
+        const int n = nr;
+        grid_reduce_seg<BS, 2>(rc, kTicketMisc, red, n, vg, [st, n](const double* t) {
+            for (int j = 0; j < n; ++j) {
+                st->red[3][j] = t[j];
+                st->red[1][j] = t[kMaxRhs + j];
+            }
         });
     }
 };
@@ -928,7 +960,7 @@ struct Solve {
         return launch_stencil<kBS>(map, sten, e, st);
     }
 
-    // r^high = eta - A x, s^2 -> red[2][.]   (Algorithm 1 lines 2 and 23)
+    // r^high = eta - A x, s^2 -> red[2][.]   (Algorithm 1: the high-precision residual)
     cudaError_t high_residual() {
         if constexpr (SCHUR) {
             // tmp_o = H_oe x_e;  t_e = A x_e - H_eo tmp_o / A;  tmp_o = H^dag_oe t_e;
@@ -988,19 +1020,19 @@ struct Solve {
         if ((e = cudaMemsetAsync(dstate, 0, sizeof(SolverState), st)) != cudaSuccess ||
             (e = cudaMemsetAsync(&dstate->all_stop, 1, sizeof(dstate->all_stop), st)) != cudaSuccess)
             return cuda_fail(e, "state init");
+        constexpr bool kLowLinks = IP != LQ_F64 && IP != LQ_F64X;   // reduced-precision inner links
         if constexpr (kPairs) {
-            // Schur: the caller's right-hand side is b (full, kept as pairs in b_x); eta-hat is
-            // built from it below
-            if ((e = convert_gauge(g, LQ_F64, LQ_LAYOUT_LEX, U, LQ_F64X, 18, LQ_LAYOUT_EO, ws + w.u_x, st)) !=
-                    cudaSuccess ||
+            // pair links and the inner links from one pass over U.  Schur: the caller's
+            // right-hand side is b (full, kept as pairs in b_x); eta-hat is built from it below
+            if ((e = convert_gauge(g, LQ_F64, LQ_LAYOUT_LEX, U, LQ_F64X, 18, LQ_LAYOUT_EO, ws + w.u_x, st, IP, IF, IL,
+                                   kLowLinks ? (void*)(ws + w.u_low) : nullptr)) != cudaSuccess ||
                 (e = convert_spinor(g, LQ_F64, LQ_LAYOUT_LEX, eta, LQ_F64X, LQ_LAYOUT_EO,
                                     ws + (SCHUR ? w.b_x : w.eta_x), st, nb)) != cudaSuccess ||
                 (e = convert_spinor(g, LQ_F64, LQ_LAYOUT_LEX, x, LQ_F64X, LQ_LAYOUT_EO, ws + w.x_x, st, nb)) !=
                     cudaSuccess)
                 return cuda_fail(e, "FP32-pair copies");
             launches += 3;
-        }
-        if constexpr (IP != LQ_F64 && IP != LQ_F64X) {   // reduced-precision inner links
+        } else if constexpr (kLowLinks) {
             if ((e = convert_gauge(g, LQ_F64, LQ_LAYOUT_LEX, U, IP, IF, IL, ws + w.u_low, st)) != cudaSuccess)
                 return cuda_fail(e, "link pack");
             launches += 1;
@@ -1018,8 +1050,10 @@ struct Solve {
                 return cuda_fail(e, "Schur right-hand side");
             launches += 1;
         } else {
-            // ||eta||^2 -> red[3][.], from the caller's FP64 eta
-            if ((e = launch_site<kSiteBS>(lexsite, OpNorm<CallerRO>{eta_caller, rc, nb, 3}, st)) != cudaSuccess)
+            // ||eta||^2 -> red[3][.] from the caller's FP64 eta; nonzero count of x -> red[1][.]
+            const CallerRO x_caller_ro = make_spinor<LQ_F64, LQ_LAYOUT_LEX, true>(x, g, false, nb);
+            if ((e = launch_site<kSiteBS>(lexsite, OpNormEtaX<CallerRO>{eta_caller, x_caller_ro, rc, nb}, st)) !=
+                cudaSuccess)
                 return cuda_fail(e, "norm");
             launches += 1;
         }
@@ -1058,11 +1092,24 @@ struct Solve {
                 launches += 1;
             }
         }
-        if ((e = high_residual()) != cudaSuccess) return cuda_fail(e, "residual");
-        if ((e = read_state()) != cudaSuccess) return cuda_fail(e, "residual");
-        account_high();
-        for (int j = 0; j < nb; ++j) s[j] = sqrt(hs.red[2][j]);
-        high_applies = 1;
+        // Algorithm 1 starts from r = eta - D^dag D x0; a zero x0 (every right-hand side still
+        // to solve) makes that eta itself, so the outer operator is not applied
+        bool x0_zero = !SCHUR;
+        if constexpr (!SCHUR)
+            for (int j = 0; j < nb; ++j) x0_zero = x0_zero && (done[j] || hs.red[1][j] == 0.0);
+        if (x0_zero) {
+            if ((e = cudaMemcpyAsync(ws + w.r_high, etao, spinor_bytes((int64_t)g.V * nb, HP),
+                                     cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+                return cuda_fail(e, "residual");
+            for (int j = 0; j < nb; ++j) s[j] = eta_norm[j];
+            high_applies = 0;
+        } else {
+            if ((e = high_residual()) != cudaSuccess) return cuda_fail(e, "residual");
+            if ((e = read_state()) != cudaSuccess) return cuda_fail(e, "residual");
+            account_high();
+            for (int j = 0; j < nb; ++j) s[j] = sqrt(hs.red[2][j]);
+            high_applies = 1;
+        }
         l = 0;
         return LQ_OK;
     }
@@ -1092,7 +1139,7 @@ struct Solve {
         return any;
     }
 
-    // cycle start (Algorithm 1 lines 8-12)
+    // cycle start (Algorithm 1)
     int start_cycle() {
         OpRestart<HiRO, SpRW, SpRW, SpRW> op;
         op.rh = rh_ro;

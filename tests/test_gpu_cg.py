@@ -173,3 +173,22 @@ def test_cg_device_loop_equals_host_loop(lqlib, mode, max_iter):
     assert ig["iters"] == ih["iters"] and ig["cycles"] == ih["cycles"]
     assert np.array_equal(xg, xh)
     assert ig["true_rel_resid"] == ih["true_rel_resid"]
+
+
+@pytest.mark.parametrize("mode", ["f64", "f64x", "mixed_f16"])
+def test_cg_zero_guess_starts_from_eta(lqlib, mode):
+    """With x0 = 0 the first outer residual eta - D^dag D x0 is eta itself and the operator is
+    not applied for it; one nonzero component (even a subnormal one) in x0 restores the apply."""
+    dims = (4, 4, 4, 4)
+    m = 0.1
+    U = synth.gauge_field(dims, seed=21)
+    eta = synth.gaussian_spinor(dims, seed=22)
+    x0, info0, st0 = _solve(lqlib, dims, m, U, eta, mode, tol=1e-10)
+    tiny = np.zeros_like(eta)
+    tiny[5, 2, 1] = 1e-310 * 1j
+    x1, info1, st1 = _solve(lqlib, dims, m, U, eta, mode, x0=tiny, tol=1e-10)
+    assert st0 == st1 == 0
+    assert info0["high_applies"] == info0["cycles"]
+    assert info1["high_applies"] == info1["cycles"] + 1
+    assert _true_resid(dims, m, U, eta, x0) <= 1e-10 * RESID_SLACK
+    assert _true_resid(dims, m, U, eta, x1) <= 1e-10 * RESID_SLACK

@@ -65,6 +65,33 @@ def test_convert_spinor_bit_exact(lqlib, dims, prec, layout):
                           F.decode_spinor(to_host(dst), dims, prec, layout))
 
 
+@pytest.mark.parametrize("layout", ["lex", "eo"])
+def test_convert_pairs_bit_exact_at_the_edges(lqlib, layout):
+    """FP64 -> FP32 pairs (hi = fl32(v), lo = fl32(v - hi)) for values that probe the split:
+    rounding ties to even either way, a carry out of the significand, the exponent range ends
+    of the fast integer route and the values outside it (zero, subnormal, tiny, near FP32
+    overflow), and random doubles spread over 2^-90 .. 2^127."""
+    dims = (4, 2, 2, 2)
+    V = synth.volume(dims)
+    rng = np.random.default_rng(9)
+    edge = np.array([0.0, -0.0, 1.0, -1.0, 1 + 2.0**-24, 1 + 3 * 2.0**-24, -(1 + 2.0**-24), 2 - 2.0**-52,
+                     1.5 * 2.0**-74, 2.0**-74, 1.9 * 2.0**-75, 2.0**126 * (2 - 2.0**-30), 2.0**126 * (2 - 2.0**-52),
+                     3e38, 1e-30, 2.0**-1022, 5e-324, 2.0**-50 + 2.0**-80, 1 + 2.0**-24 + 2.0**-60,
+                     -(2 - 2.0**-52), 7 * 2.0**-77])
+    mant = rng.uniform(1.0, 2.0, 24 * V) * rng.choice([-1.0, 1.0], 24 * V)
+    vals = np.ldexp(mant, rng.integers(-90, 127, 24 * V))
+    bits = vals.view(np.uint64)
+    tie = rng.integers(0, 3, 24 * V)
+    low = np.where(tie == 0, 0x10000000, np.where(tie == 1, 0x0FFFFFFF, 0x10000001)).astype(np.uint64)
+    bits[::5] = (bits[::5] & ~np.uint64(0x1FFFFFFF)) | low[::5]
+    vals[:edge.size] = edge
+    psi = vals.reshape(V, 4, 3, 2)
+    psi = psi[..., 0] + 1j * psi[..., 1]
+    src = to_dev(F.encode_spinor(psi, dims, "f64", "lex"))
+    dst = lqlib.convert_spinor(dims, src, "f64", "lex", dst_prec="f64x", dst_layout=layout)
+    assert np.array_equal(to_host(dst), F.encode_spinor(psi, dims, "f64x", layout))
+
+
 @pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 10, 2)])
 @pytest.mark.parametrize("prec", ["f64", "f32", "f16s", "f64x", "i32s"])
 @pytest.mark.parametrize("fmt", [18, 12])
