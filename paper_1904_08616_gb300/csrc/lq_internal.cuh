@@ -286,7 +286,7 @@ template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F32, LAYOUT, RO> {
 template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F16S, LAYOUT, RO> {
     using Real = float;
     static constexpr int K = 3;
-    static constexpr bool kScaled = true;
+    static constexpr bool kScaled = true, kHalf2 = true;
     uint4* ptr;
     float* scale;
     EoIdx e;
@@ -303,6 +303,19 @@ template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F16S, LAYOUT, RO> {
                 float2 a = h2f2(ww[j]);
                 out.v[4 * k + j] = {a.x, a.y};
             }
+        }
+    }
+    // the stored complex numbers as half2 words (re low, im high), without the scale
+    LQ_HD void load_h2(const Site& s, uint32_t out[12], float& sc) const {
+        const uint32_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
+        sc = ld<RO>(scale + sp_sidx<LAYOUT>(s, e));
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const uint4 w = ld<RO>(ptr + b + k * ks);
+            out[4 * k] = w.x;
+            out[4 * k + 1] = w.y;
+            out[4 * k + 2] = w.z;
+            out[4 * k + 3] = w.w;
         }
     }
     template <typename T> LQ_HD void load(const Site& s, Spinor<T>& out) const {
@@ -514,8 +527,15 @@ template <int LAYOUT> struct GaugeAcc<LQ_F32, 12, LAYOUT> {
 template <int LAYOUT> struct GaugeAcc<LQ_F16S, 18, LAYOUT> {
     using Real = float;
     static constexpr int K = 9;
+    static constexpr bool kHalf2 = true, kRebuild = false;
     const uint32_t* ptr;
     uint32_t Vh;
+    // the 9 complex entries as half2 words, row-major
+    LQ_HD void load_h2(const Site& s, int mu, uint32_t u[9]) const {
+        const uint32_t b = lk_base<LAYOUT>(s, mu, K, Vh), ks = lk_kstride<LAYOUT>(Vh);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) u[k] = ld<true>(ptr + b + k * ks);
+    }
     LQ_HD void load(const Site& s, int mu, Link<float>& U) const {
         const uint32_t b = lk_base<LAYOUT>(s, mu, K, Vh), ks = lk_kstride<LAYOUT>(Vh);
 #pragma unroll
@@ -528,8 +548,19 @@ template <int LAYOUT> struct GaugeAcc<LQ_F16S, 18, LAYOUT> {
 template <int LAYOUT> struct GaugeAcc<LQ_F16S, 12, LAYOUT> {
     using Real = float;
     static constexpr int K = 3;
+    static constexpr bool kHalf2 = true, kRebuild = true;
     const uint2* ptr;
     uint32_t Vh;
+    // rows 0 and 1 (6 complex entries) as half2 words; the caller rebuilds row 2
+    LQ_HD void load_h2(const Site& s, int mu, uint32_t u[9]) const {
+        const uint32_t b = lk_base<LAYOUT>(s, mu, K, Vh), ks = lk_kstride<LAYOUT>(Vh);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const uint2 w = ld<true>(ptr + b + k * ks);
+            u[2 * k] = w.x;
+            u[2 * k + 1] = w.y;
+        }
+    }
     LQ_HD void load(const Site& s, int mu, Link<float>& U) const {
         const uint32_t b = lk_base<LAYOUT>(s, mu, K, Vh), ks = lk_kstride<LAYOUT>(Vh);
 #pragma unroll
