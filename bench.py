@@ -327,7 +327,7 @@ def run_ours(args, rank, world, local_rank):
         "metric": "Dslash site-updates/s (whole mixed-precision CG solve to 1e-10)",
         "value": value, "unit": "site-updates/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {"mixed_f16": "f16 hop arithmetic with f32 accumulation (f16s storage) inner / f32-pair (fp64-class) outer",
+        "vs_baseline": None, "dtype": {"mixed_f16": "f32 accumulation, f16 spin projection (f16s storage) inner / f32-pair (fp64-class) outer",
                                        "mixed_f32": "f32 inner / f32-pair (fp64-class) outer",
                                        "f64": "f64", "f64x": "f32-pair (fp64-class)",
                                        "mixed_i32": "f32 (i32 fixed-point storage) inner / f32-pair outer"}[mode],

@@ -180,28 +180,24 @@ LQ_HD void hop_dir_rt(Spinor<R>& acc, const Spinor<R>& q, const Link<R>& U, R sc
     }
 }
 
-// Scaled-FP16 hops: the spin projection, the rebuild of the third link row and the colour
-// mat-vec run in half2 arithmetic on the stored words (a complex number is one half2 word,
-// re low, im high, so a complex times a real broadcast is one HFMA2); the two products of a
-// hop are widened to FP32 and accumulated over the eight hops, with the neighbour's scale,
-// in FP32.  The stored values are scaled to |v| <= 1 per site and links are unitary, so the
-// half2 intermediates stay of order one (|h| <= 2 per real part, |U h| < 5).
+// Scaled-FP16 hops: the spin projection runs in half2 arithmetic on the stored words (a
+// complex number is one half2 word, re low, im high; each projected component is one add of
+// two stored values, rounded once to FP16), so the neighbour spinor is never widened in
+// full: only the two projected colour vectors are.  The link mat-vec and the accumulation
+// over the eight hops, with the neighbour's scale, are FP32.  The stored values are scaled
+// to |v| <= 1 per site, so the projected components stay within |h| <= 2.
 namespace h2 {
 __device__ __forceinline__ __half2 w2h(uint32_t w) { return *reinterpret_cast<const __half2*>(&w); }
 __device__ __forceinline__ uint32_t h2w(__half2 h) { return *reinterpret_cast<const uint32_t*>(&h); }
-// i a = (-a.im, a.re),  -i a = (a.im, -a.re),  conj(a)
+// i a = (-a.im, a.re),  -i a = (a.im, -a.re)
 __device__ __forceinline__ __half2 mul_i(__half2 a) { return w2h(__byte_perm(h2w(a), 0u, 0x1032u) ^ 0x00008000u); }
 __device__ __forceinline__ __half2 mul_mi(__half2 a) { return w2h(__byte_perm(h2w(a), 0u, 0x1032u) ^ 0x80000000u); }
-__device__ __forceinline__ __half2 conj(__half2 a) { return w2h(h2w(a) ^ 0x80000000u); }
 template <int S> __device__ __forceinline__ __half2 pm(__half2 a, __half2 b) {
     if constexpr (S > 0) return __hadd2(a, b);
     else return __hsub2(a, b);
 }
-// a b for complex a, b: re(a) b + im(a) (i b), with ib = i b given
-__device__ __forceinline__ __half2 cmul(__half2 a, __half2 b, __half2 ib) {
-    return __hfma2(__high2half2(a), ib, __hmul2(__low2half2(a), b));
-}
 
+// the rank-2 projection of hop_project on half2 words
 template <int MU, int S>
 __device__ __forceinline__ void project(const uint32_t q[12], __half2 h0[3], __half2 h1[3]) {
 #pragma unroll
@@ -223,67 +219,24 @@ __device__ __forceinline__ void project(const uint32_t q[12], __half2 h0[3], __h
     }
 }
 
-// row 2 = conj(row 0 x row 1) for a two-row link
-__device__ __forceinline__ void rebuild(__half2 u[3][3]) {
-    __half2 ib[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) ib[k] = mul_i(u[1][k]);
-    const __half2* a = u[0];
-    const __half2* b = u[1];
-    u[2][0] = conj(__hsub2(cmul(a[1], b[2], ib[2]), cmul(a[2], b[1], ib[1])));
-    u[2][1] = conj(__hsub2(cmul(a[2], b[0], ib[0]), cmul(a[0], b[2], ib[2])));
-    u[2][2] = conj(__hsub2(cmul(a[0], b[1], ib[1]), cmul(a[1], b[0], ib[0])));
-}
-
-// g = U h (BACK = false) or U^dag h (BACK = true) for both colour vectors
-template <bool BACK>
-__device__ __forceinline__ void matvec(const __half2 u[3][3], const __half2 h0[3], const __half2 h1[3],
-                                       __half2 g0[3], __half2 g1[3]) {
-    // U h = re(U) h + im(U) (i h);  conj(U) h = re(U) h + im(U) (-i h)
-    __half2 r0[3], r1[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        r0[k] = BACK ? mul_mi(h0[k]) : mul_i(h0[k]);
-        r1[k] = BACK ? mul_mi(h1[k]) : mul_i(h1[k]);
-    }
-#pragma unroll
-    for (int A = 0; A < 3; ++A) {
-        __half2 x = BACK ? u[0][A] : u[A][0];
-        __half2 lo = __low2half2(x), hi = __high2half2(x);
-        g0[A] = __hfma2(hi, r0[0], __hmul2(lo, h0[0]));
-        g1[A] = __hfma2(hi, r1[0], __hmul2(lo, h1[0]));
-#pragma unroll
-        for (int B = 1; B < 3; ++B) {
-            x = BACK ? u[B][A] : u[A][B];
-            lo = __low2half2(x);
-            hi = __high2half2(x);
-            g0[A] = __hfma2(hi, r0[B], __hfma2(lo, h0[B], g0[A]));
-            g1[A] = __hfma2(hi, r1[B], __hfma2(lo, h1[B], g1[A]));
-        }
-    }
-}
-
-template <int MU, int S, bool BACK, bool REBUILD>
-__device__ __forceinline__ void hop(Spinor<float>& acc, const uint32_t q[12], const uint32_t uw[9], float sc) {
-    __half2 u[3][3];
-#pragma unroll
-    for (int k = 0; k < (REBUILD ? 6 : 9); ++k) u[k / 3][k % 3] = w2h(uw[k]);
-    if constexpr (REBUILD) rebuild(u);
-    __half2 h0[3], h1[3], g0[3], g1[3];
+// acc += sc * U' (1 + S gamma_MU) q for a stored scaled-FP16 neighbour q
+template <int MU, int S, bool BACK>
+__device__ __forceinline__ void hop(Spinor<float>& acc, const uint32_t q[12], const Link<float>& U, float sc) {
+    __half2 h0[3], h1[3];
     project<MU, S>(q, h0, h1);
-    matvec<BACK>(u, h0, h1, g0, g1);
-    cplx<float> f0[3], f1[3];
+    cplx<float> f0[3], f1[3], g0[3], g1[3];
 #pragma unroll
-    for (int A = 0; A < 3; ++A) {
-        const float2 a = __half22float2(g0[A]), b = __half22float2(g1[A]);
-        f0[A] = {a.x, a.y};
-        f1[A] = {b.x, b.y};
+    for (int c = 0; c < 3; ++c) {
+        const float2 a = __half22float2(h0[c]), b = __half22float2(h1[c]);
+        f0[c] = {a.x, a.y};
+        f1[c] = {b.x, b.y};
     }
-    hop_accumulate<MU, S, true>(acc, f0, f1, sc);
+    hop_matvec<BACK>(U, f0, f1, g0, g1);
+    hop_accumulate<MU, S, true>(acc, g0, g1, sc);
 }
 }  // namespace h2
 
-// accessors of scaled-FP16 fields expose their stored half2 words (load_h2)
+// spinor accessors of scaled-FP16 fields expose their stored half2 words (load_h2)
 template <class A, class = void> struct HasHalf2 : std::false_type {};
 template <class A> struct HasHalf2<A, std::void_t<decltype(A::kHalf2)>> : std::bool_constant<A::kHalf2> {};
 
@@ -300,7 +253,7 @@ struct Stencil {
     GA ga;
     SA sa;
 
-    static constexpr bool kHalf = HasHalf2<GA>::value && HasHalf2<SA>::value;
+    static constexpr bool kHalf = HasHalf2<SA>::value;
 
     template <int MU>
     LQ_HD void dir(const Site& s, const int c[4], Spinor<Real>& acc) const {
@@ -310,14 +263,15 @@ struct Stencil {
         constexpr bool SC = SA::kScaled;
 #ifdef __CUDA_ARCH__
         if constexpr (kHalf) {
-            uint32_t q[12], uw[9];
+            uint32_t q[12];
             float sc;
+            Link<float> U;
             sa.load_h2(nf, q, sc);
-            ga.load_h2(s, MU, uw);
-            h2::hop<MU, SF, false, GA::kRebuild>(acc, q, uw, sc);
+            ga.load(s, MU, U);
+            h2::hop<MU, SF, false>(acc, q, U, sc);
             sa.load_h2(nb, q, sc);
-            ga.load_h2(nb, MU, uw);
-            h2::hop<MU, -SF, true, GA::kRebuild>(acc, q, uw, sc);
+            ga.load(nb, MU, U);
+            h2::hop<MU, -SF, true>(acc, q, U, sc);
             return;
         }
 #endif

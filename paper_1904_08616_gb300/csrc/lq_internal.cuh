@@ -527,15 +527,8 @@ template <int LAYOUT> struct GaugeAcc<LQ_F32, 12, LAYOUT> {
 template <int LAYOUT> struct GaugeAcc<LQ_F16S, 18, LAYOUT> {
     using Real = float;
     static constexpr int K = 9;
-    static constexpr bool kHalf2 = true, kRebuild = false;
     const uint32_t* ptr;
     uint32_t Vh;
-    // the 9 complex entries as half2 words, row-major
-    LQ_HD void load_h2(const Site& s, int mu, uint32_t u[9]) const {
-        const uint32_t b = lk_base<LAYOUT>(s, mu, K, Vh), ks = lk_kstride<LAYOUT>(Vh);
-#pragma unroll
-        for (int k = 0; k < 9; ++k) u[k] = ld<true>(ptr + b + k * ks);
-    }
     LQ_HD void load(const Site& s, int mu, Link<float>& U) const {
         const uint32_t b = lk_base<LAYOUT>(s, mu, K, Vh), ks = lk_kstride<LAYOUT>(Vh);
 #pragma unroll
@@ -548,19 +541,8 @@ template <int LAYOUT> struct GaugeAcc<LQ_F16S, 18, LAYOUT> {
 template <int LAYOUT> struct GaugeAcc<LQ_F16S, 12, LAYOUT> {
     using Real = float;
     static constexpr int K = 3;
-    static constexpr bool kHalf2 = true, kRebuild = true;
     const uint2* ptr;
     uint32_t Vh;
-    // rows 0 and 1 (6 complex entries) as half2 words; the caller rebuilds row 2
-    LQ_HD void load_h2(const Site& s, int mu, uint32_t u[9]) const {
-        const uint32_t b = lk_base<LAYOUT>(s, mu, K, Vh), ks = lk_kstride<LAYOUT>(Vh);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const uint2 w = ld<true>(ptr + b + k * ks);
-            u[2 * k] = w.x;
-            u[2 * k + 1] = w.y;
-        }
-    }
     LQ_HD void load(const Site& s, int mu, Link<float>& U) const {
         const uint32_t b = lk_base<LAYOUT>(s, mu, K, Vh), ks = lk_kstride<LAYOUT>(Vh);
 #pragma unroll
