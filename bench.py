@@ -91,7 +91,9 @@ def ncu_traffic(kernel_role):
 class ClockSampler:
     def __init__(self, gpu_index):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        # the raw samples go to $LQ_BENCH_OUT (default: bench_out/ beside this file)
+        out = os.environ.get("LQ_BENCH_OUT") or os.path.join(ROOT, "bench_out")
+        self.path = os.path.join(out, f"clocks_rank{gpu_index}.csv")
         self.gpu = gpu_index
 
     def __enter__(self):
