@@ -705,10 +705,14 @@ struct InnerGraph {
     InnerGraph() = default;
     InnerGraph(const InnerGraph&) = delete;
     InnerGraph& operator=(const InnerGraph&) = delete;
-    ~InnerGraph() {
+    ~InnerGraph() { reset(); }
+    void reset() {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
         if (cs) cudaStreamDestroy(cs);
+        exec = nullptr;
+        graph = nullptr;
+        cs = nullptr;
     }
     // body(stream) enqueues one iteration's kernels
     template <class Body>
@@ -841,6 +845,7 @@ struct Solve {
     int kcalls[4] = {0, 0, 0, 0};
     EventSet evs;
     InnerGraph igraph;
+    bool graph_off = false;   // the inner-loop graph could not be built
     double eta_norm[kMaxRhs], s[kMaxRhs], s_prev[kMaxRhs], rho_k[kMaxRhs], target[kMaxRhs];
     int done[kMaxRhs], first[kMaxRhs], stagnant[kMaxRhs], status[kMaxRhs], total[kMaxRhs];
 
@@ -1182,7 +1187,7 @@ struct Solve {
     // stopped; leaves the final state record in hs
     int inner_single() {
         cudaError_t e;
-        if (!prof && (prm.flags & LQ_CG_NO_GRAPH) == 0) {
+        if (!prof && !graph_off && (prm.flags & LQ_CG_NO_GRAPH) == 0) {
             // the whole inner loop on the device: one graph launch, one read-back
             if (!igraph.exec) {
                 e = igraph.build(dstate, [&](cudaStream_t s) -> cudaError_t {
@@ -1195,12 +1200,20 @@ struct Solve {
                     if ((r = launch_stencil<IBS>(imap, sK2, eK2, s)) != cudaSuccess) return r;
                     return launch_site<kSiteBS>(isite, oK3, s);
                 });
-                if (e != cudaSuccess) return cuda_fail(e, "inner-loop graph");
+                if (e != cudaSuccess) {
+                    // no conditional graph here (driver or capture refused it): the host
+                    // drives the same kernels below for the rest of the solve
+                    (void)cudaGetLastError();
+                    igraph.reset();
+                    graph_off = true;
+                }
             }
-            if ((e = cudaGraphLaunch(igraph.exec, st)) != cudaSuccess) return cuda_fail(e, "inner-loop graph");
-            if ((e = read_state()) != cudaSuccess) return cuda_fail(e, "inner loop");
-            launches += ((SCHUR ? 5 : 3) + 1) * hs.trips;
-            return LQ_OK;
+            if (!graph_off) {
+                if ((e = cudaGraphLaunch(igraph.exec, st)) != cudaSuccess) return cuda_fail(e, "inner-loop graph");
+                if ((e = read_state()) != cudaSuccess) return cuda_fail(e, "inner loop");
+                launches += ((SCHUR ? 5 : 3) + 1) * hs.trips;
+                return LQ_OK;
+            }
         }
         int iter_before = 0;
         while (true) {
