@@ -409,7 +409,8 @@ def run_workload(args):
 
         def one():
             kw = {"block": args.lattice_block} if args.lattice_block else {"autotune": True}
-            xs, infos, st = lq.cg_solve_lattices(probs, mode=args.mode, tol=TOL, **kw)
+            xs, infos, st = lq.cg_solve_lattices(probs, mode=args.mode, tol=TOL, graph=args.inner_loop == "device",
+                                                 **kw)
             assert st == 0
             return infos
 
@@ -427,7 +428,8 @@ def run_workload(args):
         line.update({"config": {"lattices": [list(d) + [n] for d, n in specs], "m_q": 0.1, "links": "haar",
                                 "tol": TOL},
                      "value": upd / (ms * 1e-3), "ms_per_solve": ms, "ms_sequential_multi": ms_seq,
-                     "block": infos[0][0]["block"], "iters": [max(i["iters"] for i in li) for li in infos]})
+                     "block": infos[0][0]["block"], "iters": [max(i["iters"] for i in li) for li in infos],
+                     "inner_loop": args.inner_loop})
     elif args.workload == "batched":
         dims, nr = (24, 24, 24, 48), 12
         U_d = field(synth.gauge_field(dims, seed=5))
@@ -548,6 +550,9 @@ def main():
                          "measurement line for the uneven-lattice, 12-RHS and 64^3x128 workloads")
     ap.add_argument("--lattice-block", type=int, default=0, choices=[0, 64, 128, 256],
                     help="lattices workload: inner block size (0: tuned)")
+    ap.add_argument("--inner-loop", default="device", choices=["device", "host"],
+                    help="lattices workload: inner loop driven by a conditional CUDA graph (device) or "
+                         "launched kernel by kernel from the host (every kernel visible to a profiler)")
     args = ap.parse_args()
     if args.workload != "cg32":
         run_workload(args)

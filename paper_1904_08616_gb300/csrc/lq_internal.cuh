@@ -627,6 +627,7 @@ struct SolverState {
     int nr;                     // right-hand sides in the batch
     int all_stop;               // every right-hand side has stop != 0
     int trips;                  // inner-loop graph trips in the current cycle
+    int loop_base, loop_trips, loop_cap, loop_pad;   // lattice-batch loop (first lattice only)
     unsigned int ticket[4];
 };
 

@@ -167,6 +167,96 @@ struct ChunkGraph {
     }
 };
 
+// The batch's inner loop on the device: a prologue kernel records how many lattices are idle
+// (all_stop set) and the trip bound, then a conditional WHILE node repeats one iteration of
+// every lattice and a one-thread condition kernel until some running lattice stops (its
+// cycle then ends on the host), every lattice is idle, or the bound is reached.  The counters
+// live in the first lattice's state record.
+struct LatLoopArgs {
+    SolverState* st[kMaxLat];
+    int n;
+};
+
+static __global__ void lattice_loop_base(LatLoopArgs a) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        int idle = 0, cap = 0;
+        for (int l = 0; l < a.n; ++l) {
+            if (a.st[l]->all_stop) ++idle;
+            else cap = max(cap, a.st[l]->k_max);
+        }
+        a.st[0]->loop_base = idle;
+        a.st[0]->loop_trips = 0;
+        a.st[0]->loop_cap = cap + 2;
+    }
+}
+
+static __global__ void lattice_loop_cond(cudaGraphConditionalHandle h, LatLoopArgs a) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        int idle = 0;
+        for (int l = 0; l < a.n; ++l) idle += a.st[l]->all_stop ? 1 : 0;
+        SolverState* s0 = a.st[0];
+        const int t = ++s0->loop_trips;
+        cudaGraphSetConditional(h, (idle == s0->loop_base && idle < a.n && t < s0->loop_cap) ? 1u : 0u);
+    }
+}
+
+struct LoopGraph {
+    cudaStream_t cs = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    LoopGraph() = default;
+    LoopGraph(const LoopGraph&) = delete;
+    LoopGraph& operator=(const LoopGraph&) = delete;
+    ~LoopGraph() { reset(); }
+    void reset() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (cs) cudaStreamDestroy(cs);
+        exec = nullptr;
+        graph = nullptr;
+        cs = nullptr;
+    }
+    template <class IL>
+    cudaError_t build(const IL& il, const LatLoopArgs& a) {
+        cudaError_t e;
+        if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) return e;
+        if ((e = cudaGraphCreate(&graph, 0)) != cudaSuccess) return e;
+        // prologue node
+        cudaKernelNodeParams kp = {};
+        LatLoopArgs args = a;
+        void* kargs[] = {&args};
+        kp.func = (void*)lattice_loop_base;
+        kp.gridDim = dim3(1);
+        kp.blockDim = dim3(32);
+        kp.kernelParams = kargs;
+        cudaGraphNode_t base;
+        if ((e = cudaGraphAddKernelNode(&base, graph, nullptr, 0, &kp)) != cudaSuccess) return e;
+        // WHILE node after it
+        cudaGraphConditionalHandle h;
+        if ((e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault)) != cudaSuccess) return e;
+        cudaGraphNodeParams p = {};
+        p.type = cudaGraphNodeTypeConditional;
+        p.conditional.handle = h;
+        p.conditional.type = cudaGraphCondTypeWhile;
+        p.conditional.size = 1;
+        cudaGraphNode_t node;
+        if ((e = cudaGraphAddNode(&node, graph, &base, nullptr, 1, &p)) != cudaSuccess) return e;
+        cudaGraph_t bodyg = p.conditional.phGraph_out[0];
+        if ((e = cudaStreamBeginCaptureToGraph(cs, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+            cudaSuccess)
+            return e;
+        cudaError_t le = il.iteration(cs);
+        if (le == cudaSuccess) {
+            lattice_loop_cond<<<1, 32, 0, cs>>>(h, a);
+            le = cudaGetLastError();
+        }
+        e = cudaStreamEndCapture(cs, &bodyg);
+        if (le != cudaSuccess) return le;
+        if (e != cudaSuccess) return e;
+        return cudaGraphInstantiate(&exec, graph, 0);
+    }
+};
+
 template <int IP, int IF, int IL, int HP, int IBS>
 int run_lattices_bs(int n, const LatticeJob* jobs, const lq_cg_params& prm, double delta, char* ws,
                     lq_cg_info* info, cudaStream_t st) {
@@ -186,9 +276,25 @@ int run_lattices_bs(int n, const LatticeJob* jobs, const lq_cg_params& prm, doub
     InnerLaunches<S> il;
     il.build(sv.get(), n);
     const bool use_graph = (prm.flags & LQ_CG_NO_GRAPH) == 0;
-    ChunkGraph cg;
     cudaError_t e;
-    if (use_graph && (e = cg.capture(il, chunk)) != cudaSuccess) return cuda_fail(e, "inner-loop graph capture");
+    // device-driven loop (one graph launch until a lattice's cycle ends); if the conditional
+    // graph cannot be built, chunks of iterations captured as a plain graph
+    LoopGraph lg;
+    bool device_loop = false;
+    if (use_graph) {
+        LatLoopArgs la{};
+        la.n = n;
+        for (int l = 0; l < n; ++l) la.st[l] = sv[l].dstate;
+        if (lg.build(il, la) == cudaSuccess) {
+            device_loop = true;
+        } else {
+            (void)cudaGetLastError();
+            lg.reset();
+        }
+    }
+    ChunkGraph cg;
+    if (use_graph && !device_loop && (e = cg.capture(il, chunk)) != cudaSuccess)
+        return cuda_fail(e, "inner-loop graph capture");
 
     bool in_cycle[kMaxLat] = {}, finished[kMaxLat] = {};
     int chunks = 0;
@@ -206,22 +312,29 @@ int run_lattices_bs(int n, const LatticeJob* jobs, const lq_cg_params& prm, doub
             any |= in_cycle[l];
         }
         if (!any) break;
-        if (use_graph) {
+        if (device_loop) {
+            if ((e = cudaGraphLaunch(lg.exec, st)) != cudaSuccess) return cuda_fail(e, "inner-loop graph");
+        } else if (use_graph) {
             if ((e = cudaGraphLaunch(cg.exec, st)) != cudaSuccess) return cuda_fail(e, "inner-loop graph");
         } else {
             for (int j = 0; j < chunk; ++j)
                 if ((e = il.iteration(st)) != cudaSuccess) return cuda_fail(e, "inner loop");
         }
         ++chunks;
-        for (int l = 0; l < n; ++l) {
-            sv[l].launches += 3 * chunk;
-            if (in_cycle[l] && (e = sv[l].read_state_async()) != cudaSuccess) return cuda_fail(e, "inner loop");
-        }
+        for (int l = 0; l < n; ++l)
+            if ((in_cycle[l] || (device_loop && l == 0)) && (e = sv[l].read_state_async()) != cudaSuccess)
+                return cuda_fail(e, "inner loop");
         if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "inner loop");
+        // launches each lattice took part in: the iterations (and, for the device loop, the
+        // prologue and one condition kernel per trip)
+        const int trips = device_loop ? sv[0].hs.loop_trips : chunk;
+        for (int l = 0; l < n; ++l) sv[l].launches += device_loop ? 4 * trips + 1 : 3 * chunk;
         for (int l = 0; l < n; ++l) {
             if (!in_cycle[l]) continue;
-            // K2 stops every right-hand side at k_max, so the guard never decides
-            if (sv[l].hs.all_stop || ++sv[l].guard > (sv[l].k_max / chunk) + 2) {
+            // iterations launched in this lattice's cycle; K2 stops every right-hand side at
+            // k_max, so this guard never decides
+            sv[l].guard += trips;
+            if (sv[l].hs.all_stop || sv[l].guard > sv[l].k_max + 2 * (device_loop ? 1 : chunk)) {
                 if ((r = sv[l].end_cycle()) != LQ_OK) return r;
                 in_cycle[l] = false;
             }
