@@ -192,7 +192,8 @@ typedef struct lq_cg_params {
     int32_t max_iter;        /* cap on inner iterations summed over all cycles (>= 1)      */
     int32_t max_cycles;      /* cap on outer cycles (reliable updates); 0 -> 1000          */
     double delta;            /* inner-loop residual reduction per cycle; <= 0 -> mode default */
-    int32_t chunk;           /* inner iterations between host checks; 0 -> automatic       */
+    int32_t chunk;           /* host-driven inner loop: iterations between host checks;
+                                0 -> automatic                                             */
     int32_t flags;           /* LQ_CG_PROFILE: time the solver's kernels with CUDA events  */
 } lq_cg_params;
 
@@ -205,9 +206,9 @@ typedef struct lq_cg_params {
 #define LQ_CG_AUTOTUNE 8     /* lq_cg_solve_lattices: pick the inner block size by timing
                                 (cached per lattice set and GPU); default 128 threads      */
 #define LQ_CG_NO_GRAPH 16    /* launch the inner kernels one by one from the host instead of
-                                a CUDA graph (single lattices: a conditional WHILE graph runs
-                                a cycle's inner loop on the device; lattice batches: chunks
-                                of iterations are replayed from a captured graph)          */
+                                running the inner loop in a CUDA graph with a conditional
+                                WHILE node (the default; if the driver refuses such a graph
+                                the host-driven loop runs without this flag too)           */
 #define LQ_CG_BLOCK_64 0x100 /* lq_cg_solve_lattices: inner block size 64 / 128 / 256 threads */
 #define LQ_CG_BLOCK_128 0x200 /*   (at most one; overrides LQ_CG_AUTOTUNE)                  */
 #define LQ_CG_BLOCK_256 0x400
@@ -347,9 +348,10 @@ int lq_cg_solve_schur(const int32_t dims[4], double m_q, int32_t mode, int32_t n
  *   workspace at least lq_cg_workspace_bytes_lattices(n, lats, mode) bytes.
  *   info     optional, sum of nrhs records in lattice order (block = the inner block size).
  * Each inner-loop kernel is one launch over all lattices (blocks are shared out in
- * proportion to each lattice's sites); a chunk of inner iterations is captured once as a
- * CUDA graph and replayed; each lattice takes its reliable updates when its own inner loop
- * stops.  Returns LQ_OK if every solve converged, LQ_NOT_CONVERGED if some did not, or the
+ * proportion to each lattice's sites).  The inner iterations run on the device in a CUDA
+ * graph (a conditional WHILE node) until some lattice's inner loop stops; the host then
+ * takes that lattice's reliable update (Algorithm 1's outer step) and relaunches while the
+ * other lattices go on.  Returns LQ_OK if every solve converged, LQ_NOT_CONVERGED if some did not, or the
  * most negative error status.  Returns after the solves have finished.
  */
 typedef struct lq_lattice {
