@@ -55,11 +55,14 @@ def test_lattices_against_oracle(lqlib, mode):
             assert _true_resid(dims, m, U, etas[r], sol[r]) <= 1e-10 * RESID_SLACK
 
 
-def test_lattices_graph_replay_equals_direct_launches(lqlib):
-    """The captured graph replays exactly the kernels a direct launch sequence issues."""
+@pytest.mark.parametrize("mode", ["mixed_f32", "mixed_f16"])
+def test_lattices_graph_replay_equals_direct_launches(lqlib, mode):
+    """The device-driven loop (a conditional graph that returns whenever one lattice's cycle
+    ends; the lattices have different masses, so their cycles end at different iterations)
+    runs exactly the kernels a direct launch sequence issues."""
     host, probs = _problems(SMALL, seed=910)
-    xa, ia, sa = lqlib.cg_solve_lattices(probs, mode="mixed_f32", tol=1e-10, graph=True)
-    xb, ib, sb = lqlib.cg_solve_lattices(probs, mode="mixed_f32", tol=1e-10, graph=False)
+    xa, ia, sa = lqlib.cg_solve_lattices(probs, mode=mode, tol=1e-10, graph=True)
+    xb, ib, sb = lqlib.cg_solve_lattices(probs, mode=mode, tol=1e-10, graph=False)
     assert sa == sb == 0
     for a, b in zip(xa, xb):
         assert np.array_equal(to_host(a), to_host(b))
