@@ -409,7 +409,7 @@ def run_workload(args):
 
         def one():
             kw = {"block": args.lattice_block} if args.lattice_block else {"autotune": True}
-            xs, infos, st = lq.cg_solve_lattices(probs, mode=args.mode, tol=TOL, graph=args.inner_loop == "device",
+            _, infos, st = lq.cg_solve_lattices(probs, mode=args.mode, tol=TOL, graph=args.inner_loop == "device",
                                                  **kw)
             assert st == 0
             return infos

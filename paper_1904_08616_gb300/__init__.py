@@ -325,7 +325,6 @@ def cg_solve(dims, m_q, U, eta, x=None, mode="f64", tol=1e-10, max_iter=100000, 
                             ctypes.c_size_t(workspace.numel() * workspace.element_size()),
                             ctypes.byref(info), _stream(stream))
     _check(st)
-    d = {k: getattr(info, k) for k, _ in CgInfo._fields_ }
     return x, _info_dict(info), st
 
 
