@@ -181,7 +181,8 @@ int lq_convert_gauge(const int32_t dims[4], int32_t src_prec, int32_t src_layout
 typedef enum lq_cg_mode {
     LQ_CG_F64 = 0,        /* FP64 throughout (plain CG, true residual checked in FP64)     */
     LQ_CG_MIXED_F32 = 1,  /* Algorithm 1: FP32 inner loop (EO layout, 12-real links), FP64 outer */
-    LQ_CG_MIXED_F16 = 2,  /* Algorithm 1: scaled-FP16 inner storage, FP32 arithmetic, FP64 outer */
+    LQ_CG_MIXED_F16 = 2,  /* Algorithm 1: scaled-FP16 inner storage (the inner solution psi in
+                             FP32), FP32 accumulation, FP64 outer                           */
     LQ_CG_F64X = 3,       /* FP64-class CG in FP32-pair arithmetic throughout (LQ_F64X)     */
     LQ_CG_MIXED_I32 = 4   /* Algorithm 1: 32-bit fixed-point inner storage (LQ_I32S), FP32
                              arithmetic, FP64 outer (not offered for lattice batches)      */
@@ -191,7 +192,8 @@ typedef struct lq_cg_params {
     double tol;              /* stop when ||eta - D^dag D x|| <= tol ||eta|| (FP64)        */
     int32_t max_iter;        /* cap on inner iterations summed over all cycles (>= 1)      */
     int32_t max_cycles;      /* cap on outer cycles (reliable updates); 0 -> 1000          */
-    double delta;            /* inner-loop residual reduction per cycle; <= 0 -> mode default */
+    double delta;            /* inner-loop residual reduction per cycle; <= 0 -> mode default
+                                (MIXED_F32 / MIXED_I32 1e-4, MIXED_F16 1e-2, others 0)      */
     int32_t chunk;           /* host-driven inner loop: iterations between host checks;
                                 0 -> automatic                                             */
     int32_t flags;           /* LQ_CG_PROFILE: time the solver's kernels with CUDA events  */

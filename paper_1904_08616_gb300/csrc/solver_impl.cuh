@@ -43,6 +43,13 @@ namespace lq {
 
 namespace solver_detail {
 
+// Precision of the inner solution psi (the sum of the cycle's alpha p updates): FP32 when
+// the inner vectors are scaled FP16.  psi is read and written once per iteration (by K2), and
+// its FP16 quantisation, repeated every iteration, had capped the residual reduction one
+// cycle could reach (delta 0.1 instead of 0.01, twice the cycles).
+constexpr int psi_prec(int ip) { return ip == LQ_F16S ? LQ_F32 : ip; }
+
+
 constexpr int kBS = 128;      // stencil kernels
 constexpr int kSiteBS = 256;  // site-local kernels
 
@@ -577,7 +584,7 @@ inline double default_delta(int mode) {
     switch (mode) {
         case LQ_CG_MIXED_F32:
         case LQ_CG_MIXED_I32: return 1e-4;
-        case LQ_CG_MIXED_F16: return 0.1;
+        case LQ_CG_MIXED_F16: return 0.01;
         default: return 0.0;
     }
 }
@@ -604,7 +611,7 @@ inline WsLayout ws_layout(const Geom& g, int mode, bool pair_outer, int inner_fm
     if (mode == LQ_CG_MIXED_F32 || mode == LQ_CG_MIXED_F16 || mode == LQ_CG_MIXED_I32)
         w.u_low = take(gauge_bytes(g.V, ip, inner_fmt));
     const size_t lo = spinor_bytes(Vn, ip);
-    w.psi = take(lo);
+    w.psi = take(spinor_bytes(Vn, psi_prec(ip)));
     w.r = take(lo);
     w.p = take(lo);
     w.t = take(lo);
@@ -636,7 +643,7 @@ inline WsLayout ws_layout_schur(const Geom& g, int mode, int inner_fmt, int nb) 
     const int ip = inner_prec(mode);
     if (ip != LQ_F64X) w.u_low = take(gauge_bytes(g.V, ip, inner_fmt));
     const size_t lo = spinor_bytes(Hn, ip);
-    w.psi = take(lo);
+    w.psi = take(spinor_bytes(Hn, psi_prec(ip)));
     w.r = take(lo);
     w.p = take(lo);
     w.t = take(lo);
@@ -783,7 +790,10 @@ struct Solve {
     using K1Sten = Stencil<GA, SpRO, false>;
     using K1Epi = EpiK1<SpRW, SpRO>;
     using K2Sten = Stencil<GA, SpRO, true>;
-    using K2Epi = EpiK2<SpRO, SpRO, SpRW, SpRW>;
+    static constexpr int PSIP = psi_prec(IP);
+    using PsiRO = SpinorAcc<PSIP, IL, true>;
+    using PsiRW = SpinorAcc<PSIP, IL, false>;
+    using K2Epi = EpiK2<SpRO, SpRO, PsiRW, SpRW>;
     using K3Op = OpK3<SpRW, SpRO>;
     using PreEpi = EpiPreHop<SpRW>;
     static constexpr bool kPairs = (HP == LQ_F64X);
@@ -813,8 +823,10 @@ struct Solve {
     CallerRO eta_caller;
     CallerRW x_caller;
     GA Ui;
-    SpRO psi_ro, r_ro, p_ro, t_ro;
-    SpRW psi_rw, r_rw, p_rw, t_rw;
+    SpRO r_ro, p_ro, t_ro;
+    SpRW r_rw, p_rw, t_rw;
+    PsiRO psi_ro;
+    PsiRW psi_rw;
     MapLex<kSiteBS> lexsite;
     HMap hmap;
     HSiteMap hsite;
@@ -890,8 +902,8 @@ struct Solve {
         // inner fields; an FP64-class inner loop shares the outer links
         const void* Ulow = (IP == LQ_F64) ? U : (IP == LQ_F64X ? Uo : (const void*)(ws + w.u_low));
         Ui = make_gauge<IP, IF, IL>(Ulow, g);
-        psi_ro = make_spinor<IP, IL, true>(ws + w.psi, g, H, nb);
-        psi_rw = make_spinor<IP, IL, false>(ws + w.psi, g, H, nb);
+        psi_ro = make_spinor<PSIP, IL, true>(ws + w.psi, g, H, nb);
+        psi_rw = make_spinor<PSIP, IL, false>(ws + w.psi, g, H, nb);
         r_ro = make_spinor<IP, IL, true>(ws + w.r, g, H, nb);
         r_rw = make_spinor<IP, IL, false>(ws + w.r, g, H, nb);
         p_ro = make_spinor<IP, IL, true>(ws + w.p, g, H, nb);
@@ -1146,7 +1158,7 @@ struct Solve {
 
     // cycle start (Algorithm 1)
     int start_cycle() {
-        OpRestart<HiRO, SpRW, SpRW, SpRW> op;
+        OpRestart<HiRO, SpRW, SpRW, PsiRW> op;
         op.rh = rh_ro;
         op.r = r_rw;
         op.p = p_rw;
@@ -1154,7 +1166,7 @@ struct Solve {
         op.rc = rc;
         op.nr = nb;
         op.k_max = k_max;
-        OpRestartP<SpRO, SpRW, SpRW> op2;
+        OpRestartP<SpRO, SpRW, PsiRW> op2;
         op2.r = r_ro;
         op2.p = p_rw;
         op2.x = psi_rw;
@@ -1275,7 +1287,7 @@ struct Solve {
             xact.v[j] = 1;
             xs.v[j] = from_double<HReal>(s[j]);
         }
-        OpXUpdate<HiRW, SpinorAcc<IP, IL, true>> xu{x_rw, psi_ro, nb, xs, xact, HReal(0), false};
+        OpXUpdate<HiRW, PsiRO> xu{x_rw, psi_ro, nb, xs, xact, HReal(0), false};
         if ((e = launch_site<kSiteBS>(hsite, xu, st)) != cudaSuccess) return cuda_fail(e, "x update");
         launches += 1;
         if ((e = high_residual()) != cudaSuccess) return cuda_fail(e, "residual");
