@@ -192,3 +192,20 @@ def test_cg_zero_guess_starts_from_eta(lqlib, mode):
     assert info1["high_applies"] == info1["cycles"] + 1
     assert _true_resid(dims, m, U, eta, x0) <= 1e-10 * RESID_SLACK
     assert _true_resid(dims, m, U, eta, x1) <= 1e-10 * RESID_SLACK
+
+
+def test_cg_scaled_fp16_keeps_the_cg_iteration_count(lqlib):
+    """With the inner solution kept in FP32, the scaled-FP16 mode runs each cycle to its default
+    reduction of 1e-2 without extra iterations: it needs about the iterations of plain FP64 CG
+    and a handful of cycles (re-quantising psi to FP16 every iteration needed thousands of
+    iterations at this reduction)."""
+    dims = (8, 8, 8, 8)
+    m = 0.05
+    U = synth.gauge_field(dims, seed=23, kind="near_identity", eps=0.3)
+    eta = synth.gaussian_spinor(dims, seed=24)
+    _, i64, s64 = _solve(lqlib, dims, m, U, eta, "f64", tol=1e-10)
+    x, i16, s16 = _solve(lqlib, dims, m, U, eta, "mixed_f16", tol=1e-10)
+    assert s64 == s16 == 0
+    assert i16["iters"] <= 1.1 * i64["iters"]
+    assert i16["cycles"] <= 7
+    assert _true_resid(dims, m, U, eta, x) <= 1e-10 * RESID_SLACK
