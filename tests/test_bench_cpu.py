@@ -50,3 +50,15 @@ def test_whole_job_rate_one_rank():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.whole_job_rate(4.0, 8000, "cpu") == (4.0, 8000 / 0.004)
+
+
+def test_kernel_bytes_match_the_stored_formats():
+    """The roofline's algorithmic bytes per site: K1 reads p and the four links and writes t;
+    K2 reads t, p, r and psi and the links and writes psi and r (psi in FP32 beside scaled-FP16
+    vectors); K3 reads r and p and writes p.  Spinor sites: FP32 96 B, scaled FP16 48 + 4 B,
+    FP64 192 B; four 12-real links: FP32 192 B, FP16 96 B."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.kernel_bytes("mixed_f16") == {"K1": 52 + 96 + 52, "K2": 4 * 52 + 2 * 96 + 96, "K3": 3 * 52}
+    assert bench.kernel_bytes("mixed_f32") == {"K1": 96 + 192 + 96, "K2": 6 * 96 + 192, "K3": 3 * 96}
+    assert bench.kernel_bytes("f64")["K1"] == 192 + 576 + 192
