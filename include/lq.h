@@ -50,7 +50,9 @@
  *           gauge fields: int32 q = RN(u * 2^30) with no scale (entries must satisfy
  *           |u| < 2, as unitary links do).
  *   Arithmetic is FP64 for LQ_F64, FP32 pairs for LQ_F64X, FP32 for LQ_F32 / LQ_F16S /
- *   LQ_I32S.
+ *   LQ_I32S (for LQ_F16S the operator forms each spin projection, one add of two stored
+ *   values, in FP16 on the stored half2 words; every product and every sum of products is
+ *   FP32).
  *   Kernel outputs in LQ_F16S use one reciprocal of the scale per site (h = fl16(v * fl32(1/s)));
  *   lq_convert_spinor divides every component (h = fl16(fl32(v) / s)) and is bit-exact.
  *   Kernel outputs in LQ_I32S use q = RN(fl32(v) * fl32(2^30 / s)) in FP32; lq_convert_spinor
