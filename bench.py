@@ -516,6 +516,39 @@ def run_workload(args):
                                 "system": "D x = b"},
                      "value": None, "unit": "ms", "solvers": res,
                      "schur_speedup": res["normal_equations"]["ms"] / res["schur"]["ms"]})
+    elif args.workload == "grad":
+        # the link-gradient kernel against its roofline on 32^4 (fields larger than the L2), and
+        # the gradient of L = Re <chi, (D^dag D)^-1 eta> with respect to U and eta on 16^4 (links
+        # exp(0.5iH), m_q = 0.1): forward solve, adjoint solve, two applies of D, two link gradients
+        from paper_1904_08616_gb300.autograd import dirac_solve
+        peak, peak_kind = measured_peaks()
+        g_d, psi_d = spinors(DIMS, [81]), spinors(DIMS, [82])
+        out = torch.empty(lq.field_bytes(DIMS, "gauge", "f64"), dtype=torch.uint8, device=dev)
+        ms_k, _ = _timed(lambda: lq.link_grad(DIMS, g_d, psi_d, out=out), max(args.steps, 10), args.warmup)
+        V = int(np.prod(DIMS))
+        gbs = 960 * V / (ms_k * 1e-3) / 1e9
+        dims16, m16 = (16, 16, 16, 16), 0.1
+        V16 = int(np.prod(dims16))
+        U16 = torch.from_numpy(synth.gauge_field(dims16, seed=83, kind="near_identity", eps=0.5)).to(dev)
+        eta16 = torch.from_numpy(synth.gaussian_spinor(dims16, seed=84)).to(dev)
+        chi16 = torch.from_numpy(synth.gaussian_spinor(dims16, seed=85)).to(dev)
+        res = {}
+        for m in ("f64", "f64x", "mixed_f32"):
+            def grad_once(m=m):
+                Ur = U16.clone().requires_grad_(True)
+                er = eta16.clone().requires_grad_(True)
+                x = dirac_solve(dims16, m16, Ur, er, mode=m, tol=1e-10)
+                loss = torch.sum((chi16.conj() * x).real)
+                loss.backward()
+                return Ur.grad
+            ms_g, gU = _timed(grad_once, args.steps, args.warmup)
+            res[m] = {"ms_per_gradient": ms_g, "grad_U_norm": float(torch.linalg.vector_norm(gU))}
+        line.update({"config": {"link_grad_lattice": list(DIMS), "gradient_lattice": list(dims16), "m_q": m16,
+                                "links": "exp(0.5iH)", "tol": 1e-10, "V16": V16},
+                     "value": gbs, "unit": "GB/s",
+                     "link_grad": {"us": ms_k * 1e3, "bytes_per_site": 960, "gbs": gbs, "frac": gbs / peak,
+                                   "peak": peak, "peak_kind": peak_kind},
+                     "gradient": res})
     elif args.workload == "large":
         dims, nr = (64, 64, 64, 128), 4
         U_d = field(synth.gauge_field(dims, seed=70, kind="haar"))
@@ -548,9 +581,11 @@ def main():
     ap.add_argument("--mode", default="mixed_f16", choices=["mixed_f16", "mixed_f32", "f64", "f64x", "mixed_i32"])
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 / other-mode comparison solves")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--workload", default="cg32", choices=["cg32", "lattices", "batched", "large", "schur", "dslash"],
+    ap.add_argument("--workload", default="cg32",
+                    choices=["cg32", "lattices", "batched", "large", "schur", "dslash", "grad"],
                     help="cg32: the 32^4 mixed-precision solve (the bench line); the others print a "
-                         "measurement line for the uneven-lattice, 12-RHS and 64^3x128 workloads")
+                         "measurement line for the uneven-lattice, 12-RHS, 64^3x128, Schur, operator-only "
+                         "and gradient workloads")
     ap.add_argument("--lattice-block", type=int, default=0, choices=[0, 64, 128, 256],
                     help="lattices workload: inner block size (0: tuned)")
     ap.add_argument("--inner-loop", default="device", choices=["device", "host"],

@@ -12,49 +12,20 @@ namespace {
 
 constexpr int kGradBS = 128;
 
-// (1 + S gamma_MU) q as a full four-spin spinor: upper h = up + S B dn, lower S B^dag h
-template <int MU, int S>
-__device__ __forceinline__ void project_full(const Spinor<double>& q, Spinor<double>& o) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const cplx<double> p0 = q.v[c], p1 = q.v[3 + c], p2 = q.v[6 + c], p3 = q.v[9 + c];
-        cplx<double> h0, h1, l2, l3;
-        if constexpr (MU == 0) {
-            h0 = pm<S>(p0, ctimes_mi(p3));
-            h1 = pm<S>(p1, ctimes_mi(p2));
-            l2 = ctimes_i(h1);
-            l3 = ctimes_i(h0);
-        } else if constexpr (MU == 1) {
-            h0 = pm<-S>(p0, p3);
-            h1 = pm<S>(p1, p2);
-            l2 = h1;
-            l3 = cneg(h0);
-        } else if constexpr (MU == 2) {
-            h0 = pm<S>(p0, ctimes_mi(p2));
-            h1 = pm<S>(p1, ctimes_i(p3));
-            l2 = ctimes_i(h0);
-            l3 = ctimes_mi(h1);
-        } else {
-            h0 = pm<S>(p0, p2);
-            h1 = pm<S>(p1, p3);
-            l2 = h0;
-            l3 = h1;
-        }
-        o.v[c] = h0;
-        o.v[3 + c] = h1;
-        o.v[6 + c] = (S > 0) ? l2 : cneg(l2);
-        o.v[9 + c] = (S > 0) ? l3 : cneg(l3);
-    }
-}
+// The spin sums collapse onto the rank-2 projections: for P = 1 + S gamma_mu, whose lower
+// spin half is S B^dag times its upper half h (chiral basis), sum_s a_s conj((P b)_s) equals
+// sum_{k=0,1} (P a)_k conj((P b)_k) with (P a)_k the upper half of P a.  So
+//   G_mu(n) = 1/2 sum_{k=0,1} [ (P^- g(n))_k (P^- psi(n+mu))_k^H + (P^+ psi(n))_k (P^+ g(n+mu))_k^H ],
+// two 3x3 outer products of colour vectors per term instead of four.
 
-// M[A][B] += sum_spin a_A conj(b_B)
-__device__ __forceinline__ void outer_acc(const Spinor<double>& a, const Spinor<double>& b, cplx<double> M[3][3]) {
+// M[A][B] += a0_A conj(b0_B) + a1_A conj(b1_B)
+__device__ __forceinline__ void outer_acc2(const cplx<double> a0[3], const cplx<double> a1[3],
+                                           const cplx<double> b0[3], const cplx<double> b1[3],
+                                           cplx<double> M[3][3]) {
 #pragma unroll
-    for (int s = 0; s < 4; ++s)
+    for (int A = 0; A < 3; ++A)
 #pragma unroll
-        for (int A = 0; A < 3; ++A)
-#pragma unroll
-            for (int B = 0; B < 3; ++B) M[A][B] = cfmac(b.v[3 * s + B], a.v[3 * s + A], M[A][B]);
+        for (int B = 0; B < 3; ++B) M[A][B] = cfmac(b1[B], a1[A], cfmac(b0[B], a0[A], M[A][B]));
 }
 
 template <int MU>
@@ -63,18 +34,21 @@ __device__ __forceinline__ void grad_dir(const Geom& g, const SpinorAcc<LQ_F64, 
                                          const int c[4], const Spinor<double>& gn, const Spinor<double>& pn,
                                          double scale, bool accumulate, double2* out) {
     const Site nf = nb_site(lex_fwd(g, s.lex, c, MU), s.p, 0);
-    Spinor<double> gf, pf, w, v;
+    Spinor<double> gf, pf;
     G.load(nf, gf);
     P.load(nf, pf);
-    project_full<MU, -1>(pf, w);   // P^{-mu} psi(n + mu)
-    project_full<MU, +1>(pn, v);   // P^{+mu} psi(n)
+    cplx<double> a0[3], a1[3], b0[3], b1[3];
     cplx<double> M[3][3];
 #pragma unroll
     for (int A = 0; A < 3; ++A)
 #pragma unroll
         for (int B = 0; B < 3; ++B) M[A][B] = {0.0, 0.0};
-    outer_acc(gn, w, M);
-    outer_acc(v, gf, M);
+    hop_project<MU, -1>(gn, a0, a1);   // P^{-mu} g(n)
+    hop_project<MU, -1>(pf, b0, b1);   // P^{-mu} psi(n + mu)
+    outer_acc2(a0, a1, b0, b1, M);
+    hop_project<MU, +1>(pn, a0, a1);   // P^{+mu} psi(n)
+    hop_project<MU, +1>(gf, b0, b1);   // P^{+mu} g(n + mu)
+    outer_acc2(a0, a1, b0, b1, M);
     double2* o = out + ((size_t)s.lex * 4 + MU) * 9;
     const double f = 0.5 * scale;
 #pragma unroll
