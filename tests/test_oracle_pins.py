@@ -501,3 +501,19 @@ def test_solve_d_matches_dense_solve():
     Dd = dense.dense_dirac(dims, m, U)
     xd = np.linalg.solve(Dd, dense.flat(b))
     assert np.linalg.norm(dense.flat(x) - xd) / np.linalg.norm(xd) < 1e-11
+
+
+def test_projected_spin_sums_reduce_to_the_upper_half():
+    """For P = 1 + S gamma_mu in the chiral basis, the lower spin half of P b is S B_mu^dag times
+    its upper half, so sum_s a_s conj((P b)_s) = sum_{k=0,1} (P a)_k conj((P b)_k): the identity
+    the link-gradient kernel uses to sum over two spin components instead of four."""
+    rng = np.random.default_rng(31)
+    for mu in range(4):
+        for S in (1.0, -1.0):
+            P = np.eye(4) + S * oracle.gamma(mu)
+            for _ in range(4):
+                a = rng.normal(size=4) + 1j * rng.normal(size=4)
+                b = rng.normal(size=4) + 1j * rng.normal(size=4)
+                lhs = np.sum(a * np.conj(P @ b))
+                rhs = np.sum((P @ a)[:2] * np.conj((P @ b)[:2]))
+                assert abs(lhs - rhs) <= 1e-13 * (1 + abs(lhs))
