@@ -306,6 +306,11 @@ def cg_solve(dims, m_q, U, eta, x=None, mode="f64", tol=1e-10, max_iter=100000, 
 
     x (if given) is the starting guess and receives the solution.  Returns (x, info, status)
     where info is a dict of the solver statistics; raises LqError on errors (status < 0).
+    mode: "f64", "f64x", "mixed_f32", "mixed_f16" or "mixed_i32"; delta <= 0 takes the mode's
+    default inner reduction per cycle.  profile=True times the solver's kernels with CUDA
+    events (host-driven inner loop); graph=False launches the inner kernels from the host
+    instead of running each cycle's inner loop in a conditional CUDA graph; native_f64 and
+    link18 select native FP64 outer arithmetic and 18-real inner links (mixed modes).
     """
     import torch
     m = CG_MODE[mode] if isinstance(mode, str) else int(mode)
