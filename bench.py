@@ -38,6 +38,8 @@ EPS = 0.3
 TOL = 1e-10
 SEED_U, SEED_ETA = 3, 4
 FLOPS_PER_SITE = 1464            # the paper's nominal count per stencil (Introduction)
+# both arms (the library and the CPU oracle) report this metric; the workload says what a step is
+METRIC = "Dslash site-updates/s"
 WORKLOAD = "mixed-precision CG to 1e-10 on 32^4, m_q=0.05, links exp(0.3iH)"
 
 # algorithmic bytes per site of the inner-loop kernels (each field read or written once)
@@ -146,41 +148,82 @@ def make_inputs():
     return U, eta
 
 
-def oracle_rate(U, eta, nsites, reps=1):
-    """The CPU oracle (plain C, one thread) applying D^dag D's two stencils on nsites
-    sampled sites of the same 32^4 fields; returns (site-updates/s, seconds)."""
+def oracle_rate(U, eta, nsites, reps=1, threads=1):
+    """The CPU oracle (plain C) applying D^dag D's two stencils on nsites sampled sites of the
+    same 32^4 fields, its loop over sites split over `threads` host cores; returns
+    (site-updates/s, seconds, threads used)."""
     import numpy as np
     import oracle
     V = U.shape[0]
     sites = np.random.default_rng(0).integers(0, V, nsites)
-    t0 = time.perf_counter()
-    for _ in range(reps):
-        oracle.dslash_sites(DIMS, MASS, U, eta, sites, dagger=False)
-        oracle.dslash_sites(DIMS, MASS, U, eta, sites, dagger=True)
-    dt = time.perf_counter() - t0
-    return 2 * nsites * reps / dt, dt
+    used = oracle.set_threads(threads)
+    try:
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            oracle.dslash_sites(DIMS, MASS, U, eta, sites, dagger=False)
+            oracle.dslash_sites(DIMS, MASS, U, eta, sites, dagger=True)
+        dt = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(1)
+    return 2 * nsites * reps / dt, dt, used
+
+
+def oracle_cg_times(all_rate, threads, f64_iters=None):
+    """The oracle's textbook FP64 CG to 1e-10, timed on the host: the 4^4 Haar system
+    (m_q = 0.1, one thread) and the 16^4 exp(0.5iH) system (m_q = 0.1, all cores), both run to
+    the end; the 32^4 and 64^3x128 figures are projected as (two applies of D per iteration
+    at the measured all-core site-update rate) x iterations, and labelled as such."""
+    import oracle
+    import synth
+    out = {}
+    for name, dims, kind, eps, m, seeds, thr in (("4^4 haar m_q=0.1", (4, 4, 4, 4), "haar", 0.0, 0.1, (1, 2), 1),
+                                                 ("16^4 exp(0.5iH) m_q=0.1", (16, 16, 16, 16), "near_identity",
+                                                  0.5, 0.1, (7, 8), threads)):
+        U = synth.gauge_field(dims, seed=seeds[0], kind=kind, eps=eps)
+        eta = synth.gaussian_spinor(dims, seed=seeds[1])
+        used = oracle.set_threads(thr)
+        try:
+            t0 = time.perf_counter()
+            _, it, rel = oracle.cg(dims, m, U, eta, tol=TOL)
+            dt = time.perf_counter() - t0
+        finally:
+            oracle.set_threads(1)
+        out[name] = {"s": dt, "iters": it, "true_rel_resid": rel, "cores": used, "kind": "measured"}
+    per_iter_32 = 2 * 32 ** 4 / all_rate
+    out["32^4 exp(0.3iH) m_q=0.05 (the bench system)"] = {
+        "s_per_iter": per_iter_32, "cores": threads, "kind": "projected: 2 applies per iteration at the measured "
+        "all-core rate x iterations of the FP64 CG on the same system",
+        "iters": f64_iters, "s": per_iter_32 * f64_iters if f64_iters else None}
+    out["64^3x128 haar m_q=0.02"] = {"s_per_iter": 2 * 64 ** 3 * 128 / all_rate, "cores": threads,
+                                     "kind": "projected: 2 applies per iteration at the measured all-core rate"}
+    return out
 
 
 def run_reference(args, rank):
     if rank != 0:
         return
+    import oracle
     U, eta = make_inputs()
-    nsites = 1 << 17
+    threads = oracle.max_threads()
+    nsites = 1 << 19
     for _ in range(args.warmup):
-        oracle_rate(U, eta, nsites)
+        oracle_rate(U, eta, nsites, threads=threads)
     t0 = time.perf_counter()
+    used = 1
     for _ in range(args.steps):
-        oracle_rate(U, eta, nsites)
+        _, _, used = oracle_rate(U, eta, nsites, threads=threads)
     dt = time.perf_counter() - t0
     value = 2 * nsites * args.steps / dt
-    sample = f"D and D^dag of Eq. 1 on {nsites} sampled sites of the 32^4 fields per step (FP64 C oracle)"
+    sample = (f"D and D^dag of Eq. 1 on {nsites} sampled sites of the 32^4 fields per step (FP64 C oracle, "
+              f"site loop over {used} host cores)")
     line = {
-        "impl": "reference", "metric": "Dslash site-updates/s", "value": value, "unit": "site-updates/s",
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "site-updates/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "lattice": list(DIMS), "m_q": MASS},
-        "cpu_baseline": {"value": value, "unit": "site-updates/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "site-updates/s", "cores": used, "kind": "oracle", "sample": sample,
+                         "nproc": os.cpu_count()},
         "e2e": {"value": value, "unit": "site-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -228,13 +271,22 @@ def run_ours(args, rank, world, local_rank):
                      dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def solve(m, profile=False):
+    def solve(m, profile=False, native_f64=False):
         x_d.zero_()
         _, info, st = lq.cg_solve(DIMS, MASS, U_d, eta_d, x=x_d, mode=m, tol=TOL, workspace=ws,
-                                  stream=stream, profile=profile)
+                                  stream=stream, profile=profile, native_f64=native_f64)
         if st != 0:
             raise RuntimeError(f"solve did not converge: {info}")
         return info
+
+    def fp64_residual():
+        """||eta - D^dag D x|| / ||eta|| of the current x, through the library's native FP64
+        operator kernels (LEX, 18-real links), independent of the solver's own residual."""
+        t = lq.dslash_apply(DIMS, MASS, U_d, x_d, prec="f64", link_fmt=18, layout="lex", stream=stream)
+        q = lq.dslash_adjoint(DIMS, MASS, U_d, t, prec="f64", link_fmt=18, layout="lex", stream=stream)
+        e = eta_d.view(torch.float64)
+        r = e - q.view(torch.float64)
+        return float(torch.linalg.vector_norm(r) / torch.linalg.vector_norm(e))
 
     def barrier():
         if world > 1:
@@ -255,6 +307,7 @@ def run_ours(args, rank, world, local_rank):
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
+        resid64 = fp64_residual()
         # the same K steps again with CUDA events around every solver kernel, for the
         # per-kernel split and the roofline (the events cost about 3% of a step, so they stay
         # out of the timed steps above)
@@ -284,22 +337,29 @@ def run_ours(args, rank, world, local_rank):
     e2e_ms = h0.elapsed_time(h1) / args.steps
     _, e2e_value = whole_job_rate(e2e_ms, upd, dev)
 
-    # plain FP64 CG (native FP64 and FP32-pair arithmetic) and the other mixed variant on the
-    # same system (one run each after one warm run)
+    # plain FP64 CG (native FP64 and FP32-pair arithmetic), the other mixed variants, and the
+    # mixed solvers with a native FP64 outer loop (residual, reductions and solution in FP64,
+    # as the configuration states it) on the same system: the median of three timed runs
+    # after one warm run, each followed by the FP64 recomputation of its residual
     compare = {}
     if not args.no_compare:
-        others = [m for m in ("f64", "f64x", "mixed_f32", "mixed_f16", "mixed_i32") if m != mode]
-        for m in others:
-            solve(m)
+        variants = [(m, False) for m in ("f64", "f64x", "mixed_f32", "mixed_f16", "mixed_i32") if m != mode]
+        variants += [(m, True) for m in ("mixed_f16", "mixed_f32")]
+        for m, nat in variants:
+            solve(m, native_f64=nat)
             torch.cuda.synchronize()
-            c0 = torch.cuda.Event(enable_timing=True)
-            c1 = torch.cuda.Event(enable_timing=True)
-            c0.record(stream)
-            ci = solve(m, profile=True)
-            c1.record(stream)
-            torch.cuda.synchronize()
-            compare[m] = {"ms": c0.elapsed_time(c1), "iters": ci["iters"], "cycles": ci["cycles"],
-                          "true_rel_resid": ci["true_rel_resid"]}
+            ts = []
+            for _ in range(3):
+                c0 = torch.cuda.Event(enable_timing=True)
+                c1 = torch.cuda.Event(enable_timing=True)
+                c0.record(stream)
+                ci = solve(m, native_f64=nat)
+                c1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(c0.elapsed_time(c1))
+            compare[m + ("+native_f64_outer" if nat else "")] = {
+                "ms": statistics.median(ts), "iters": ci["iters"], "cycles": ci["cycles"],
+                "true_rel_resid": ci["true_rel_resid"], "true_rel_resid_fp64_recomputed": fp64_residual()}
 
     if rank != 0:
         return
@@ -325,11 +385,19 @@ def run_ours(args, rank, world, local_rank):
             "algorithmic_bytes_per_launch": bytes_per_launch}
     cpu = None
     if world == 1 and not args.no_cpu:
-        rate, secs = oracle_rate(U, eta, 1 << 21, reps=1)
-        cpu = {"value": rate, "unit": "site-updates/s", "cores": 1, "kind": "oracle",
-               "sample": f"D and D^dag of Eq. 1 on 2^21 sampled sites of the 32^4 fields ({secs:.1f} s, FP64 C oracle)"}
+        import oracle
+        nth = oracle.max_threads()
+        rate1, secs1, _ = oracle_rate(U, eta, 1 << 19, reps=1, threads=1)
+        rate, secs, used = oracle_rate(U, eta, 1 << 21, reps=1, threads=nth)
+        cpu = {"value": rate, "unit": "site-updates/s", "cores": used, "kind": "oracle",
+               "sample": (f"D and D^dag of Eq. 1 on 2^21 sampled sites of the 32^4 fields ({secs:.1f} s, FP64 C "
+                          f"oracle, site loop over {used} host cores)"),
+               "nproc": os.cpu_count(),
+               "single_thread": {"value": rate1, "unit": "site-updates/s", "cores": 1,
+                                 "sample": f"2^19 sampled sites, {secs1:.1f} s"},
+               "cg_time_to_1e-10": oracle_cg_times(rate, used, compare.get("f64", {}).get("iters"))}
     line = {
-        "metric": "Dslash site-updates/s (whole mixed-precision CG solve to 1e-10)",
+        "metric": METRIC,
         "value": value, "unit": "site-updates/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"mixed_f16": "f32 accumulation, f16 spin projection (f16s storage) inner / f32-pair (fp64-class) outer",
@@ -339,6 +407,7 @@ def run_ours(args, rank, world, local_rank):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "lattice": list(DIMS), "m_q": MASS, "links": "exp(0.3iH), 12-real inner",
                    "inner": mode, "tol": TOL, "rhs_per_gpu": 1,
+                   "step": "one whole solve from x = 0; every D or D^dag applied to the lattice counts V site-updates",
                    "l2": "no flush: each inner kernel streams > 200 MB, above the 126 MB L2"},
         "roofline": roof,
         "cpu_baseline": cpu,
@@ -349,9 +418,12 @@ def run_ours(args, rank, world, local_rank):
         "gflops_1464": value * FLOPS_PER_SITE / 1e9,
         "cg": {"time_to_1e-10_ms": ms_max, "iters": info["iters"], "cycles": info["cycles"],
                "high_applies": info["high_applies"], "true_rel_resid": info["true_rel_resid"],
+               "true_rel_resid_fp64_recomputed": resid64,
                "compare": compare,
                "mixed_vs_fp64_speedup": (compare["f64"]["ms"] / ms_max) if "f64" in compare else None,
-               "mixed_vs_fp64x_speedup": (compare["f64x"]["ms"] / ms_max) if "f64x" in compare else None},
+               "mixed_vs_fp64x_speedup": (compare["f64x"]["ms"] / ms_max) if "f64x" in compare else None,
+               "native_f64_outer_vs_fp64_speedup": (compare["f64"]["ms"] / compare[mode + "+native_f64_outer"]["ms"])
+               if "f64" in compare and mode + "+native_f64_outer" in compare else None},
         "kernels": kern,
     }
     print(json.dumps(line), flush=True)

@@ -281,9 +281,14 @@ int lq_cg_solve(const int32_t dims[4], double m_q, int32_t mode, const void *U,
  * scratch is a fixed array inside this library (lq_cg_noalloc_max_workspace_bytes() bytes,
  * 64 MiB), which every GPU that loads the library holds until the process exits.
  *   - Lattices whose lq_cg_workspace_bytes(dims, mode) exceeds that size are rejected with
- *     LQ_ERR_WORKSPACE (e.g. 16^4 fits in the mixed modes, 12^4 in LQ_CG_F64).
+ *     LQ_ERR_WORKSPACE (12^4 fits in every mode, 16^4 in none).
  *   - The first call on a device looks up the array's device address (once per device,
- *     with that device current); make that first call before any stream capture.
+ *     with that device current).  With CUDA's lazy module loading (the default) that first
+ *     call is also when the array's memory is reserved on the device, so it can fail with
+ *     LQ_ERR_CUDA for lack of memory: callers under a no-allocation rule make one call (a
+ *     tiny solve) at start-up, before any stream capture.
+ *   - The looked-up address is kept for the life of the process; resetting the device
+ *     (cudaDeviceReset) while the library is loaded is not supported.
  *   - All calls share the one array, which keeps the previous call's contents; the solver
  *     re-initialises everything it reads.  Calls that overlap on the GPU (other streams,
  *     other host threads) race on the array and must not be issued.

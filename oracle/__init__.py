@@ -52,8 +52,24 @@ def lib():
                                          ctypes.c_int32, ctypes.c_int32, _i32p, _i32p, _dp]
             L.lq_oracle_alg1.restype = ctypes.c_int
             L.lq_oracle_reconstruct12.argtypes = [ctypes.c_int64, _dp, _dp]
+            L.lq_oracle_max_threads.argtypes = []
+            L.lq_oracle_max_threads.restype = ctypes.c_int
+            L.lq_oracle_set_threads.argtypes = [ctypes.c_int]
+            L.lq_oracle_set_threads.restype = ctypes.c_int
             _lib = L
     return _lib
+
+
+def max_threads() -> int:
+    """Host cores the oracle's site loops can use (1 if it was built without OpenMP)."""
+    return int(lib().lq_oracle_max_threads())
+
+
+def set_threads(n: int) -> int:
+    """Split the loops over output sites of dslash / dslash_sites (and so of normal_op, cg and
+    alg1) over n threads; 1 (the default) is serial.  Results do not depend on n.  Returns
+    the thread count in use."""
+    return int(lib().lq_oracle_set_threads(int(n)))
 
 
 def _dims(dims):

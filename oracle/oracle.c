@@ -24,8 +24,35 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef double complex cplx;
+
+/* Threads over which the loops over output sites of lq_oracle_dslash and
+ * lq_oracle_dslash_sites are split (1 = serial, the default).  Each output site is computed
+ * by the same per-site routine and written by exactly one thread, so the results do not
+ * depend on this number; it only serves to time the oracle on all host cores. */
+static int g_threads = 1;
+
+/* Cores the oracle can use: the OpenMP processor count, or 1 without OpenMP. */
+int lq_oracle_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_num_procs();
+#else
+    return 1;
+#endif
+}
+
+/* Sets the thread count (clamped to 1..lq_oracle_max_threads()); returns the count in use. */
+int lq_oracle_set_threads(int n)
+{
+    const int mx = lq_oracle_max_threads();
+    g_threads = n < 1 ? 1 : (n > mx ? mx : n);
+    return g_threads;
+}
 
 /* ------------------------------------------------------------------------------------
  * Gamma matrices, chiral Euclidean basis (Hermitian, {g_mu, g_nu} = 2 delta):
@@ -172,6 +199,9 @@ void lq_oracle_dslash(const int32_t L[4], double m_q, const double *U_reals,
     const cplx *U = (const cplx *)U_reals;
     const cplx *psi = (const cplx *)psi_reals;
     cplx *out = (cplx *)out_reals;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(g_threads) if (g_threads > 1)
+#endif
     for (int64_t n = 0; n < V; ++n) {
         cplx o[4][3];
         site_apply(L, m_q, U, psi, n, dagger, P, o);
@@ -191,6 +221,9 @@ void lq_oracle_dslash_sites(const int32_t L[4], double m_q, const double *U_real
     const cplx *U = (const cplx *)U_reals;
     const cplx *psi = (const cplx *)psi_reals;
     cplx *out = (cplx *)out_reals;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(g_threads) if (g_threads > 1)
+#endif
     for (int64_t k = 0; k < nsites; ++k) {
         cplx o[4][3];
         site_apply(L, m_q, U, psi, sites[k], dagger, P, o);

@@ -14,8 +14,9 @@
 
 namespace {
 
-// Largest workspace the fixed array serves (see lq_cg_workspace_bytes).  64 MiB covers,
-// for example, a 16^4 lattice in either mixed mode and a 12^4 lattice in FP64 mode.
+// Largest workspace the fixed array serves (see lq_cg_workspace_bytes).  64 MiB covers a
+// 12^4 lattice in every mode (35-43 MiB); a 16^4 lattice needs 73 MiB in FP64 and 110-133 MiB
+// in the other modes, so it is rejected.
 constexpr size_t kNoAllocScratchBytes = (size_t)64 << 20;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
@@ -26,7 +27,11 @@ void* g_scratch_ptr[kMaxDevices] = {};
 
 // Device address of the array on the current device.  In host code the array's name is
 // only a host-side stand-in, so the address must come from cudaGetSymbolAddress, once per
-// device, with that device current.
+// device, with that device current.  Under CUDA's lazy module loading this first lookup is
+// also when the module holding the array is loaded on the device, i.e. when its 64 MiB are
+// reserved (and can fail for lack of memory).  The cached address stays valid as long as
+// the device's primary context lives: a cudaDeviceReset while the library is loaded
+// would leave it dangling.
 int scratch_for_current_device(void** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);

@@ -191,3 +191,15 @@ def test_lattices_argument_checks(lqlib):
     bad = _lattices(lqlib, specs)
     bad[0].m_q = float("inf")
     assert call(bad) == -1
+
+
+def test_noalloc_array_size_against_the_workspace_query(lqlib):
+    """The fixed no-allocation scratch (64 MiB) holds a 12^4 solve in every mode and a 16^4
+    solve in none, as the header states."""
+    L = lqlib.load()
+    L.lq_cg_noalloc_max_workspace_bytes.restype = ctypes.c_size_t
+    cap = L.lq_cg_noalloc_max_workspace_bytes()
+    assert cap == 64 << 20
+    for mode in ("f64", "f64x", "mixed_f32", "mixed_f16", "mixed_i32"):
+        assert 0 < lqlib.cg_workspace_bytes((12, 12, 12, 12), mode) <= cap, mode
+        assert lqlib.cg_workspace_bytes((16, 16, 16, 16), mode) > cap, mode

@@ -517,3 +517,25 @@ def test_projected_spin_sums_reduce_to_the_upper_half():
                 lhs = np.sum(a * np.conj(P @ b))
                 rhs = np.sum((P @ a)[:2] * np.conj((P @ b)[:2]))
                 assert abs(lhs - rhs) <= 1e-13 * (1 + abs(lhs))
+
+
+def test_threaded_site_loops_equal_the_serial_ones():
+    """Splitting the oracle's loops over output sites across host cores (used only to time
+    it) changes no bit of D psi, D^dag psi or the sampled-site values."""
+    dims = (4, 6, 2, 8)
+    U = synth.gauge_field(dims, seed=41)
+    psi = synth.gaussian_spinor(dims, seed=42)
+    sites = np.random.default_rng(43).integers(0, synth.volume(dims), 97)
+    oracle.set_threads(1)
+    ref = [oracle.dslash(dims, 0.1, U, psi, dagger=d) for d in (False, True)]
+    ref_s = oracle.dslash_sites(dims, 0.1, U, psi, sites, dagger=True)
+    try:
+        used = oracle.set_threads(max(2, oracle.max_threads()))
+        assert 1 <= used <= oracle.max_threads()
+        got = [oracle.dslash(dims, 0.1, U, psi, dagger=d) for d in (False, True)]
+        got_s = oracle.dslash_sites(dims, 0.1, U, psi, sites, dagger=True)
+    finally:
+        oracle.set_threads(1)
+    for a, b in zip(got, ref):
+        assert np.array_equal(a, b)
+    assert np.array_equal(got_s, ref_s)
