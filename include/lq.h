@@ -89,7 +89,8 @@ extern "C" {
 
 typedef enum lq_status {
     LQ_OK = 0,
-    LQ_NOT_CONVERGED = 1,     /* solver stopped at max_iter / stagnation; x holds the best iterate */
+    LQ_NOT_CONVERGED = 1,     /* solver stopped at max_iter, max_cycles or stagnation (5 cycles
+                                 without a new best true residual); x holds the last iterate   */
     LQ_ERR_ARG = -1,          /* bad enum value, null pointer, bad tolerance or count       */
     LQ_ERR_DIMS = -2,         /* odd, non-positive or too large lattice extents             */
     LQ_ERR_ALIGN = -3,        /* pointer not 16-byte aligned, or output aliases an input    */
@@ -199,6 +200,7 @@ typedef struct lq_cg_params {
     int32_t chunk;           /* host-driven inner loop: iterations between host checks;
                                 0 -> automatic                                             */
     int32_t flags;           /* LQ_CG_PROFILE: time the solver's kernels with CUDA events  */
+    int32_t max_inner;       /* cap on inner iterations per cycle (Algorithm 1's k); 0 -> 1000 */
 } lq_cg_params;
 
 /* lq_cg_params.flags */

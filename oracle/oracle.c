@@ -319,6 +319,12 @@ int lq_oracle_cg(const int32_t L[4], double m_q, const double *U_reals,
  *       p_0 = r_0 + beta_0 (p_k - <r_0, p_k> r_0),   beta_0 = s_l / (s_{l-1} rho_k),
  *     i.e. the old direction, with its component along the new residual removed, is
  *     continued with the CG coefficient rescaled into the unit-norm units of r_0;
+ *   - that continuation is exact only while the inner recurrence tracks the true
+ *     residual, s_l = s_{l-1} sqrt(rho_k) up to rounding.  When the new true residual
+ *     exceeds twice the recurrence's prediction (s_l > 2 s_{l-1} sqrt(rho_k): once the
+ *     tolerance lies below what the high precision resolves, the residual is rounding noise
+ *     and beta_0 ~ 1/rho_k would blow the stale direction up), the cycle starts afresh
+ *     from p_0 = r_0, as the first one does;
  *   - rho_0 = ||r_0||^2 (one, up to the rounding of r_0);
  *   - the solution update is psi^high += s_l psi_k, where psi_k already holds all k
  *     inner updates;
@@ -351,13 +357,13 @@ int lq_oracle_alg1(const int32_t L[4], double m_q, const double *U_reals,
     normal_op(L, m_q, U_reals, x_high, tmp, q);
     for (int64_t i = 0; i < n; ++i) r_high[i] = eta[i] - q[i];
     double s = sqrt(vnorm2(n, r_high)), s_prev = 0.0, rho = 1.0;
-    int l = 0, inner_total = 0;
+    int l = 0, inner_total = 0, fresh = 1;
 
     while (s > tol * eta_norm && l < max_cycles) {
         /* psi_0 = 0 ; r_0 = r^high / s^high */
         for (int64_t i = 0; i < n; ++i) { psi[i] = 0.0; r[i] = r_high[i] / s; }
         round_low(n, r, low_is_f32);
-        if (l == 0) {
+        if (fresh) {
             for (int64_t i = 0; i < n; ++i) p[i] = r[i];
         } else {
             /* p_0 = r_0 + beta_0 (p_k - <r_0, p_k> r_0),  beta_0 = s_l / (s_{l-1} rho_k) */
@@ -391,8 +397,10 @@ int lq_oracle_alg1(const int32_t L[4], double m_q, const double *U_reals,
         /* r^high_{l+1} = b - (D^dag D)^high psi^high_{l+1} ; s_{l+1} = ||r^high_{l+1}|| */
         normal_op(L, m_q, U_reals, x_high, tmp, q);
         for (int64_t i = 0; i < n; ++i) r_high[i] = eta[i] - q[i];
+        const double s_new = sqrt(vnorm2(n, r_high));
+        fresh = !(s_new <= 2.0 * s * sqrt(rho));
         s_prev = s;
-        s = sqrt(vnorm2(n, r_high));
+        s = s_new;
         ++l;
         if (k == 0) break;   /* no progress possible */
     }

@@ -42,7 +42,8 @@ class LqError(RuntimeError):
 
 class CgParams(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("max_cycles", ctypes.c_int32),
-                ("delta", ctypes.c_double), ("chunk", ctypes.c_int32), ("flags", ctypes.c_int32)]
+                ("delta", ctypes.c_double), ("chunk", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("max_inner", ctypes.c_int32)]
 
 
 class CgInfo(ctypes.Structure):
@@ -301,13 +302,14 @@ def cg_workspace_bytes(dims, mode="f64", nrhs=1) -> int:
 
 
 def cg_solve(dims, m_q, U, eta, x=None, mode="f64", tol=1e-10, max_iter=100000, max_cycles=0, delta=0.0,
-             chunk=0, workspace=None, stream=None, profile=False, native_f64=False, link18=False, graph=True):
+             chunk=0, max_inner=0, workspace=None, stream=None, profile=False, native_f64=False, link18=False, graph=True):
     """Solve D^dag D x = eta (Algorithm 1).  U: F64 LEX 18-real links, eta / x: F64 LEX spinors.
 
     x (if given) is the starting guess and receives the solution.  Returns (x, info, status)
     where info is a dict of the solver statistics; raises LqError on errors (status < 0).
     mode: "f64", "f64x", "mixed_f32", "mixed_f16" or "mixed_i32"; delta <= 0 takes the mode's
-    default inner reduction per cycle.  profile=True times the solver's kernels with CUDA
+    default inner reduction per cycle; max_inner caps the inner iterations of one cycle
+    (0: 1000).  profile=True times the solver's kernels with CUDA
     events (host-driven inner loop); graph=False launches the inner kernels from the host
     instead of running each cycle's inner loop in a conditional CUDA graph; native_f64 and
     link18 select native FP64 outer arithmetic and 18-real inner links (mixed modes).
@@ -323,7 +325,7 @@ def cg_solve(dims, m_q, U, eta, x=None, mode="f64", tol=1e-10, max_iter=100000, 
         workspace = _empty_bytes(wb, eta)
     flags = (CG_PROFILE if profile else 0) | (CG_NATIVE_F64 if native_f64 else 0) | (CG_LINK18 if link18 else 0) \
         | (0 if graph else CG_NO_GRAPH)
-    prm = CgParams(float(tol), int(max_iter), int(max_cycles), float(delta), int(chunk), flags)
+    prm = CgParams(float(tol), int(max_iter), int(max_cycles), float(delta), int(chunk), flags, int(max_inner))
     info = CgInfo()
     st = load().lq_cg_solve(_dims(dims), float(m_q), m, _ptr(U, gb, "U"), _ptr(eta, sb, "eta"),
                             _ptr(x, sb, "x"), ctypes.byref(prm), _ptr(workspace, wb, "workspace"),
@@ -334,7 +336,7 @@ def cg_solve(dims, m_q, U, eta, x=None, mode="f64", tol=1e-10, max_iter=100000, 
 
 
 def cg_solve_multi(dims, m_q, nrhs, U, eta, x=None, mode="f64", tol=1e-10, max_iter=100000, max_cycles=0,
-                   delta=0.0, chunk=0, workspace=None, stream=None, profile=False, native_f64=False, link18=False,
+                   delta=0.0, chunk=0, max_inner=0, workspace=None, stream=None, profile=False, native_f64=False, link18=False,
                    graph=True):
     """nrhs independent solves D^dag D x_r = eta_r sharing the links (eta, x: nrhs stacked FP64
     LEX fields).  Returns (x, [info per right-hand side], status)."""
@@ -350,7 +352,7 @@ def cg_solve_multi(dims, m_q, nrhs, U, eta, x=None, mode="f64", tol=1e-10, max_i
         workspace = _empty_bytes(wb, eta)
     flags = (CG_PROFILE if profile else 0) | (CG_NATIVE_F64 if native_f64 else 0) | (CG_LINK18 if link18 else 0) \
         | (0 if graph else CG_NO_GRAPH)
-    prm = CgParams(float(tol), int(max_iter), int(max_cycles), float(delta), int(chunk), flags)
+    prm = CgParams(float(tol), int(max_iter), int(max_cycles), float(delta), int(chunk), flags, int(max_inner))
     infos = (CgInfo * n)()
     st = load().lq_cg_solve_multi(_dims(dims), float(m_q), m, n, _ptr(U, gb, "U"), _ptr(eta, sb, "eta"),
                                   _ptr(x, sb, "x"), ctypes.byref(prm), _ptr(workspace, wb, "workspace"),
@@ -366,7 +368,7 @@ def cg_workspace_bytes_schur(dims, mode="mixed_f32", nrhs=1) -> int:
 
 
 def cg_solve_schur(dims, m_q, U, b, x=None, nrhs=1, mode="mixed_f32", tol=1e-10, max_iter=100000, max_cycles=0,
-                   delta=0.0, chunk=0, workspace=None, stream=None, profile=False, link18=False, graph=True):
+                   delta=0.0, chunk=0, max_inner=0, workspace=None, stream=None, profile=False, link18=False, graph=True):
     """Solve D x = b (nrhs stacked FP64 LEX fields) by the even-odd Schur complement.
     Returns (x, [info per right-hand side], status)."""
     import torch
@@ -380,7 +382,7 @@ def cg_solve_schur(dims, m_q, U, b, x=None, nrhs=1, mode="mixed_f32", tol=1e-10,
     if workspace is None:
         workspace = _empty_bytes(wb, b)
     flags = (CG_PROFILE if profile else 0) | (CG_LINK18 if link18 else 0) | (0 if graph else CG_NO_GRAPH)
-    prm = CgParams(float(tol), int(max_iter), int(max_cycles), float(delta), int(chunk), flags)
+    prm = CgParams(float(tol), int(max_iter), int(max_cycles), float(delta), int(chunk), flags, int(max_inner))
     infos = (CgInfo * n)()
     st = load().lq_cg_solve_schur(_dims(dims), float(m_q), m, n, _ptr(U, gb, "U"), _ptr(b, sb, "b"),
                                   _ptr(x, sb, "x"), ctypes.byref(prm), _ptr(workspace, wb, "workspace"),
@@ -413,7 +415,7 @@ def cg_workspace_bytes_lattices(problems, mode="mixed_f32") -> int:
     return int(load().lq_cg_workspace_bytes_lattices(len(problems), _lattice_array(problems), m))
 
 
-def cg_solve_lattices(problems, mode="mixed_f32", tol=1e-10, max_iter=100000, max_cycles=0, delta=0.0, chunk=0,
+def cg_solve_lattices(problems, mode="mixed_f32", tol=1e-10, max_iter=100000, max_cycles=0, delta=0.0, chunk=0, max_inner=0,
                       workspace=None, stream=None, autotune=False, graph=True, block=None):
     """Solve several lattices of different sizes together (lq_cg_solve_lattices).
 
@@ -442,7 +444,7 @@ def cg_solve_lattices(problems, mode="mixed_f32", tol=1e-10, max_iter=100000, ma
     flags = (CG_AUTOTUNE if autotune else 0) | (0 if graph else CG_NO_GRAPH)
     if block is not None:
         flags |= {64: 0x100, 128: 0x200, 256: 0x400}[int(block)]
-    prm = CgParams(float(tol), int(max_iter), int(max_cycles), float(delta), int(chunk), flags)
+    prm = CgParams(float(tol), int(max_iter), int(max_cycles), float(delta), int(chunk), flags, int(max_inner))
     total = sum(int(p.get("nrhs", 1)) for p in problems)
     infos = (CgInfo * total)()
     st = load().lq_cg_solve_lattices(len(problems), arr, m, ctypes.byref(prm), _ptr(workspace, wb, "workspace"),

@@ -345,7 +345,8 @@ int lq_cg_solve_multi(const int32_t dims[4], double m_q, int32_t mode, int32_t n
     if (params) prm = *params;
     if (!(prm.tol > 0.0) || !isfinite(prm.tol)) return fail(LQ_ERR_ARG, "tol must be positive and finite");
     if (prm.max_iter < 1) return fail(LQ_ERR_ARG, "max_iter must be >= 1");
-    if (prm.max_cycles < 0 || prm.chunk < 0) return fail(LQ_ERR_ARG, "max_cycles and chunk must be >= 0");
+    if (prm.max_cycles < 0 || prm.chunk < 0 || prm.max_inner < 0)
+        return fail(LQ_ERR_ARG, "max_cycles, chunk and max_inner must be >= 0");
     if (!(prm.delta < 1.0) || !isfinite(prm.delta)) return fail(LQ_ERR_ARG, "delta must be < 1");
     if ((r = check_ptr(U, "U")) || (r = check_ptr(eta, "eta")) || (r = check_ptr(x, "x"))) return r;
     if ((r = check_ptr(workspace, "workspace"))) return r == LQ_ERR_ARG ? fail(LQ_ERR_WORKSPACE, "workspace is NULL") : r;
@@ -406,7 +407,8 @@ int lq_cg_solve_lattices(int32_t n, const lq_lattice* lats, int32_t mode, const 
     if (params) prm = *params;
     if (!(prm.tol > 0.0) || !isfinite(prm.tol)) return fail(LQ_ERR_ARG, "tol must be positive and finite");
     if (prm.max_iter < 1) return fail(LQ_ERR_ARG, "max_iter must be >= 1");
-    if (prm.max_cycles < 0 || prm.chunk < 0) return fail(LQ_ERR_ARG, "max_cycles and chunk must be >= 0");
+    if (prm.max_cycles < 0 || prm.chunk < 0 || prm.max_inner < 0)
+        return fail(LQ_ERR_ARG, "max_cycles, chunk and max_inner must be >= 0");
     if (!(prm.delta < 1.0) || !isfinite(prm.delta)) return fail(LQ_ERR_ARG, "delta must be < 1");
     if (prm.flags & (LQ_CG_PROFILE | LQ_CG_NATIVE_F64 | LQ_CG_LINK18))
         return fail(LQ_ERR_ARG, "LQ_CG_PROFILE, LQ_CG_NATIVE_F64 and LQ_CG_LINK18 do not apply to lattice batches");
@@ -458,7 +460,8 @@ int lq_cg_solve_schur(const int32_t dims[4], double m_q, int32_t mode, int32_t n
     if (params) prm = *params;
     if (!(prm.tol > 0.0) || !isfinite(prm.tol)) return fail(LQ_ERR_ARG, "tol must be positive and finite");
     if (prm.max_iter < 1) return fail(LQ_ERR_ARG, "max_iter must be >= 1");
-    if (prm.max_cycles < 0 || prm.chunk < 0) return fail(LQ_ERR_ARG, "max_cycles and chunk must be >= 0");
+    if (prm.max_cycles < 0 || prm.chunk < 0 || prm.max_inner < 0)
+        return fail(LQ_ERR_ARG, "max_cycles, chunk and max_inner must be >= 0");
     if (!(prm.delta < 1.0) || !isfinite(prm.delta)) return fail(LQ_ERR_ARG, "delta must be < 1");
     if ((r = check_ptr(U, "U")) || (r = check_ptr(b, "b")) || (r = check_ptr(x, "x"))) return r;
     if ((r = check_ptr(workspace, "workspace"))) return r == LQ_ERR_ARG ? fail(LQ_ERR_WORKSPACE, "workspace is NULL") : r;

@@ -17,7 +17,11 @@
 // Readings of Algorithm 1 (the text has index garbles):
 //   * at the start of cycle l, r_0 = r^high_l / s_l;
 //   * the first cycle starts from p_0 = r_0, later ones continue the old direction:
-//       p_0 = r_0 + beta_0 (p_k - <r_0, p_k> r_0),  beta_0 = s_l / (s_{l-1} rho_k);
+//       p_0 = r_0 + beta_0 (p_k - <r_0, p_k> r_0),  beta_0 = s_l / (s_{l-1} rho_k),
+//     unless the new true residual exceeds twice the inner recurrence's prediction
+//     (s_l > 2 s_{l-1} sqrt(rho_k), as below the resolution of the outer arithmetic), when
+//     the cycle starts afresh from p_0 = r_0;
+//   * the inner loop takes at most k iterations per cycle (lq_cg_params.max_inner, 1000);
 //   * rho_0 = ||r_0||^2; psi^high += s_l psi_k;
 //   * the inner loop stops when rho_n <= max(delta^2, (tol ||eta|| / s_l)^2) or n = k;
 //   * the outer loop stops when s <= tol ||eta|| (relative criterion).
@@ -858,7 +862,9 @@ struct Solve {
     EventSet evs;
     InnerGraph igraph;
     bool graph_off = false;   // the inner-loop graph could not be built
-    double eta_norm[kMaxRhs], s[kMaxRhs], s_prev[kMaxRhs], rho_k[kMaxRhs], target[kMaxRhs];
+    double eta_norm[kMaxRhs], s[kMaxRhs], s_prev[kMaxRhs], rho_k[kMaxRhs], target[kMaxRhs], best[kMaxRhs];
+    // first[j]: the next cycle starts from p_0 = r_0 (the first cycle, or after the true
+    // residual left the inner recurrence's prediction) instead of continuing the direction
     int done[kMaxRhs], first[kMaxRhs], stagnant[kMaxRhs], status[kMaxRhs], total[kMaxRhs];
 
     Solve() = default;
@@ -1127,6 +1133,7 @@ struct Solve {
             for (int j = 0; j < nb; ++j) s[j] = sqrt(hs.red[2][j]);
             high_applies = 1;
         }
+        for (int j = 0; j < nb; ++j) best[j] = s[j];
         l = 0;
         return LQ_OK;
     }
@@ -1134,6 +1141,7 @@ struct Solve {
     // convergence and limits, per right-hand side; true if some right-hand side needs a cycle
     bool plan() {
         const int max_cycles = prm.max_cycles > 0 ? prm.max_cycles : 1000;
+        const int per_cycle = prm.max_inner > 0 ? prm.max_inner : 1000;
         int total_max = 0;
         bool any = false;
         for (int j = 0; j < nb; ++j) {
@@ -1153,6 +1161,7 @@ struct Solve {
             }
         }
         k_max = prm.max_iter - total_max;
+        if (k_max > per_cycle) k_max = per_cycle;
         return any;
     }
 
@@ -1297,10 +1306,17 @@ struct Solve {
         for (int j = 0; j < nb; ++j) {
             if (!xact.v[j]) continue;
             const double s_new = sqrt(hs.red[2][j]);
-            stagnant[j] = (s_new > 0.999 * s[j]) ? stagnant[j] + 1 : 0;
+            // stagnation: cycles since the true residual last improved on its best by 0.1%
+            if (s_new < 0.999 * best[j]) {
+                best[j] = s_new;
+                stagnant[j] = 0;
+            } else {
+                stagnant[j] += 1;
+            }
+            // continue the direction only while the recurrence predicted the true residual
+            first[j] = !(s_new <= 2.0 * s[j] * sqrt(rho_k[j]));
             s_prev[j] = s[j];
             s[j] = s_new;
-            first[j] = 0;
             out[j].cycles += 1;
         }
         ++l;

@@ -122,6 +122,7 @@ def test_cg_argument_checks(lqlib):
     assert call(p=lqlib.CgParams(-1.0, 100, 0, 0.0, 0, 0)) == -1
     assert call(p=lqlib.CgParams(1e-10, 0, 0, 0.0, 0, 0)) == -1
     assert call(p=lqlib.CgParams(1e-10, 10, 0, 1.5, 0, 0)) == -1
+    assert call(p=lqlib.CgParams(1e-10, 10, 0, 0.0, 0, 0, -1)) == -1     # max_inner < 0
     assert call(x=0x30000000) == -3                  # x aliases eta
     assert "alias" in lqlib.last_error() or "overlap" in lqlib.last_error()
 

@@ -539,3 +539,20 @@ def test_threaded_site_loops_equal_the_serial_ones():
     for a, b in zip(got, ref):
         assert np.array_equal(a, b)
     assert np.array_equal(got_s, ref_s)
+
+
+def test_alg1_restarts_afresh_below_the_arithmetic():
+    """A tolerance of 1e-20 is below what FP64 resolves: after the true residual reaches
+    rounding level (~1e-16) it no longer follows the inner recurrence, and continuing the
+    old direction with beta_0 ~ 1/rho_k would let each later cycle run to its cap k (1000)
+    with no progress.  Starting those cycles afresh from p_0 = r_0 keeps every cycle at
+    the length of a normal one and the residual at rounding level."""
+    dims = (4, 4, 4, 4)
+    U = synth.gauge_field(dims, seed=1)
+    eta = synth.gaussian_spinor(dims, seed=2)
+    _, c4, i4, r4 = oracle.alg1(dims, 0.1, U, eta, tol=1e-20, low="f32", delta=1e-4, max_cycles=4)
+    assert r4 < 1e-14
+    _, c12, i12, r12 = oracle.alg1(dims, 0.1, U, eta, tol=1e-20, low="f32", delta=1e-4, max_cycles=12)
+    assert c12 == 12
+    assert i12 - i4 <= 8 * 2 * (i4 // 4 + 1)
+    assert r12 < 1e-14
