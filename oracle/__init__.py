@@ -52,6 +52,7 @@ def lib():
                                          ctypes.c_int32, ctypes.c_int32, _i32p, _i32p, _dp]
             L.lq_oracle_alg1.restype = ctypes.c_int
             L.lq_oracle_reconstruct12.argtypes = [ctypes.c_int64, _dp, _dp]
+            L.lq_oracle_reconstruct10.argtypes = [ctypes.c_int64, _dp, _dp]
             L.lq_oracle_max_threads.argtypes = []
             L.lq_oracle_max_threads.restype = ctypes.c_int
             L.lq_oracle_set_threads.argtypes = [ctypes.c_int]
@@ -203,6 +204,24 @@ def reconstruct12(rows) -> np.ndarray:
     flat = rows.reshape(n, 2, 3)
     out = np.empty((n, 3, 3), dtype=np.complex128)
     lib().lq_oracle_reconstruct12(ctypes.c_int64(n), _cptr(flat.view(np.float64), ctypes.c_double),
+                                  _cptr(out.view(np.float64), ctypes.c_double))
+    return out.reshape(*lead, 3, 3)
+
+
+def reconstruct10(stored) -> np.ndarray:
+    """Full 3x3 links from their 10-real form: row 0 and the two entries of row 1 outside
+    column k (k = the column of row 0 with the largest max(|Re|, |Im|), lowest on ties);
+    row 1's entry k follows from row 1 being orthogonal to row 0, row 2 = conj(row0 x row1).
+
+    stored: complex (..., 5) = (u00, u01, u02, first kept u1j, second kept u1j);
+    returns complex (..., 3, 3).
+    """
+    stored = np.ascontiguousarray(stored, dtype=np.complex128)
+    lead = stored.shape[:-1]
+    n = int(np.prod(lead)) if lead else 1
+    flat = stored.reshape(n, 5)
+    out = np.empty((n, 3, 3), dtype=np.complex128)
+    lib().lq_oracle_reconstruct10(ctypes.c_int64(n), _cptr(flat.view(np.float64), ctypes.c_double),
                                   _cptr(out.view(np.float64), ctypes.c_double))
     return out.reshape(*lead, 3, 3)
 

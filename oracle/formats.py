@@ -6,8 +6,11 @@ oracle computes with.  They follow the format definitions in include/lq.h; the C
 kernels implement the same definitions in their own code.
 
 Precisions:  "f64", "f32", "f16s", "f64x" (FP64 values as float pairs hi = fl32(v),
-lo = fl32(v - hi), laid out like "f64" with every double replaced by (hi, lo)).  Link formats: 18 (full 3x3) or 12 (rows 0 and 1;
-row 2 is conj(row0 x row1), an exact identity for SU(3)).  Layouts: "lex" (site-major,
+lo = fl32(v - hi), laid out like "f64" with every double replaced by (hi, lo)).  Link formats: 18 (full 3x3), 12 (rows 0 and 1;
+row 2 is conj(row0 x row1), an exact identity for SU(3)) or 10 (row 0 and the two entries of
+row 1 outside column k, where k is the column of the stored row 0 with the largest
+max(|Re|, |Im|), lowest on ties; the missing entry follows from the orthogonality of rows 0
+and 1, then row 2 as for 12; not for "f64x").  Layouts: "lex" (site-major,
 lexicographic) and "eo" (parity-split, chunked structure of arrays).
 
 Scaled FP16 spinors ("f16s"): per site, s = max over the 24 reals of |fl32(v)| (an FP32
@@ -24,7 +27,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import reconstruct12
+from . import reconstruct10, reconstruct12
 
 PRECS = ("f64", "f32", "f16s", "f64x", "i32s")
 _ELEM = {"f64": np.float64, "f32": np.float32, "f16s": np.float16, "i32s": np.int32}
@@ -55,7 +58,7 @@ def _spinor_chunk(prec):
 
 
 def _link_chunk(prec, fmt):
-    if fmt == 18:
+    if fmt in (18, 10):
         return 2
     return {"f64": 2, "f64x": 2, "f32": 4, "f16s": 4, "i32s": 4}[prec]
 
@@ -198,10 +201,36 @@ def gauge_bytes(dims, prec, fmt) -> int:
     return V * 4 * fmt * per
 
 
+def _stored_value(r, prec):
+    """Stored (rounded) link reals as exact float64 numbers, in units where they compare
+    like the stored elements (Q1.30 integers stay integers)."""
+    return np.asarray(r).astype(np.float64)
+
+
+def link10_column(row0_stored, prec):
+    """k of the 10-real form for each link: the column of the stored row 0 (reals
+    (..., 6)) whose larger component max(|Re|, |Im|) is largest, the lowest on ties."""
+    v = np.abs(_stored_value(row0_stored, prec)).reshape(*np.shape(row0_stored)[:-1], 3, 2)
+    return np.argmax(v.max(axis=-1), axis=-1)
+
+
 def encode_gauge(U, dims, prec="f64", fmt=18, layout="lex") -> np.ndarray:
-    """complex (V, 4, 3, 3) -> stored buffer (uint8).  fmt 12 keeps rows 0 and 1."""
+    """complex (V, 4, 3, 3) -> stored buffer (uint8).  fmt 12 keeps rows 0 and 1; fmt 10
+    keeps row 0 and the two entries of row 1 outside column link10_column(row 0)."""
     V = _vol(dims)
     U = np.ascontiguousarray(U, dtype=np.complex128).reshape(V, 4, 3, 3)
+    if fmt == 10:
+        if prec == "f64x":
+            raise ValueError("the 10-real link form is not defined for f64x")
+        row0 = _round(np.ascontiguousarray(U[:, :, 0, :]).view(np.float64).reshape(V, 4, 6), prec)
+        k = link10_column(row0, prec)
+        cols = np.array([[1, 2], [0, 2], [0, 1]])[k]                        # (V, 4, 2)
+        kept = np.take_along_axis(U[:, :, 1, :], cols, axis=-1)             # (V, 4, 2)
+        rest = _round(np.ascontiguousarray(kept).view(np.float64).reshape(V, 4, 4), prec)
+        data = np.concatenate([row0, rest], axis=-1)
+        if layout == "eo":
+            data = _to_eo_gauge(data, dims, fmt, _link_chunk(prec, fmt))
+        return np.ascontiguousarray(data).view(np.uint8).reshape(-1)
     rows = U if fmt == 18 else U[:, :, :2, :]
     reals = np.ascontiguousarray(rows).view(np.float64).reshape(V, 4, fmt)
     data = reals if prec == "f64x" else _round(reals, prec)
@@ -213,7 +242,7 @@ def encode_gauge(U, dims, prec="f64", fmt=18, layout="lex") -> np.ndarray:
 
 
 def decode_gauge(buf, dims, prec="f64", fmt=18, layout="lex") -> np.ndarray:
-    """Stored buffer -> complex128 (V, 4, 3, 3); 12-real links get row 2 rebuilt in FP64."""
+    """Stored buffer -> complex128 (V, 4, 3, 3); 12- and 10-real links are rebuilt in FP64."""
     V = _vol(dims)
     buf = np.ascontiguousarray(np.asarray(buf).view(np.uint8).reshape(-1))
     if buf.size != gauge_bytes(dims, prec, fmt):
@@ -224,6 +253,8 @@ def decode_gauge(buf, dims, prec="f64", fmt=18, layout="lex") -> np.ndarray:
     vals = np.ascontiguousarray(data.reshape(V, 4, fmt).astype(np.float64))
     if prec == "i32s":
         vals = vals / Q30
+    if fmt == 10:
+        return np.ascontiguousarray(reconstruct10(vals.view(np.complex128).reshape(V, 4, 5)))
     c = vals.view(np.complex128).reshape(V, 4, fmt // 6, 3)
     if fmt == 12:
         c = reconstruct12(c)

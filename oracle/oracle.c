@@ -432,3 +432,52 @@ void lq_oracle_reconstruct12(int64_t nlinks, const double *rows_reals, double *f
         o[8] = conj(a[0] * b[1] - a[1] * b[0]);
     }
 }
+
+/* ------------------------------------------------------------------------------------
+ * 10-real link format.  The paper streams each link as 10 input words instead of 18
+ * (Introduction; Section 2.2), chosen so that no trigonometric function is needed, but the
+ * construction it cites is not in the text.  This one follows from unitarity alone:
+ *   stored: row 0 (u00, u01, u02) and the two entries of row 1 outside column k, in
+ *     increasing column order, where k is the column of row 0 whose larger component
+ *     max(|Re u0k|, |Im u0k|) is the largest (the lowest such column on ties), judged on
+ *     the stored values;
+ *   rebuilt: rows 0 and 1 of a unitary matrix are orthogonal, sum_j u1j conj(u0j) = 0, so
+ *       u1k = -(sum_{j != k} u1j conj(u0j)) / conj(u0k),
+ *     and row 2 = conj(row0 x row1) as in the 12-real form.
+ * Row 0 has unit norm, so some column has |u0j|^2 >= 1/3, hence a component of magnitude
+ * >= 1/sqrt(6); the chosen column therefore has |u0k| >= 1/sqrt(6), which bounds the
+ * amplification of the stored values' rounding by the division.
+ * in: [nlinks][5] complex, out: [nlinks][3][3] complex.
+ * ---------------------------------------------------------------------------------- */
+static double larger_part(cplx z)
+{
+    const double a = fabs(creal(z)), b = fabs(cimag(z));
+    return a > b ? a : b;
+}
+
+void lq_oracle_reconstruct10(int64_t nlinks, const double *stored_reals, double *full_reals)
+{
+    const cplx *in = (const cplx *)stored_reals;
+    cplx *out = (cplx *)full_reals;
+    for (int64_t n = 0; n < nlinks; ++n) {
+        const cplx *w = in + 5 * n;
+        cplx *o = out + 9 * n;
+        int k = 0;
+        for (int j = 1; j < 3; ++j)
+            if (larger_part(w[j]) > larger_part(w[k])) k = j;
+        for (int j = 0; j < 3; ++j) o[j] = w[j];
+        /* row 1: the stored entries fill the columns other than k, in increasing order */
+        int at = 3;
+        cplx sum = 0.0;
+        for (int j = 0; j < 3; ++j) {
+            if (j == k) continue;
+            o[3 + j] = w[at++];
+            sum += o[3 + j] * conj(w[j]);
+        }
+        o[3 + k] = -sum / conj(w[k]);
+        const cplx *a = o, *b = o + 3;
+        o[6] = conj(a[1] * b[2] - a[2] * b[1]);
+        o[7] = conj(a[2] * b[0] - a[0] * b[2]);
+        o[8] = conj(a[0] * b[1] - a[1] * b[0]);
+    }
+}

@@ -16,6 +16,7 @@ import pytest
 import oracle
 import synth
 from oracle import dense
+from oracle import formats as F
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -556,3 +557,111 @@ def test_alg1_restarts_afresh_below_the_arithmetic():
     assert c12 == 12
     assert i12 - i4 <= 8 * 2 * (i4 // 4 + 1)
     assert r12 < 1e-14
+
+
+# ----------------------------------------------------------------------------- 10-real links
+def _su3_from_rows(M):
+    """Unit-determinant test matrices built by hand (exact in binary where possible)."""
+    M = np.asarray(M, dtype=np.complex128)
+    assert np.allclose(M @ M.conj().T, np.eye(3), atol=1e-15)
+    assert abs(np.linalg.det(M) - 1.0) < 1e-15
+    return M
+
+
+def test_reconstruct10_exact_for_su3():
+    """Haar and near-identity SU(3) links stored in the 10-real form come back to rounding
+    level, the same as from their full 18 reals."""
+    rng = synth.make_rng(301)
+    for U in (synth.haar_su3(rng, 4096), synth.near_identity_su3(rng, 4096, 0.3),
+              synth.near_identity_su3(rng, 4096, 0.02)):
+        dims = (4, 4, 8, 8)
+        U = U.reshape(1024, 4, 3, 3)
+        R = F.decode_gauge(F.encode_gauge(U, dims, "f64", 10, "lex"), dims, "f64", 10, "lex")
+        assert np.abs(R - U).max() < 4e-15
+
+
+def test_reconstruct10_column_choice_and_recovery():
+    """The stored row-1 entries are the ones outside column k (largest max(|Re|,|Im|) of
+    row 0, the lowest column on ties), and the missing one is recovered exactly."""
+    a = np.sqrt(0.5)
+    cases = [
+        # row 0 = (0, 0, 1): k = 2, row 1's (u10, u11) are stored
+        (_su3_from_rows([[0, 0, 1], [1, 0, 0], [0, 1, 0]]), 2),
+        # row 0 = (a, i a, 0): a tie between columns 0 and 1 goes to column 0
+        (_su3_from_rows([[a, 1j * a, 0], [1j * a, a, 0], [0, 0, 1]]), 0),
+        # row 0 = (0, 1, 0) up to phases: k = 1
+        (_su3_from_rows([[0, 1j, 0], [1j, 0, 0], [0, 0, 1]]), 1),
+        # the identity: k = 0
+        (np.eye(3, dtype=np.complex128), 0),
+    ]
+    for M, k in cases:
+        U = np.broadcast_to(M, (16, 4, 3, 3)).copy()
+        dims = (2, 2, 2, 2)
+        buf = F.encode_gauge(U, dims, "f64", 10, "lex")
+        stored = buf.view(np.complex128).reshape(16, 4, 5)
+        others = [j for j in range(3) if j != k]
+        assert np.array_equal(stored[0, 0, 3:], M[1, others])
+        assert np.array_equal(F.link10_column(np.ascontiguousarray(M[0]).view(np.float64), "f64"), k)
+        R = F.decode_gauge(buf, dims, "f64", 10, "lex")
+        assert np.abs(R - U).max() < 1e-15
+
+
+def test_reconstruct10_recovers_the_orthogonal_entry():
+    """Brute force on the definition: for unitary links, the recovered row-1 entry makes
+    rows 0 and 1 orthogonal and row 1 a unit vector; for a matrix that is not unitary the
+    form does not reproduce it (the 10 stored reals do not determine a general matrix)."""
+    rng = synth.make_rng(303)
+    U = synth.haar_su3(rng, 64)
+    R = oracle.reconstruct10(np.concatenate([U[:, 0, :], U[:, 1, 1:]], axis=-1))   # k = 0 assumed
+    k = F.link10_column(np.ascontiguousarray(U[:, 0, :]).view(np.float64).reshape(64, 6), "f64")
+    sel = k == 0
+    assert sel.any()
+    assert np.abs(R[sel] - U[sel]).max() < 4e-15
+    assert np.abs(np.einsum("nj,nj->n", R[:, 1, :], R[:, 0, :].conj())).max() < 1e-14
+    assert np.abs(np.linalg.norm(R[sel, 1, :], axis=-1) - 1).max() < 1e-14
+    M = (rng.normal(size=(64, 3, 3)) + 1j * rng.normal(size=(64, 3, 3)))
+    dims = (2, 2, 2, 2)
+    Mr = F.decode_gauge(F.encode_gauge(M.reshape(16, 4, 3, 3), dims, "f64", 10, "lex"), dims, "f64", 10, "lex")
+    assert np.abs(Mr - M.reshape(16, 4, 3, 3)).max() > 1e-3
+
+
+def _su3_with_first_row(v, rng):
+    """SU(3) matrices whose row 0 is the unit vector v up to a phase (QR completion)."""
+    n = v.shape[0]
+    M = rng.normal(size=(n, 3, 3)) + 1j * rng.normal(size=(n, 3, 3))
+    M[:, :, 0] = v.conj()
+    Q, _ = np.linalg.qr(M)
+    U = Q.conj().transpose(0, 2, 1)
+    return U / (np.linalg.det(U) ** (1.0 / 3.0))[:, None, None]
+
+
+def test_reconstruct10_conditioning_fp32():
+    """Stored in FP32 (rounding <= 2^-24 relative per real), the rebuilt entries stay within
+    a fixed multiple of the storage rounding, also for rows 0 with vanishing entries: the
+    division is by the chosen |u0k| >= 1/sqrt(6)."""
+    rng = synth.make_rng(305)
+    n = 1 << 12
+    v = rng.normal(size=(n, 3)) + 1j * rng.normal(size=(n, 3))
+    v[np.arange(n), rng.integers(0, 3, n)] *= 1e-7                # one entry of row 0 nearly zero
+    v[: n // 2][np.arange(n // 2), rng.integers(0, 3, n // 2)] *= 1e-7   # and half of them a second one
+    v /= np.linalg.norm(v, axis=1)[:, None]
+    allU = np.concatenate([synth.haar_su3(rng, 1 << 14), _su3_with_first_row(v, rng)])
+    m = allU.shape[0] // 4
+    allU = allU.reshape(m, 4, 3, 3)
+    dims = (m, 1, 1, 1)
+    R = F.decode_gauge(F.encode_gauge(allU, dims, "f32", 10, "lex"), dims, "f32", 10, "lex")
+    assert np.abs(R - allU).max() <= 64 * 2.0 ** -24
+    row0 = np.ascontiguousarray(allU[..., 0, :]).view(np.float64).astype(np.float32)
+    k = F.link10_column(row0, "f32")
+    mag = np.abs(np.take_along_axis(allU[..., 0, :], k[..., None], axis=-1))
+    assert mag.min() >= 1 / np.sqrt(6) - 1e-7
+
+
+def test_dslash_with_10real_links():
+    """D with links rebuilt from their 10 stored reals equals D with the full links."""
+    dims = (4, 4, 2, 6)
+    U = synth.gauge_field(dims, seed=307)
+    psi = synth.gaussian_spinor(dims, seed=308)
+    R = F.decode_gauge(F.encode_gauge(U, dims, "f64", 10, "eo"), dims, "f64", 10, "eo")
+    for dag in (False, True):
+        assert oracle.rel_l2(oracle.dslash(dims, 0.1, R, psi, dag), oracle.dslash(dims, 0.1, U, psi, dag)) < 1e-14
