@@ -22,15 +22,24 @@
  * Site order, LQ_LAYOUT_LEX: n = x + Lx*(y + Ly*(z + Lz*t)), x fastest; site-major:
  *   spinor  [n][spin 4][colour 3][re, im]
  *   gauge   [n][mu 4][row r][col 3][re, im], r = 3 rows (LQ_LINK18) or the first 2 rows
- *           (LQ_LINK12; row 2 is rebuilt as conj(row0 x row1), exact for SU(3)).
+ *           (LQ_LINK12; row 2 is rebuilt as conj(row0 x row1), exact for SU(3));
+ *           LQ_LINK10: [n][mu 4][entry 5][re, im] = row 0 (u00, u01, u02), then the two
+ *           entries of row 1 outside column k, in increasing column order.  k is the column
+ *           of row 0 whose larger component max(|Re u0k|, |Im u0k|) is the largest (the lowest
+ *           such column on ties), judged on the stored values.  Rebuilt: row 1's entry k from
+ *           the orthogonality of rows 0 and 1, u1k = -(sum_{j != k} u1j conj(u0j)) / conj(u0k)
+ *           (|u0k| >= 1/sqrt(6), so the division amplifies rounding by at most ~2.5), then
+ *           row 2 as for LQ_LINK12; exact for SU(3) up to rounding.  The paper streams links
+ *           as 10 words instead of 18 without trigonometric functions (Introduction,
+ *           Section 2.2); its construction is not given, and this one is the library's.
  * Site order, LQ_LAYOUT_EO (parity-split structure of arrays, the fast internal layout):
  *   parity p = (x+y+z+t) mod 2, checkerboard index cb = n / 2, Vh = V / 2.  A field is cut
  *   into fixed-width chunks per site; chunk k of site (p, cb) is stored at chunk slot
  *     spinor:  (p*K + k)*Vh + cb
  *     gauge :  ((mu*2 + p)*K + k)*Vh + cb
- *   chunk widths in reals: spinor F64 2, F32 4, F16S 8, I32S 4; gauge LINK18 2 (all
- *   precisions), LINK12 F64 2, F32 4, F16S 4, I32S 4; K = reals per site (24) or per link
- *   (18/12) / width.
+ *   chunk widths in reals: spinor F64 2, F32 4, F16S 8, I32S 4; gauge LINK18 and LINK10 2
+ *   (all precisions), LINK12 F64 2, F32 4, F16S 4, I32S 4; K = reals per site (24) or per
+ *   link (18/12/10) / width.
  * Precisions (element types of the stored fields):
  *   LQ_F64  double; LQ_F32 float;
  *   LQ_F16S spinors: per site s = max |fl32(v)| over its 24 reals (float) and 24 halves
@@ -101,7 +110,7 @@ typedef enum lq_status {
 } lq_status;
 
 typedef enum lq_prec { LQ_F64 = 0, LQ_F32 = 1, LQ_F16S = 2, LQ_F64X = 3, LQ_I32S = 4 } lq_prec;
-typedef enum lq_link_fmt { LQ_LINK18 = 18, LQ_LINK12 = 12 } lq_link_fmt;
+typedef enum lq_link_fmt { LQ_LINK18 = 18, LQ_LINK12 = 12, LQ_LINK10 = 10 } lq_link_fmt;
 typedef enum lq_layout { LQ_LAYOUT_LEX = 0, LQ_LAYOUT_EO = 1 } lq_layout;
 
 /* Field kinds for lq_field_bytes. */
@@ -115,7 +124,8 @@ size_t lq_field_bytes(const int32_t dims[4], int32_t kind, int32_t prec, int32_t
  * lq_dslash_apply -- out = D psi, Eq. (1) of the paper (Introduction), on the whole lattice.
  *   m_q      quark mass of Eq. (1).
  *   prec     precision of U, psi and out (all three the same).
- *   link_fmt LQ_LINK18 or LQ_LINK12 (12-real links are rebuilt in registers).
+ *   link_fmt LQ_LINK18, LQ_LINK12 or LQ_LINK10 (12- and 10-real links are rebuilt in
+ *            registers; LQ_F64X fields take LQ_LINK18 only).
  *   layout   LQ_LAYOUT_LEX or LQ_LAYOUT_EO, shared by U, psi and out.
  *   U, psi   inputs (device); out output (device), must not overlap psi or U.
  * One kernel launch on cuda_stream; returns without waiting.
@@ -163,7 +173,8 @@ int lq_dslash_hop(const int32_t dims[4], int32_t out_parity, int32_t dagger, dou
  * lq_convert_spinor / lq_convert_gauge -- re-encode a field into another precision,
  * link format or layout (the "pack/convert" step; the paper prepares its reduced link
  * form beforehand, Section 2.2).  Gauge sources must be LQ_LINK18; LQ_LINK12 keeps rows
- * 0 and 1.  Rounding is round-to-nearest-even, through FP32 for FP16 targets; F16S
+ * 0 and 1, LQ_LINK10 row 0 and two entries of row 1 (column choice made on the rounded
+ * row 0, as the header comment defines).  Rounding is round-to-nearest-even, through FP32 for FP16 targets; F16S
  * spinor encoding follows the rule in the header comment.  dst must not overlap src.
  */
 int lq_convert_spinor(const int32_t dims[4], int32_t src_prec, int32_t src_layout,
@@ -209,6 +220,10 @@ typedef struct lq_cg_params {
                                 of FP32 pairs (mixed modes; slower on GB300)              */
 #define LQ_CG_LINK18 4       /* inner links stored 18-real (no reconstruction) in the mixed
                                 modes; default 12-real                                     */
+#define LQ_CG_LINK10 32      /* inner links stored in the 10-real form (lq_cg_solve,
+                                lq_cg_solve_multi and lq_cg_solve_noalloc in the mixed modes
+                                with the FP32-pair outer loop; not with LQ_CG_LINK18 or
+                                LQ_CG_NATIVE_F64)                                          */
 #define LQ_CG_AUTOTUNE 8     /* lq_cg_solve_lattices: pick the inner block size by timing
                                 (cached per lattice set and GPU); default 128 threads      */
 #define LQ_CG_NO_GRAPH 16    /* launch the inner kernels one by one from the host instead of

@@ -7,7 +7,7 @@ fallback: if liblq.so cannot be built or loaded, every call raises.
 Fields are passed as CUDA tensors whose bytes hold the stored field (any dtype; a
 complex128 tensor of shape (V, 4, 3) is exactly an F64 LEX spinor, (V, 4, 3, 3) an F64
 LEX 18-real gauge field).  Precisions: "f64", "f32", "f16s", "f64x" (FP64-class values as
-FP32 pairs); layouts: "lex", "eo"; link formats: 18, 12.
+FP32 pairs), "i32s"; layouts: "lex", "eo"; link formats: 18, 12, 10.
 """
 from __future__ import annotations
 
@@ -29,7 +29,7 @@ __all__ = [
 PREC = {"f64": 0, "f32": 1, "f16s": 2, "f64x": 3, "i32s": 4}
 LAYOUT = {"lex": 0, "eo": 1}
 CG_MODE = {"f64": 0, "mixed_f32": 1, "mixed_f16": 2, "f64x": 3, "mixed_i32": 4}
-CG_PROFILE, CG_NATIVE_F64, CG_LINK18, CG_AUTOTUNE, CG_NO_GRAPH = 1, 2, 4, 8, 16
+CG_PROFILE, CG_NATIVE_F64, CG_LINK18, CG_AUTOTUNE, CG_NO_GRAPH, CG_LINK10 = 1, 2, 4, 8, 16, 32
 STATUS = {0: "OK", 1: "NOT_CONVERGED", -1: "ERR_ARG", -2: "ERR_DIMS", -3: "ERR_ALIGN",
           -4: "ERR_CUDA", -5: "ERR_WORKSPACE", -6: "ERR_NONFINITE", -7: "ERR_BREAKDOWN"}
 
@@ -302,7 +302,7 @@ def cg_workspace_bytes(dims, mode="f64", nrhs=1) -> int:
 
 
 def cg_solve(dims, m_q, U, eta, x=None, mode="f64", tol=1e-10, max_iter=100000, max_cycles=0, delta=0.0,
-             chunk=0, max_inner=0, workspace=None, stream=None, profile=False, native_f64=False, link18=False, graph=True):
+             chunk=0, max_inner=0, workspace=None, stream=None, profile=False, native_f64=False, link18=False, link10=False, graph=True):
     """Solve D^dag D x = eta (Algorithm 1).  U: F64 LEX 18-real links, eta / x: F64 LEX spinors.
 
     x (if given) is the starting guess and receives the solution.  Returns (x, info, status)
@@ -311,8 +311,9 @@ def cg_solve(dims, m_q, U, eta, x=None, mode="f64", tol=1e-10, max_iter=100000, 
     default inner reduction per cycle; max_inner caps the inner iterations of one cycle
     (0: 1000).  profile=True times the solver's kernels with CUDA
     events (host-driven inner loop); graph=False launches the inner kernels from the host
-    instead of running each cycle's inner loop in a conditional CUDA graph; native_f64 and
-    link18 select native FP64 outer arithmetic and 18-real inner links (mixed modes).
+    instead of running each cycle's inner loop in a conditional CUDA graph; native_f64,
+    link18 and link10 select native FP64 outer arithmetic, 18-real and 10-real inner links
+    (mixed modes; link10 with the FP32-pair outer loop only).
     """
     import torch
     m = CG_MODE[mode] if isinstance(mode, str) else int(mode)
@@ -324,7 +325,7 @@ def cg_solve(dims, m_q, U, eta, x=None, mode="f64", tol=1e-10, max_iter=100000, 
     if workspace is None:
         workspace = _empty_bytes(wb, eta)
     flags = (CG_PROFILE if profile else 0) | (CG_NATIVE_F64 if native_f64 else 0) | (CG_LINK18 if link18 else 0) \
-        | (0 if graph else CG_NO_GRAPH)
+        | (CG_LINK10 if link10 else 0) | (0 if graph else CG_NO_GRAPH)
     prm = CgParams(float(tol), int(max_iter), int(max_cycles), float(delta), int(chunk), flags, int(max_inner))
     info = CgInfo()
     st = load().lq_cg_solve(_dims(dims), float(m_q), m, _ptr(U, gb, "U"), _ptr(eta, sb, "eta"),
@@ -336,7 +337,7 @@ def cg_solve(dims, m_q, U, eta, x=None, mode="f64", tol=1e-10, max_iter=100000, 
 
 
 def cg_solve_multi(dims, m_q, nrhs, U, eta, x=None, mode="f64", tol=1e-10, max_iter=100000, max_cycles=0,
-                   delta=0.0, chunk=0, max_inner=0, workspace=None, stream=None, profile=False, native_f64=False, link18=False,
+                   delta=0.0, chunk=0, max_inner=0, workspace=None, stream=None, profile=False, native_f64=False, link18=False, link10=False,
                    graph=True):
     """nrhs independent solves D^dag D x_r = eta_r sharing the links (eta, x: nrhs stacked FP64
     LEX fields).  Returns (x, [info per right-hand side], status)."""
@@ -351,7 +352,7 @@ def cg_solve_multi(dims, m_q, nrhs, U, eta, x=None, mode="f64", tol=1e-10, max_i
     if workspace is None:
         workspace = _empty_bytes(wb, eta)
     flags = (CG_PROFILE if profile else 0) | (CG_NATIVE_F64 if native_f64 else 0) | (CG_LINK18 if link18 else 0) \
-        | (0 if graph else CG_NO_GRAPH)
+        | (CG_LINK10 if link10 else 0) | (0 if graph else CG_NO_GRAPH)
     prm = CgParams(float(tol), int(max_iter), int(max_cycles), float(delta), int(chunk), flags, int(max_inner))
     infos = (CgInfo * n)()
     st = load().lq_cg_solve_multi(_dims(dims), float(m_q), m, n, _ptr(U, gb, "U"), _ptr(eta, sb, "eta"),

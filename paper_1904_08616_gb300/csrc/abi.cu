@@ -42,7 +42,7 @@ size_t spinor_bytes(int64_t nsites, int prec) {
 }
 
 size_t gauge_bytes(int64_t V, int prec, int fmt) {
-    if (fmt != 18 && fmt != 12) return 0;
+    if (fmt != 18 && fmt != 12 && fmt != 10) return 0;
     switch (prec) {
         case LQ_F64:
         case LQ_F64X: return (size_t)V * 4 * fmt * 8;
@@ -65,7 +65,7 @@ constexpr int64_t kMaxSiteFields = int64_t(1) << 28;
 
 bool valid_prec(int p) { return p == LQ_F64 || p == LQ_F32 || p == LQ_F16S || p == LQ_F64X || p == LQ_I32S; }
 bool valid_layout(int l) { return l == LQ_LAYOUT_LEX || l == LQ_LAYOUT_EO; }
-bool valid_fmt(int f) { return f == LQ_LINK18 || f == LQ_LINK12; }
+bool valid_fmt(int f) { return f == LQ_LINK18 || f == LQ_LINK12 || f == LQ_LINK10; }
 bool valid_cg_mode(int m) {
     return m == LQ_CG_F64 || m == LQ_CG_MIXED_F32 || m == LQ_CG_MIXED_F16 || m == LQ_CG_F64X || m == LQ_CG_MIXED_I32;
 }
@@ -410,8 +410,9 @@ int lq_cg_solve_lattices(int32_t n, const lq_lattice* lats, int32_t mode, const 
     if (prm.max_cycles < 0 || prm.chunk < 0 || prm.max_inner < 0)
         return fail(LQ_ERR_ARG, "max_cycles, chunk and max_inner must be >= 0");
     if (!(prm.delta < 1.0) || !isfinite(prm.delta)) return fail(LQ_ERR_ARG, "delta must be < 1");
-    if (prm.flags & (LQ_CG_PROFILE | LQ_CG_NATIVE_F64 | LQ_CG_LINK18))
-        return fail(LQ_ERR_ARG, "LQ_CG_PROFILE, LQ_CG_NATIVE_F64 and LQ_CG_LINK18 do not apply to lattice batches");
+    if (prm.flags & (LQ_CG_PROFILE | LQ_CG_NATIVE_F64 | LQ_CG_LINK18 | LQ_CG_LINK10))
+        return fail(LQ_ERR_ARG,
+                    "LQ_CG_PROFILE, LQ_CG_NATIVE_F64, LQ_CG_LINK18 and LQ_CG_LINK10 do not apply to lattice batches");
     {
         const int bsel = prm.flags & (LQ_CG_BLOCK_64 | LQ_CG_BLOCK_128 | LQ_CG_BLOCK_256);
         if (bsel & (bsel - 1)) return fail(LQ_ERR_ARG, "at most one LQ_CG_BLOCK_* flag");

@@ -18,7 +18,7 @@ __host__ __device__ inline int spinor_chunk(int prec) {
 }
 __host__ __device__ inline int link_chunk(int prec, int fmt) {
     prec = base_prec(prec);
-    return fmt == 18 ? 2 : (prec == LQ_F64 ? 2 : 4);
+    return (fmt == 18 || fmt == 10) ? 2 : (prec == LQ_F64 ? 2 : 4);
 }
 
 struct FieldDesc {
@@ -217,8 +217,45 @@ __global__ void __launch_bounds__(kConvBS) convert_spinor_kernel(Geom g, FieldDe
     }
 }
 
-// the reals of link (s, mu) in a destination format: elements j < dst.fmt of the 18-real link
+// a link real as the destination stores it, read back exactly (Q1.30: the integer)
+__device__ inline double stored_link_value(int prec, double x) {
+    if (prec == LQ_F32) return (double)(float)x;
+    if (prec == LQ_F16S) return (double)__half2float(__float2half_rn((float)x));
+    if (prec == LQ_I32S) return (double)__double2int_rn(x * 0x1p30);
+    return x;
+}
+
+// the reals of link (s, mu) in a destination format: elements j < dst.fmt of the 18-real link;
+// the 10-real form keeps row 0 and the two entries of row 1 outside column k, k chosen on
+// the stored row 0 (largest max(|Re|, |Im|), lowest on ties)
 __device__ inline void store_link(const FieldDesc& dst, const Geom& g, const Site& s, int mu, const double v[18]) {
+    if (dst.fmt == 10) {
+        double m[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            m[j] = abs_max(stored_link_value(dst.prec, v[2 * j]), stored_link_value(dst.prec, v[2 * j + 1]));
+        const int k = link10_column(m[0], m[1], m[2]);
+        double w[10];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) w[j] = v[j];
+        int at = 6;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            if (c == k) continue;
+            w[at] = v[6 + 2 * c];
+            w[at + 1] = v[7 + 2 * c];
+            at += 2;
+        }
+#pragma unroll
+        for (int j = 0; j < 10; ++j) {
+            const int64_t i = lk_elem(dst, g, s, mu, j);
+            if (dst.prec == LQ_F64) ((double*)dst.ptr)[i] = w[j];
+            else if (dst.prec == LQ_F32) ((float*)dst.ptr)[i] = (float)w[j];
+            else if (dst.prec == LQ_I32S) ((int*)dst.ptr)[i] = __double2int_rn(w[j] * 0x1p30);
+            else ((__half*)dst.ptr)[i] = __float2half_rn((float)w[j]);
+        }
+        return;
+    }
     if (dst.prec == LQ_F64X && dst.layout == LQ_LAYOUT_EO && dst.fmt == 18) {
 #pragma unroll
         for (int k = 0; k < 9; ++k) {

@@ -103,6 +103,12 @@ cudaError_t hop_i32(const Geom& g, int p, bool dag, double a, double b, int fmt,
     cudaError_t apply_##NAME(const Geom& g, double m_q, int fmt, int layout, bool dag, const void* U, \
                              const void* psi, void* out, cudaStream_t st, int lnr) {                  \
         const bool lex = layout == LQ_LAYOUT_LEX;                                                     \
+        if (fmt == 10) {                                                                              \
+            if (lex) return dag ? run_apply<PREC, 10, LQ_LAYOUT_LEX, true>(g, m_q, U, psi, out, st, lnr)   \
+                                : run_apply<PREC, 10, LQ_LAYOUT_LEX, false>(g, m_q, U, psi, out, st, lnr); \
+            return dag ? run_apply<PREC, 10, LQ_LAYOUT_EO, true>(g, m_q, U, psi, out, st, lnr)             \
+                       : run_apply<PREC, 10, LQ_LAYOUT_EO, false>(g, m_q, U, psi, out, st, lnr);           \
+        }                                                                                             \
         if (fmt == 18) {                                                                              \
             if (lex) return dag ? run_apply<PREC, 18, LQ_LAYOUT_LEX, true>(g, m_q, U, psi, out, st, lnr)   \
                                 : run_apply<PREC, 18, LQ_LAYOUT_LEX, false>(g, m_q, U, psi, out, st, lnr); \
@@ -117,6 +123,12 @@ cudaError_t hop_i32(const Geom& g, int p, bool dag, double a, double b, int fmt,
     cudaError_t hop_##NAME(const Geom& g, int p, bool dag, double a, double b, int fmt, const void* U, \
                            const void* psi_other, const void* y, void* out, cudaStream_t st) {        \
         const bool hy = y != nullptr;                                                                 \
+        if (fmt == 10) {                                                                              \
+            if (dag) return hy ? run_hop<PREC, 10, true, true>(g, p, a, b, U, psi_other, y, out, st)  \
+                               : run_hop<PREC, 10, true, false>(g, p, a, b, U, psi_other, y, out, st); \
+            return hy ? run_hop<PREC, 10, false, true>(g, p, a, b, U, psi_other, y, out, st)          \
+                      : run_hop<PREC, 10, false, false>(g, p, a, b, U, psi_other, y, out, st);        \
+        }                                                                                             \
         if (fmt == 18) {                                                                              \
             if (dag) return hy ? run_hop<PREC, 18, true, true>(g, p, a, b, U, psi_other, y, out, st)  \
                                : run_hop<PREC, 18, true, false>(g, p, a, b, U, psi_other, y, out, st); \

@@ -590,6 +590,120 @@ template <int LAYOUT> struct GaugeAcc<LQ_I32S, 12, LAYOUT> {
     }
 };
 
+// ------------------------------------------------------------------------------------
+// 10-real links: row 0 and the two entries of row 1 outside column k, one complex number
+// per chunk (K = 5 in every precision).  k is the column of row 0 whose larger component
+// max(|Re|, |Im|) is the largest (the lowest on ties), found from the stored values in
+// their own exact domain, so that every decoder makes the encoder's choice.  Row 1's entry
+// k follows from the orthogonality of rows 0 and 1 of a unitary matrix,
+//   u1k = -(sum_{j != k} u1j conj(u0j)) / conj(u0k),   |u0k| >= 1/sqrt(6),
+// and row 2 = conj(row0 x row1) as for LINK12.
+// ------------------------------------------------------------------------------------
+template <typename M> LQ_HD int link10_column(M m0, M m1, M m2) {
+    int k = 0;
+    M mk = m0;
+    if (m1 > mk) {
+        k = 1;
+        mk = m1;
+    }
+    if (m2 > mk) k = 2;
+    return k;
+}
+
+// U.u[0] holds row 0; b0, b1 are row 1's stored entries (columns other than k, in order)
+template <typename R> LQ_HD void reconstruct10(Link<R>& U, cplx<R> b0, cplx<R> b1, int k) {
+    const cplx<R> a0 = U.u[0][0], a1 = U.u[0][1], a2 = U.u[0][2];
+    const cplx<R> ak = k == 0 ? a0 : (k == 1 ? a1 : a2);
+    const cplx<R> aj1 = k == 0 ? a1 : a0;
+    const cplx<R> aj2 = k == 2 ? a1 : a2;
+    // x = -(b0 conj(aj1) + b1 conj(aj2)) / conj(ak) = -(...) ak / |ak|^2
+    const cplx<R> S = cfma(b1, cconj(aj2), cmul(b0, cconj(aj1)));
+    const R inv = R(1) / fma(ak.re, ak.re, ak.im * ak.im);
+    const cplx<R> x = cscale(-inv, cmul(S, ak));
+    U.u[1][0] = k == 0 ? x : b0;
+    U.u[1][1] = k == 0 ? b0 : (k == 1 ? x : b1);
+    U.u[1][2] = k == 2 ? x : b1;
+    reconstruct_row2(U);
+}
+
+template <typename T> LQ_HD T abs_max(T a, T b) {
+    const T x = a < T(0) ? -a : a, y = b < T(0) ? -b : b;
+    return x > y ? x : y;
+}
+
+template <int LAYOUT> struct GaugeAcc<LQ_F64, 10, LAYOUT> {
+    using Real = double;
+    static constexpr int K = 5;
+    const double2* ptr;
+    uint32_t Vh;
+    LQ_HD void load(const Site& s, int mu, Link<double>& U) const {
+        const uint32_t b = lk_base<LAYOUT>(s, mu, K, Vh), ks = lk_kstride<LAYOUT>(Vh);
+        double2 w[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) w[k] = ld<true>(ptr + b + k * ks);
+        const int c = link10_column(abs_max(w[0].x, w[0].y), abs_max(w[1].x, w[1].y), abs_max(w[2].x, w[2].y));
+#pragma unroll
+        for (int j = 0; j < 3; ++j) U.u[0][j] = {w[j].x, w[j].y};
+        reconstruct10(U, cplx<double>{w[3].x, w[3].y}, cplx<double>{w[4].x, w[4].y}, c);
+    }
+};
+
+template <int LAYOUT> struct GaugeAcc<LQ_F32, 10, LAYOUT> {
+    using Real = float;
+    static constexpr int K = 5;
+    const float2* ptr;
+    uint32_t Vh;
+    LQ_HD void load(const Site& s, int mu, Link<float>& U) const {
+        const uint32_t b = lk_base<LAYOUT>(s, mu, K, Vh), ks = lk_kstride<LAYOUT>(Vh);
+        float2 w[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) w[k] = ld<true>(ptr + b + k * ks);
+        const int c = link10_column(abs_max(w[0].x, w[0].y), abs_max(w[1].x, w[1].y), abs_max(w[2].x, w[2].y));
+#pragma unroll
+        for (int j = 0; j < 3; ++j) U.u[0][j] = {w[j].x, w[j].y};
+        reconstruct10(U, cplx<float>{w[3].x, w[3].y}, cplx<float>{w[4].x, w[4].y}, c);
+    }
+};
+
+// FP16: one half2 word per complex entry; the halves widen to FP32 exactly, so the column
+// choice compares the stored values
+template <int LAYOUT> struct GaugeAcc<LQ_F16S, 10, LAYOUT> {
+    using Real = float;
+    static constexpr int K = 5;
+    const uint32_t* ptr;
+    uint32_t Vh;
+    LQ_HD void load(const Site& s, int mu, Link<float>& U) const {
+        const uint32_t b = lk_base<LAYOUT>(s, mu, K, Vh), ks = lk_kstride<LAYOUT>(Vh);
+        float2 w[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) w[k] = h2f2(ld<true>(ptr + b + k * ks));
+        const int c = link10_column(abs_max(w[0].x, w[0].y), abs_max(w[1].x, w[1].y), abs_max(w[2].x, w[2].y));
+#pragma unroll
+        for (int j = 0; j < 3; ++j) U.u[0][j] = {w[j].x, w[j].y};
+        reconstruct10(U, cplx<float>{w[3].x, w[3].y}, cplx<float>{w[4].x, w[4].y}, c);
+    }
+};
+
+// Q1.30: the column choice compares the stored integers (their FP32 images may round
+// together)
+template <int LAYOUT> struct GaugeAcc<LQ_I32S, 10, LAYOUT> {
+    using Real = float;
+    static constexpr int K = 5;
+    const int2* ptr;
+    uint32_t Vh;
+    LQ_HD void load(const Site& s, int mu, Link<float>& U) const {
+        const uint32_t b = lk_base<LAYOUT>(s, mu, K, Vh), ks = lk_kstride<LAYOUT>(Vh);
+        int2 w[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) w[k] = ld<true>(ptr + b + k * ks);
+        const int c = link10_column(abs_max(w[0].x, w[0].y), abs_max(w[1].x, w[1].y), abs_max(w[2].x, w[2].y));
+#pragma unroll
+        for (int j = 0; j < 3; ++j) U.u[0][j] = {(float)w[j].x * kInvQ30, (float)w[j].y * kInvQ30};
+        reconstruct10(U, cplx<float>{(float)w[3].x * kInvQ30, (float)w[3].y * kInvQ30},
+                      cplx<float>{(float)w[4].x * kInvQ30, (float)w[4].y * kInvQ30}, c);
+    }
+};
+
 // FP32 pairs: one float4 chunk = one complex entry; 9 (LINK18) or 6 (LINK12) per link
 template <int FMT, int LAYOUT> struct GaugeAcc<LQ_F64X, FMT, LAYOUT> {
     using Real = dd;

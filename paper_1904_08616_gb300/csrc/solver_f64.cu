@@ -27,7 +27,11 @@ int cg_solve(const Geom& g, double m_q, int mode, int nrhs, const void* U, const
     if (mode == LQ_CG_F64X && native) return fail(LQ_ERR_ARG, "LQ_CG_NATIVE_F64 does not apply to LQ_CG_F64X");
     const bool mixed = mode == LQ_CG_MIXED_F32 || mode == LQ_CG_MIXED_F16 || mode == LQ_CG_MIXED_I32;
     const bool pairs = (mode == LQ_CG_F64X) || (mixed && !native);
-    const int fmt = (prm.flags & LQ_CG_LINK18) ? 18 : 12;
+    if ((prm.flags & LQ_CG_LINK10) && (prm.flags & LQ_CG_LINK18))
+        return fail(LQ_ERR_ARG, "LQ_CG_LINK10 and LQ_CG_LINK18 exclude each other");
+    if ((prm.flags & LQ_CG_LINK10) && mixed && !pairs)
+        return fail(LQ_ERR_ARG, "LQ_CG_LINK10 runs with the FP32-pair outer loop (not with LQ_CG_NATIVE_F64)");
+    const int fmt = (prm.flags & LQ_CG_LINK18) ? 18 : ((prm.flags & LQ_CG_LINK10) ? 10 : 12);
     {
         const WsLayout w = ws_layout(g, mode, pairs, fmt, batch_size(nrhs));
         if (ws == nullptr || ws_bytes < w.total)

@@ -40,6 +40,7 @@ int cg_solve_schur(const Geom& g, double m_q, int mode, int nrhs, const void* U,
     using namespace solver_detail;
     if (mode == LQ_CG_F64) return fail(LQ_ERR_ARG, "the Schur solve runs its outer loop in FP32 pairs: use LQ_CG_F64X");
     if (prm.flags & LQ_CG_NATIVE_F64) return fail(LQ_ERR_ARG, "LQ_CG_NATIVE_F64 does not apply to the Schur solve");
+    if (prm.flags & LQ_CG_LINK10) return fail(LQ_ERR_ARG, "LQ_CG_LINK10 does not apply to the Schur solve");
     const int fmt = (mode == LQ_CG_F64X || (prm.flags & LQ_CG_LINK18)) ? 18 : 12;
     {
         const WsLayout w = ws_layout_schur(g, mode, fmt, batch_size(nrhs));

@@ -40,10 +40,10 @@ def test_field_bytes_match_format_definitions(lqlib):
         for prec in ("f64", "f32", "f16s"):
             for layout in ("lex", "eo"):
                 assert lqlib.field_bytes(dims, "spinor", prec, 18, layout) == F.spinor_bytes(dims, prec)
-                for fmt in (18, 12):
+                for fmt in (18, 12, 10):
                     assert lqlib.field_bytes(dims, "gauge", prec, fmt, layout) == F.gauge_bytes(dims, prec, fmt)
     assert lqlib.field_bytes((3, 4, 4, 4), "spinor") == 0
-    assert lqlib.field_bytes((4, 4, 4, 4), "gauge", "f32", 10) == 0
+    assert lqlib.field_bytes((4, 4, 4, 4), "gauge", "f32", 11) == 0
 
 
 def test_workspace_query(lqlib):
@@ -73,7 +73,7 @@ def test_apply_argument_checks(lqlib):
     assert _apply(L, (4096, 4096, 4096, 2)) == -2          # volume beyond 10^8 sites
     assert _apply(L, (100, 100, 100, 102)) == -2
     assert _apply(L, (4, 4, 4, 4), prec=5) == -1
-    assert _apply(L, (4, 4, 4, 4), fmt=10) == -1
+    assert _apply(L, (4, 4, 4, 4), fmt=11) == -1
     assert _apply(L, (4, 4, 4, 4), layout=2) == -1
     assert _apply(L, (4, 4, 4, 4), U=0) == -1
     assert _apply(L, (4, 4, 4, 4), psi=P1 + 8) == -3          # misaligned
@@ -81,6 +81,7 @@ def test_apply_argument_checks(lqlib):
     assert _apply(L, (4, 4, 4, 4), out=P1 + 4096) == -3       # partial overlap
     assert _apply(L, (4, 4, 4, 4), m=float("nan")) == -1
     assert _apply(L, (4, 4, 4, 4), prec=3, fmt=12) == -1       # FP32-pair fields are 18-real
+    assert _apply(L, (4, 4, 4, 4), prec=3, fmt=10) == -1
     assert L.lq_dslash_adjoint((ctypes.c_int32 * 4)(4, 4, 4, 3), 0.1, 0, 18, 0, None, None, None, None) == -2
 
 
