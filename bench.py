@@ -539,8 +539,9 @@ def run_workload(args):
         spinor_b = {"f64": 192, "f64x": 192, "f32": 96, "f16s": 52, "i32s": 100}
         link_b = {"f64": 8, "f64x": 8, "f32": 4, "f16s": 2, "i32s": 4}
         rows = {}
-        for prec, fmt, layout in (("f64", 18, "lex"), ("f64", 18, "eo"), ("f64x", 18, "eo"), ("f32", 18, "eo"),
-                                  ("f32", 12, "eo"), ("f16s", 12, "eo"), ("f16s", 18, "eo"), ("i32s", 12, "eo")):
+        for prec, fmt, layout in (("f64", 18, "lex"), ("f64", 18, "eo"), ("f64", 10, "eo"), ("f64x", 18, "eo"),
+                                  ("f32", 18, "eo"), ("f32", 12, "eo"), ("f32", 10, "eo"), ("f16s", 12, "eo"),
+                                  ("f16s", 18, "eo"), ("f16s", 10, "eo"), ("i32s", 12, "eo"), ("i32s", 10, "eo")):
             Ub = lq.convert_gauge(DIMS, U_d, "f64", "lex", dst_prec=prec, dst_fmt=fmt, dst_layout=layout)
             pb = lq.convert_spinor(DIMS, p_d, "f64", "lex", dst_prec=prec, dst_layout=layout)
             out = torch.empty_like(pb)
