@@ -428,6 +428,9 @@ struct EpiAxpby {
     }
 };
 
+template <class E, class = void> struct HasPrefetch : std::false_type {};
+template <class E> struct HasPrefetch<E, std::void_t<decltype(&E::prefetch)>> : std::true_type {};
+
 // Optional minimum resident blocks per SM requested from the compiler (its register
 // budget) for the FP32-arithmetic and the FP32-pair stencils; 0 leaves the choice to ptxas.
 #ifndef LQ_STENCIL_MINB_F32
@@ -453,6 +456,9 @@ __device__ __forceinline__ void stencil_body(const Map& map, const Sten& sten, E
         Site s;
         int c[4];
         if (!map.site(tile, s, c)) continue;
+        // an epilogue may ask for its site-local inputs ahead of the stencil (their loads
+        // then hit L1 instead of waiting on DRAM after the eight hops)
+        if constexpr (HasPrefetch<Epi>::value) epi.prefetch(s);
         Spinor<typename Sten::Real> acc;
         sten.apply(s, c, acc);
         epi.apply(s, acc, red);

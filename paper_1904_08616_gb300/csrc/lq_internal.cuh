@@ -176,6 +176,16 @@ template <bool RO, typename T> LQ_HD T ld(const T* p) {
 #endif
 }
 
+// Brings the cache line holding p into L1 ahead of its load (no register is written, so a
+// warp can ask for data it will use later without stalling on it now).
+LQ_HD void prefetch_l1(const void* p) {
+#ifdef __CUDA_ARCH__
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+#else
+    (void)p;
+#endif
+}
+
 // x / y in FP32, correctly rounded
 LQ_HD float div_rn(float x, float y) {
 #ifdef __CUDA_ARCH__
@@ -233,6 +243,11 @@ template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F64, LAYOUT, RO> {
     static constexpr bool kScaled = false;
     double2* ptr;
     EoIdx e;
+    LQ_HD void prefetch(const Site& s) const {
+        const uint32_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
+#pragma unroll
+        for (int k = 0; k < K; ++k) prefetch_l1(ptr + b + k * ks);
+    }
     template <typename T> LQ_HD void load(const Site& s, Spinor<T>& out) const {
         const uint32_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
 #pragma unroll
@@ -258,6 +273,11 @@ template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F32, LAYOUT, RO> {
     static constexpr bool kScaled = false;
     float4* ptr;
     EoIdx e;
+    LQ_HD void prefetch(const Site& s) const {
+        const uint32_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
+#pragma unroll
+        for (int k = 0; k < K; ++k) prefetch_l1(ptr + b + k * ks);
+    }
     template <typename T> LQ_HD void load(const Site& s, Spinor<T>& out) const {
         const uint32_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
 #pragma unroll
@@ -290,6 +310,12 @@ template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F16S, LAYOUT, RO> {
     uint4* ptr;
     float* scale;
     EoIdx e;
+    LQ_HD void prefetch(const Site& s) const {
+        const uint32_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
+#pragma unroll
+        for (int k = 0; k < K; ++k) prefetch_l1(ptr + b + k * ks);
+        prefetch_l1(scale + sp_sidx<LAYOUT>(s, e));
+    }
     // the stored halves as floats, without the site's scale (returned separately)
     LQ_HD void load_raw(const Site& s, Spinor<float>& out, float& sc) const {
         const uint32_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
@@ -376,6 +402,12 @@ template <int LAYOUT, bool RO> struct SpinorAcc<LQ_I32S, LAYOUT, RO> {
     int4* ptr;
     float* scale;
     EoIdx e;
+    LQ_HD void prefetch(const Site& s) const {
+        const uint32_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
+#pragma unroll
+        for (int k = 0; k < K; ++k) prefetch_l1(ptr + b + k * ks);
+        prefetch_l1(scale + sp_sidx<LAYOUT>(s, e));
+    }
     // the stored integers as floats, and s * 2^-30 separately
     LQ_HD void load_raw(const Site& s, Spinor<float>& out, float& sc) const {
         const uint32_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
@@ -422,6 +454,11 @@ template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F64X, LAYOUT, RO> {
     static constexpr bool kScaled = false;
     float4* ptr;
     EoIdx e;
+    LQ_HD void prefetch(const Site& s) const {
+        const uint32_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
+#pragma unroll
+        for (int k = 0; k < K; ++k) prefetch_l1(ptr + b + k * ks);
+    }
     template <typename T> LQ_HD void load(const Site& s, Spinor<T>& out) const {
         const uint32_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
 #pragma unroll

