@@ -511,8 +511,8 @@ def run_workload(args):
         eta_d = spinors(dims, [500 + r for r in range(nr)])
         sb = lq.field_bytes(dims, "spinor", "f64")
 
-        def multi():
-            _, infos, st = lq.cg_solve_multi(dims, 0.1, nr, U_d, eta_d, mode=args.mode, tol=TOL)
+        def multi(rb=None):
+            _, infos, st = lq.cg_solve_multi(dims, 0.1, nr, U_d, eta_d, mode=args.mode, tol=TOL, rhs_block=rb)
             assert st == 0
             return infos
 
@@ -525,10 +525,13 @@ def run_workload(args):
             return out
 
         ms, infos = _timed(multi, args.steps, args.warmup)
+        by_rb = {rb: _timed(lambda rb=rb: multi(rb), args.steps, args.warmup)[0] for rb in (1, 2, 4)}
         ms_single, _ = _timed(single, args.steps, args.warmup)
         line.update({"config": {"lattice": list(dims), "nrhs": nr, "m_q": 0.1, "links": "haar", "tol": TOL},
                      "value": _updates(dims, infos) / (ms * 1e-3), "ms_per_solve": ms,
-                     "ms_one_by_one": ms_single, "iters": max(i["iters"] for i in infos)})
+                     "ms_per_solve_by_rhs_per_thread": by_rb,
+                     "ms_one_by_one": ms_single, "speedup_vs_one_by_one": ms_single / ms,
+                     "iters": max(i["iters"] for i in infos)})
     elif args.workload == "dslash":
         # the operator alone on the 32^4 fields, every stored format: site-updates/s, GB/s
         # against the measured copy peak and the 8 TB/s nominal, GFLOP/s at 1464 flops/site

@@ -230,6 +230,14 @@ typedef struct lq_cg_params {
                                 running the inner loop in a CUDA graph with a conditional
                                 WHILE node (the default; if the driver refuses such a graph
                                 the host-driven loop runs without this flag too)           */
+#define LQ_CG_RHS_BLOCK_1 0x1000 /* lq_cg_solve_multi: right-hand sides per thread in the inner
+                                    stencil kernels (register blocking: each link is decoded once
+                                    and applied to that many right-hand sides of a site); at most
+                                    one flag, capped at the batch size; default 2 with
+                                    scaled-FP16 inner fields, else 1 (mixed modes with 12-real
+                                    inner links; the others always use 1)                     */
+#define LQ_CG_RHS_BLOCK_2 0x2000
+#define LQ_CG_RHS_BLOCK_4 0x4000
 #define LQ_CG_BLOCK_64 0x100 /* lq_cg_solve_lattices: inner block size 64 / 128 / 256 threads */
 #define LQ_CG_BLOCK_128 0x200 /*   (at most one; overrides LQ_CG_AUTOTUNE)                  */
 #define LQ_CG_BLOCK_256 0x400

@@ -30,6 +30,7 @@ PREC = {"f64": 0, "f32": 1, "f16s": 2, "f64x": 3, "i32s": 4}
 LAYOUT = {"lex": 0, "eo": 1}
 CG_MODE = {"f64": 0, "mixed_f32": 1, "mixed_f16": 2, "f64x": 3, "mixed_i32": 4}
 CG_PROFILE, CG_NATIVE_F64, CG_LINK18, CG_AUTOTUNE, CG_NO_GRAPH, CG_LINK10 = 1, 2, 4, 8, 16, 32
+CG_RHS_BLOCK_1, CG_RHS_BLOCK_2, CG_RHS_BLOCK_4 = 0x1000, 0x2000, 0x4000
 STATUS = {0: "OK", 1: "NOT_CONVERGED", -1: "ERR_ARG", -2: "ERR_DIMS", -3: "ERR_ALIGN",
           -4: "ERR_CUDA", -5: "ERR_WORKSPACE", -6: "ERR_NONFINITE", -7: "ERR_BREAKDOWN"}
 
@@ -338,9 +339,11 @@ def cg_solve(dims, m_q, U, eta, x=None, mode="f64", tol=1e-10, max_iter=100000, 
 
 def cg_solve_multi(dims, m_q, nrhs, U, eta, x=None, mode="f64", tol=1e-10, max_iter=100000, max_cycles=0,
                    delta=0.0, chunk=0, max_inner=0, workspace=None, stream=None, profile=False, native_f64=False, link18=False, link10=False,
-                   graph=True):
+                   graph=True, rhs_block=None):
     """nrhs independent solves D^dag D x_r = eta_r sharing the links (eta, x: nrhs stacked FP64
-    LEX fields).  Returns (x, [info per right-hand side], status)."""
+    LEX fields).  rhs_block (1, 2 or 4; None: the library's default) sets how many right-hand
+    sides one thread of the inner stencil kernels serves.  Returns (x, [info per right-hand
+    side], status)."""
     import torch
     m = CG_MODE[mode] if isinstance(mode, str) else int(mode)
     n = int(nrhs)
@@ -353,6 +356,8 @@ def cg_solve_multi(dims, m_q, nrhs, U, eta, x=None, mode="f64", tol=1e-10, max_i
         workspace = _empty_bytes(wb, eta)
     flags = (CG_PROFILE if profile else 0) | (CG_NATIVE_F64 if native_f64 else 0) | (CG_LINK18 if link18 else 0) \
         | (CG_LINK10 if link10 else 0) | (0 if graph else CG_NO_GRAPH)
+    if rhs_block is not None:
+        flags |= {1: CG_RHS_BLOCK_1, 2: CG_RHS_BLOCK_2, 4: CG_RHS_BLOCK_4}[int(rhs_block)]
     prm = CgParams(float(tol), int(max_iter), int(max_cycles), float(delta), int(chunk), flags, int(max_inner))
     infos = (CgInfo * n)()
     st = load().lq_cg_solve_multi(_dims(dims), float(m_q), m, n, _ptr(U, gb, "U"), _ptr(eta, sb, "eta"),

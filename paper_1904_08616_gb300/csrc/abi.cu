@@ -348,6 +348,10 @@ int lq_cg_solve_multi(const int32_t dims[4], double m_q, int32_t mode, int32_t n
     if (prm.max_cycles < 0 || prm.chunk < 0 || prm.max_inner < 0)
         return fail(LQ_ERR_ARG, "max_cycles, chunk and max_inner must be >= 0");
     if (!(prm.delta < 1.0) || !isfinite(prm.delta)) return fail(LQ_ERR_ARG, "delta must be < 1");
+    {
+        const int rsel = prm.flags & (LQ_CG_RHS_BLOCK_1 | LQ_CG_RHS_BLOCK_2 | LQ_CG_RHS_BLOCK_4);
+        if (rsel & (rsel - 1)) return fail(LQ_ERR_ARG, "at most one LQ_CG_RHS_BLOCK_* flag");
+    }
     if ((r = check_ptr(U, "U")) || (r = check_ptr(eta, "eta")) || (r = check_ptr(x, "x"))) return r;
     if ((r = check_ptr(workspace, "workspace"))) return r == LQ_ERR_ARG ? fail(LQ_ERR_WORKSPACE, "workspace is NULL") : r;
     const size_t sb = spinor_bytes((int64_t)g.V * nrhs, LQ_F64), gb = gauge_bytes(g.V, LQ_F64, 18);

@@ -318,6 +318,67 @@ struct Stencil {
             dir<3>(s, c, acc);
         }
     }
+
+    // Register blocking over right-hand sides: the hopping sums of RB consecutive right-hand
+    // sides s.rhs .. s.rhs + RB - 1 of one site.  Each link is loaded, decoded and rebuilt
+    // once per direction and applied to all RB neighbour spinors (unrolled stencils only).
+    template <int MU, int RB>
+    LQ_HD void dir_rb(const Site& s, const int c[4], Spinor<Real> (&acc)[RB]) const {
+        constexpr int SF = DAG ? +1 : -1;
+        const Site nf = nb_site(lex_fwd(g, s.lex, c, MU), s.p, s.rhs);
+        const Site nb = nb_site(lex_bwd(g, s.lex, c, MU), s.p, s.rhs);
+        constexpr bool SC = SA::kScaled;
+        Link<Real> U;
+        ga.load(s, MU, U);
+#pragma unroll
+        for (int i = 0; i < RB; ++i) {
+            const Site q = Site{nf.lex, nf.p, nf.cb, nf.rhs + i};
+#ifdef __CUDA_ARCH__
+            if constexpr (kHalf) {
+                uint32_t w[12];
+                float sc;
+                sa.load_h2(q, w, sc);
+                h2::hop<MU, SF, false>(acc[i], w, U, sc);
+                continue;
+            }
+#endif
+            Spinor<Real> v;
+            Real sc;
+            sa.load_raw(q, v, sc);
+            hop_dir<MU, SF, false, SC>(acc[i], v, U, sc);
+        }
+        ga.load(nb, MU, U);
+#pragma unroll
+        for (int i = 0; i < RB; ++i) {
+            const Site q = Site{nb.lex, nb.p, nb.cb, nb.rhs + i};
+#ifdef __CUDA_ARCH__
+            if constexpr (kHalf) {
+                uint32_t w[12];
+                float sc;
+                sa.load_h2(q, w, sc);
+                h2::hop<MU, -SF, true>(acc[i], w, U, sc);
+                continue;
+            }
+#endif
+            Spinor<Real> v;
+            Real sc;
+            sa.load_raw(q, v, sc);
+            hop_dir<MU, -SF, true, SC>(acc[i], v, U, sc);
+        }
+    }
+
+    template <int RB>
+    LQ_HD void apply_rb(const Site& s, const int c[4], Spinor<Real> (&acc)[RB]) const {
+        static_assert(!kRolled, "register blocking is for the unrolled stencils");
+#pragma unroll
+        for (int i = 0; i < RB; ++i)
+#pragma unroll
+            for (int k = 0; k < 12; ++k) acc[i].v[k] = {Real(0), Real(0)};
+        dir_rb<0, RB>(s, c, acc);
+        dir_rb<1, RB>(s, c, acc);
+        dir_rb<2, RB>(s, c, acc);
+        dir_rb<3, RB>(s, c, acc);
+    }
 };
 
 // ------------------------------------------------------------------------------------
@@ -325,7 +386,9 @@ struct Stencil {
 // ------------------------------------------------------------------------------------
 // With nr right-hand sides a map covers (site, rhs) pairs, rhs fastest: the nr threads of
 // one site are adjacent, so their link loads coincide.  nr is a power of two (lnr = log2)
-// dividing BS, so a thread keeps the same rhs = threadIdx.x mod nr in every tile.
+// dividing BS, so a thread keeps the same rhs = threadIdx.x mod nr in every tile.  With
+// register blocking (MapEoFull, lrb = log2 RB > 0) a thread takes RB consecutive right-hand
+// sides of its site, the first being RB (threadIdx.x mod nr / RB).
 template <int BS> struct MapLex {            // all V sites, lexicographic
     Geom g;
     int lnr = 0;
@@ -341,11 +404,14 @@ template <int BS> struct MapLex {            // all V sites, lexicographic
 template <int BS> struct MapEoFull {         // all V sites; tiles alternate parity over the same cb range
     Geom g;
     int lnr = 0;
-    __host__ __device__ int ntiles() const { return 2 * (int)((((int64_t)g.Vh << lnr) + BS - 1) / BS); }
+    int lrb = 0;
+    __host__ __device__ int ntiles() const {
+        return 2 * (int)((((int64_t)g.Vh << (lnr - lrb)) + BS - 1) / BS);
+    }
     __device__ __forceinline__ bool site(int tile, Site& s, int c[4]) const {
-        const int f = (tile >> 1) * BS + (int)threadIdx.x;
-        if (f >= (g.Vh << lnr)) return false;
-        s = site_from_eo(g, tile & 1, f >> lnr, c, f & ((1 << lnr) - 1));
+        const int f = (tile >> 1) * BS + (int)threadIdx.x, lg = lnr - lrb;
+        if (f >= (g.Vh << lg)) return false;
+        s = site_from_eo(g, tile & 1, f >> lg, c, (f & ((1 << lg) - 1)) << lrb);
         return true;
     }
 };
@@ -428,6 +494,10 @@ struct EpiAxpby {
     }
 };
 
+// right-hand sides per thread of an epilogue (1 unless it declares kRB)
+template <class E, class = void> struct RhsBlock { static constexpr int value = 1; };
+template <class E> struct RhsBlock<E, std::void_t<decltype(E::kRB)>> { static constexpr int value = E::kRB; };
+
 template <class E, class = void> struct HasPrefetch : std::false_type {};
 template <class E> struct HasPrefetch<E, std::void_t<decltype(&E::prefetch)>> : std::true_type {};
 
@@ -459,9 +529,16 @@ __device__ __forceinline__ void stencil_body(const Map& map, const Sten& sten, E
         // an epilogue may ask for its site-local inputs ahead of the stencil (their loads
         // then hit L1 instead of waiting on DRAM after the eight hops)
         if constexpr (HasPrefetch<Epi>::value) epi.prefetch(s);
-        Spinor<typename Sten::Real> acc;
-        sten.apply(s, c, acc);
-        epi.apply(s, acc, red);
+        constexpr int RB = RhsBlock<Epi>::value;
+        if constexpr (RB > 1) {
+            Spinor<typename Sten::Real> acc[RB];
+            sten.template apply_rb<RB>(s, c, acc);
+            epi.apply_rb(s, acc, red);
+        } else {
+            Spinor<typename Sten::Real> acc;
+            sten.apply(s, c, acc);
+            epi.apply(s, acc, red);
+        }
     }
     epi.template finish<BS>(red, vg);
 }

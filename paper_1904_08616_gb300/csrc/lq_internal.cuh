@@ -783,7 +783,7 @@ struct SolverState {
 };
 
 constexpr int kMaxPartials = 4096;     // blocks per reducing kernel
-constexpr int kMaxRedValues = 3;       // values reduced per thread
+constexpr int kMaxRedValues = 4;       // values reduced per thread
 constexpr int kTicketK1 = 0, kTicketK2 = 1, kTicketK3 = 2, kTicketMisc = 3;
 
 // The blocks a kernel body sees as its grid: the hardware grid, or one lattice's share of

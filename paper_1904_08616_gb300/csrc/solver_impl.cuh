@@ -116,23 +116,44 @@ template <typename T> struct PerRhs { T v[kMaxRhs]; };
 // ------------------------------------------------------------------------------------
 // inner-loop kernels
 // ------------------------------------------------------------------------------------
-// K1: t = a p + b hop(p), ||t||^2 -> alpha
-template <class TA, class PA>
+// The right-hand sides a thread serves: RB consecutive ones starting at this value (the
+// maps give every thread a fixed group).
+LQ_HD int thread_rhs0(int nr, int rb) {
+#ifdef __CUDA_ARCH__
+    return ((int)threadIdx.x & (nr / rb - 1)) * rb;
+#else
+    (void)nr;
+    (void)rb;
+    return 0;
+#endif
+}
+
+// K1: t = a p + b hop(p), ||t||^2 -> alpha.  RB right-hand sides per thread (register
+// blocking: the stencil has applied each link to all of them).
+template <class TA, class PA, int RB = 1>
 struct EpiK1 {
     using Real = typename TA::Real;
-    static constexpr int NRED = 1;
+    static constexpr int kRB = RB;
+    static constexpr int NRED = RB;
     TA t;
     PA p;
     Real a, b;
     RedCtx rc;
     int nr;
-    bool on;
+    bool on[RB];
     LQ_HD bool init() {
         if (rc.st->all_stop) return false;
-        on = rc.st->stop[thread_rhs(nr)] == 0;
+        const int j0 = thread_rhs0(nr, RB);
+#pragma unroll
+        for (int i = 0; i < RB; ++i) on[i] = rc.st->stop[j0 + i] == 0;
         return true;
     }
-    LQ_HD bool active() const { return on; }
+    LQ_HD bool active() const {
+        bool any = false;
+#pragma unroll
+        for (int i = 0; i < RB; ++i) any |= on[i];
+        return any;
+    }
     template <typename R>
     LQ_HD void apply(const Site& s, const Spinor<R>& acc, double* red) const {
         Spinor<R> pv, o;
@@ -143,13 +164,28 @@ struct EpiK1 {
         t.store(s, o);
         red[0] += to_double(norm2(o));
     }
-    template <int BS> __device__ __forceinline__ void finish(const double (&red)[1], const VGrid& vg) const {
+    template <typename R>
+    LQ_HD void apply_rb(const Site& s, const Spinor<R> (&acc)[RB], double* red) const {
+#pragma unroll
+        for (int i = 0; i < RB; ++i) {
+            if (!on[i]) continue;
+            const Site si{s.lex, s.p, s.cb, s.rhs + i};
+            Spinor<R> pv, o;
+            p.load(si, pv);
+#pragma unroll
+            for (int k = 0; k < 12; ++k)
+                o.v[k] = {fma((R)b, acc[i].v[k].re, (R)a * pv.v[k].re), fma((R)b, acc[i].v[k].im, (R)a * pv.v[k].im)};
+            t.store(si, o);
+            red[i] += to_double(norm2(o));
+        }
+    }
+    template <int BS> __device__ __forceinline__ void finish(const double (&red)[RB], const VGrid& vg) const {
         SolverState* st = rc.st;
         const int n = nr;
-        grid_reduce_seg<BS, 1>(rc, kTicketK1, red, n, vg, [st, n](const double* tot) {
+        grid_reduce_seg<BS, RB>(rc, kTicketK1, red, n / RB, vg, [st, n](const double* tot) {
             for (int j = 0; j < n; ++j) {
                 if (st->stop[j]) continue;
-                const double sg = tot[j];
+                const double sg = tot[(j % RB) * kMaxRhs + j / RB];
                 st->sigma[j] = sg;
                 if (!isfinite(sg)) {
                     st->stop[j] = 3;
@@ -166,10 +202,11 @@ struct EpiK1 {
 };
 
 // K2: q = a t + b hop^dag(t); psi += alpha p; r -= alpha q; ||r||^2 -> beta, stop test
-template <class TA, class PA, class XA, class RA>
+template <class TA, class PA, class XA, class RA, int RB = 1>
 struct EpiK2 {
     using Real = typename RA::Real;
-    static constexpr int NRED = 1;
+    static constexpr int kRB = RB;
+    static constexpr int NRED = RB;
     TA t;
     PA p;
     XA x;
@@ -177,28 +214,38 @@ struct EpiK2 {
     Real a, b;
     RedCtx rc;
     int nr;
-    Real alpha;
-    bool on;
+    Real alpha[RB];
+    bool on[RB];
     LQ_HD bool init() {
         if (rc.st->all_stop) return false;
-        const int j = thread_rhs(nr);
-        on = rc.st->stop[j] == 0;
-        alpha = from_double<Real>(rc.st->alpha[j]);
+        const int j0 = thread_rhs0(nr, RB);
+#pragma unroll
+        for (int i = 0; i < RB; ++i) {
+            on[i] = rc.st->stop[j0 + i] == 0;
+            alpha[i] = from_double<Real>(rc.st->alpha[j0 + i]);
+        }
         return true;
     }
-    LQ_HD bool active() const { return on; }
+    LQ_HD bool active() const {
+        bool any = false;
+#pragma unroll
+        for (int i = 0; i < RB; ++i) any |= on[i];
+        return any;
+    }
     // psi is read once per site and never by a neighbour: asked for before the stencil, its
     // load after the eight hops hits L1 (K2 6% faster on the 32^4 workload; prefetching the
     // other fields as well gained nothing more)
-    LQ_HD void prefetch(const Site& s) const { x.prefetch(s); }
+    LQ_HD void prefetch(const Site& s) const {
+#pragma unroll
+        for (int i = 0; i < RB; ++i) x.prefetch(Site{s.lex, s.p, s.cb, s.rhs + i});
+    }
     template <typename R>
-    LQ_HD void apply(const Site& s, const Spinor<R>& acc, double* red) const {
+    LQ_HD void update(const Site& s, const Spinor<R>& acc, R al, double& red) const {
         Spinor<R> tv, pv, xv, rv;
         t.load(s, tv);
         p.load(s, pv);
         x.load(s, xv);
         r.load(s, rv);
-        const R al = (R)alpha;
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
             const R qre = fma((R)b, acc.v[k].re, (R)a * tv.v[k].re);
@@ -208,16 +255,26 @@ struct EpiK2 {
         }
         x.store(s, xv);
         r.store(s, rv);
-        red[0] += to_double(norm2(rv));
+        red += to_double(norm2(rv));
     }
-    template <int BS> __device__ __forceinline__ void finish(const double (&red)[1], const VGrid& vg) const {
+    template <typename R>
+    LQ_HD void apply(const Site& s, const Spinor<R>& acc, double* red) const {
+        update(s, acc, (R)alpha[0], red[0]);
+    }
+    template <typename R>
+    LQ_HD void apply_rb(const Site& s, const Spinor<R> (&acc)[RB], double* red) const {
+#pragma unroll
+        for (int i = 0; i < RB; ++i)
+            if (on[i]) update(Site{s.lex, s.p, s.cb, s.rhs + i}, acc[i], (R)alpha[i], red[i]);
+    }
+    template <int BS> __device__ __forceinline__ void finish(const double (&red)[RB], const VGrid& vg) const {
         SolverState* st = rc.st;
         const int n = nr;
-        grid_reduce_seg<BS, 1>(rc, kTicketK2, red, n, vg, [st, n](const double* tot) {
+        grid_reduce_seg<BS, RB>(rc, kTicketK2, red, n / RB, vg, [st, n](const double* tot) {
             int all = 1;
             for (int j = 0; j < n; ++j) {
                 if (!st->stop[j]) {
-                    const double rn = tot[j];
+                    const double rn = tot[(j % RB) * kMaxRhs + j / RB];
                     st->iter[j] += 1;
                     if (!isfinite(rn)) {
                         st->stop[j] = 3;
@@ -773,9 +830,13 @@ struct EventSet {
 // SCHUR: the even-odd Schur solve of D x = b (FP32-pair outer arithmetic, EO layout):
 // CG on Mhat^dag Mhat over the even sites, Mhat = A - H_eo H_oe / A with A = m_q + 4 and
 // H the hopping term of Eq. (1); each operator is a hop to the odd sites and a hop back.
-template <int IP, int IF, int IL, int HP, int IBS = kBS, bool SCHUR = false>
+// RB: right-hand sides per thread in the inner stencil kernels K1 and K2 (register blocking;
+// EO layout, unrolled stencils, not the Schur solve).
+template <int IP, int IF, int IL, int HP, int IBS = kBS, bool SCHUR = false, int RB = 1>
 struct Solve {
     static_assert(!SCHUR || (HP == LQ_F64X && IL == LQ_LAYOUT_EO), "the Schur solve runs on FP32-pair EO fields");
+    static_assert(RB == 1 || (!SCHUR && IL == LQ_LAYOUT_EO && !std::is_same<typename PrecT<IP>::Real, dd>::value),
+                  "register blocking over right-hand sides needs the unrolled EO stencils");
     using Real = typename PrecT<IP>::Real;
     using HReal = typename PrecT<HP>::Real;
     static constexpr int HL = Outer<HP>::L;
@@ -796,12 +857,12 @@ struct Solve {
     using HMap = typename std::conditional<SCHUR, MapEoHalf<kBS>, FullHMap<kBS>>::type;
     using HSiteMap = typename std::conditional<SCHUR, MapEoHalf<kSiteBS>, FullHMap<kSiteBS>>::type;
     using K1Sten = Stencil<GA, SpRO, false>;
-    using K1Epi = EpiK1<SpRW, SpRO>;
+    using K1Epi = EpiK1<SpRW, SpRO, RB>;
     using K2Sten = Stencil<GA, SpRO, true>;
     static constexpr int PSIP = psi_prec(IP);
     using PsiRO = SpinorAcc<PSIP, IL, true>;
     using PsiRW = SpinorAcc<PSIP, IL, false>;
-    using K2Epi = EpiK2<SpRO, SpRO, PsiRW, SpRW>;
+    using K2Epi = EpiK2<SpRO, SpRO, PsiRW, SpRW, RB>;
     using K3Op = OpK3<SpRW, SpRO>;
     using PreEpi = EpiPreHop<SpRW>;
     static constexpr bool kPairs = (HP == LQ_F64X);
@@ -945,6 +1006,7 @@ struct Solve {
             hmap = HMap{g, lnr};
             hsite = HSiteMap{g, lnr};
             imap = IMap{g, lnr};
+            if constexpr (RB > 1) imap.lrb = log2i(RB);
             isite = ISiteMap{g, lnr};
             sK1 = K1Sten{g, Ui, p_ro};
             sK2 = K2Sten{g, Ui, t_ro};
@@ -1362,11 +1424,12 @@ struct Solve {
     }
 };
 
-// The single-lattice driver: one batch of nb right-hand sides (SCHUR: eta is b of D x = b).
-template <int IP, int IF, int IL, int HP, bool SCHUR = false>
-int run_solver(const Geom& g, double m_q, int nb, const void* U, const void* eta, void* x, const lq_cg_params& prm,
-               double delta, const WsLayout& w, char* ws, lq_cg_info* info, cudaStream_t st) {
-    Solve<IP, IF, IL, HP, kBS, SCHUR> sv;
+// The single-lattice driver: one batch of nb right-hand sides (SCHUR: eta is b of D x = b),
+// with RB right-hand sides per thread in the inner stencil kernels.
+template <int IP, int IF, int IL, int HP, bool SCHUR = false, int RB = 1>
+int run_solver_rb(const Geom& g, double m_q, int nb, const void* U, const void* eta, void* x, const lq_cg_params& prm,
+                  double delta, const WsLayout& w, char* ws, lq_cg_info* info, cudaStream_t st) {
+    Solve<IP, IF, IL, HP, kBS, SCHUR, RB> sv;
     sv.init(g, m_q, nb, U, eta, x, prm, delta, w, ws, st);
     int r;
     if ((r = sv.begin()) != LQ_OK) return r;
@@ -1376,6 +1439,34 @@ int run_solver(const Geom& g, double m_q, int nb, const void* U, const void* eta
         if ((r = sv.end_cycle()) != LQ_OK) return r;
     }
     return sv.finish(info);
+}
+
+// Right-hand sides per thread for a batch of nb: the LQ_CG_RHS_BLOCK_* flag if one is set
+// (capped at nb); by default 2 for scaled-FP16 inner fields and 1 otherwise.  Measured on
+// the 24^3 x 48 workload with 12 right-hand sides (one GB300): scaled FP16 123.6 / 119.7 /
+// 141.7 ms and FP32 128.0 / 130.7 / 175.0 ms for 1 / 2 / 4 right-hand sides per thread.  The
+// link is decoded once per direction for all of them, but their accumulators raise the
+// kernels' registers (K1 80 -> 128 -> 255, K2 96 -> 167 -> 253 with scaled FP16), which
+// costs resident warps; only the scaled-FP16 stencil, whose link decode is the larger part
+// of each hop, gains.
+inline int rhs_block(const lq_cg_params& prm, int nb, int inner_prec) {
+    int rb = (prm.flags & LQ_CG_RHS_BLOCK_4) ? 4
+             : (prm.flags & LQ_CG_RHS_BLOCK_2) ? 2
+             : (prm.flags & LQ_CG_RHS_BLOCK_1) ? 1
+             : (inner_prec == LQ_F16S ? 2 : 1);
+    while (rb > nb) rb >>= 1;
+    return rb;
+}
+
+template <int IP, int IF, int IL, int HP, bool SCHUR = false>
+int run_solver(const Geom& g, double m_q, int nb, const void* U, const void* eta, void* x, const lq_cg_params& prm,
+               double delta, const WsLayout& w, char* ws, lq_cg_info* info, cudaStream_t st) {
+    if constexpr (!SCHUR && IL == LQ_LAYOUT_EO && IF == 12 && !std::is_same<typename PrecT<IP>::Real, dd>::value) {
+        const int rb = rhs_block(prm, nb, IP);
+        if (rb == 4) return run_solver_rb<IP, IF, IL, HP, SCHUR, 4>(g, m_q, nb, U, eta, x, prm, delta, w, ws, info, st);
+        if (rb == 2) return run_solver_rb<IP, IF, IL, HP, SCHUR, 2>(g, m_q, nb, U, eta, x, prm, delta, w, ws, info, st);
+    }
+    return run_solver_rb<IP, IF, IL, HP, SCHUR, 1>(g, m_q, nb, U, eta, x, prm, delta, w, ws, info, st);
 }
 
 // Instantiations live in solver_f64.cu (FP64 and FP32-pair inner loops), solver_f32.cu,

@@ -99,7 +99,7 @@ def test_cg_multi_against_oracle(lqlib, mode, nrhs):
         assert oracle.rel_l2(xs[i], F.decode_spinor(to_host(x1), dims)) <= 1e-7
 
 
-def test_cg_multi_uneven_right_hand_sides(lqlib):
+def test_cg_multi_uneven_right_hand_sides(lqlib, rhs_block=None):
     """Within one batch: a zero right-hand side, one that starts at its solution, one that
     hits the iteration cap, and a regular one; each gets its own status."""
     dims = (4, 4, 2, 4)
@@ -112,7 +112,7 @@ def test_cg_multi_uneven_right_hand_sides(lqlib):
     xsol, _, _ = oracle.cg(dims, m, U, e2, tol=1e-13)
     xs, infos, st = _solve_multi(lqlib, dims, m, U, [e0, e1, e2, e3], "mixed_f32",
                                  x0s=[np.zeros_like(e0), synth.gaussian_spinor(dims, seed=65), xsol,
-                                      np.zeros_like(e0)], tol=1e-10)
+                                      np.zeros_like(e0)], tol=1e-10, rhs_block=rhs_block)
     assert st == 0
     assert infos[1]["status"] == 0 and np.all(xs[1] == 0)
     assert infos[2]["iters"] == 0 and infos[2]["status"] == 0
@@ -120,8 +120,42 @@ def test_cg_multi_uneven_right_hand_sides(lqlib):
     for i in (0, 2, 3):
         assert _true_resid(dims, m, U, [e0, e1, e2, e3][i], xs[i]) <= 1e-10 * RESID_SLACK
     # an iteration cap that stops every right-hand side early
-    xs, infos, st = _solve_multi(lqlib, dims, m, U, [e0, e2], "mixed_f32", tol=1e-10, max_iter=4)
+    xs, infos, st = _solve_multi(lqlib, dims, m, U, [e0, e2], "mixed_f32", tol=1e-10, max_iter=4,
+                                 rhs_block=rhs_block)
     assert st == 1 and all(i["status"] == 1 for i in infos)
+
+
+@pytest.mark.parametrize("rhs_block", [2, 4])
+def test_cg_multi_uneven_right_hand_sides_blocked(lqlib, rhs_block):
+    """The same mixed batch with two or four right-hand sides per thread: stopped and idle
+    right-hand sides inside one thread's group are skipped while the others go on."""
+    test_cg_multi_uneven_right_hand_sides(lqlib, rhs_block=rhs_block)
+
+
+@pytest.mark.parametrize("mode", ["mixed_f32", "mixed_f16", "mixed_i32"])
+@pytest.mark.parametrize("nrhs", [4, 8, 12])
+@pytest.mark.parametrize("rhs_block", [1, 2, 4])
+def test_cg_multi_register_blocking(lqlib, mode, nrhs, rhs_block):
+    """Each blocking factor (right-hand sides per thread in the inner stencil kernels) on a
+    lattice with a ragged last tile: every solve meets the tolerance in the oracle's FP64
+    residual and agrees with the single-right-hand-side solver; the arithmetic per right-hand
+    side is the same, so the iteration counts match those of one thread per right-hand side
+    up to the order of the grid reductions."""
+    dims = (6, 4, 10, 2)
+    m = 0.05
+    U = synth.gauge_field(dims, seed=71, kind="near_identity", eps=0.3)
+    etas = [synth.gaussian_spinor(dims, seed=700 + i) for i in range(nrhs)]
+    xs, infos, st = _solve_multi(lqlib, dims, m, U, etas, mode, tol=1e-10, rhs_block=rhs_block)
+    assert st == 0
+    _, infos1, _ = _solve_multi(lqlib, dims, m, U, etas, mode, tol=1e-10, rhs_block=1)
+    Ud = to_dev(F.encode_gauge(U, dims))
+    for i in range(nrhs):
+        assert infos[i]["status"] == 0
+        assert _true_resid(dims, m, U, etas[i], xs[i]) <= 1e-10 * RESID_SLACK
+        assert abs(infos[i]["iters"] - infos1[i]["iters"]) <= 2
+    for i in (0, nrhs - 1):
+        x1, _, _ = lqlib.cg_solve(dims, m, Ud, to_dev(F.encode_spinor(etas[i], dims)), mode=mode, tol=1e-10)
+        assert oracle.rel_l2(xs[i], F.decode_spinor(to_host(x1), dims)) <= 1e-7
 
 
 def test_cg_multi_full_size_24x24x24x48(lqlib):
