@@ -542,16 +542,20 @@ def run_workload(args):
         spinor_b = {"f64": 192, "f64x": 192, "f32": 96, "f16s": 52, "i32s": 100}
         link_b = {"f64": 8, "f64x": 8, "f32": 4, "f16s": 2, "i32s": 4}
         rows = {}
-        for prec, fmt, layout in (("f64", 18, "lex"), ("f64", 18, "eo"), ("f64", 10, "eo"), ("f64x", 18, "eo"),
-                                  ("f32", 18, "eo"), ("f32", 12, "eo"), ("f32", 10, "eo"), ("f16s", 12, "eo"),
-                                  ("f16s", 18, "eo"), ("f16s", 10, "eo"), ("i32s", 12, "eo"), ("i32s", 10, "eo")):
+        variants = (("f64", 18, "lex"), ("f64", 18, "eo"), ("f64", 10, "eo"), ("f64x", 18, "eo"),
+                    ("f32", 18, "eo"), ("f32", 12, "eo"), ("f32", 10, "eo"), ("f16s", 12, "eo"),
+                    ("f16s", 18, "eo"), ("f16s", 10, "eo"), ("i32s", 12, "eo"), ("i32s", 10, "eo"))
+        if args.variants:
+            keep = set(args.variants.split(","))
+            variants = tuple(v for v in variants if f"{v[0]}/{v[1]}/{v[2]}" in keep)
+        for prec, fmt, layout in variants:
             Ub = lq.convert_gauge(DIMS, U_d, "f64", "lex", dst_prec=prec, dst_fmt=fmt, dst_layout=layout)
             pb = lq.convert_spinor(DIMS, p_d, "f64", "lex", dst_prec=prec, dst_layout=layout)
             out = torch.empty_like(pb)
             for _ in range(max(args.warmup, 3)):
                 lq.dslash_apply(DIMS, MASS, Ub, pb, out=out, prec=prec, link_fmt=fmt, layout=layout)
             torch.cuda.synchronize()
-            reps = 20
+            reps = args.reps
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record()
@@ -572,7 +576,8 @@ def run_workload(args):
         line.update({"config": {"lattice": list(DIMS), "m_q": MASS, "links": "exp(0.3iH)",
                                 "l2": "every variant streams more than the 126 MB L2 (smallest: 210 MB, f16s/12)",
                                 "peak_kind": peak_kind, "peak_gbs": peak},
-                     "value": rows["f16s/12/eo"]["site_updates_per_s"], "variants": rows})
+                     "value": rows["f16s/12/eo"]["site_updates_per_s"] if "f16s/12/eo" in rows else None,
+                     "variants": rows})
     elif args.workload == "schur":
         # D x = b on the 32^4 workload: the even-odd Schur solve against solving D^dag D x = D^dag b
         U, b = make_inputs()
@@ -662,6 +667,9 @@ def main():
                     help="cg32: the 32^4 mixed-precision solve (the bench line); the others print a "
                          "measurement line for the uneven-lattice, 12-RHS, 64^3x128, Schur, operator-only "
                          "and gradient workloads")
+    ap.add_argument("--variants", default="",
+                    help="dslash workload: comma-separated prec/link-reals/layout rows to run (default: all)")
+    ap.add_argument("--reps", type=int, default=20, help="dslash workload: timed applies per variant")
     ap.add_argument("--lattice-block", type=int, default=0, choices=[0, 64, 128, 256],
                     help="lattices workload: inner block size (0: tuned)")
     ap.add_argument("--inner-loop", default="device", choices=["device", "host"],
