@@ -447,6 +447,16 @@ int lq_halo_dslash(const int32_t dims_local[4], double m_q, int32_t dagger, cons
 int lq_link_grad(const int32_t dims[4], const void *g, const void *psi, double scale,
                  int32_t accumulate, void *out, void *cuda_stream);
 
+/*
+ * lq_bounds_violations -- in the bounds-checked debug build (liblq_checked.so, compiled with
+ * LQ_BOUNDS_CHECK; the stand-in for a memory checker), every field access of the operator and
+ * solver kernels is checked against the slots of its field; an access out of range is skipped
+ * (a load yields zero) and counted.  Returns the number of such accesses since the last call
+ * (after waiting for the device) and, if any, the first offending slot index in *first
+ * (optional); resets the count.  The normal build returns -1.  The paper has no counterpart.
+ */
+long long lq_bounds_violations(unsigned long long *first);
+
 /* Message of the last error on this host thread ("" if none). */
 const char *lq_last_error(void);
 

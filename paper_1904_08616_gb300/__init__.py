@@ -23,7 +23,7 @@ __all__ = [
     "dslash_hop", "link_grad", "convert_spinor", "convert_spinor_multi", "convert_gauge", "cg_workspace_bytes",
     "cg_solve", "cg_solve_multi", "cg_workspace_bytes_lattices", "cg_solve_lattices",
     "cg_workspace_bytes_schur", "cg_solve_schur",
-    "last_error", "version",
+    "last_error", "version", "bounds_violations", "checked",
 ]
 
 PREC = {"f64": 0, "f32": 1, "f16s": 2, "f64x": 3, "i32s": 4}
@@ -65,21 +65,30 @@ _Dims = ctypes.c_int32 * 4
 _vp = ctypes.c_void_p
 
 
+def checked() -> bool:
+    """True when this process uses the bounds-checked debug library (environment variable
+    LQ_LIB_VARIANT=checked): every field access of the kernels is checked against its field
+    and counted (bounds_violations)."""
+    return os.environ.get("LQ_LIB_VARIANT", "") == "checked"
+
+
 def lib_path() -> str:
-    return _build.LIB
+    return _build.LIB_CHECKED if checked() else _build.LIB
 
 
 def load(build_if_missing: bool = True):
-    """Load liblq.so (compiling it with nvcc first if it is missing or stale)."""
+    """Load liblq.so (compiling it with nvcc first if it is missing or stale), or the
+    bounds-checked liblq_checked.so when LQ_LIB_VARIANT=checked."""
     global _lib
     with _lock:
         if _lib is not None:
             return _lib
+        path = lib_path()
         if build_if_missing:
-            _build.build()
-        if not os.path.exists(_build.LIB):
-            raise LqError(-4, f"{_build.LIB} is missing; run paper_1904_08616_gb300.build")
-        L = ctypes.CDLL(_build.LIB)
+            _build.build(checked=checked())
+        if not os.path.exists(path):
+            raise LqError(-4, f"{path} is missing; run paper_1904_08616_gb300.build")
+        L = ctypes.CDLL(path)
         i32, f64 = ctypes.c_int32, ctypes.c_double
         L.lq_field_bytes.argtypes = [_Dims, i32, i32, i32, i32]
         L.lq_field_bytes.restype = ctypes.c_size_t
@@ -127,10 +136,20 @@ def load(build_if_missing: bool = True):
         L.lq_cg_solve.argtypes = [_Dims, f64, i32, _vp, _vp, _vp, ctypes.POINTER(CgParams), _vp,
                                   ctypes.c_size_t, ctypes.POINTER(CgInfo), _vp]
         L.lq_cg_solve.restype = ctypes.c_int
+        L.lq_bounds_violations.argtypes = [ctypes.POINTER(ctypes.c_ulonglong)]
+        L.lq_bounds_violations.restype = ctypes.c_longlong
         L.lq_last_error.restype = ctypes.c_char_p
         L.lq_version.restype = ctypes.c_char_p
         _lib = L
     return _lib
+
+
+def bounds_violations():
+    """(count, first slot) of the field accesses the bounds-checked library skipped since the
+    last call (waits for the device); count is -1 with the normal library."""
+    first = ctypes.c_ulonglong(0)
+    n = int(load().lq_bounds_violations(ctypes.byref(first)))
+    return n, (int(first.value) if n > 0 else None)
 
 
 def last_error() -> str:

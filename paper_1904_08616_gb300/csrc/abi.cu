@@ -4,6 +4,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <vector>
+
 #include "lq_abi_internal.h"
 #include "dslash_dispatch.cuh"
 
@@ -40,6 +42,13 @@ size_t spinor_bytes(int64_t nsites, int prec) {
         default: return 0;
     }
 }
+
+// readers of the per-translation-unit out-of-range records of the bounds-checked build
+static std::vector<OobReaderFn>& oob_readers() {
+    static std::vector<OobReaderFn> v;
+    return v;
+}
+void register_oob_reader(OobReaderFn r) { oob_readers().push_back(r); }
 
 size_t gauge_bytes(int64_t V, int prec, int fmt) {
     if (fmt != 18 && fmt != 12 && fmt != 10) return 0;
@@ -168,27 +177,32 @@ size_t lq_field_bytes(const int32_t dims[4], int32_t kind, int32_t prec, int32_t
 
 int lq_dslash_apply(const int32_t dims[4], double m_q, int32_t prec, int32_t link_fmt, int32_t layout,
                     const void* U, const void* psi, void* out, void* cuda_stream) {
+    NvtxRange nvtx("lq_dslash_apply");
     return do_apply(dims, m_q, prec, link_fmt, layout, U, psi, out, cuda_stream, false);
 }
 
 int lq_dslash_adjoint(const int32_t dims[4], double m_q, int32_t prec, int32_t link_fmt, int32_t layout,
                       const void* U, const void* psi, void* out, void* cuda_stream) {
+    NvtxRange nvtx("lq_dslash_adjoint");
     return do_apply(dims, m_q, prec, link_fmt, layout, U, psi, out, cuda_stream, true);
 }
 
 int lq_dslash_apply_multi(const int32_t dims[4], double m_q, int32_t prec, int32_t link_fmt, int32_t layout,
                           int32_t nrhs, const void* U, const void* psi, void* out, void* cuda_stream) {
+    NvtxRange nvtx("lq_dslash_apply_multi");
     return do_apply(dims, m_q, prec, link_fmt, layout, U, psi, out, cuda_stream, false, nrhs);
 }
 
 int lq_dslash_adjoint_multi(const int32_t dims[4], double m_q, int32_t prec, int32_t link_fmt, int32_t layout,
                             int32_t nrhs, const void* U, const void* psi, void* out, void* cuda_stream) {
+    NvtxRange nvtx("lq_dslash_adjoint_multi");
     return do_apply(dims, m_q, prec, link_fmt, layout, U, psi, out, cuda_stream, true, nrhs);
 }
 
 int lq_dslash_hop(const int32_t dims[4], int32_t out_parity, int32_t dagger, double a, double b, int32_t prec,
                   int32_t link_fmt, const void* U, const void* psi_other, const void* y, void* out,
                   void* cuda_stream) {
+    NvtxRange nvtx("lq_dslash_hop");
     Geom g;
     int r;
     if ((r = check_dims(dims, &g)) != LQ_OK) return r;
@@ -223,6 +237,7 @@ size_t lq_halo_face_bytes(const int32_t dims_local[4]) {
 
 int lq_halo_pack(const int32_t dims_local[4], int32_t dagger, const void* U, const void* psi, void* to_prev,
                  void* to_next, void* cuda_stream) {
+    NvtxRange nvtx("lq_halo_pack");
     Geom g;
     int r;
     if ((r = check_slab(dims_local, &g)) != LQ_OK) return r;
@@ -240,6 +255,7 @@ int lq_halo_pack(const int32_t dims_local[4], int32_t dagger, const void* U, con
 
 int lq_halo_dslash(const int32_t dims_local[4], double m_q, int32_t dagger, const void* U, const void* psi,
                    const void* from_next, const void* from_prev, void* out, void* cuda_stream) {
+    NvtxRange nvtx("lq_halo_dslash");
     Geom g;
     int r;
     if ((r = check_slab(dims_local, &g)) != LQ_OK) return r;
@@ -259,6 +275,7 @@ int lq_halo_dslash(const int32_t dims_local[4], double m_q, int32_t dagger, cons
 
 int lq_link_grad(const int32_t dims[4], const void* gfield, const void* psi, double scale, int32_t accumulate,
                  void* out, void* cuda_stream) {
+    NvtxRange nvtx("lq_link_grad");
     Geom g;
     int r;
     if ((r = check_dims(dims, &g)) != LQ_OK) return r;
@@ -273,6 +290,7 @@ int lq_link_grad(const int32_t dims[4], const void* gfield, const void* psi, dou
 
 int lq_convert_spinor(const int32_t dims[4], int32_t src_prec, int32_t src_layout, const void* src, int32_t dst_prec,
                       int32_t dst_layout, void* dst, void* cuda_stream) {
+    NvtxRange nvtx("lq_convert_spinor");
     Geom g;
     int r;
     if ((r = check_dims(dims, &g)) != LQ_OK) return r;
@@ -288,6 +306,7 @@ int lq_convert_spinor(const int32_t dims[4], int32_t src_prec, int32_t src_layou
 
 int lq_convert_spinor_multi(const int32_t dims[4], int32_t nrhs, int32_t src_prec, int32_t src_layout,
                             const void* src, int32_t dst_prec, int32_t dst_layout, void* dst, void* cuda_stream) {
+    NvtxRange nvtx("lq_convert_spinor_multi");
     Geom g;
     int r;
     if ((r = check_dims(dims, &g)) != LQ_OK) return r;
@@ -305,6 +324,7 @@ int lq_convert_spinor_multi(const int32_t dims[4], int32_t nrhs, int32_t src_pre
 
 int lq_convert_gauge(const int32_t dims[4], int32_t src_prec, int32_t src_layout, const void* src, int32_t dst_prec,
                      int32_t dst_fmt, int32_t dst_layout, void* dst, void* cuda_stream) {
+    NvtxRange nvtx("lq_convert_gauge");
     Geom g;
     int r;
     if ((r = check_dims(dims, &g)) != LQ_OK) return r;
@@ -333,6 +353,7 @@ size_t lq_cg_workspace_bytes(const int32_t dims[4], int32_t mode) { return lq_cg
 int lq_cg_solve_multi(const int32_t dims[4], double m_q, int32_t mode, int32_t nrhs, const void* U, const void* eta,
                       void* x, const lq_cg_params* params, void* workspace, size_t ws_bytes, lq_cg_info* info,
                       void* cuda_stream) {
+    NvtxRange nvtx("lq_cg_solve_multi");
     if (info && nrhs > 0) memset(info, 0, sizeof(*info) * (size_t)nrhs);
     Geom g;
     int r;
@@ -399,6 +420,7 @@ size_t lq_cg_workspace_bytes_lattices(int32_t n, const lq_lattice* lats, int32_t
 
 int lq_cg_solve_lattices(int32_t n, const lq_lattice* lats, int32_t mode, const lq_cg_params* params,
                          void* workspace, size_t ws_bytes, lq_cg_info* info, void* cuda_stream) {
+    NvtxRange nvtx("lq_cg_solve_lattices");
     Geom gs[kMaxLattices];
     int nr[kMaxLattices];
     int r;
@@ -489,6 +511,20 @@ int lq_cg_solve(const int32_t dims[4], double m_q, int32_t mode, const void* U, 
 }
 
 const char* lq_last_error(void) { return g_err; }
+
+
+long long lq_bounds_violations(unsigned long long* first) {
+#ifdef LQ_BOUNDS_CHECK
+    if (first) *first = ~0ull;
+    if (cudaDeviceSynchronize() != cudaSuccess) return -1;
+    long long total = 0;
+    for (OobReaderFn r : lq::oob_readers()) total += r(first);
+    return total;
+#else
+    (void)first;
+    return -1;
+#endif
+}
 
 const char* lq_version(void) { return "lq 0.1 (sm_103a)"; }
 

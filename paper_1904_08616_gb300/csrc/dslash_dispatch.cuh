@@ -29,6 +29,10 @@ inline SpinorAcc<PREC, LAYOUT, RO> make_spinor(const void* buf, const Geom& g, b
         a.ptr = (uint4*)buf;
         a.scale = (float*)((char*)buf + 48 * nsites);
     }
+#ifdef LQ_BOUNDS_CHECK
+    a.nslots = (uint32_t)(SpinorAcc<PREC, LAYOUT, RO>::K * nsites);
+    a.nscales = (uint32_t)nsites;
+#endif
     return a;
 }
 
@@ -37,6 +41,9 @@ inline GaugeAcc<PREC, FMT, LAYOUT> make_gauge(const void* buf, const Geom& g) {
     GaugeAcc<PREC, FMT, LAYOUT> a;
     a.ptr = (decltype(a.ptr))buf;
     a.Vh = (uint32_t)g.Vh;
+#ifdef LQ_BOUNDS_CHECK
+    a.nslots = (uint32_t)(4 * GaugeAcc<PREC, FMT, LAYOUT>::K * (int64_t)g.V);
+#endif
     return a;
 }
 

@@ -387,7 +387,7 @@ struct Stencil {
 // With nr right-hand sides a map covers (site, rhs) pairs, rhs fastest: the nr threads of
 // one site are adjacent, so their link loads coincide.  nr is a power of two (lnr = log2)
 // dividing BS, so a thread keeps the same rhs = threadIdx.x mod nr in every tile.  With
-// register blocking (MapEoFull, lrb = log2 RB > 0) a thread takes RB consecutive right-hand
+// register blocking (MapEoFullRB, lrb = log2 RB > 0) a thread takes RB consecutive right-hand
 // sides of its site, the first being RB (threadIdx.x mod nr / RB).
 template <int BS> struct MapLex {            // all V sites, lexicographic
     Geom g;
@@ -402,6 +402,18 @@ template <int BS> struct MapLex {            // all V sites, lexicographic
 };
 
 template <int BS> struct MapEoFull {         // all V sites; tiles alternate parity over the same cb range
+    Geom g;
+    int lnr = 0;
+    __host__ __device__ int ntiles() const { return 2 * (int)((((int64_t)g.Vh << lnr) + BS - 1) / BS); }
+    __device__ __forceinline__ bool site(int tile, Site& s, int c[4]) const {
+        const int f = (tile >> 1) * BS + (int)threadIdx.x;
+        if (f >= (g.Vh << lnr)) return false;
+        s = site_from_eo(g, tile & 1, f >> lnr, c, f & ((1 << lnr) - 1));
+        return true;
+    }
+};
+
+template <int BS> struct MapEoFullRB {       // the same with 2^lrb right-hand sides per thread
     Geom g;
     int lnr = 0;
     int lrb = 0;
@@ -509,6 +521,13 @@ template <class E> struct HasPrefetch<E, std::void_t<decltype(&E::prefetch)>> : 
 #ifndef LQ_STENCIL_MINB_PAIR
 #define LQ_STENCIL_MINB_PAIR 0
 #endif
+// Optional cap on the resident blocks per SM of the FP32-arithmetic stencils (the grid of the
+// grid-stride kernels is sized to it); 0: the occupancy limit.
+#ifndef LQ_STENCIL_MAXB_F32
+#define LQ_STENCIL_MAXB_F32 0
+#endif
+template <class Real> struct StencilMaxBlocks { static constexpr int value = 0; };
+template <> struct StencilMaxBlocks<float> { static constexpr int value = LQ_STENCIL_MAXB_F32; };
 template <class Real> struct StencilMinBlocks { static constexpr int value = 0; };
 template <> struct StencilMinBlocks<float> { static constexpr int value = LQ_STENCIL_MINB_F32; };
 template <> struct StencilMinBlocks<dd> { static constexpr int value = LQ_STENCIL_MINB_PAIR; };
@@ -556,11 +575,12 @@ __global__ void __launch_bounds__(BS, MINB) stencil_kernel_minb(Map map, Sten st
 // Grid size for a grid-stride kernel: every SM filled to its occupancy, never more
 // blocks than tiles, never more than the partial-sum buffer holds.
 template <class KernelPtr>
-inline int grid_for(KernelPtr k, int bs, int ntiles) {
+inline int grid_for(KernelPtr k, int bs, int ntiles, int max_per_sm = 0) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, bs, 0);
+    if (max_per_sm > 0 && per_sm > max_per_sm) per_sm = max_per_sm;
     if (per_sm < 1) per_sm = 1;
     long long g = (long long)sms * per_sm;
     if (g > ntiles) g = ntiles;
@@ -582,7 +602,7 @@ inline cudaError_t launch_stencil(const Map& map, const Sten& sten, const Epi& e
     if (cached_grid_tiles == nt) {
         grid = cached_grid;
     } else {
-        grid = grid_for(k, BS, nt);
+        grid = grid_for(k, BS, nt, StencilMaxBlocks<typename Sten::Real>::value);
         cached_grid_tiles = nt;
         cached_grid = grid;
     }

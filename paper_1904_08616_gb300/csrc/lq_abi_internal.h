@@ -5,11 +5,27 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/lq.h"
 
 namespace lq {
 
+// A named range on the NVTX timeline around a phase of a call (shown by Nsight Systems and
+// Nsight Compute; without a tool attached the calls return at once).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 struct Geom;
+
+// bounds-checked build: reader of one translation unit's out-of-range record (count, first
+// slot); each unit registers its own at load time
+using OobReaderFn = unsigned int (*)(unsigned long long* first);
+void register_oob_reader(OobReaderFn r);
 
 // per-thread error message for lq_last_error()
 void set_error(const char* fmt, ...);

@@ -176,6 +176,65 @@ template <bool RO, typename T> LQ_HD T ld(const T* p) {
 #endif
 }
 
+// ------------------------------------------------------------------------------------
+// Bounds-checked debug build (compiled with LQ_BOUNDS_CHECK): every slot a field accessor
+// touches is checked against the slots its buffer holds.  An access out of range is
+// skipped (a load yields zero) and counted in a record of its translation unit; the host
+// reads the records back through lq_bounds_violations().  Nothing traps or faults.  In the
+// normal build the checks compile to nothing.
+// ------------------------------------------------------------------------------------
+#ifdef LQ_BOUNDS_CHECK
+using OobReaderFn = unsigned int (*)(unsigned long long* first);
+void register_oob_reader(OobReaderFn r);
+namespace {
+__device__ unsigned int g_oob_count;
+__device__ unsigned long long g_oob_first;
+unsigned int read_oob(unsigned long long* first) {
+    unsigned int c = 0;
+    unsigned long long f = 0;
+    const unsigned int zero = 0;
+    if (cudaMemcpyFromSymbol(&c, g_oob_count, sizeof(c)) != cudaSuccess) return 0;
+    if (c && first && cudaMemcpyFromSymbol(&f, g_oob_first, sizeof(f)) == cudaSuccess && *first == ~0ull) *first = f;
+    if (c) cudaMemcpyToSymbol(g_oob_count, &zero, sizeof(zero));
+    return c;
+}
+struct OobRegistrar {
+    OobRegistrar() { register_oob_reader(&read_oob); }
+} g_oob_registrar;
+}  // namespace
+LQ_HD bool oob_ok(uint32_t i, uint32_t n) {
+    if (i < n) return true;
+#ifdef __CUDA_ARCH__
+    if (atomicAdd(&g_oob_count, 1u) == 0u) g_oob_first = i;
+#endif
+    return false;
+}
+#endif
+
+// The slot bounds of a field accessor (checked only in the debug build).
+struct SlotBounds {
+#ifdef LQ_BOUNDS_CHECK
+    uint32_t nslots = 0xffffffffu, nscales = 0xffffffffu;
+    LQ_HD bool slot_ok(uint32_t i) const { return oob_ok(i, nslots); }
+    LQ_HD bool scale_ok(uint32_t i) const { return oob_ok(i, nscales); }
+#else
+    LQ_HD static constexpr bool slot_ok(uint32_t) { return true; }
+    LQ_HD static constexpr bool scale_ok(uint32_t) { return true; }
+#endif
+    // slot b + off of p; the address is formed as (p + b) + off, as the accessors always did,
+    // so that the compiler keeps its 64-bit address arithmetic
+    template <bool RO, typename T> LQ_HD T at(const T* p, uint32_t b, uint32_t off) const {
+        return slot_ok(b + off) ? ld<RO>(p + b + off) : T{};
+    }
+    template <typename T> LQ_HD void set(T* p, uint32_t b, uint32_t off, const T& v) const {
+        if (slot_ok(b + off)) p[b + off] = v;
+    }
+    template <bool RO> LQ_HD float scale_at(const float* p, uint32_t i) const { return scale_ok(i) ? ld<RO>(p + i) : 0.f; }
+    LQ_HD void scale_set(float* p, uint32_t i, float v) const {
+        if (scale_ok(i)) p[i] = v;
+    }
+};
+
 // Brings the cache line holding p into L1 ahead of its load (no register is written, so a
 // warp can ask for data it will use later without stalling on it now).
 LQ_HD void prefetch_l1(const void* p) {
@@ -237,7 +296,7 @@ template <int LAYOUT> LQ_HD uint32_t sp_sidx(const Site& s, const EoIdx& e) {
     else return ((uint32_t)s.p * e.sstride + (uint32_t)s.cb) * e.nr + (uint32_t)s.rhs;
 }
 
-template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F64, LAYOUT, RO> {
+template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F64, LAYOUT, RO> : SlotBounds {
     using Real = double;
     static constexpr int K = 12;
     static constexpr bool kScaled = false;
@@ -246,20 +305,21 @@ template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F64, LAYOUT, RO> {
     LQ_HD void prefetch(const Site& s) const {
         const uint32_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
 #pragma unroll
-        for (int k = 0; k < K; ++k) prefetch_l1(ptr + b + k * ks);
+        for (int k = 0; k < K; ++k)
+            if (slot_ok(b + k * ks)) prefetch_l1(ptr + b + k * ks);
     }
     template <typename T> LQ_HD void load(const Site& s, Spinor<T>& out) const {
         const uint32_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
-            double2 v = ld<RO>(ptr + b + k * ks);
+            double2 v = at<RO>(ptr, b, k * ks);
             out.v[k] = {from_double<T>(v.x), from_double<T>(v.y)};
         }
     }
     template <typename T> LQ_HD void store(const Site& s, const Spinor<T>& in) const {
         const uint32_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) ptr[b + k * ks] = make_double2(to_double(in.v[k].re), to_double(in.v[k].im));
+        for (int k = 0; k < 12; ++k) set(ptr, b, k * ks, make_double2(to_double(in.v[k].re), to_double(in.v[k].im)));
     }
     LQ_HD void load_raw(const Site& s, Spinor<double>& out, double& sc) const {
         load(s, out);
@@ -267,7 +327,7 @@ template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F64, LAYOUT, RO> {
     }
 };
 
-template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F32, LAYOUT, RO> {
+template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F32, LAYOUT, RO> : SlotBounds {
     using Real = float;
     static constexpr int K = 6;
     static constexpr bool kScaled = false;
@@ -276,13 +336,14 @@ template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F32, LAYOUT, RO> {
     LQ_HD void prefetch(const Site& s) const {
         const uint32_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
 #pragma unroll
-        for (int k = 0; k < K; ++k) prefetch_l1(ptr + b + k * ks);
+        for (int k = 0; k < K; ++k)
+            if (slot_ok(b + k * ks)) prefetch_l1(ptr + b + k * ks);
     }
     template <typename T> LQ_HD void load(const Site& s, Spinor<T>& out) const {
         const uint32_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
-            float4 v = ld<RO>(ptr + b + k * ks);
+            float4 v = at<RO>(ptr, b, k * ks);
             out.v[2 * k] = {(T)v.x, (T)v.y};
             out.v[2 * k + 1] = {(T)v.z, (T)v.w};
         }
@@ -291,8 +352,8 @@ template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F32, LAYOUT, RO> {
         const uint32_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
 #pragma unroll
         for (int k = 0; k < 6; ++k)
-            ptr[b + k * ks] = make_float4(to_float(in.v[2 * k].re), to_float(in.v[2 * k].im),
-                                          to_float(in.v[2 * k + 1].re), to_float(in.v[2 * k + 1].im));
+            set(ptr, b, k * ks, make_float4(to_float(in.v[2 * k].re), to_float(in.v[2 * k].im),
+                                          to_float(in.v[2 * k + 1].re), to_float(in.v[2 * k + 1].im)));
     }
     LQ_HD void load_raw(const Site& s, Spinor<float>& out, float& sc) const {
         load(s, out);
@@ -303,7 +364,7 @@ template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F32, LAYOUT, RO> {
 // Scaled FP16: value = half * scale, scale = max |fl32(v)| of the site.  Loads compute
 // half * scale in T (exact when T = double); stores round to FP32 first, then divide by
 // the scale in FP32 (correctly rounded) and round to FP16.
-template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F16S, LAYOUT, RO> {
+template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F16S, LAYOUT, RO> : SlotBounds {
     using Real = float;
     static constexpr int K = 3;
     static constexpr bool kScaled = true, kHalf2 = true;
@@ -313,16 +374,17 @@ template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F16S, LAYOUT, RO> {
     LQ_HD void prefetch(const Site& s) const {
         const uint32_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
 #pragma unroll
-        for (int k = 0; k < K; ++k) prefetch_l1(ptr + b + k * ks);
-        prefetch_l1(scale + sp_sidx<LAYOUT>(s, e));
+        for (int k = 0; k < K; ++k)
+            if (slot_ok(b + k * ks)) prefetch_l1(ptr + b + k * ks);
+        if (scale_ok(sp_sidx<LAYOUT>(s, e))) prefetch_l1(scale + sp_sidx<LAYOUT>(s, e));
     }
     // the stored halves as floats, without the site's scale (returned separately)
     LQ_HD void load_raw(const Site& s, Spinor<float>& out, float& sc) const {
         const uint32_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
-        sc = ld<RO>(scale + sp_sidx<LAYOUT>(s, e));
+        sc = scale_at<RO>(scale, sp_sidx<LAYOUT>(s, e));
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            uint4 w = ld<RO>(ptr + b + k * ks);
+            uint4 w = at<RO>(ptr, b, k * ks);
             const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -334,10 +396,10 @@ template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F16S, LAYOUT, RO> {
     // the stored complex numbers as half2 words (re low, im high), without the scale
     LQ_HD void load_h2(const Site& s, uint32_t out[12], float& sc) const {
         const uint32_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
-        sc = ld<RO>(scale + sp_sidx<LAYOUT>(s, e));
+        sc = scale_at<RO>(scale, sp_sidx<LAYOUT>(s, e));
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const uint4 w = ld<RO>(ptr + b + k * ks);
+            const uint4 w = at<RO>(ptr, b, k * ks);
             out[4 * k] = w.x;
             out[4 * k + 1] = w.y;
             out[4 * k + 2] = w.z;
@@ -346,10 +408,10 @@ template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F16S, LAYOUT, RO> {
     }
     template <typename T> LQ_HD void load(const Site& s, Spinor<T>& out) const {
         const uint32_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
-        const T sc = (T)ld<RO>(scale + sp_sidx<LAYOUT>(s, e));
+        const T sc = (T)scale_at<RO>(scale, sp_sidx<LAYOUT>(s, e));
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            uint4 w = ld<RO>(ptr + b + k * ks);
+            uint4 w = at<RO>(ptr, b, k * ks);
             const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -366,7 +428,7 @@ template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F16S, LAYOUT, RO> {
         float m = 0.f;
 #pragma unroll
         for (int k = 0; k < 24; ++k) m = fmaxf(m, fabsf(f[k]));
-        scale[sp_sidx<LAYOUT>(s, e)] = m;
+        scale_set(scale, sp_sidx<LAYOUT>(s, e), m);
         // one correctly rounded reciprocal per site, then products (kernel outputs; the
         // bit-exact format conversion in convert.cu divides every component)
         const float inv = (m > 0.f) ? div_rn(1.0f, m) : 0.f;
@@ -375,7 +437,7 @@ template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F16S, LAYOUT, RO> {
             float q[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) q[j] = f[8 * k + j] * inv;
-            ptr[b + k * ks] = make_uint4(f22h2(q[0], q[1]), f22h2(q[2], q[3]), f22h2(q[4], q[5]), f22h2(q[6], q[7]));
+            set(ptr, b, k * ks, make_uint4(f22h2(q[0], q[1]), f22h2(q[2], q[3]), f22h2(q[4], q[5]), f22h2(q[6], q[7])));
         }
     }
 };
@@ -395,7 +457,7 @@ LQ_HD int f2i_rn(float x) {
 #endif
 }
 
-template <int LAYOUT, bool RO> struct SpinorAcc<LQ_I32S, LAYOUT, RO> {
+template <int LAYOUT, bool RO> struct SpinorAcc<LQ_I32S, LAYOUT, RO> : SlotBounds {
     using Real = float;
     static constexpr int K = 6;
     static constexpr bool kScaled = true;
@@ -405,26 +467,27 @@ template <int LAYOUT, bool RO> struct SpinorAcc<LQ_I32S, LAYOUT, RO> {
     LQ_HD void prefetch(const Site& s) const {
         const uint32_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
 #pragma unroll
-        for (int k = 0; k < K; ++k) prefetch_l1(ptr + b + k * ks);
-        prefetch_l1(scale + sp_sidx<LAYOUT>(s, e));
+        for (int k = 0; k < K; ++k)
+            if (slot_ok(b + k * ks)) prefetch_l1(ptr + b + k * ks);
+        if (scale_ok(sp_sidx<LAYOUT>(s, e))) prefetch_l1(scale + sp_sidx<LAYOUT>(s, e));
     }
     // the stored integers as floats, and s * 2^-30 separately
     LQ_HD void load_raw(const Site& s, Spinor<float>& out, float& sc) const {
         const uint32_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
-        sc = ld<RO>(scale + sp_sidx<LAYOUT>(s, e)) * kInvQ30;
+        sc = scale_at<RO>(scale, sp_sidx<LAYOUT>(s, e)) * kInvQ30;
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
-            const int4 w = ld<RO>(ptr + b + k * ks);
+            const int4 w = at<RO>(ptr, b, k * ks);
             out.v[2 * k] = {(float)w.x, (float)w.y};
             out.v[2 * k + 1] = {(float)w.z, (float)w.w};
         }
     }
     template <typename T> LQ_HD void load(const Site& s, Spinor<T>& out) const {
         const uint32_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
-        const T sc = (T)ld<RO>(scale + sp_sidx<LAYOUT>(s, e)) * (T)kInvQ30;
+        const T sc = (T)scale_at<RO>(scale, sp_sidx<LAYOUT>(s, e)) * (T)kInvQ30;
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
-            const int4 w = ld<RO>(ptr + b + k * ks);
+            const int4 w = at<RO>(ptr, b, k * ks);
             out.v[2 * k] = {(T)w.x * sc, (T)w.y * sc};
             out.v[2 * k + 1] = {(T)w.z * sc, (T)w.w * sc};
         }
@@ -437,18 +500,18 @@ template <int LAYOUT, bool RO> struct SpinorAcc<LQ_I32S, LAYOUT, RO> {
         float m = 0.f;
 #pragma unroll
         for (int k = 0; k < 24; ++k) m = fmaxf(m, fabsf(f[k]));
-        scale[sp_sidx<LAYOUT>(s, e)] = m;
+        scale_set(scale, sp_sidx<LAYOUT>(s, e), m);
         const float inv = (m > 0.f) ? div_rn(kQ30, m) : 0.f;
 #pragma unroll
         for (int k = 0; k < 6; ++k)
-            ptr[b + k * ks] = make_int4(f2i_rn(f[4 * k] * inv), f2i_rn(f[4 * k + 1] * inv), f2i_rn(f[4 * k + 2] * inv),
-                                        f2i_rn(f[4 * k + 3] * inv));
+            set(ptr, b, k * ks, make_int4(f2i_rn(f[4 * k] * inv), f2i_rn(f[4 * k + 1] * inv), f2i_rn(f[4 * k + 2] * inv),
+                                        f2i_rn(f[4 * k + 3] * inv)));
     }
 };
 
 // FP32 pairs: the LQ_F64 layout with every double replaced by (hi, lo); one float4 chunk
 // is one complex number (re.hi, re.lo, im.hi, im.lo).
-template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F64X, LAYOUT, RO> {
+template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F64X, LAYOUT, RO> : SlotBounds {
     using Real = dd;
     static constexpr int K = 12;
     static constexpr bool kScaled = false;
@@ -457,13 +520,14 @@ template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F64X, LAYOUT, RO> {
     LQ_HD void prefetch(const Site& s) const {
         const uint32_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
 #pragma unroll
-        for (int k = 0; k < K; ++k) prefetch_l1(ptr + b + k * ks);
+        for (int k = 0; k < K; ++k)
+            if (slot_ok(b + k * ks)) prefetch_l1(ptr + b + k * ks);
     }
     template <typename T> LQ_HD void load(const Site& s, Spinor<T>& out) const {
         const uint32_t b = sp_base<LAYOUT>(s, K, e), ks = sp_kstride<LAYOUT>(e);
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
-            float4 v = ld<RO>(ptr + b + k * ks);
+            float4 v = at<RO>(ptr, b, k * ks);
             out.v[k] = {from_pair<T>(v.x, v.y), from_pair<T>(v.z, v.w)};
         }
     }
@@ -472,7 +536,7 @@ template <int LAYOUT, bool RO> struct SpinorAcc<LQ_F64X, LAYOUT, RO> {
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
             const dd re = to_pair(in.v[k].re), im = to_pair(in.v[k].im);
-            ptr[b + k * ks] = make_float4(re.hi, re.lo, im.hi, im.lo);
+            set(ptr, b, k * ks, make_float4(re.hi, re.lo, im.hi, im.lo));
         }
     }
     LQ_HD void load_raw(const Site& s, Spinor<dd>& out, dd& sc) const {
@@ -511,7 +575,7 @@ template <int LAYOUT> LQ_HD uint32_t lk_kstride(uint32_t Vh) {
 template <int PREC, int FMT, int LAYOUT> struct GaugeAcc;
 
 // FP64: double2 chunks (one complex), 9 or 6 per link
-template <int FMT, int LAYOUT> struct GaugeAcc<LQ_F64, FMT, LAYOUT> {
+template <int FMT, int LAYOUT> struct GaugeAcc<LQ_F64, FMT, LAYOUT> : SlotBounds {
     using Real = double;
     static constexpr int K = FMT / 2;
     const double2* ptr;
@@ -520,7 +584,7 @@ template <int FMT, int LAYOUT> struct GaugeAcc<LQ_F64, FMT, LAYOUT> {
         const uint32_t b = lk_base<LAYOUT>(s, mu, K, Vh), ks = lk_kstride<LAYOUT>(Vh);
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            double2 v = ld<true>(ptr + b + k * ks);
+            double2 v = at<true>(ptr, b, k * ks);
             U.u[k / 3][k % 3] = {v.x, v.y};
         }
         if constexpr (FMT == 12) reconstruct_row2(U);
@@ -528,7 +592,7 @@ template <int FMT, int LAYOUT> struct GaugeAcc<LQ_F64, FMT, LAYOUT> {
 };
 
 // FP32 18: float2 chunks; FP32 12: float4 chunks (two complex)
-template <int LAYOUT> struct GaugeAcc<LQ_F32, 18, LAYOUT> {
+template <int LAYOUT> struct GaugeAcc<LQ_F32, 18, LAYOUT> : SlotBounds {
     using Real = float;
     static constexpr int K = 9;
     const float2* ptr;
@@ -537,12 +601,12 @@ template <int LAYOUT> struct GaugeAcc<LQ_F32, 18, LAYOUT> {
         const uint32_t b = lk_base<LAYOUT>(s, mu, K, Vh), ks = lk_kstride<LAYOUT>(Vh);
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
-            float2 v = ld<true>(ptr + b + k * ks);
+            float2 v = at<true>(ptr, b, k * ks);
             U.u[k / 3][k % 3] = {v.x, v.y};
         }
     }
 };
-template <int LAYOUT> struct GaugeAcc<LQ_F32, 12, LAYOUT> {
+template <int LAYOUT> struct GaugeAcc<LQ_F32, 12, LAYOUT> : SlotBounds {
     using Real = float;
     static constexpr int K = 3;
     const float4* ptr;
@@ -551,7 +615,7 @@ template <int LAYOUT> struct GaugeAcc<LQ_F32, 12, LAYOUT> {
         const uint32_t b = lk_base<LAYOUT>(s, mu, K, Vh), ks = lk_kstride<LAYOUT>(Vh);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            float4 v = ld<true>(ptr + b + k * ks);
+            float4 v = at<true>(ptr, b, k * ks);
             const int c0 = 2 * k, c1 = 2 * k + 1;
             U.u[c0 / 3][c0 % 3] = {v.x, v.y};
             U.u[c1 / 3][c1 % 3] = {v.z, v.w};
@@ -561,7 +625,7 @@ template <int LAYOUT> struct GaugeAcc<LQ_F32, 12, LAYOUT> {
 };
 
 // FP16 18: one half2 (one complex) per chunk; FP16 12: uint2 = four halves (two complex)
-template <int LAYOUT> struct GaugeAcc<LQ_F16S, 18, LAYOUT> {
+template <int LAYOUT> struct GaugeAcc<LQ_F16S, 18, LAYOUT> : SlotBounds {
     using Real = float;
     static constexpr int K = 9;
     const uint32_t* ptr;
@@ -570,12 +634,12 @@ template <int LAYOUT> struct GaugeAcc<LQ_F16S, 18, LAYOUT> {
         const uint32_t b = lk_base<LAYOUT>(s, mu, K, Vh), ks = lk_kstride<LAYOUT>(Vh);
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
-            float2 v = h2f2(ld<true>(ptr + b + k * ks));
+            float2 v = h2f2(at<true>(ptr, b, k * ks));
             U.u[k / 3][k % 3] = {v.x, v.y};
         }
     }
 };
-template <int LAYOUT> struct GaugeAcc<LQ_F16S, 12, LAYOUT> {
+template <int LAYOUT> struct GaugeAcc<LQ_F16S, 12, LAYOUT> : SlotBounds {
     using Real = float;
     static constexpr int K = 3;
     const uint2* ptr;
@@ -584,7 +648,7 @@ template <int LAYOUT> struct GaugeAcc<LQ_F16S, 12, LAYOUT> {
         const uint32_t b = lk_base<LAYOUT>(s, mu, K, Vh), ks = lk_kstride<LAYOUT>(Vh);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            uint2 w = ld<true>(ptr + b + k * ks);
+            uint2 w = at<true>(ptr, b, k * ks);
             float2 a = h2f2(w.x), c = h2f2(w.y);
             const int c0 = 2 * k, c1 = 2 * k + 1;
             U.u[c0 / 3][c0 % 3] = {a.x, a.y};
@@ -595,7 +659,7 @@ template <int LAYOUT> struct GaugeAcc<LQ_F16S, 12, LAYOUT> {
 };
 
 // Q1.30 links (no scale; |entries| < 2): int2 chunks (LINK18) or int4 chunks (LINK12)
-template <int LAYOUT> struct GaugeAcc<LQ_I32S, 18, LAYOUT> {
+template <int LAYOUT> struct GaugeAcc<LQ_I32S, 18, LAYOUT> : SlotBounds {
     using Real = float;
     static constexpr int K = 9;
     const int2* ptr;
@@ -604,12 +668,12 @@ template <int LAYOUT> struct GaugeAcc<LQ_I32S, 18, LAYOUT> {
         const uint32_t b = lk_base<LAYOUT>(s, mu, K, Vh), ks = lk_kstride<LAYOUT>(Vh);
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
-            const int2 v = ld<true>(ptr + b + k * ks);
+            const int2 v = at<true>(ptr, b, k * ks);
             U.u[k / 3][k % 3] = {(float)v.x * kInvQ30, (float)v.y * kInvQ30};
         }
     }
 };
-template <int LAYOUT> struct GaugeAcc<LQ_I32S, 12, LAYOUT> {
+template <int LAYOUT> struct GaugeAcc<LQ_I32S, 12, LAYOUT> : SlotBounds {
     using Real = float;
     static constexpr int K = 3;
     const int4* ptr;
@@ -618,7 +682,7 @@ template <int LAYOUT> struct GaugeAcc<LQ_I32S, 12, LAYOUT> {
         const uint32_t b = lk_base<LAYOUT>(s, mu, K, Vh), ks = lk_kstride<LAYOUT>(Vh);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const int4 w = ld<true>(ptr + b + k * ks);
+            const int4 w = at<true>(ptr, b, k * ks);
             const int c0 = 2 * k, c1 = 2 * k + 1;
             U.u[c0 / 3][c0 % 3] = {(float)w.x * kInvQ30, (float)w.y * kInvQ30};
             U.u[c1 / 3][c1 % 3] = {(float)w.z * kInvQ30, (float)w.w * kInvQ30};
@@ -668,7 +732,7 @@ template <typename T> LQ_HD T abs_max(T a, T b) {
     return x > y ? x : y;
 }
 
-template <int LAYOUT> struct GaugeAcc<LQ_F64, 10, LAYOUT> {
+template <int LAYOUT> struct GaugeAcc<LQ_F64, 10, LAYOUT> : SlotBounds {
     using Real = double;
     static constexpr int K = 5;
     const double2* ptr;
@@ -677,7 +741,7 @@ template <int LAYOUT> struct GaugeAcc<LQ_F64, 10, LAYOUT> {
         const uint32_t b = lk_base<LAYOUT>(s, mu, K, Vh), ks = lk_kstride<LAYOUT>(Vh);
         double2 w[5];
 #pragma unroll
-        for (int k = 0; k < 5; ++k) w[k] = ld<true>(ptr + b + k * ks);
+        for (int k = 0; k < 5; ++k) w[k] = at<true>(ptr, b, k * ks);
         const int c = link10_column(abs_max(w[0].x, w[0].y), abs_max(w[1].x, w[1].y), abs_max(w[2].x, w[2].y));
 #pragma unroll
         for (int j = 0; j < 3; ++j) U.u[0][j] = {w[j].x, w[j].y};
@@ -685,7 +749,7 @@ template <int LAYOUT> struct GaugeAcc<LQ_F64, 10, LAYOUT> {
     }
 };
 
-template <int LAYOUT> struct GaugeAcc<LQ_F32, 10, LAYOUT> {
+template <int LAYOUT> struct GaugeAcc<LQ_F32, 10, LAYOUT> : SlotBounds {
     using Real = float;
     static constexpr int K = 5;
     const float2* ptr;
@@ -694,7 +758,7 @@ template <int LAYOUT> struct GaugeAcc<LQ_F32, 10, LAYOUT> {
         const uint32_t b = lk_base<LAYOUT>(s, mu, K, Vh), ks = lk_kstride<LAYOUT>(Vh);
         float2 w[5];
 #pragma unroll
-        for (int k = 0; k < 5; ++k) w[k] = ld<true>(ptr + b + k * ks);
+        for (int k = 0; k < 5; ++k) w[k] = at<true>(ptr, b, k * ks);
         const int c = link10_column(abs_max(w[0].x, w[0].y), abs_max(w[1].x, w[1].y), abs_max(w[2].x, w[2].y));
 #pragma unroll
         for (int j = 0; j < 3; ++j) U.u[0][j] = {w[j].x, w[j].y};
@@ -704,7 +768,7 @@ template <int LAYOUT> struct GaugeAcc<LQ_F32, 10, LAYOUT> {
 
 // FP16: one half2 word per complex entry; the halves widen to FP32 exactly, so the column
 // choice compares the stored values
-template <int LAYOUT> struct GaugeAcc<LQ_F16S, 10, LAYOUT> {
+template <int LAYOUT> struct GaugeAcc<LQ_F16S, 10, LAYOUT> : SlotBounds {
     using Real = float;
     static constexpr int K = 5;
     const uint32_t* ptr;
@@ -713,7 +777,7 @@ template <int LAYOUT> struct GaugeAcc<LQ_F16S, 10, LAYOUT> {
         const uint32_t b = lk_base<LAYOUT>(s, mu, K, Vh), ks = lk_kstride<LAYOUT>(Vh);
         float2 w[5];
 #pragma unroll
-        for (int k = 0; k < 5; ++k) w[k] = h2f2(ld<true>(ptr + b + k * ks));
+        for (int k = 0; k < 5; ++k) w[k] = h2f2(at<true>(ptr, b, k * ks));
         const int c = link10_column(abs_max(w[0].x, w[0].y), abs_max(w[1].x, w[1].y), abs_max(w[2].x, w[2].y));
 #pragma unroll
         for (int j = 0; j < 3; ++j) U.u[0][j] = {w[j].x, w[j].y};
@@ -723,7 +787,7 @@ template <int LAYOUT> struct GaugeAcc<LQ_F16S, 10, LAYOUT> {
 
 // Q1.30: the column choice compares the stored integers (their FP32 images may round
 // together)
-template <int LAYOUT> struct GaugeAcc<LQ_I32S, 10, LAYOUT> {
+template <int LAYOUT> struct GaugeAcc<LQ_I32S, 10, LAYOUT> : SlotBounds {
     using Real = float;
     static constexpr int K = 5;
     const int2* ptr;
@@ -732,7 +796,7 @@ template <int LAYOUT> struct GaugeAcc<LQ_I32S, 10, LAYOUT> {
         const uint32_t b = lk_base<LAYOUT>(s, mu, K, Vh), ks = lk_kstride<LAYOUT>(Vh);
         int2 w[5];
 #pragma unroll
-        for (int k = 0; k < 5; ++k) w[k] = ld<true>(ptr + b + k * ks);
+        for (int k = 0; k < 5; ++k) w[k] = at<true>(ptr, b, k * ks);
         const int c = link10_column(abs_max(w[0].x, w[0].y), abs_max(w[1].x, w[1].y), abs_max(w[2].x, w[2].y));
 #pragma unroll
         for (int j = 0; j < 3; ++j) U.u[0][j] = {(float)w[j].x * kInvQ30, (float)w[j].y * kInvQ30};
@@ -742,7 +806,7 @@ template <int LAYOUT> struct GaugeAcc<LQ_I32S, 10, LAYOUT> {
 };
 
 // FP32 pairs: one float4 chunk = one complex entry; 9 (LINK18) or 6 (LINK12) per link
-template <int FMT, int LAYOUT> struct GaugeAcc<LQ_F64X, FMT, LAYOUT> {
+template <int FMT, int LAYOUT> struct GaugeAcc<LQ_F64X, FMT, LAYOUT> : SlotBounds {
     using Real = dd;
     static constexpr int K = FMT / 2;
     const float4* ptr;
@@ -751,7 +815,7 @@ template <int FMT, int LAYOUT> struct GaugeAcc<LQ_F64X, FMT, LAYOUT> {
         const uint32_t b = lk_base<LAYOUT>(s, mu, K, Vh), ks = lk_kstride<LAYOUT>(Vh);
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            float4 v = ld<true>(ptr + b + k * ks);
+            float4 v = at<true>(ptr, b, k * ks);
             U.u[k / 3][k % 3] = {dd{v.x, v.y}, dd{v.z, v.w}};
         }
         if constexpr (FMT == 12) reconstruct_row2(U);

@@ -116,6 +116,124 @@ template <typename T> struct PerRhs { T v[kMaxRhs]; };
 // ------------------------------------------------------------------------------------
 // inner-loop kernels
 // ------------------------------------------------------------------------------------
+// K1: t = a p + b hop(p), ||t||^2 -> alpha
+template <class TA, class PA>
+struct EpiK1 {
+    using Real = typename TA::Real;
+    static constexpr int NRED = 1;
+    TA t;
+    PA p;
+    Real a, b;
+    RedCtx rc;
+    int nr;
+    bool on;
+    LQ_HD bool init() {
+        if (rc.st->all_stop) return false;
+        on = rc.st->stop[thread_rhs(nr)] == 0;
+        return true;
+    }
+    LQ_HD bool active() const { return on; }
+    template <typename R>
+    LQ_HD void apply(const Site& s, const Spinor<R>& acc, double* red) const {
+        Spinor<R> pv, o;
+        p.load(s, pv);
+#pragma unroll
+        for (int k = 0; k < 12; ++k)
+            o.v[k] = {fma((R)b, acc.v[k].re, (R)a * pv.v[k].re), fma((R)b, acc.v[k].im, (R)a * pv.v[k].im)};
+        t.store(s, o);
+        red[0] += to_double(norm2(o));
+    }
+    template <int BS> __device__ __forceinline__ void finish(const double (&red)[1], const VGrid& vg) const {
+        SolverState* st = rc.st;
+        const int n = nr;
+        grid_reduce_seg<BS, 1>(rc, kTicketK1, red, n, vg, [st, n](const double* tot) {
+            for (int j = 0; j < n; ++j) {
+                if (st->stop[j]) continue;
+                const double sg = tot[j];
+                st->sigma[j] = sg;
+                if (!isfinite(sg)) {
+                    st->stop[j] = 3;
+                    st->alpha[j] = 0.0;
+                } else if (!(sg > 0.0)) {
+                    st->stop[j] = 2;
+                    st->alpha[j] = 0.0;
+                } else {
+                    st->alpha[j] = st->rho[j] / sg;
+                }
+            }
+        });
+    }
+};
+
+// K2: q = a t + b hop^dag(t); psi += alpha p; r -= alpha q; ||r||^2 -> beta, stop test
+template <class TA, class PA, class XA, class RA>
+struct EpiK2 {
+    using Real = typename RA::Real;
+    static constexpr int NRED = 1;
+    TA t;
+    PA p;
+    XA x;
+    RA r;
+    Real a, b;
+    RedCtx rc;
+    int nr;
+    Real alpha;
+    bool on;
+    LQ_HD bool init() {
+        if (rc.st->all_stop) return false;
+        const int j = thread_rhs(nr);
+        on = rc.st->stop[j] == 0;
+        alpha = from_double<Real>(rc.st->alpha[j]);
+        return true;
+    }
+    LQ_HD bool active() const { return on; }
+    // psi is read once per site and never by a neighbour: asked for before the stencil, its
+    // load after the eight hops hits L1 (K2 6% faster on the 32^4 workload; prefetching the
+    // other fields as well gained nothing more)
+    LQ_HD void prefetch(const Site& s) const { x.prefetch(s); }
+    template <typename R>
+    LQ_HD void apply(const Site& s, const Spinor<R>& acc, double* red) const {
+        Spinor<R> tv, pv, xv, rv;
+        t.load(s, tv);
+        p.load(s, pv);
+        x.load(s, xv);
+        r.load(s, rv);
+        const R al = (R)alpha;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            const R qre = fma((R)b, acc.v[k].re, (R)a * tv.v[k].re);
+            const R qim = fma((R)b, acc.v[k].im, (R)a * tv.v[k].im);
+            xv.v[k] = {fma(al, pv.v[k].re, xv.v[k].re), fma(al, pv.v[k].im, xv.v[k].im)};
+            rv.v[k] = {fma(-al, qre, rv.v[k].re), fma(-al, qim, rv.v[k].im)};
+        }
+        x.store(s, xv);
+        r.store(s, rv);
+        red[0] += to_double(norm2(rv));
+    }
+    template <int BS> __device__ __forceinline__ void finish(const double (&red)[1], const VGrid& vg) const {
+        SolverState* st = rc.st;
+        const int n = nr;
+        grid_reduce_seg<BS, 1>(rc, kTicketK2, red, n, vg, [st, n](const double* tot) {
+            int all = 1;
+            for (int j = 0; j < n; ++j) {
+                if (!st->stop[j]) {
+                    const double rn = tot[j];
+                    st->iter[j] += 1;
+                    if (!isfinite(rn)) {
+                        st->stop[j] = 3;
+                    } else {
+                        st->beta[j] = rn / st->rho[j];
+                        st->rho[j] = rn;
+                        if (rn <= st->stop_rho[j] || st->iter[j] >= st->k_max) st->stop[j] = 1;
+                    }
+                }
+                all &= (st->stop[j] != 0);
+            }
+            st->all_stop = all;
+        });
+    }
+};
+
 // The right-hand sides a thread serves: RB consecutive ones starting at this value (the
 // maps give every thread a fixed group).
 LQ_HD int thread_rhs0(int nr, int rb) {
@@ -128,10 +246,10 @@ LQ_HD int thread_rhs0(int nr, int rb) {
 #endif
 }
 
-// K1: t = a p + b hop(p), ||t||^2 -> alpha.  RB right-hand sides per thread (register
-// blocking: the stencil has applied each link to all of them).
-template <class TA, class PA, int RB = 1>
-struct EpiK1 {
+// K1 with RB > 1 right-hand sides per thread (register blocking: the stencil has applied
+// each link to all of them); the single-right-hand-side form EpiK1 is above.
+template <class TA, class PA, int RB>
+struct EpiK1Blk {
     using Real = typename TA::Real;
     static constexpr int kRB = RB;
     static constexpr int NRED = RB;
@@ -201,9 +319,9 @@ struct EpiK1 {
     }
 };
 
-// K2: q = a t + b hop^dag(t); psi += alpha p; r -= alpha q; ||r||^2 -> beta, stop test
-template <class TA, class PA, class XA, class RA, int RB = 1>
-struct EpiK2 {
+// K2 with RB > 1 right-hand sides per thread; the single-right-hand-side form EpiK2 is above.
+template <class TA, class PA, class XA, class RA, int RB>
+struct EpiK2Blk {
     using Real = typename RA::Real;
     static constexpr int kRB = RB;
     static constexpr int NRED = RB;
@@ -852,17 +970,19 @@ struct Solve {
     using FullMap = typename std::conditional<IL == LQ_LAYOUT_LEX, MapLex<B>, MapEoFull<B>>::type;
     template <int B>
     using FullHMap = typename std::conditional<HL == LQ_LAYOUT_LEX, MapLex<B>, MapEoFull<B>>::type;
-    using IMap = typename std::conditional<SCHUR, MapEoHalf<IBS>, FullMap<IBS>>::type;
+    using IMap = typename std::conditional<SCHUR, MapEoHalf<IBS>,
+                                           typename std::conditional<RB == 1, FullMap<IBS>, MapEoFullRB<IBS>>::type>::type;
     using ISiteMap = typename std::conditional<SCHUR, MapEoHalf<kSiteBS>, FullMap<kSiteBS>>::type;
     using HMap = typename std::conditional<SCHUR, MapEoHalf<kBS>, FullHMap<kBS>>::type;
     using HSiteMap = typename std::conditional<SCHUR, MapEoHalf<kSiteBS>, FullHMap<kSiteBS>>::type;
     using K1Sten = Stencil<GA, SpRO, false>;
-    using K1Epi = EpiK1<SpRW, SpRO, RB>;
+    using K1Epi = typename std::conditional<RB == 1, EpiK1<SpRW, SpRO>, EpiK1Blk<SpRW, SpRO, RB>>::type;
     using K2Sten = Stencil<GA, SpRO, true>;
     static constexpr int PSIP = psi_prec(IP);
     using PsiRO = SpinorAcc<PSIP, IL, true>;
     using PsiRW = SpinorAcc<PSIP, IL, false>;
-    using K2Epi = EpiK2<SpRO, SpRO, PsiRW, SpRW, RB>;
+    using K2Epi = typename std::conditional<RB == 1, EpiK2<SpRO, SpRO, PsiRW, SpRW>,
+                                            EpiK2Blk<SpRO, SpRO, PsiRW, SpRW, RB>>::type;
     using K3Op = OpK3<SpRW, SpRO>;
     using PreEpi = EpiPreHop<SpRW>;
     static constexpr bool kPairs = (HP == LQ_F64X);
@@ -1098,6 +1218,7 @@ struct Solve {
     // state record, field conversions, ||eta||, x = 0 for zero right-hand sides, and the
     // first outer residual
     int begin() {
+        NvtxRange nvtx("lq solve: set-up (conversions, norms, first residual)");
         cudaError_t e;
         if (prof) {
             evs.ev.resize(6 * chunk + 2);
@@ -1233,6 +1354,7 @@ struct Solve {
 
     // cycle start (Algorithm 1)
     int start_cycle() {
+        NvtxRange nvtx("lq solve: cycle start (Algorithm 1 restart)");
         OpRestart<HiRO, SpRW, SpRW, PsiRW> op;
         op.rh = rh_ro;
         op.r = r_rw;
@@ -1273,6 +1395,7 @@ struct Solve {
     // the inner CG of one lattice: chunks of K1, K2, K3 until every right-hand side has
     // stopped; leaves the final state record in hs
     int inner_single() {
+        NvtxRange nvtx("lq solve: inner CG");
         cudaError_t e;
         if (!prof && !graph_off && (prm.flags & LQ_CG_NO_GRAPH) == 0) {
             // the whole inner loop on the device: one graph launch, one read-back
@@ -1344,6 +1467,7 @@ struct Solve {
     // outcome of the cycle (hs holds the final inner state), psi^high += s psi_k, and the
     // outer residual
     int end_cycle() {
+        NvtxRange nvtx("lq solve: reliable update (solution, FP64-class residual)");
         cudaError_t e;
         PerRhs<HReal> xs{};
         PerRhs<int> xact{};
@@ -1391,6 +1515,7 @@ struct Solve {
 
     // write-back, per-right-hand-side records; returns the worst status
     int finish(lq_cg_info* info) {
+        NvtxRange nvtx("lq solve: write-back");
         cudaError_t e;
         if constexpr (SCHUR) {
             // x_o = (b_o - H_oe x_e) / A

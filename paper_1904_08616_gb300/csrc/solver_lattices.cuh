@@ -312,6 +312,7 @@ int run_lattices_bs(int n, const LatticeJob* jobs, const lq_cg_params& prm, doub
             any |= in_cycle[l];
         }
         if (!any) break;
+        NvtxRange nvtx("lq lattices: inner CG of every running lattice");
         if (device_loop) {
             if ((e = cudaGraphLaunch(lg.exec, st)) != cudaSuccess) return cuda_fail(e, "inner-loop graph");
         } else if (use_graph) {

@@ -205,3 +205,13 @@ def test_noalloc_array_size_against_the_workspace_query(lqlib):
     for mode in ("f64", "f64x", "mixed_f32", "mixed_f16", "mixed_i32"):
         assert 0 < lqlib.cg_workspace_bytes((12, 12, 12, 12), mode) <= cap, mode
         assert lqlib.cg_workspace_bytes((16, 16, 16, 16), mode) > cap, mode
+
+
+def test_checked_build_exports_every_declared_symbol(lqlib):
+    """The bounds-checked debug variant is the same library with checks compiled in: it
+    builds (nvcc cross-compiles here) and exports the same entry points."""
+    from paper_1904_08616_gb300 import build as B
+    path = B.build(checked=True)
+    L = ctypes.CDLL(path)
+    for name in declared_functions():
+        assert hasattr(L, name), name
