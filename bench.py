@@ -482,10 +482,10 @@ def run_workload(args):
             probs.append({"dims": dims, "m_q": 0.1, "nrhs": nr, "U": field(synth.gauge_field(dims, seed=960 + 100 * i)),
                           "eta": spinors(dims, [961 + 100 * i + r for r in range(nr)])})
 
-        def one():
+        def one(own=False):
             kw = {"block": args.lattice_block} if args.lattice_block else {"autotune": True}
             _, infos, st = lq.cg_solve_lattices(probs, mode=args.mode, tol=TOL, graph=args.inner_loop == "device",
-                                                 **kw)
+                                                 own_cycles=own, **kw)
             assert st == 0
             return infos
 
@@ -498,11 +498,14 @@ def run_workload(args):
             return allinf
 
         ms, infos = _timed(one, args.steps, args.warmup)
+        ms_own = _timed(lambda: one(True), args.steps, args.warmup)[0]
         ms_seq = None if args.no_compare else _timed(seq, args.steps, args.warmup)[0]
         upd = sum(_updates(p["dims"], inf) for p, inf in zip(probs, infos))
         line.update({"config": {"lattices": [list(d) + [n] for d, n in specs], "m_q": 0.1, "links": "haar",
                                 "tol": TOL},
                      "value": upd / (ms * 1e-3), "ms_per_solve": ms, "ms_sequential_multi": ms_seq,
+                     "ms_per_solve_own_cycles": ms_own,
+                     "speedup_vs_sequential": (ms_seq / ms) if ms_seq else None,
                      "block": infos[0][0]["block"], "iters": [max(i["iters"] for i in li) for li in infos],
                      "inner_loop": args.inner_loop})
     elif args.workload == "batched":

@@ -238,6 +238,11 @@ typedef struct lq_cg_params {
                                     inner links; the others always use 1)                     */
 #define LQ_CG_RHS_BLOCK_2 0x2000
 #define LQ_CG_RHS_BLOCK_4 0x4000
+#define LQ_CG_LATTICE_OWN_CYCLES 0x800 /* lq_cg_solve_lattices: each lattice takes its reliable
+                                    update as soon as its own inner loop stops while the others
+                                    go on; by default the batch runs until every lattice's inner
+                                    loop has stopped and takes all of them in one host round
+                                    trip                                                       */
 #define LQ_CG_BLOCK_64 0x100 /* lq_cg_solve_lattices: inner block size 64 / 128 / 256 threads */
 #define LQ_CG_BLOCK_128 0x200 /*   (at most one; overrides LQ_CG_AUTOTUNE)                  */
 #define LQ_CG_BLOCK_256 0x400

@@ -31,6 +31,7 @@ LAYOUT = {"lex": 0, "eo": 1}
 CG_MODE = {"f64": 0, "mixed_f32": 1, "mixed_f16": 2, "f64x": 3, "mixed_i32": 4}
 CG_PROFILE, CG_NATIVE_F64, CG_LINK18, CG_AUTOTUNE, CG_NO_GRAPH, CG_LINK10 = 1, 2, 4, 8, 16, 32
 CG_RHS_BLOCK_1, CG_RHS_BLOCK_2, CG_RHS_BLOCK_4 = 0x1000, 0x2000, 0x4000
+CG_LATTICE_OWN_CYCLES = 0x800
 STATUS = {0: "OK", 1: "NOT_CONVERGED", -1: "ERR_ARG", -2: "ERR_DIMS", -3: "ERR_ALIGN",
           -4: "ERR_CUDA", -5: "ERR_WORKSPACE", -6: "ERR_NONFINITE", -7: "ERR_BREAKDOWN"}
 
@@ -441,11 +442,14 @@ def cg_workspace_bytes_lattices(problems, mode="mixed_f32") -> int:
 
 
 def cg_solve_lattices(problems, mode="mixed_f32", tol=1e-10, max_iter=100000, max_cycles=0, delta=0.0, chunk=0, max_inner=0,
-                      workspace=None, stream=None, autotune=False, graph=True, block=None):
+                      workspace=None, stream=None, autotune=False, graph=True, block=None, own_cycles=False):
     """Solve several lattices of different sizes together (lq_cg_solve_lattices).
 
     problems: list of dicts {"dims", "m_q", "U", "eta", "nrhs" (1, 2, 4 or 8), "x" (optional
     start guess)}, U an F64 LEX 18-real gauge field, eta / x nrhs stacked F64 LEX spinors.
+    own_cycles=True lets each lattice take its reliable update as soon as its own inner loop
+    stops (default: the batch's reliable updates are taken together, one host round trip per
+    round of cycles).
     Returns ([x per lattice], [[info per right-hand side] per lattice], status).
     """
     import torch
@@ -466,7 +470,7 @@ def cg_solve_lattices(problems, mode="mixed_f32", tol=1e-10, max_iter=100000, ma
     wb = int(load().lq_cg_workspace_bytes_lattices(len(problems), arr, m))
     if workspace is None:
         workspace = _empty_bytes(wb, problems[0]["eta"])
-    flags = (CG_AUTOTUNE if autotune else 0) | (0 if graph else CG_NO_GRAPH)
+    flags = (CG_AUTOTUNE if autotune else 0) | (0 if graph else CG_NO_GRAPH) | (CG_LATTICE_OWN_CYCLES if own_cycles else 0)
     if block is not None:
         flags |= {64: 0x100, 128: 0x200, 256: 0x400}[int(block)]
     prm = CgParams(float(tol), int(max_iter), int(max_cycles), float(delta), int(chunk), flags, int(max_inner))

@@ -1466,7 +1466,11 @@ struct Solve {
 
     // outcome of the cycle (hs holds the final inner state), psi^high += s psi_k, and the
     // outer residual
-    int end_cycle() {
+    // The outcome of the cycle (hs holds the final inner state): psi^high += s psi_k and the
+    // outer residual are enqueued here; end_cycle_collect() takes the residual once the state
+    // record has been read back (several lattices share that one read); end_cycle() does both.
+    PerRhs<int> xact_pending{};
+    int end_cycle_launch() {
         NvtxRange nvtx("lq solve: reliable update (solution, FP64-class residual)");
         cudaError_t e;
         PerRhs<HReal> xs{};
@@ -1486,15 +1490,18 @@ struct Solve {
             xact.v[j] = 1;
             xs.v[j] = from_double<HReal>(s[j]);
         }
+        xact_pending = xact;
         OpXUpdate<HiRW, PsiRO> xu{x_rw, psi_ro, nb, xs, xact, HReal(0), false};
         if ((e = launch_site<kSiteBS>(hsite, xu, st)) != cudaSuccess) return cuda_fail(e, "x update");
         launches += 1;
         if ((e = high_residual()) != cudaSuccess) return cuda_fail(e, "residual");
-        if ((e = read_state()) != cudaSuccess) return cuda_fail(e, "residual");
+        return LQ_OK;
+    }
+    void end_cycle_collect() {
         account_high();
         high_applies += 1;
         for (int j = 0; j < nb; ++j) {
-            if (!xact.v[j]) continue;
+            if (!xact_pending.v[j]) continue;
             const double s_new = sqrt(hs.red[2][j]);
             // stagnation: cycles since the true residual last improved on its best by 0.1%
             if (s_new < 0.999 * best[j]) {
@@ -1510,6 +1517,13 @@ struct Solve {
             out[j].cycles += 1;
         }
         ++l;
+    }
+    int end_cycle() {
+        int r;
+        if ((r = end_cycle_launch()) != LQ_OK) return r;
+        cudaError_t e;
+        if ((e = read_state()) != cudaSuccess) return cuda_fail(e, "residual");
+        end_cycle_collect();
         return LQ_OK;
     }
 

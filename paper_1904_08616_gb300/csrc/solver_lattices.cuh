@@ -175,6 +175,7 @@ struct ChunkGraph {
 struct LatLoopArgs {
     SolverState* st[kMaxLat];
     int n;
+    int together;   // run until every lattice's inner loop has stopped (else until one has)
 };
 
 static __global__ void lattice_loop_base(LatLoopArgs a) {
@@ -196,7 +197,8 @@ static __global__ void lattice_loop_cond(cudaGraphConditionalHandle h, LatLoopAr
         for (int l = 0; l < a.n; ++l) idle += a.st[l]->all_stop ? 1 : 0;
         SolverState* s0 = a.st[0];
         const int t = ++s0->loop_trips;
-        cudaGraphSetConditional(h, (idle == s0->loop_base && idle < a.n && t < s0->loop_cap) ? 1u : 0u);
+        const bool more = a.together ? idle < a.n : (idle == s0->loop_base && idle < a.n);
+        cudaGraphSetConditional(h, (more && t < s0->loop_cap) ? 1u : 0u);
     }
 }
 
@@ -281,9 +283,13 @@ int run_lattices_bs(int n, const LatticeJob* jobs, const lq_cg_params& prm, doub
     // graph cannot be built, chunks of iterations captured as a plain graph
     LoopGraph lg;
     bool device_loop = false;
+    // reliable updates of all lattices taken together (one host round trip per round of
+    // cycles), unless each lattice is to take its own as soon as its inner loop stops
+    const bool together = (prm.flags & LQ_CG_LATTICE_OWN_CYCLES) == 0;
     if (use_graph) {
         LatLoopArgs la{};
         la.n = n;
+        la.together = together ? 1 : 0;
         for (int l = 0; l < n; ++l) la.st[l] = sv[l].dstate;
         if (lg.build(il, la) == cudaSuccess) {
             device_loop = true;
@@ -330,15 +336,29 @@ int run_lattices_bs(int n, const LatticeJob* jobs, const lq_cg_params& prm, doub
         // prologue and one condition kernel per trip)
         const int trips = device_loop ? sv[0].hs.loop_trips : chunk;
         for (int l = 0; l < n; ++l) sv[l].launches += device_loop ? 4 * trips + 1 : 3 * chunk;
+        bool ended[kMaxLat] = {};
+        int n_in = 0, n_ended = 0;
         for (int l = 0; l < n; ++l) {
             if (!in_cycle[l]) continue;
+            ++n_in;
             // iterations launched in this lattice's cycle; K2 stops every right-hand side at
             // k_max, so this guard never decides
             sv[l].guard += trips;
-            if (sv[l].hs.all_stop || sv[l].guard > sv[l].k_max + 2 * (device_loop ? 1 : chunk)) {
-                if ((r = sv[l].end_cycle()) != LQ_OK) return r;
-                in_cycle[l] = false;
-            }
+            ended[l] = sv[l].hs.all_stop || sv[l].guard > sv[l].k_max + 2 * (device_loop ? 1 : chunk);
+            n_ended += ended[l] ? 1 : 0;
+        }
+        if (n_ended == 0 || (together && n_ended < n_in)) continue;
+        // the ended lattices' reliable updates: solution updates and outer residuals enqueued
+        // for all of them, one read-back of their state records, then each one's outcome
+        for (int l = 0; l < n; ++l)
+            if (ended[l] && (r = sv[l].end_cycle_launch()) != LQ_OK) return r;
+        for (int l = 0; l < n; ++l)
+            if (ended[l] && (e = sv[l].read_state_async()) != cudaSuccess) return cuda_fail(e, "residual");
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "residual");
+        for (int l = 0; l < n; ++l) {
+            if (!ended[l]) continue;
+            sv[l].end_cycle_collect();
+            in_cycle[l] = false;
         }
     }
     int worst = LQ_OK, at = 0;

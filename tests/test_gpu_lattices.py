@@ -56,13 +56,15 @@ def test_lattices_against_oracle(lqlib, mode):
 
 
 @pytest.mark.parametrize("mode", ["mixed_f32", "mixed_f16"])
-def test_lattices_graph_replay_equals_direct_launches(lqlib, mode):
-    """The device-driven loop (a conditional graph that returns whenever one lattice's cycle
-    ends; the lattices have different masses, so their cycles end at different iterations)
-    runs exactly the kernels a direct launch sequence issues."""
+@pytest.mark.parametrize("own_cycles", [False, True])
+def test_lattices_graph_replay_equals_direct_launches(lqlib, mode, own_cycles):
+    """The device-driven loop (a conditional graph that returns when every lattice's inner
+    loop has stopped, or with own_cycles when one has; the lattices have different masses, so
+    their cycles end at different iterations) runs exactly the kernels a direct launch
+    sequence issues."""
     host, probs = _problems(SMALL, seed=910)
-    xa, ia, sa = lqlib.cg_solve_lattices(probs, mode=mode, tol=1e-10, graph=True)
-    xb, ib, sb = lqlib.cg_solve_lattices(probs, mode=mode, tol=1e-10, graph=False)
+    xa, ia, sa = lqlib.cg_solve_lattices(probs, mode=mode, tol=1e-10, graph=True, own_cycles=own_cycles)
+    xb, ib, sb = lqlib.cg_solve_lattices(probs, mode=mode, tol=1e-10, graph=False, own_cycles=own_cycles)
     assert sa == sb == 0
     for a, b in zip(xa, xb):
         assert np.array_equal(to_host(a), to_host(b))
@@ -155,3 +157,18 @@ def test_lattices_full_size_uneven_workload(lqlib):
         assert all(i["status"] == 0 and i["true_rel_resid"] <= 1e-10 for i in inf)
         for r in (0, 3):
             assert _true_resid(dims, m, U, etas[r], sol[r]) <= 1e-10 * RESID_SLACK
+
+
+@pytest.mark.parametrize("mode", ["mixed_f32", "mixed_f16", "f64"])
+def test_lattices_cycles_together_equal_cycles_apart(lqlib, mode):
+    """Taking the reliable updates of all lattices together (a lattice whose inner loop has
+    stopped waits, its blocks idle, until the others' have) changes no lattice's sequence of
+    operations: the solutions are the same bits as with each lattice's own cycles."""
+    host, probs = _problems(SMALL, seed=930)
+    xa, ia, sa = lqlib.cg_solve_lattices(probs, mode=mode, tol=1e-10)
+    xb, ib, sb = lqlib.cg_solve_lattices(probs, mode=mode, tol=1e-10, own_cycles=True)
+    assert sa == sb == 0
+    for a, b in zip(xa, xb):
+        assert np.array_equal(to_host(a), to_host(b))
+    for la, lb in zip(ia, ib):
+        assert [(r["iters"], r["cycles"]) for r in la] == [(r["iters"], r["cycles"]) for r in lb]
