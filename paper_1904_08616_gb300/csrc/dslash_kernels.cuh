@@ -234,7 +234,96 @@ __device__ __forceinline__ void hop(Spinor<float>& acc, const uint32_t q[12], co
     hop_matvec<BACK>(U, f0, f1, g0, g1);
     hop_accumulate<MU, S, true>(acc, g0, g1, sc);
 }
+
+// The same hop with the stored FP16 rows 0 and 1 of a 12-real link used as they are: each
+// product of two FP16 values is exact in FP32, so an FP32 fused multiply-add with FP16
+// multiplicands (one rounding, as after exact widening) replaces the widening of the twelve
+// link halves.  Row 2 = conj(row 0 x row 1) is rebuilt in FP32 the same way, and only the
+// projected components that meet row 2 are widened.
+struct hw {
+    uint16_t re, im;
+};
+__device__ __forceinline__ hw split(uint32_t w) {
+    hw h;
+    asm("mov.b32 {%0, %1}, %2;" : "=h"(h.re), "=h"(h.im) : "r"(w));
+    return h;
+}
+// c + a b  (a, b FP16, c and the result FP32)
+__device__ __forceinline__ float fmah(uint16_t a, uint16_t b, float c) {
+    float d;
+    asm("fma.rn.f32.f16 %0, %1, %2, %3;" : "=f"(d) : "h"(a), "h"(b), "f"(c));
+    return d;
+}
+// -a for an FP16 value (folded into the multiply-add that consumes it)
+__device__ __forceinline__ uint16_t hneg(uint16_t a) {
+    uint16_t d;
+    asm("neg.f16 %0, %1;" : "=h"(d) : "h"(a));
+    return d;
+}
+// c + u h and c + conj(u) h for an FP16 link entry u and an FP16 value h
+__device__ __forceinline__ cplx<float> cfmah(hw u, hw h, cplx<float> c) {
+    return {fmah(u.re, h.re, fmah(hneg(u.im), h.im, c.re)), fmah(u.re, h.im, fmah(u.im, h.re, c.im))};
+}
+__device__ __forceinline__ cplx<float> cfmach(hw u, hw h, cplx<float> c) {
+    return {fmah(u.re, h.re, fmah(u.im, h.im, c.re)), fmah(u.re, h.im, fmah(hneg(u.im), h.re, c.im))};
+}
+
+template <int MU, int S, bool BACK>
+__device__ __forceinline__ void hop_rows(Spinor<float>& acc, const uint32_t q[12], const uint32_t lw[6], float sc) {
+    __half2 h0[3], h1[3];
+    project<MU, S>(q, h0, h1);
+    hw u[2][3], a0[3], a1[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        u[0][c] = split(lw[c]);
+        u[1][c] = split(lw[3 + c]);
+        a0[c] = split(h2w(h0[c]));
+        a1[c] = split(h2w(h1[c]));
+    }
+    // row 2: r[k] = conj(u0[i] u1[j] - u0[j] u1[i]), (i, j, k) cyclic
+    cplx<float> r2[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int i = (k + 1) % 3, j = (k + 2) % 3;
+        const hw ai = u[0][i], aj = u[0][j], bi = u[1][i], bj = u[1][j];
+        r2[k].re = fmah(ai.re, bj.re, fmah(hneg(ai.im), bj.im, fmah(hneg(aj.re), bi.re, fmah(aj.im, bi.im, 0.f))));
+        r2[k].im = fmah(hneg(ai.re), bj.im, fmah(hneg(ai.im), bj.re, fmah(aj.re, bi.im, fmah(aj.im, bi.re, 0.f))));
+    }
+    const cplx<float> z{0.f, 0.f};
+    cplx<float> g0[3], g1[3];
+    if constexpr (!BACK) {
+        // g[A] = sum_B U[A][B] h[B]; row 2 meets every component, widened
+        cplx<float> f0[3], f1[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float2 a = __half22float2(h0[c]), b = __half22float2(h1[c]);
+            f0[c] = {a.x, a.y};
+            f1[c] = {b.x, b.y};
+        }
+#pragma unroll
+        for (int A = 0; A < 2; ++A) {
+            g0[A] = cfmah(u[A][2], a0[2], cfmah(u[A][1], a0[1], cfmah(u[A][0], a0[0], z)));
+            g1[A] = cfmah(u[A][2], a1[2], cfmah(u[A][1], a1[1], cfmah(u[A][0], a1[0], z)));
+        }
+        g0[2] = cfma(r2[2], f0[2], cfma(r2[1], f0[1], cmul(r2[0], f0[0])));
+        g1[2] = cfma(r2[2], f1[2], cfma(r2[1], f1[1], cmul(r2[0], f1[0])));
+    } else {
+        // g[A] = sum_B conj(U[B][A]) h[B]; row 2 meets h[2] only
+        const float2 a = __half22float2(h0[2]), b = __half22float2(h1[2]);
+        const cplx<float> f02{a.x, a.y}, f12{b.x, b.y};
+#pragma unroll
+        for (int A = 0; A < 3; ++A) {
+            g0[A] = cfmac(r2[A], f02, cfmach(u[1][A], a0[1], cfmach(u[0][A], a0[0], z)));
+            g1[A] = cfmac(r2[A], f12, cfmach(u[1][A], a1[1], cfmach(u[0][A], a1[0], z)));
+        }
+    }
+    hop_accumulate<MU, S, true>(acc, g0, g1, sc);
+}
 }  // namespace h2
+
+// gauge accessors that expose the stored FP16 rows of 12-real links (load_rows_h2)
+template <class A, class = void> struct HasRowsH2 : std::false_type {};
+template <class A> struct HasRowsH2<A, std::void_t<decltype(A::kRowsH2)>> : std::bool_constant<A::kRowsH2> {};
 
 // spinor accessors of scaled-FP16 fields expose their stored half2 words (load_h2)
 template <class A, class = void> struct HasHalf2 : std::false_type {};
@@ -262,7 +351,17 @@ struct Stencil {
         const Site nb = nb_site(lex_bwd(g, s.lex, c, MU), s.p, s.rhs);
         constexpr bool SC = SA::kScaled;
 #ifdef __CUDA_ARCH__
-        if constexpr (kHalf) {
+        if constexpr (kHalf && HasRowsH2<GA>::value) {
+            uint32_t q[12], lw[6];
+            float sc;
+            sa.load_h2(nf, q, sc);
+            ga.load_rows_h2(s, MU, lw);
+            h2::hop_rows<MU, SF, false>(acc, q, lw, sc);
+            sa.load_h2(nb, q, sc);
+            ga.load_rows_h2(nb, MU, lw);
+            h2::hop_rows<MU, -SF, true>(acc, q, lw, sc);
+            return;
+        } else if constexpr (kHalf) {
             uint32_t q[12];
             float sc;
             Link<float> U;

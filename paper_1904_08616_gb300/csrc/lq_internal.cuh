@@ -642,8 +642,19 @@ template <int LAYOUT> struct GaugeAcc<LQ_F16S, 18, LAYOUT> : SlotBounds {
 template <int LAYOUT> struct GaugeAcc<LQ_F16S, 12, LAYOUT> : SlotBounds {
     using Real = float;
     static constexpr int K = 3;
+    static constexpr bool kRowsH2 = true;
     const uint2* ptr;
     uint32_t Vh;
+    // the stored rows 0 and 1 as half2 words (w[3 r + c] = U[r][c], re low, im high)
+    LQ_HD void load_rows_h2(const Site& s, int mu, uint32_t w[6]) const {
+        const uint32_t b = lk_base<LAYOUT>(s, mu, K, Vh), ks = lk_kstride<LAYOUT>(Vh);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const uint2 v = at<true>(ptr, b, k * ks);
+            w[2 * k] = v.x;
+            w[2 * k + 1] = v.y;
+        }
+    }
     LQ_HD void load(const Site& s, int mu, Link<float>& U) const {
         const uint32_t b = lk_base<LAYOUT>(s, mu, K, Vh), ks = lk_kstride<LAYOUT>(Vh);
 #pragma unroll
