@@ -233,9 +233,9 @@ typedef struct lq_cg_params {
 #define LQ_CG_RHS_BLOCK_1 0x1000 /* lq_cg_solve_multi: right-hand sides per thread in the inner
                                     stencil kernels (register blocking: each link is decoded once
                                     and applied to that many right-hand sides of a site); at most
-                                    one flag, capped at the batch size; default 2 with
-                                    scaled-FP16 inner fields, else 1 (mixed modes with 12-real
-                                    inner links; the others always use 1)                     */
+                                    one flag, capped at the batch size; default 1 (blocking
+                                    applies to mixed modes with 12-real inner links; the
+                                    others always use 1)                                      */
 #define LQ_CG_RHS_BLOCK_2 0x2000
 #define LQ_CG_RHS_BLOCK_4 0x4000
 #define LQ_CG_LATTICE_OWN_CYCLES 0x800 /* lq_cg_solve_lattices: each lattice takes its reliable

@@ -1581,18 +1581,15 @@ int run_solver_rb(const Geom& g, double m_q, int nb, const void* U, const void* 
 }
 
 // Right-hand sides per thread for a batch of nb: the LQ_CG_RHS_BLOCK_* flag if one is set
-// (capped at nb); by default 2 for scaled-FP16 inner fields and 1 otherwise.  Measured on
-// the 24^3 x 48 workload with 12 right-hand sides (one GB300): scaled FP16 123.6 / 119.7 /
-// 141.7 ms and FP32 128.0 / 130.7 / 175.0 ms for 1 / 2 / 4 right-hand sides per thread.  The
-// link is decoded once per direction for all of them, but their accumulators raise the
-// kernels' registers (K1 80 -> 128 -> 255, K2 96 -> 167 -> 253 with scaled FP16), which
-// costs resident warps; only the scaled-FP16 stencil, whose link decode is the larger part
-// of each hop, gains.
-inline int rhs_block(const lq_cg_params& prm, int nb, int inner_prec) {
-    int rb = (prm.flags & LQ_CG_RHS_BLOCK_4) ? 4
-             : (prm.flags & LQ_CG_RHS_BLOCK_2) ? 2
-             : (prm.flags & LQ_CG_RHS_BLOCK_1) ? 1
-             : (inner_prec == LQ_F16S ? 2 : 1);
+// (capped at nb), else 1.  Measured on the 24^3 x 48 workload with 12 right-hand sides (one
+// GB300): scaled FP16 114.1 / 119.0 / 140.2 ms and FP32 127.4 / 130.7 / 174.8 ms for 1 / 2 /
+// 4 right-hand sides per thread.  The link is decoded once per direction for all of them,
+// but their accumulators raise the kernels' registers (scaled FP16 K1 96 -> 168 -> 251, K2
+// 128 -> 168 -> 249), which costs resident warps; since the scaled-FP16 hop multiplies with
+// the stored FP16 link rows directly, its link decode is too small a part of a hop for
+// blocking to pay.
+inline int rhs_block(const lq_cg_params& prm, int nb) {
+    int rb = (prm.flags & LQ_CG_RHS_BLOCK_4) ? 4 : (prm.flags & LQ_CG_RHS_BLOCK_2) ? 2 : 1;
     while (rb > nb) rb >>= 1;
     return rb;
 }
@@ -1601,7 +1598,7 @@ template <int IP, int IF, int IL, int HP, bool SCHUR = false>
 int run_solver(const Geom& g, double m_q, int nb, const void* U, const void* eta, void* x, const lq_cg_params& prm,
                double delta, const WsLayout& w, char* ws, lq_cg_info* info, cudaStream_t st) {
     if constexpr (!SCHUR && IL == LQ_LAYOUT_EO && IF == 12 && !std::is_same<typename PrecT<IP>::Real, dd>::value) {
-        const int rb = rhs_block(prm, nb, IP);
+        const int rb = rhs_block(prm, nb);
         if (rb == 4) return run_solver_rb<IP, IF, IL, HP, SCHUR, 4>(g, m_q, nb, U, eta, x, prm, delta, w, ws, info, st);
         if (rb == 2) return run_solver_rb<IP, IF, IL, HP, SCHUR, 2>(g, m_q, nb, U, eta, x, prm, delta, w, ws, info, st);
     }
