@@ -226,10 +226,11 @@ typedef struct lq_cg_params {
                                 LQ_CG_NATIVE_F64)                                          */
 #define LQ_CG_AUTOTUNE 8     /* lq_cg_solve_lattices: pick the inner block size by timing
                                 (cached per lattice set and GPU); default 128 threads      */
-#define LQ_CG_NO_GRAPH 16    /* launch the inner kernels one by one from the host instead of
-                                running the inner loop in a CUDA graph with a conditional
-                                WHILE node (the default; if the driver refuses such a graph
-                                the host-driven loop runs without this flag too)           */
+#define LQ_CG_NO_GRAPH 16    /* drive the cycles from the host and launch the inner kernels
+                                one by one, instead of running the whole solve's cycles in
+                                one CUDA graph with conditional WHILE nodes (the default; if
+                                the driver refuses such a graph the host-driven loop runs
+                                without this flag too)                                     */
 #define LQ_CG_RHS_BLOCK_1 0x1000 /* lq_cg_solve_multi: right-hand sides per thread in the inner
                                     stencil kernels (register blocking: each link is decoded once
                                     and applied to that many right-hand sides of a site); at most
@@ -240,9 +241,9 @@ typedef struct lq_cg_params {
 #define LQ_CG_RHS_BLOCK_4 0x4000
 #define LQ_CG_LATTICE_OWN_CYCLES 0x800 /* lq_cg_solve_lattices: each lattice takes its reliable
                                     update as soon as its own inner loop stops while the others
-                                    go on; by default the batch runs until every lattice's inner
-                                    loop has stopped and takes all of them in one host round
-                                    trip                                                       */
+                                    go on (the host drives the cycles); by default every
+                                    lattice's cycle ends together and the whole solve runs
+                                    on the device as one graph launch                          */
 #define LQ_CG_BLOCK_64 0x100 /* lq_cg_solve_lattices: inner block size 64 / 128 / 256 threads */
 #define LQ_CG_BLOCK_128 0x200 /*   (at most one; overrides LQ_CG_AUTOTUNE)                  */
 #define LQ_CG_BLOCK_256 0x400
@@ -291,11 +292,14 @@ size_t lq_cg_workspace_bytes_multi(const int32_t dims[4], int32_t mode, int32_t 
  *   workspace, ws_bytes  device scratch of at least lq_cg_workspace_bytes(dims, mode),
  *            16-byte aligned; its contents on entry are ignored.
  *   info     optional (host) statistics.
- * Kernels run on cuda_stream; the call returns after the solve has finished.  Each cycle's
- * inner loop runs as one CUDA graph launch (a conditional WHILE node, the loop condition set
- * on the device from the solver's state record); the host reads the state record back once
- * per cycle.  With LQ_CG_PROFILE or LQ_CG_NO_GRAPH the host launches the inner kernels itself
- * and polls the record between chunks of iterations.
+ * Kernels run on cuda_stream; the call returns after the solve has finished.  After the
+ * set-up (field conversions, norms, the first outer residual) every cycle of Algorithm 1 runs
+ * on the device as one CUDA graph launch: a conditional WHILE node over the cycles, each
+ * holding the restart, a nested WHILE node over the inner iterations and the reliable update,
+ * with every decision (convergence, limits, stagnation, the restart's parameters) taken by
+ * one-thread kernels on the solver's state record; the host reads the record back once, at
+ * the end.  With LQ_CG_PROFILE or LQ_CG_NO_GRAPH the host drives the cycles, launches the
+ * inner kernels itself and polls the record between chunks of iterations.
  * Returns LQ_OK when the FP64 true residual meets tol, LQ_NOT_CONVERGED otherwise.
  */
 int lq_cg_solve(const int32_t dims[4], double m_q, int32_t mode, const void *U,
@@ -387,11 +391,14 @@ int lq_cg_solve_schur(const int32_t dims[4], double m_q, int32_t mode, int32_t n
  *   workspace at least lq_cg_workspace_bytes_lattices(n, lats, mode) bytes.
  *   info     optional, sum of nrhs records in lattice order (block = the inner block size).
  * Each inner-loop kernel is one launch over all lattices (blocks are shared out in
- * proportion to each lattice's sites).  The inner iterations run on the device in a CUDA
- * graph (a conditional WHILE node) until some lattice's inner loop stops; the host then
- * takes that lattice's reliable update (Algorithm 1's outer step) and relaunches while the
- * other lattices go on.  Returns LQ_OK if every solve converged, LQ_NOT_CONVERGED if some did not, or the
- * most negative error status.  Returns after the solves have finished.
+ * proportion to each lattice's sites).  By default the whole batch runs as one CUDA graph
+ * launch: rounds of cycles in a conditional WHILE node, each round restarting every lattice
+ * that needs a cycle, iterating all of them until every inner loop has stopped, and taking
+ * each moved lattice's reliable update (Algorithm 1's outer step) under a conditional IF node;
+ * all decisions are taken on the device.  With LQ_CG_LATTICE_OWN_CYCLES the host takes each
+ * lattice's reliable update as soon as its own inner loop stops while the others go on.
+ * Returns LQ_OK if every solve converged, LQ_NOT_CONVERGED if some did not, or the most
+ * negative error status.  Returns after the solves have finished.
  */
 typedef struct lq_lattice {
     int32_t dims[4];

@@ -331,8 +331,8 @@ def cg_solve(dims, m_q, U, eta, x=None, mode="f64", tol=1e-10, max_iter=100000, 
     mode: "f64", "f64x", "mixed_f32", "mixed_f16" or "mixed_i32"; delta <= 0 takes the mode's
     default inner reduction per cycle; max_inner caps the inner iterations of one cycle
     (0: 1000).  profile=True times the solver's kernels with CUDA
-    events (host-driven inner loop); graph=False launches the inner kernels from the host
-    instead of running each cycle's inner loop in a conditional CUDA graph; native_f64,
+    events (host-driven cycles); graph=False drives the cycles from the host instead of
+    running the whole solve's cycles in one CUDA graph launch; native_f64,
     link18 and link10 select native FP64 outer arithmetic, 18-real and 10-real inner links
     (mixed modes; link10 with the FP32-pair outer loop only).
     """

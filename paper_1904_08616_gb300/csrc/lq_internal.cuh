@@ -840,6 +840,31 @@ template <int FMT, int LAYOUT> struct GaugeAcc<LQ_F64X, FMT, LAYOUT> : SlotBound
 // ------------------------------------------------------------------------------------
 constexpr int kMaxRhs = 8;         // right-hand sides per solver batch (a power of two)
 
+// Algorithm 1's outer loop as data: the quantities of the reliable updates per right-hand
+// side and the parameters of the next cycle's kernels.  The same functions advance it on the
+// host (host-driven solves) or in one-thread kernels inside a solve's CUDA graph.
+struct CycleCtl {
+    double eta_norm[kMaxRhs];   // ||eta||
+    double s[kMaxRhs];          // ||r^high|| of the current iterate (Algorithm 1's s_l)
+    double s_prev[kMaxRhs];     // s of the previous cycle
+    double rho_k[kMaxRhs];      // the last cycle's final inner ||r||^2 (in that cycle's units)
+    double target[kMaxRhs];     // tol * ||eta||
+    double best[kMaxRhs];       // smallest s so far (stagnation test)
+    double is[kMaxRhs];         // next cycle: 1/s
+    double stop_rho[kMaxRhs];   // next cycle: inner stop at rho <= stop_rho
+    double b0[kMaxRhs];         // next cycle: beta_0 of a continued direction
+    double xs[kMaxRhs];         // this cycle's solution update psi^high += xs psi
+    int done[kMaxRhs], first[kMaxRhs], stagnant[kMaxRhs], status[kMaxRhs];
+    int total[kMaxRhs], cycles[kMaxRhs];
+    int act[kMaxRhs];           // next cycle: takes part
+    int cont[kMaxRhs];          // next cycle: continues its direction (act and not first)
+    int xact[kMaxRhs];          // this cycle: solution updated and residual to collect
+    int nb, l, k_max, any_cont, high_applies, launches;
+    int max_cycles, max_iter, per_cycle;
+    int want;                   // another cycle is needed (device-driven lattice batches)
+    double delta;
+};
+
 struct SolverState {
     double rho[kMaxRhs];        // ||r||^2 of the inner iterate, in the cycle's units
     double alpha[kMaxRhs], beta[kMaxRhs];
@@ -855,6 +880,7 @@ struct SolverState {
     int trips;                  // inner-loop graph trips in the current cycle
     int loop_base, loop_trips, loop_cap, loop_pad;   // lattice-batch loop (first lattice only)
     unsigned int ticket[4];
+    CycleCtl ctl;
 };
 
 constexpr int kMaxPartials = 4096;     // blocks per reducing kernel

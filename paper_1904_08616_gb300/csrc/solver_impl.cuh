@@ -460,17 +460,16 @@ struct OpRestart {
     PA p;
     XA x;
     RedCtx rc;
-    int nr, k_max;
-    PerRhs<Real> is;          // 1/s
-    PerRhs<double> stop_rho;
-    PerRhs<int> act, first;
+    int nr;
     Real my_is;
     bool on, my_first;
+    // the cycle's parameters (act, first, 1/s, stop_rho, k_max) come from rc.st->ctl
     LQ_HD bool init() {
         const int j = thread_rhs(nr);
-        on = act.v[j] != 0;
-        my_first = first.v[j] != 0;
-        my_is = is.v[j];
+        const CycleCtl& c = rc.st->ctl;
+        on = c.act[j] != 0;
+        my_first = c.first[j] != 0;
+        my_is = from_double<Real>(c.is[j]);
         return true;
     }
     LQ_HD bool active() const { return on; }
@@ -501,13 +500,11 @@ struct OpRestart {
     }
     template <int BS> __device__ __forceinline__ void finish(const double (&red)[3], const VGrid& vg) const {
         SolverState* st = rc.st;
-        const int n = nr, km = k_max;
-        const PerRhs<double> sr = stop_rho;
-        const PerRhs<int> ac = act;
-        grid_reduce_seg<BS, 3>(rc, kTicketMisc, red, n, vg, [st, n, km, sr, ac](const double* tot) {
+        const int n = nr;
+        grid_reduce_seg<BS, 3>(rc, kTicketMisc, red, n, vg, [st, n](const double* tot) {
             int all = 1;
             for (int j = 0; j < n; ++j) {
-                if (ac.v[j]) {
+                if (st->ctl.act[j]) {
                     st->red[0][j] = tot[0 * kMaxRhs + j];
                     st->red[1][j] = tot[1 * kMaxRhs + j];
                     st->rho[j] = tot[2 * kMaxRhs + j];
@@ -518,9 +515,9 @@ struct OpRestart {
                 }
                 st->iter[j] = 0;
                 st->p_iter[j] = 0;
-                st->stop_rho[j] = sr.v[j];
+                st->stop_rho[j] = st->ctl.stop_rho[j];
             }
-            st->k_max = km;
+            st->k_max = st->ctl.k_max;
             st->trips = 0;
             st->all_stop = all;
         });
@@ -537,16 +534,16 @@ struct OpRestartP {
     XA x;
     RedCtx rc;
     int nr;
-    PerRhs<Real> b0;
-    PerRhs<int> on_v;     // act and not first
     Real cre, cim, my_b0;
     bool on;
+    // beta_0 and whether the right-hand side continues its direction come from rc.st->ctl
     LQ_HD bool init() {
         const int j = thread_rhs(nr);
-        on = on_v.v[j] != 0;
+        const CycleCtl& c = rc.st->ctl;
+        on = c.cont[j] != 0;
         cre = from_double<Real>(rc.st->red[0][j]);
         cim = from_double<Real>(rc.st->red[1][j]);
-        my_b0 = b0.v[j];
+        my_b0 = from_double<Real>(c.b0[j]);
         return true;
     }
     LQ_HD bool active() const { return on; }
@@ -567,7 +564,8 @@ struct OpRestartP {
     template <int BS> __device__ __forceinline__ void finish(const double (&)[1], const VGrid& vg) const {}
 };
 
-// psi^high += s psi  (the cycle's update of Algorithm 1 as read above), in the outer arithmetic
+// psi^high += s psi  (the cycle's update of Algorithm 1 as read above), in the outer
+// arithmetic, for the right-hand sides that ctl marks (xact, with s in xs)
 template <class XA, class PsiA>
 struct OpXUpdate {
     using Real = typename XA::Real;
@@ -575,14 +573,13 @@ struct OpXUpdate {
     XA x;
     PsiA psi;
     int nr;
-    PerRhs<Real> s;
-    PerRhs<int> act;
+    const CycleCtl* ctl;
     Real my_s;
     bool on;
     LQ_HD bool init() {
         const int j = thread_rhs(nr);
-        on = act.v[j] != 0;
-        my_s = s.v[j];
+        on = ctl->xact[j] != 0;
+        my_s = from_double<Real>(ctl->xs[j]);
         return true;
     }
     LQ_HD bool active() const { return on; }
@@ -887,7 +884,8 @@ static __global__ void inner_loop_cond(cudaGraphConditionalHandle h, SolverState
 }
 
 // One cycle's inner CG as a CUDA graph: a conditional WHILE node whose body is K1, K2, K3 and
-// inner_loop_cond, captured once per solve and launched once per cycle.
+// inner_loop_cond, captured once per solve and launched once per cycle.  Used by host-driven
+// cycles when the whole-solve graph (SolveGraph, below) cannot be built.
 struct InnerGraph {
     cudaStream_t cs = nullptr;
     cudaGraph_t graph = nullptr;
@@ -929,6 +927,220 @@ struct InnerGraph {
             le = cudaGetLastError();
         }
         e = cudaStreamEndCapture(cs, &bodyg);
+        if (le != cudaSuccess) return le;
+        if (e != cudaSuccess) return e;
+        return cudaGraphInstantiate(&exec, graph, 0);
+    }
+};
+
+// ------------------------------------------------------------------------------------
+// Algorithm 1's outer loop on a CycleCtl.  Host-driven solves call these on a host copy and
+// upload it before the kernels that read it; device-driven solves run them in one-thread
+// kernels of the solve's graph, so both follow the same decisions.
+// ------------------------------------------------------------------------------------
+// convergence and limits per right-hand side, and the next cycle's inner iteration cap;
+// true if some right-hand side needs another cycle
+LQ_HD bool ctl_plan(CycleCtl& c) {
+    int total_max = 0;
+    bool any = false;
+    for (int j = 0; j < c.nb; ++j) {
+        if (c.done[j]) continue;
+        if (!isfinite(c.s[j])) {
+            c.status[j] = LQ_ERR_NONFINITE;
+            c.done[j] = 1;
+        } else if (c.s[j] <= c.target[j]) {
+            c.done[j] = 1;
+        } else if (c.l >= c.max_cycles || c.total[j] >= c.max_iter || c.stagnant[j] >= 5) {
+            c.status[j] = LQ_NOT_CONVERGED;
+            c.done[j] = 1;
+        }
+        if (!c.done[j]) {
+            any = true;
+            if (c.total[j] > total_max) total_max = c.total[j];
+        }
+    }
+    c.k_max = c.max_iter - total_max;
+    if (c.k_max > c.per_cycle) c.k_max = c.per_cycle;
+    return any;
+}
+
+// the next cycle's restart (Algorithm 1): r_0 = r^high / s, the inner stopping point
+// rho <= max(delta^2, (tol ||eta|| / s)^2), and beta_0 = s_l / (s_{l-1} rho_k) for a
+// right-hand side that continues its direction; right-hand sides that are done take no part
+LQ_HD void ctl_params(CycleCtl& c) {
+    c.any_cont = 0;
+    for (int j = 0; j < kMaxRhs; ++j) {
+        const bool in = j < c.nb;
+        const int act = in && !c.done[j];
+        const double rel = in ? c.target[j] / (c.s[j] > 0 ? c.s[j] : 1.0) : 0.0;
+        c.act[j] = act;
+        c.is[j] = act ? 1.0 / c.s[j] : 0.0;
+        c.stop_rho[j] = fmax(c.delta * c.delta, rel * rel);
+        c.cont[j] = act && !c.first[j];
+        c.b0[j] = c.cont[j] ? c.s[j] / (c.s_prev[j] * c.rho_k[j]) : 0.0;
+        c.any_cont |= c.cont[j];
+    }
+}
+
+// the end of a cycle's inner loop: its iterations and stop code per right-hand side, and
+// the solution update psi^high += s psi to apply
+LQ_HD void ctl_mid(CycleCtl& c, const SolverState& st) {
+    for (int j = 0; j < kMaxRhs; ++j) {
+        c.xact[j] = 0;
+        if (j >= c.nb || c.done[j]) continue;
+        c.total[j] += st.iter[j];
+        if (st.stop[j] >= 2) {
+            // breakdown or non-finite: x stays the last reliable iterate
+            c.status[j] = st.stop[j] == 2 ? LQ_ERR_BREAKDOWN : LQ_ERR_NONFINITE;
+            c.done[j] = 1;
+            continue;
+        }
+        c.rho_k[j] = st.rho[j];
+        c.xact[j] = 1;
+        c.xs[j] = c.s[j];
+    }
+}
+
+// the new outer residual s = ||r^high|| (st.red[2]): stagnation (cycles since s last
+// improved on its best by 0.1%) and whether the next cycle continues the direction (only
+// while the inner recurrence predicted the true residual)
+LQ_HD void ctl_collect(CycleCtl& c, const SolverState& st) {
+    c.high_applies += 1;
+    for (int j = 0; j < c.nb; ++j) {
+        if (!c.xact[j]) continue;
+        const double s_new = sqrt(st.red[2][j]);
+        if (s_new < 0.999 * c.best[j]) {
+            c.best[j] = s_new;
+            c.stagnant[j] = 0;
+        } else {
+            c.stagnant[j] += 1;
+        }
+        c.first[j] = !(s_new <= 2.0 * c.s[j] * sqrt(c.rho_k[j]));
+        c.s_prev[j] = c.s[j];
+        c.s[j] = s_new;
+        c.cycles[j] += 1;
+    }
+    ++c.l;
+}
+
+// The one-thread kernels of a device-driven solve.  ctl_first and ctl_end decide whether
+// another cycle runs (the outer WHILE node's condition); ctl_arm opens the cycle's inner
+// loop; ctl_end also counts the cycle's launches (fixed ones plus per_trip per inner trip).
+static __global__ void ctl_first_kernel(SolverState* st, cudaGraphConditionalHandle outer) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        CycleCtl& c = st->ctl;
+        const bool any = ctl_plan(c);
+        ctl_params(c);
+        c.launches += 1;
+        cudaGraphSetConditional(outer, any ? 1u : 0u);
+    }
+}
+static __global__ void ctl_arm_kernel(cudaGraphConditionalHandle inner) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(inner, 1u);
+}
+static __global__ void ctl_mid_kernel(SolverState* st) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) ctl_mid(st->ctl, *st);
+}
+static __global__ void ctl_end_kernel(SolverState* st, cudaGraphConditionalHandle outer, int per_trip, int fixed) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        CycleCtl& c = st->ctl;
+        ctl_collect(c, *st);
+        c.launches += fixed + per_trip * st->trips;
+        const bool any = ctl_plan(c);
+        ctl_params(c);
+        cudaGraphSetConditional(outer, any ? 1u : 0u);
+    }
+}
+
+// Adds a conditional node with handle h after the work captured so far on cs (which is
+// capturing) and makes later captured work depend on it; *body receives its body graph.
+inline cudaError_t capture_conditional(cudaStream_t cs, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                                       cudaGraph_t* body) {
+    cudaStreamCaptureStatus status;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(cs, &status, nullptr, &g, &deps, nullptr, &nd);
+    if (e != cudaSuccess) return e;
+    if (status != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = type;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    if ((e = cudaGraphAddNode(&node, g, deps, nullptr, nd, &p)) != cudaSuccess) return e;
+    *body = p.conditional.phGraph_out[0];
+    return cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
+// A whole solve's cycles as one CUDA graph (Algorithm 1 with every decision on the device):
+//   ctl_first; WHILE (another cycle) { ctl_arm; restart(); WHILE (inner loop runs)
+//   { iteration(); inner_loop_cond }; ctl_mid; tail(); ctl_end }
+// restart() enqueues the cycle start, iteration() one inner CG iteration and tail() the
+// solution update and the outer residual.  Built once per solve, launched once.
+struct SolveGraph {
+    cudaStream_t cs = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    SolveGraph() = default;
+    SolveGraph(const SolveGraph&) = delete;
+    SolveGraph& operator=(const SolveGraph&) = delete;
+    ~SolveGraph() { reset(); }
+    void reset() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (cs) cudaStreamDestroy(cs);
+        exec = nullptr;
+        graph = nullptr;
+        cs = nullptr;
+    }
+    template <class Restart, class Iteration, class Tail>
+    cudaError_t build(SolverState* st, int per_trip, int fixed, Restart restart, Iteration iteration, Tail tail) {
+        constexpr cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
+        cudaError_t e, le;
+        if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) return e;
+        if ((e = cudaGraphCreate(&graph, 0)) != cudaSuccess) return e;
+        cudaGraphConditionalHandle outer, inner;
+        if ((e = cudaGraphConditionalHandleCreate(&outer, graph, 0, cudaGraphCondAssignDefault)) != cudaSuccess)
+            return e;
+        // top level: the first decision, then the cycle loop
+        if ((e = cudaStreamBeginCaptureToGraph(cs, graph, nullptr, nullptr, 0, mode)) != cudaSuccess) return e;
+        ctl_first_kernel<<<1, 32, 0, cs>>>(st, outer);
+        le = cudaGetLastError();
+        cudaGraph_t cycle = nullptr, body = nullptr;
+        if (le == cudaSuccess) le = capture_conditional(cs, outer, cudaGraphCondTypeWhile, &cycle);
+        e = cudaStreamEndCapture(cs, &graph);
+        if (le != cudaSuccess) return le;
+        if (e != cudaSuccess) return e;
+        // one cycle
+        if ((e = cudaGraphConditionalHandleCreate(&inner, cycle, 1, cudaGraphCondAssignDefault)) != cudaSuccess)
+            return e;
+        if ((e = cudaStreamBeginCaptureToGraph(cs, cycle, nullptr, nullptr, 0, mode)) != cudaSuccess) return e;
+        ctl_arm_kernel<<<1, 32, 0, cs>>>(inner);
+        le = cudaGetLastError();
+        if (le == cudaSuccess) le = restart(cs);
+        if (le == cudaSuccess) le = capture_conditional(cs, inner, cudaGraphCondTypeWhile, &body);
+        if (le == cudaSuccess) {
+            ctl_mid_kernel<<<1, 32, 0, cs>>>(st);
+            le = cudaGetLastError();
+        }
+        if (le == cudaSuccess) le = tail(cs);
+        if (le == cudaSuccess) {
+            ctl_end_kernel<<<1, 32, 0, cs>>>(st, outer, per_trip, fixed);
+            le = cudaGetLastError();
+        }
+        e = cudaStreamEndCapture(cs, &cycle);
+        if (le != cudaSuccess) return le;
+        if (e != cudaSuccess) return e;
+        // one inner iteration and the loop test
+        if ((e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, mode)) != cudaSuccess) return e;
+        le = iteration(cs);
+        if (le == cudaSuccess) {
+            inner_loop_cond<<<1, 32, 0, cs>>>(inner, st);
+            le = cudaGetLastError();
+        }
+        e = cudaStreamEndCapture(cs, &body);
         if (le != cudaSuccess) return le;
         if (e != cudaSuccess) return e;
         return cudaGraphInstantiate(&exec, graph, 0);
@@ -1037,20 +1249,18 @@ struct Solve {
     K2Sten sPre2;
     PreEpi ePre;
 
-    // host-side state
+    // host-side state; hc is Algorithm 1's outer loop (the device copy, dstate->ctl, is what
+    // the cycle kernels read: uploaded by host-driven solves, advanced in place by the graph)
     SolverState hs{};
+    CycleCtl hc{};
     lq_cg_info out[kMaxRhs];
     bool prof = false;
-    int chunk = 8, launches = 0, high_applies = 0, l = 0, k_max = 0, guard = 0;
+    int chunk = 8, launches = 0, k_max = 0, guard = 0;
     double kms[4] = {0, 0, 0, 0};
     int kcalls[4] = {0, 0, 0, 0};
     EventSet evs;
     InnerGraph igraph;
     bool graph_off = false;   // the inner-loop graph could not be built
-    double eta_norm[kMaxRhs], s[kMaxRhs], s_prev[kMaxRhs], rho_k[kMaxRhs], target[kMaxRhs], best[kMaxRhs];
-    // first[j]: the next cycle starts from p_0 = r_0 (the first cycle, or after the true
-    // residual left the inner recurrence's prediction) instead of continuing the direction
-    int done[kMaxRhs], first[kMaxRhs], stagnant[kMaxRhs], status[kMaxRhs], total[kMaxRhs];
 
     Solve() = default;
     Solve(const Solve&) = delete;
@@ -1156,7 +1366,8 @@ struct Solve {
     // out = ya y + hb hop(in) over the sites of map, in the outer arithmetic (Schur set-up,
     // residual and reconstruction steps)
     template <class Map, class OutA, class InA, class YA, bool DAG, bool HASY>
-    cudaError_t outer_hop(const Map& map, const OutA& out, const InA& in, const YA& y, double ya, double hb) {
+    cudaError_t outer_hop(const Map& map, const OutA& out, const InA& in, const YA& y, double ya, double hb,
+                          cudaStream_t s) {
         Stencil<HiGA, InA, DAG> sten{g, Uh, in};
         EpiAxpby<OutA, YA, HASY, false> e;
         e.out = out;
@@ -1166,28 +1377,28 @@ struct Solve {
         e.rc = rc;
         e.slot = 0;
         launches += 1;
-        return launch_stencil<kBS>(map, sten, e, st);
+        return launch_stencil<kBS>(map, sten, e, s);
     }
 
     // r^high = eta - A x, s^2 -> red[2][.]   (Algorithm 1: the high-precision residual)
-    cudaError_t high_residual() {
+    cudaError_t high_residual(cudaStream_t s) {
         if constexpr (SCHUR) {
             // tmp_o = H_oe x_e;  t_e = A x_e - H_eo tmp_o / A;  tmp_o = H^dag_oe t_e;
             // r_e = eta-hat - (A t_e - H^dag_eo tmp_o / A)
-            if (prof) cudaEventRecord(evs.ev[6 * chunk], st);
+            if (prof) cudaEventRecord(evs.ev[6 * chunk], s);
             cudaError_t er;
-            if ((er = outer_hop<HMap, HiRW, HiRO, HiRO, false, false>(hmap_odd, tmh_rw, x_ro, x_ro, 0.0, 0.5)) !=
+            if ((er = outer_hop<HMap, HiRW, HiRO, HiRO, false, false>(hmap_odd, tmh_rw, x_ro, x_ro, 0.0, 0.5, s)) !=
                     cudaSuccess ||
-                (er = outer_hop<HMap, HiRW, HiRO, HiRO, false, true>(hmap, th_rw, tmh_ro, x_ro, a, -0.5 / a)) !=
+                (er = outer_hop<HMap, HiRW, HiRO, HiRO, false, true>(hmap, th_rw, tmh_ro, x_ro, a, -0.5 / a, s)) !=
                     cudaSuccess ||
-                (er = outer_hop<HMap, HiRW, HiRO, HiRO, true, false>(hmap_odd, tmh_rw, th_ro, th_ro, 0.0, 0.5)) !=
+                (er = outer_hop<HMap, HiRW, HiRO, HiRO, true, false>(hmap_odd, tmh_rw, th_ro, th_ro, 0.0, 0.5, s)) !=
                     cudaSuccess)
                 return er;
             Stencil<HiGA, HiRO, true> s4{g, Uh, tmh_ro};
             EpiResid<HiRO, HiRO, HiRW> e4{eta_ro, th_ro, rh_rw, from_double<HReal>(a), from_double<HReal>(-0.5 / a), rc, nb, 2};
-            er = launch_stencil<kBS>(hmap, s4, e4, st);
+            er = launch_stencil<kBS>(hmap, s4, e4, s);
             launches += 1;
-            if (prof) cudaEventRecord(evs.ev[6 * chunk + 1], st);
+            if (prof) cudaEventRecord(evs.ev[6 * chunk + 1], s);
             return er;
         }
         Stencil<HiGA, HiRO, false> s1{g, Uh, x_ro};
@@ -1198,14 +1409,14 @@ struct Solve {
         e1.b = from_double<HReal>(b);
         e1.rc = rc;
         e1.slot = 0;
-        if (prof) cudaEventRecord(evs.ev[6 * chunk], st);
-        cudaError_t er = launch_stencil<kBS>(hmap, s1, e1, st);
+        if (prof) cudaEventRecord(evs.ev[6 * chunk], s);
+        cudaError_t er = launch_stencil<kBS>(hmap, s1, e1, s);
         if (er != cudaSuccess) return er;
         Stencil<HiGA, HiRO, true> s2{g, Uh, th_ro};
         EpiResid<HiRO, HiRO, HiRW> e2{eta_ro, th_ro, rh_rw, from_double<HReal>(a), from_double<HReal>(b), rc, nb, 2};
-        er = launch_stencil<kBS>(hmap, s2, e2, st);
+        er = launch_stencil<kBS>(hmap, s2, e2, s);
         launches += 2;
-        if (prof) cudaEventRecord(evs.ev[6 * chunk + 1], st);
+        if (prof) cudaEventRecord(evs.ev[6 * chunk + 1], s);
         return er;
     }
     // after the stream has been synchronised: add the residual's event time
@@ -1250,12 +1461,12 @@ struct Solve {
         if constexpr (SCHUR) {
             // bhat_e = b_e - H_eo b_o / A (in t^high);  tmp_o = H^dag_oe bhat_e;
             // eta-hat = Mhat^dag bhat_e = A bhat_e - H^dag_eo tmp_o / A;  ||eta-hat||^2 -> red[3]
-            if ((e = outer_hop<HMap, HiRW, HiRO, HiRO, false, true>(hmap, th_rw, b_ro, b_ro, 1.0, -0.5 / a)) !=
+            if ((e = outer_hop<HMap, HiRW, HiRO, HiRO, false, true>(hmap, th_rw, b_ro, b_ro, 1.0, -0.5 / a, st)) !=
                     cudaSuccess ||
-                (e = outer_hop<HMap, HiRW, HiRO, HiRO, true, false>(hmap_odd, tmh_rw, th_ro, th_ro, 0.0, 0.5)) !=
+                (e = outer_hop<HMap, HiRW, HiRO, HiRO, true, false>(hmap_odd, tmh_rw, th_ro, th_ro, 0.0, 0.5, st)) !=
                     cudaSuccess ||
                 (e = outer_hop<HMap, HiRW, HiRO, HiRO, true, true>(hmap, make_spinor<HP, HL, false>(etao, g, true, nb),
-                                                                   tmh_ro, th_ro, a, -0.5 / a)) != cudaSuccess ||
+                                                                   tmh_ro, th_ro, a, -0.5 / a, st)) != cudaSuccess ||
                 (e = launch_site<kSiteBS>(hsite, OpNorm<HiRO>{eta_ro, rc, nb, 3}, st)) != cudaSuccess)
                 return cuda_fail(e, "Schur right-hand side");
             launches += 1;
@@ -1271,23 +1482,27 @@ struct Solve {
 
         PerRhs<int> zero_rhs{};
         bool any_zero = false;
+        memset(&hc, 0, sizeof(hc));
+        hc.nb = nb;
+        hc.delta = delta;
+        hc.max_cycles = prm.max_cycles > 0 ? prm.max_cycles : 1000;
+        hc.max_iter = prm.max_iter;
+        hc.per_cycle = prm.max_inner > 0 ? prm.max_inner : 1000;
         for (int j = 0; j < nb; ++j) {
-            eta_norm[j] = sqrt(hs.red[3][j]);
-            out[j].eta_norm = eta_norm[j];
-            done[j] = 0;
-            first[j] = 1;
-            stagnant[j] = 0;
-            status[j] = LQ_OK;
-            total[j] = 0;
-            s_prev[j] = rho_k[j] = 0.0;
-            target[j] = prm.tol * eta_norm[j];
-            if (!isfinite(eta_norm[j])) {
-                status[j] = LQ_ERR_NONFINITE;
-                done[j] = 1;
-            } else if (eta_norm[j] == 0.0) {
+            // first[j]: the next cycle starts from p_0 = r_0 (the first cycle, or after the
+            // true residual left the inner recurrence's prediction)
+            hc.eta_norm[j] = sqrt(hs.red[3][j]);
+            out[j].eta_norm = hc.eta_norm[j];
+            hc.first[j] = 1;
+            hc.status[j] = LQ_OK;
+            hc.target[j] = prm.tol * hc.eta_norm[j];
+            if (!isfinite(hc.eta_norm[j])) {
+                hc.status[j] = LQ_ERR_NONFINITE;
+                hc.done[j] = 1;
+            } else if (hc.eta_norm[j] == 0.0) {
                 zero_rhs.v[j] = 1;
                 any_zero = true;
-                done[j] = 1;
+                hc.done[j] = 1;
             }
         }
         if (any_zero) {
@@ -1306,90 +1521,66 @@ struct Solve {
         // to solve) makes that eta itself, so the outer operator is not applied
         bool x0_zero = !SCHUR;
         if constexpr (!SCHUR)
-            for (int j = 0; j < nb; ++j) x0_zero = x0_zero && (done[j] || hs.red[1][j] == 0.0);
+            for (int j = 0; j < nb; ++j) x0_zero = x0_zero && (hc.done[j] || hs.red[1][j] == 0.0);
         if (x0_zero) {
             if ((e = cudaMemcpyAsync(ws + w.r_high, etao, spinor_bytes((int64_t)g.V * nb, HP),
                                      cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
                 return cuda_fail(e, "residual");
-            for (int j = 0; j < nb; ++j) s[j] = eta_norm[j];
-            high_applies = 0;
+            for (int j = 0; j < nb; ++j) hc.s[j] = hc.eta_norm[j];
+            hc.high_applies = 0;
         } else {
-            if ((e = high_residual()) != cudaSuccess) return cuda_fail(e, "residual");
+            if ((e = high_residual(st)) != cudaSuccess) return cuda_fail(e, "residual");
             if ((e = read_state()) != cudaSuccess) return cuda_fail(e, "residual");
             account_high();
-            for (int j = 0; j < nb; ++j) s[j] = sqrt(hs.red[2][j]);
-            high_applies = 1;
+            for (int j = 0; j < nb; ++j) hc.s[j] = sqrt(hs.red[2][j]);
+            hc.high_applies = 1;
         }
-        for (int j = 0; j < nb; ++j) best[j] = s[j];
-        l = 0;
+        for (int j = 0; j < nb; ++j) hc.best[j] = hc.s[j];
         return LQ_OK;
     }
 
+    // the host copy of the outer loop's state to the device (the cycle kernels read it there)
+    cudaError_t upload_ctl() { return cudaMemcpyAsync(&dstate->ctl, &hc, sizeof(hc), cudaMemcpyHostToDevice, st); }
+
     // convergence and limits, per right-hand side; true if some right-hand side needs a cycle
     bool plan() {
-        const int max_cycles = prm.max_cycles > 0 ? prm.max_cycles : 1000;
-        const int per_cycle = prm.max_inner > 0 ? prm.max_inner : 1000;
-        int total_max = 0;
-        bool any = false;
-        for (int j = 0; j < nb; ++j) {
-            if (done[j]) continue;
-            if (!isfinite(s[j])) {
-                status[j] = LQ_ERR_NONFINITE;
-                done[j] = 1;
-            } else if (s[j] <= target[j]) {
-                done[j] = 1;
-            } else if (l >= max_cycles || total[j] >= prm.max_iter || stagnant[j] >= 5) {
-                status[j] = LQ_NOT_CONVERGED;
-                done[j] = 1;
-            }
-            if (!done[j]) {
-                any = true;
-                if (total[j] > total_max) total_max = total[j];
-            }
-        }
-        k_max = prm.max_iter - total_max;
-        if (k_max > per_cycle) k_max = per_cycle;
+        const bool any = ctl_plan(hc);
+        k_max = hc.k_max;
         return any;
+    }
+
+    // the cycle-start kernels (Algorithm 1's restart), reading their parameters from
+    // dstate->ctl; any_cont: some right-hand side continues its direction
+    cudaError_t launch_restart(cudaStream_t s, bool any_cont) {
+        OpRestart<HiRO, SpRW, SpRW, PsiRW> op{rh_ro, r_rw, p_rw, psi_rw, rc, nb, Real(0), false, false};
+        cudaError_t e = launch_site<kSiteBS>(hsite, op, s);
+        if (e != cudaSuccess || !any_cont) return e;
+        OpRestartP<SpRO, SpRW, PsiRW> op2{r_ro, p_rw, psi_rw, rc, nb, Real(0), Real(0), Real(0), false};
+        return launch_site<kSiteBS>(isite, op2, s);
     }
 
     // cycle start (Algorithm 1)
     int start_cycle() {
         NvtxRange nvtx("lq solve: cycle start (Algorithm 1 restart)");
-        OpRestart<HiRO, SpRW, SpRW, PsiRW> op;
-        op.rh = rh_ro;
-        op.r = r_rw;
-        op.p = p_rw;
-        op.x = psi_rw;
-        op.rc = rc;
-        op.nr = nb;
-        op.k_max = k_max;
-        OpRestartP<SpRO, SpRW, PsiRW> op2;
-        op2.r = r_ro;
-        op2.p = p_rw;
-        op2.x = psi_rw;
-        op2.rc = rc;
-        op2.nr = nb;
-        bool any_cont = false;
-        for (int j = 0; j < nb; ++j) {
-            const bool act = !done[j];
-            const double rel_target = target[j] / (s[j] > 0 ? s[j] : 1.0);
-            op.act.v[j] = act;
-            op.first.v[j] = first[j];
-            op.is.v[j] = from_double<Real>(act ? 1.0 / s[j] : 0.0);
-            op.stop_rho.v[j] = fmax(delta * delta, rel_target * rel_target);
-            op2.on_v.v[j] = act && !first[j];
-            op2.b0.v[j] = from_double<Real>(act && !first[j] ? s[j] / (s_prev[j] * rho_k[j]) : 0.0);
-            any_cont |= act && !first[j];
-        }
-        cudaError_t e = launch_site<kSiteBS>(hsite, op, st);
-        launches += 1;
-        if (e == cudaSuccess && any_cont) {
-            e = launch_site<kSiteBS>(isite, op2, st);
-            launches += 1;
-        }
+        ctl_params(hc);
+        cudaError_t e = upload_ctl();
+        if (e == cudaSuccess) e = launch_restart(st, hc.any_cont != 0);
         if (e != cudaSuccess) return cuda_fail(e, "cycle start");
+        launches += hc.any_cont ? 2 : 1;
         guard = 0;
         return LQ_OK;
+    }
+
+    // one inner CG iteration (K1, K2, K3; Schur: with the two hops to the odd sites)
+    cudaError_t launch_iteration(cudaStream_t s) {
+        cudaError_t r;
+        if constexpr (SCHUR)
+            if ((r = launch_stencil<IBS>(omap, sPre1, ePre, s)) != cudaSuccess) return r;
+        if ((r = launch_stencil<IBS>(imap, sK1, eK1, s)) != cudaSuccess) return r;
+        if constexpr (SCHUR)
+            if ((r = launch_stencil<IBS>(omap, sPre2, ePre, s)) != cudaSuccess) return r;
+        if ((r = launch_stencil<IBS>(imap, sK2, eK2, s)) != cudaSuccess) return r;
+        return launch_site<kSiteBS>(isite, oK3, s);
     }
 
     // the inner CG of one lattice: chunks of K1, K2, K3 until every right-hand side has
@@ -1400,16 +1591,7 @@ struct Solve {
         if (!prof && !graph_off && (prm.flags & LQ_CG_NO_GRAPH) == 0) {
             // the whole inner loop on the device: one graph launch, one read-back
             if (!igraph.exec) {
-                e = igraph.build(dstate, [&](cudaStream_t s) -> cudaError_t {
-                    cudaError_t r;
-                    if constexpr (SCHUR)
-                        if ((r = launch_stencil<IBS>(omap, sPre1, ePre, s)) != cudaSuccess) return r;
-                    if ((r = launch_stencil<IBS>(imap, sK1, eK1, s)) != cudaSuccess) return r;
-                    if constexpr (SCHUR)
-                        if ((r = launch_stencil<IBS>(omap, sPre2, ePre, s)) != cudaSuccess) return r;
-                    if ((r = launch_stencil<IBS>(imap, sK2, eK2, s)) != cudaSuccess) return r;
-                    return launch_site<kSiteBS>(isite, oK3, s);
-                });
+                e = igraph.build(dstate, [&](cudaStream_t s) { return launch_iteration(s); });
                 if (e != cudaSuccess) {
                     // no conditional graph here (driver or capture refused it): the host
                     // drives the same kernels below for the rest of the solve
@@ -1469,54 +1651,25 @@ struct Solve {
     // The outcome of the cycle (hs holds the final inner state): psi^high += s psi_k and the
     // outer residual are enqueued here; end_cycle_collect() takes the residual once the state
     // record has been read back (several lattices share that one read); end_cycle() does both.
-    PerRhs<int> xact_pending{};
+    // x^high += s psi for the right-hand sides dstate->ctl marks, then the outer residual
+    cudaError_t launch_tail(cudaStream_t s) {
+        OpXUpdate<HiRW, PsiRO> xu{x_rw, psi_ro, nb, &dstate->ctl, HReal(0), false};
+        cudaError_t e = launch_site<kSiteBS>(hsite, xu, s);
+        if (e != cudaSuccess) return e;
+        return high_residual(s);
+    }
     int end_cycle_launch() {
         NvtxRange nvtx("lq solve: reliable update (solution, FP64-class residual)");
-        cudaError_t e;
-        PerRhs<HReal> xs{};
-        PerRhs<int> xact{};
-        for (int j = 0; j < nb; ++j) {
-            if (done[j]) continue;
-            total[j] += hs.iter[j];
-            if (hs.stop[j] >= 2) {
-                // breakdown or non-finite: keep x as it is (the last reliable iterate)
-                status[j] = fail(hs.stop[j] == 2 ? LQ_ERR_BREAKDOWN : LQ_ERR_NONFINITE,
-                                 hs.stop[j] == 2 ? "CG breakdown: <p, D^dag D p> <= 0"
-                                                 : "inner CG produced non-finite values");
-                done[j] = 1;
-                continue;
-            }
-            rho_k[j] = hs.rho[j];
-            xact.v[j] = 1;
-            xs.v[j] = from_double<HReal>(s[j]);
-        }
-        xact_pending = xact;
-        OpXUpdate<HiRW, PsiRO> xu{x_rw, psi_ro, nb, xs, xact, HReal(0), false};
-        if ((e = launch_site<kSiteBS>(hsite, xu, st)) != cudaSuccess) return cuda_fail(e, "x update");
+        ctl_mid(hc, hs);
+        cudaError_t e = upload_ctl();
+        if (e == cudaSuccess) e = launch_tail(st);
+        if (e != cudaSuccess) return cuda_fail(e, "reliable update");
         launches += 1;
-        if ((e = high_residual()) != cudaSuccess) return cuda_fail(e, "residual");
         return LQ_OK;
     }
     void end_cycle_collect() {
         account_high();
-        high_applies += 1;
-        for (int j = 0; j < nb; ++j) {
-            if (!xact_pending.v[j]) continue;
-            const double s_new = sqrt(hs.red[2][j]);
-            // stagnation: cycles since the true residual last improved on its best by 0.1%
-            if (s_new < 0.999 * best[j]) {
-                best[j] = s_new;
-                stagnant[j] = 0;
-            } else {
-                stagnant[j] += 1;
-            }
-            // continue the direction only while the recurrence predicted the true residual
-            first[j] = !(s_new <= 2.0 * s[j] * sqrt(rho_k[j]));
-            s_prev[j] = s[j];
-            s[j] = s_new;
-            out[j].cycles += 1;
-        }
-        ++l;
+        ctl_collect(hc, hs);
     }
     int end_cycle() {
         int r;
@@ -1527,13 +1680,42 @@ struct Solve {
         return LQ_OK;
     }
 
+    // Every cycle on the device: one graph (SolveGraph) holds Algorithm 1's loop with its
+    // decisions, launched once; the host reads the state back at the end.  Returns false
+    // (nothing launched) if the graph cannot be built here; the host then drives the cycles.
+    bool device_cycles(int* r) {
+        if (prof || graph_off || (prm.flags & LQ_CG_NO_GRAPH) != 0) return false;
+        NvtxRange nvtx("lq solve: cycles (one graph)");
+        SolveGraph sg;
+        const int counted = launches;   // the builders count their launches while captured
+        const int per_trip = (SCHUR ? 5 : 3) + 1, fixed = 2 + 1 + 1 + 1 + (SCHUR ? 4 : 2) + 1;
+        cudaError_t e = sg.build(
+            dstate, per_trip, fixed, [&](cudaStream_t s) { return launch_restart(s, true); },
+            [&](cudaStream_t s) { return launch_iteration(s); }, [&](cudaStream_t s) { return launch_tail(s); });
+        launches = counted;
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            return false;
+        }
+        *r = LQ_OK;
+        if ((e = upload_ctl()) != cudaSuccess || (e = cudaGraphLaunch(sg.exec, st)) != cudaSuccess ||
+            (e = read_state()) != cudaSuccess) {
+            *r = cuda_fail(e, "solve graph");
+            return true;
+        }
+        hc = hs.ctl;
+        launches += hc.launches;
+        k_max = hc.k_max;
+        return true;
+    }
+
     // write-back, per-right-hand-side records; returns the worst status
     int finish(lq_cg_info* info) {
         NvtxRange nvtx("lq solve: write-back");
         cudaError_t e;
         if constexpr (SCHUR) {
             // x_o = (b_o - H_oe x_e) / A
-            if ((e = outer_hop<HMap, HiRW, HiRO, HiRO, false, true>(hmap_odd, x_rw, x_ro, b_ro, 1.0 / a, -0.5 / a)) !=
+            if ((e = outer_hop<HMap, HiRW, HiRO, HiRO, false, true>(hmap_odd, x_rw, x_ro, b_ro, 1.0 / a, -0.5 / a, st)) !=
                 cudaSuccess)
                 return cuda_fail(e, "odd-site solution");
         }
@@ -1545,10 +1727,14 @@ struct Solve {
         if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "x write-back");
         int worst = LQ_OK;
         for (int j = 0; j < nb; ++j) {
-            out[j].iters = total[j];
-            out[j].high_applies = high_applies;
-            out[j].true_rel_resid = eta_norm[j] > 0 ? s[j] / eta_norm[j] : 0.0;
-            out[j].status = status[j];
+            const int sj = hc.status[j];
+            if (sj == LQ_ERR_BREAKDOWN) fail(sj, "CG breakdown: <p, D^dag D p> <= 0");
+            if (sj == LQ_ERR_NONFINITE) fail(sj, "non-finite values (in eta, or produced by the solve)");
+            out[j].iters = hc.total[j];
+            out[j].cycles = hc.cycles[j];
+            out[j].high_applies = hc.high_applies;
+            out[j].true_rel_resid = hc.eta_norm[j] > 0 ? hc.s[j] / hc.eta_norm[j] : 0.0;
+            out[j].status = sj;
             out[j].launches = launches;
             out[j].block = IBS;
             for (int q = 0; q < 4; ++q) {
@@ -1556,8 +1742,8 @@ struct Solve {
                 out[j].kernel_calls[q] = kcalls[q];
             }
             if (info) info[j] = out[j];
-            if (status[j] < 0 && (worst >= 0 || status[j] < worst)) worst = status[j];
-            if (status[j] == LQ_NOT_CONVERGED && worst == LQ_OK) worst = LQ_NOT_CONVERGED;
+            if (sj < 0 && (worst >= 0 || sj < worst)) worst = sj;
+            if (sj == LQ_NOT_CONVERGED && worst == LQ_OK) worst = LQ_NOT_CONVERGED;
         }
         return worst;
     }
@@ -1572,10 +1758,14 @@ int run_solver_rb(const Geom& g, double m_q, int nb, const void* U, const void* 
     sv.init(g, m_q, nb, U, eta, x, prm, delta, w, ws, st);
     int r;
     if ((r = sv.begin()) != LQ_OK) return r;
-    while (sv.plan()) {
-        if ((r = sv.start_cycle()) != LQ_OK) return r;
-        if ((r = sv.inner_single()) != LQ_OK) return r;
-        if ((r = sv.end_cycle()) != LQ_OK) return r;
+    if (sv.device_cycles(&r)) {
+        if (r != LQ_OK) return r;
+    } else {
+        while (sv.plan()) {
+            if ((r = sv.start_cycle()) != LQ_OK) return r;
+            if ((r = sv.inner_single()) != LQ_OK) return r;
+            if ((r = sv.end_cycle()) != LQ_OK) return r;
+        }
     }
     return sv.finish(info);
 }

@@ -7,10 +7,13 @@
 // holding that lattice's geometry, fields and state record) and the block ranges that serve
 // each lattice; a block finds its lattice, then runs the ordinary kernel body with that
 // lattice's share of the grid as its virtual grid, so reductions and tickets stay per
-// lattice.  Lattices whose inner loop has stopped leave their blocks idle.  A chunk of
-// iterations (chunk x {K1, K2, K3}) is captured once into a CUDA graph and replayed; the
-// host reads the state records between chunks and runs the outer steps (reliable update,
-// restart) of the lattices whose cycle ended, on the same stream.
+// lattice.  Lattices whose inner loop has stopped leave their blocks idle.  By default the
+// whole batch is one CUDA graph (LatticeSolveGraph): rounds of cycles, each lattice's outer
+// steps (restart, reliable update) and every decision on the device.  Host-driven forms
+// remain for LQ_CG_LATTICE_OWN_CYCLES (a conditional graph over the inner iterations that
+// returns when one lattice's cycle ends), for LQ_CG_NO_GRAPH and for drivers without nested
+// conditional nodes: the host reads the state records between launches and runs the outer
+// steps of the lattices whose cycle ended, on the same stream.
 //
 // The inner block size (threads per block of K1/K2) is a template parameter; the tuner
 // times K1 over the actual lattices for each candidate and caches the winner by a JSON key
@@ -259,6 +262,185 @@ struct LoopGraph {
     }
 };
 
+// A lattice batch's whole solve as one CUDA graph (reliable updates taken together, every
+// decision on the device):
+//   lat_first; WHILE (some lattice needs a cycle) { arm; restart of every lattice;
+//   lattice_loop_base; WHILE (some lattice's inner loop runs) { one iteration of every
+//   lattice; lattice_loop_cond }; for each lattice { lat_mid; IF (its solution moved)
+//   { its update and outer residual; lat_end } }; lat_decide }
+// A lattice with nothing left to do takes part as idle blocks and no-op cycle kernels.
+struct LatCtlArgs {
+    SolverState* st[kMaxLat];
+    int n;
+};
+static __global__ void lat_first_kernel(LatCtlArgs a, cudaGraphConditionalHandle outer) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        bool any = false;
+        for (int l = 0; l < a.n; ++l) {
+            CycleCtl& c = a.st[l]->ctl;
+            const bool w = ctl_plan(c);
+            ctl_params(c);
+            c.want = w;
+            c.launches += 1;
+            any |= w;
+        }
+        cudaGraphSetConditional(outer, any ? 1u : 0u);
+    }
+}
+static __global__ void lat_mid_kernel(SolverState* st, cudaGraphConditionalHandle run) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        CycleCtl& c = st->ctl;
+        ctl_mid(c, *st);
+        int moved = 0;
+        for (int j = 0; j < kMaxRhs; ++j) moved |= c.xact[j];
+        if (!moved) c.want = 0;
+        cudaGraphSetConditional(run, moved ? 1u : 0u);
+    }
+}
+static __global__ void lat_end_kernel(SolverState* st) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        CycleCtl& c = st->ctl;
+        ctl_collect(c, *st);
+        c.want = ctl_plan(c);
+        ctl_params(c);
+    }
+}
+// launches per round charged to every lattice: arm, base, decide, its two restart kernels and
+// lat_mid, four per inner trip (three shared iteration kernels and the loop test), and its
+// update, two residual kernels and lat_end when its solution moved
+static __global__ void lat_decide_kernel(LatCtlArgs a, cudaGraphConditionalHandle outer) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        bool any = false;
+        const int trips = a.st[0]->loop_trips;
+        for (int l = 0; l < a.n; ++l) {
+            CycleCtl& c = a.st[l]->ctl;
+            int moved = 0;
+            for (int j = 0; j < kMaxRhs; ++j) moved |= c.xact[j];
+            c.launches += 6 + 4 * trips + (moved ? 4 : 0);
+            any |= c.want != 0;
+        }
+        cudaGraphSetConditional(outer, any ? 1u : 0u);
+    }
+}
+
+struct LatticeSolveGraph {
+    cudaStream_t cs = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    LatticeSolveGraph() = default;
+    LatticeSolveGraph(const LatticeSolveGraph&) = delete;
+    LatticeSolveGraph& operator=(const LatticeSolveGraph&) = delete;
+    ~LatticeSolveGraph() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (cs) cudaStreamDestroy(cs);
+    }
+    template <class S, class IL>
+    cudaError_t build(S* sv, int n, const IL& il) {
+        constexpr cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
+        LatCtlArgs ca{};
+        LatLoopArgs la{};
+        ca.n = la.n = n;
+        la.together = 1;
+        for (int l = 0; l < n; ++l) ca.st[l] = la.st[l] = sv[l].dstate;
+        cudaError_t e, le;
+        if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) return e;
+        if ((e = cudaGraphCreate(&graph, 0)) != cudaSuccess) return e;
+        cudaGraphConditionalHandle outer, inner, run[kMaxLat];
+        if ((e = cudaGraphConditionalHandleCreate(&outer, graph, 0, cudaGraphCondAssignDefault)) != cudaSuccess)
+            return e;
+        if ((e = cudaStreamBeginCaptureToGraph(cs, graph, nullptr, nullptr, 0, mode)) != cudaSuccess) return e;
+        lat_first_kernel<<<1, 32, 0, cs>>>(ca, outer);
+        le = cudaGetLastError();
+        cudaGraph_t round = nullptr, body = nullptr, tail[kMaxLat] = {};
+        if (le == cudaSuccess) le = capture_conditional(cs, outer, cudaGraphCondTypeWhile, &round);
+        e = cudaStreamEndCapture(cs, &graph);
+        if (le != cudaSuccess) return le;
+        if (e != cudaSuccess) return e;
+        // one round of cycles
+        if ((e = cudaGraphConditionalHandleCreate(&inner, round, 1, cudaGraphCondAssignDefault)) != cudaSuccess)
+            return e;
+        for (int l = 0; l < n; ++l)
+            if ((e = cudaGraphConditionalHandleCreate(&run[l], round, 0, cudaGraphCondAssignDefault)) != cudaSuccess)
+                return e;
+        if ((e = cudaStreamBeginCaptureToGraph(cs, round, nullptr, nullptr, 0, mode)) != cudaSuccess) return e;
+        ctl_arm_kernel<<<1, 32, 0, cs>>>(inner);
+        le = cudaGetLastError();
+        for (int l = 0; l < n && le == cudaSuccess; ++l) le = sv[l].launch_restart(cs, true);
+        if (le == cudaSuccess) {
+            lattice_loop_base<<<1, 32, 0, cs>>>(la);
+            le = cudaGetLastError();
+        }
+        if (le == cudaSuccess) le = capture_conditional(cs, inner, cudaGraphCondTypeWhile, &body);
+        for (int l = 0; l < n && le == cudaSuccess; ++l) {
+            lat_mid_kernel<<<1, 32, 0, cs>>>(sv[l].dstate, run[l]);
+            le = cudaGetLastError();
+            if (le == cudaSuccess) le = capture_conditional(cs, run[l], cudaGraphCondTypeIf, &tail[l]);
+        }
+        if (le == cudaSuccess) {
+            lat_decide_kernel<<<1, 32, 0, cs>>>(ca, outer);
+            le = cudaGetLastError();
+        }
+        e = cudaStreamEndCapture(cs, &round);
+        if (le != cudaSuccess) return le;
+        if (e != cudaSuccess) return e;
+        // one iteration of every lattice and the loop test
+        if ((e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, mode)) != cudaSuccess) return e;
+        le = il.iteration(cs);
+        if (le == cudaSuccess) {
+            lattice_loop_cond<<<1, 32, 0, cs>>>(inner, la);
+            le = cudaGetLastError();
+        }
+        e = cudaStreamEndCapture(cs, &body);
+        if (le != cudaSuccess) return le;
+        if (e != cudaSuccess) return e;
+        // each lattice's reliable update
+        for (int l = 0; l < n; ++l) {
+            if ((e = cudaStreamBeginCaptureToGraph(cs, tail[l], nullptr, nullptr, 0, mode)) != cudaSuccess) return e;
+            le = sv[l].launch_tail(cs);
+            if (le == cudaSuccess) {
+                lat_end_kernel<<<1, 32, 0, cs>>>(sv[l].dstate);
+                le = cudaGetLastError();
+            }
+            e = cudaStreamEndCapture(cs, &tail[l]);
+            if (le != cudaSuccess) return le;
+            if (e != cudaSuccess) return e;
+        }
+        return cudaGraphInstantiate(&exec, graph, 0);
+    }
+};
+
+// Runs every cycle of the batch in one LatticeSolveGraph launch; false (nothing launched)
+// if the graph cannot be built here, and the host then drives the rounds.
+template <class S, class IL>
+bool lattice_device_cycles(S* sv, int n, const IL& il, cudaStream_t st, int* r) {
+    NvtxRange nvtx("lq lattices: cycles (one graph)");
+    int counted[kMaxLat];
+    for (int l = 0; l < n; ++l) counted[l] = sv[l].launches;
+    LatticeSolveGraph lg;
+    cudaError_t e = lg.build(sv, n, il);
+    for (int l = 0; l < n; ++l) sv[l].launches = counted[l];   // the builders counted while captured
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    *r = LQ_OK;
+    for (int l = 0; l < n && e == cudaSuccess; ++l) e = sv[l].upload_ctl();
+    if (e == cudaSuccess) e = cudaGraphLaunch(lg.exec, st);
+    for (int l = 0; l < n && e == cudaSuccess; ++l) e = sv[l].read_state_async();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        *r = cuda_fail(e, "lattice solve graph");
+        return true;
+    }
+    for (int l = 0; l < n; ++l) {
+        sv[l].hc = sv[l].hs.ctl;
+        sv[l].launches += sv[l].hc.launches;
+        sv[l].k_max = sv[l].hc.k_max;
+    }
+    return true;
+}
+
 template <int IP, int IF, int IL, int HP, int IBS>
 int run_lattices_bs(int n, const LatticeJob* jobs, const lq_cg_params& prm, double delta, char* ws,
                     lq_cg_info* info, cudaStream_t st) {
@@ -302,9 +484,15 @@ int run_lattices_bs(int n, const LatticeJob* jobs, const lq_cg_params& prm, doub
     if (use_graph && !device_loop && (e = cg.capture(il, chunk)) != cudaSuccess)
         return cuda_fail(e, "inner-loop graph capture");
 
+    // every round of cycles in one graph launch when the rounds are taken together
+    bool on_device = false;
+    if (device_loop && together) {
+        on_device = lattice_device_cycles(sv.get(), n, il, st, &r);
+        if (on_device && r != LQ_OK) return r;
+    }
     bool in_cycle[kMaxLat] = {}, finished[kMaxLat] = {};
     int chunks = 0;
-    while (true) {
+    while (!on_device) {
         bool any = false;
         for (int l = 0; l < n; ++l) {
             if (!in_cycle[l] && !finished[l]) {

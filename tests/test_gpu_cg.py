@@ -160,9 +160,11 @@ def test_cg_full_size_32(lqlib, mode):
 @pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("max_iter", [100000, 7])
 def test_cg_device_loop_equals_host_loop(lqlib, mode, max_iter):
-    """The inner loop run on the device (a conditional CUDA graph) takes the same steps as the
-    host-driven loop: the kernels and their order are the same, so the solution is
-    bit-identical, with the same iteration and cycle counts (also when max_iter cuts a cycle)."""
+    """The solve run on the device (one CUDA graph: the cycles and each cycle's inner loop as
+    conditional WHILE nodes, Algorithm 1's decisions in one-thread kernels) takes the same
+    steps as the host-driven loop: the kernels, their order and the decisions are the same, so
+    the solution is bit-identical, with the same iteration and cycle counts (also when
+    max_iter cuts a cycle)."""
     dims = (4, 6, 4, 4)
     m = 0.05
     U = synth.gauge_field(dims, seed=19, kind="near_identity", eps=0.3)

@@ -58,10 +58,10 @@ def test_lattices_against_oracle(lqlib, mode):
 @pytest.mark.parametrize("mode", ["mixed_f32", "mixed_f16"])
 @pytest.mark.parametrize("own_cycles", [False, True])
 def test_lattices_graph_replay_equals_direct_launches(lqlib, mode, own_cycles):
-    """The device-driven loop (a conditional graph that returns when every lattice's inner
-    loop has stopped, or with own_cycles when one has; the lattices have different masses, so
-    their cycles end at different iterations) runs exactly the kernels a direct launch
-    sequence issues."""
+    """The device-driven solve (by default one graph for the whole batch, its rounds of cycles
+    and their decisions on the device; with own_cycles a conditional graph that returns when
+    one lattice's inner loop has stopped; the lattices have different masses, so their cycles
+    end at different iterations) runs exactly the kernels a direct launch sequence issues."""
     host, probs = _problems(SMALL, seed=910)
     xa, ia, sa = lqlib.cg_solve_lattices(probs, mode=mode, tol=1e-10, graph=True, own_cycles=own_cycles)
     xb, ib, sb = lqlib.cg_solve_lattices(probs, mode=mode, tol=1e-10, graph=False, own_cycles=own_cycles)

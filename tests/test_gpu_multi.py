@@ -174,8 +174,8 @@ def test_cg_multi_full_size_24x24x24x48(lqlib):
 
 
 def test_cg_multi_device_loop_equals_host_loop(lqlib):
-    """A batch whose right-hand sides stop at different iterations: the device-driven inner
-    loop (conditional CUDA graph) and the host-driven one give the same bits and counts."""
+    """A batch whose right-hand sides stop at different iterations and cycles: the solve run
+    on the device (one CUDA graph) and the host-driven one give the same bits and counts."""
     dims = (4, 4, 2, 4)
     m = 0.05
     U = synth.gauge_field(dims, seed=66, kind="near_identity", eps=0.3)
