@@ -535,6 +535,28 @@ def run_workload(args):
                      "ms_per_solve_by_rhs_per_thread": by_rb,
                      "ms_one_by_one": ms_single, "speedup_vs_one_by_one": ms_single / ms,
                      "iters": max(i["iters"] for i in infos)})
+    elif args.workload == "cycles":
+        # the whole solve's cycles in one graph launch (the default) against host-driven
+        # cycles (graph=False), on small to large lattices: median device time per solve
+        res = {}
+        for dims in ((8, 8, 8, 8), (16, 16, 16, 16), DIMS):
+            U_d = field(synth.gauge_field(dims, seed=SEED_U, kind="near_identity", eps=EPS))
+            eta_d = field(synth.gaussian_spinor(dims, seed=SEED_ETA))
+            for mode in ("mixed_f16", "mixed_f32", "f64x"):
+                row = {}
+                for loop in ("device", "host"):
+                    def run(loop=loop, mode=mode, dims=dims):
+                        _, info, st = lq.cg_solve(dims, MASS, U_d, eta_d, mode=mode, tol=TOL, graph=loop == "device")
+                        assert st == 0
+                        return info
+                    ms, info = _timed(run, args.steps, args.warmup)
+                    row[loop + "_ms"] = ms
+                row.update({"iters": info["iters"], "cycles": info["cycles"],
+                            "host_over_device": row["host_ms"] / row["device_ms"]})
+                res["x".join(map(str, dims)) + "/" + mode] = row
+        line.update({"config": {"lattices": ["8x8x8x8", "16x16x16x16", "x".join(map(str, DIMS))], "m_q": MASS,
+                                "links": "exp(0.3iH)", "tol": TOL},
+                     "value": None, "unit": "ms", "solves": res})
     elif args.workload == "dslash":
         # the operator alone on the 32^4 fields, every stored format: site-updates/s, GB/s
         # against the measured copy peak and the 8 TB/s nominal, GFLOP/s at 1464 flops/site
@@ -666,18 +688,18 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 / other-mode comparison solves")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--workload", default="cg32",
-                    choices=["cg32", "lattices", "batched", "large", "schur", "dslash", "grad"],
+                    choices=["cg32", "lattices", "batched", "large", "schur", "dslash", "grad", "cycles"],
                     help="cg32: the 32^4 mixed-precision solve (the bench line); the others print a "
-                         "measurement line for the uneven-lattice, 12-RHS, 64^3x128, Schur, operator-only "
-                         "and gradient workloads")
+                         "measurement line for the uneven-lattice, 12-RHS, 64^3x128, Schur, operator-only, "
+                         "gradient and device- against host-driven cycle workloads")
     ap.add_argument("--variants", default="",
                     help="dslash workload: comma-separated prec/link-reals/layout rows to run (default: all)")
     ap.add_argument("--reps", type=int, default=20, help="dslash workload: timed applies per variant")
     ap.add_argument("--lattice-block", type=int, default=0, choices=[0, 64, 128, 256],
                     help="lattices workload: inner block size (0: tuned)")
     ap.add_argument("--inner-loop", default="device", choices=["device", "host"],
-                    help="lattices workload: inner loop driven by a conditional CUDA graph (device) or "
-                         "launched kernel by kernel from the host (every kernel visible to a profiler)")
+                    help="lattices workload: the whole batch as one CUDA graph launch (device) or host-driven "
+                         "cycles with the kernels launched one by one (every kernel visible to a profiler)")
     args = ap.parse_args()
     if args.workload != "cg32":
         run_workload(args)

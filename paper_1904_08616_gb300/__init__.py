@@ -448,8 +448,8 @@ def cg_solve_lattices(problems, mode="mixed_f32", tol=1e-10, max_iter=100000, ma
     problems: list of dicts {"dims", "m_q", "U", "eta", "nrhs" (1, 2, 4 or 8), "x" (optional
     start guess)}, U an F64 LEX 18-real gauge field, eta / x nrhs stacked F64 LEX spinors.
     own_cycles=True lets each lattice take its reliable update as soon as its own inner loop
-    stops (default: the batch's reliable updates are taken together, one host round trip per
-    round of cycles).
+    stops, the host driving the cycles (default: the reliable updates are taken together and
+    the whole batch runs as one CUDA graph launch).
     Returns ([x per lattice], [[info per right-hand side] per lattice], status).
     """
     import torch

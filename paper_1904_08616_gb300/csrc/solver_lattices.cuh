@@ -1,19 +1,21 @@
-// Several lattices of different sizes solved together (Algorithm 1 for each), with the
-// inner CG kernels of all lattices sharing launches.  The paper solves one system at a
-// time; this is the library's batching of uneven problems.
+// Several lattices of different sizes solved together (Algorithm 1 for each).  The paper
+// solves one system at a time; this is the library's batching of uneven problems.
 //
-// Each inner kernel (K1, K2, K3 of solver_impl.cuh) runs as ONE launch over every lattice:
-// the launch carries a table of per-lattice work descriptors (map, stencil, epilogue, all
-// holding that lattice's geometry, fields and state record) and the block ranges that serve
-// each lattice; a block finds its lattice, then runs the ordinary kernel body with that
-// lattice's share of the grid as its virtual grid, so reductions and tickets stay per
-// lattice.  Lattices whose inner loop has stopped leave their blocks idle.  By default the
-// whole batch is one CUDA graph (LatticeSolveGraph): rounds of cycles, each lattice's outer
-// steps (restart, reliable update) and every decision on the device.  Host-driven forms
-// remain for LQ_CG_LATTICE_OWN_CYCLES (a conditional graph over the inner iterations that
-// returns when one lattice's cycle ends), for LQ_CG_NO_GRAPH and for drivers without nested
-// conditional nodes: the host reads the state records between launches and runs the outer
-// steps of the lattices whose cycle ended, on the same stream.
+// The grid of each inner kernel (K1, K2, K3 of solver_impl.cuh) is shared out among the
+// lattices in proportion to their tiles (split_blocks), and a lattice's blocks run the
+// ordinary kernel body with its share as their virtual grid, so reductions and tickets stay
+// per lattice.  By default the whole batch is one CUDA graph (LatticeSolveGraph): rounds of
+// cycles with each lattice's outer steps (restart, reliable update) and every decision on
+// the device, and in the inner loop each lattice's K1, K2, K3 as launches of its own over its
+// share, parallel branches of the graph that run side by side.  Host-driven forms remain for
+// LQ_CG_LATTICE_OWN_CYCLES (a conditional graph over the inner iterations that returns when
+// one lattice's cycle ends), for LQ_CG_NO_GRAPH and for drivers without nested conditional
+// nodes; they issue each inner kernel as ONE launch over every lattice (a table of
+// per-lattice work descriptors: map, stencil, epilogue; a block finds its lattice by its
+// index) and the host reads the state records between launches and runs the outer steps of
+// the lattices whose cycle ended, on the same stream.  Both forms give every lattice the same
+// blocks and so the same sums, bit for bit.  Lattices whose inner loop has stopped leave
+// their blocks idle.
 //
 // The inner block size (threads per block of K1/K2) is a template parameter; the tuner
 // times K1 over the actual lattices for each candidate and caches the winner by a JSON key
@@ -127,6 +129,18 @@ template <class S> struct InnerLaunches {
         k1()<<<t1.boff[t1.n], BS, 0, s>>>(t1);
         k2()<<<t2.boff[t2.n], BS, 0, s>>>(t2);
         k3()<<<t3.boff[t3.n], kSiteBS, 0, s>>>(t3);
+        return cudaGetLastError();
+    }
+    // lattice l's share of one iteration as launches of its own (the single-lattice kernels,
+    // with the blocks the shared launches give it, so the same sums in the same order): the
+    // branches of a graph in which the lattices' kernels run side by side
+    cudaError_t iteration_of(int l, cudaStream_t s) const {
+        stencil_kernel<BS, typename S::IMap, typename S::K1Sten, typename S::K1Epi>
+            <<<t1.boff[l + 1] - t1.boff[l], BS, 0, s>>>(t1.job[l].map, t1.job[l].sten, t1.job[l].epi);
+        stencil_kernel<BS, typename S::IMap, typename S::K2Sten, typename S::K2Epi>
+            <<<t2.boff[l + 1] - t2.boff[l], BS, 0, s>>>(t2.job[l].map, t2.job[l].sten, t2.job[l].epi);
+        site_kernel<kSiteBS, typename S::ISiteMap, typename S::K3Op>
+            <<<t3.boff[l + 1] - t3.boff[l], kSiteBS, 0, s>>>(t3.job[l].map, t3.job[l].op);
         return cudaGetLastError();
     }
 };
@@ -268,7 +282,10 @@ struct LoopGraph {
 //   lattice_loop_base; WHILE (some lattice's inner loop runs) { one iteration of every
 //   lattice; lattice_loop_cond }; for each lattice { lat_mid; IF (its solution moved)
 //   { its update and outer residual; lat_end } }; lat_decide }
-// A lattice with nothing left to do takes part as idle blocks and no-op cycle kernels.
+// The lattices' kernels are parallel branches of the graph, each lattice with its own
+// launches over the blocks the shared launches would give it, so a small lattice's kernels
+// run beside a large one's instead of inside its launches.  A lattice with nothing left to
+// do takes part with idle blocks and no-op cycle kernels.
 struct LatCtlArgs {
     SolverState* st[kMaxLat];
     int n;
@@ -325,19 +342,41 @@ static __global__ void lat_decide_kernel(LatCtlArgs a, cudaGraphConditionalHandl
 
 struct LatticeSolveGraph {
     cudaStream_t cs = nullptr;
+    cudaStream_t ls[kMaxLat] = {};   // one capture branch per lattice
+    cudaEvent_t ev[kMaxLat + 1] = {};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    int n = 0;
     LatticeSolveGraph() = default;
     LatticeSolveGraph(const LatticeSolveGraph&) = delete;
     LatticeSolveGraph& operator=(const LatticeSolveGraph&) = delete;
     ~LatticeSolveGraph() {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
+        for (int l = 0; l < kMaxLat; ++l)
+            if (ls[l]) cudaStreamDestroy(ls[l]);
+        for (int l = 0; l <= kMaxLat; ++l)
+            if (ev[l]) cudaEventDestroy(ev[l]);
         if (cs) cudaStreamDestroy(cs);
     }
+    // while cs is capturing: f(l, ls[l]) for every lattice as parallel branches, joined on cs
+    template <class F>
+    cudaError_t branches(F f) {
+        cudaError_t e;
+        if ((e = cudaEventRecord(ev[kMaxLat], cs)) != cudaSuccess) return e;
+        for (int l = 0; l < n; ++l) {
+            if ((e = cudaStreamWaitEvent(ls[l], ev[kMaxLat], 0)) != cudaSuccess) return e;
+            if ((e = f(l, ls[l])) != cudaSuccess) return e;
+            if ((e = cudaEventRecord(ev[l], ls[l])) != cudaSuccess) return e;
+        }
+        for (int l = 0; l < n; ++l)
+            if ((e = cudaStreamWaitEvent(cs, ev[l], 0)) != cudaSuccess) return e;
+        return cudaSuccess;
+    }
     template <class S, class IL>
-    cudaError_t build(S* sv, int n, const IL& il) {
+    cudaError_t build(S* sv, int n_, const IL& il) {
         constexpr cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
+        n = n_;
         LatCtlArgs ca{};
         LatLoopArgs la{};
         ca.n = la.n = n;
@@ -345,6 +384,10 @@ struct LatticeSolveGraph {
         for (int l = 0; l < n; ++l) ca.st[l] = la.st[l] = sv[l].dstate;
         cudaError_t e, le;
         if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) return e;
+        for (int l = 0; l < n; ++l)
+            if ((e = cudaStreamCreateWithFlags(&ls[l], cudaStreamNonBlocking)) != cudaSuccess) return e;
+        for (int l = 0; l <= kMaxLat; ++l)
+            if ((e = cudaEventCreateWithFlags(&ev[l], cudaEventDisableTiming)) != cudaSuccess) return e;
         if ((e = cudaGraphCreate(&graph, 0)) != cudaSuccess) return e;
         cudaGraphConditionalHandle outer, inner, run[kMaxLat];
         if ((e = cudaGraphConditionalHandleCreate(&outer, graph, 0, cudaGraphCondAssignDefault)) != cudaSuccess)
@@ -357,7 +400,8 @@ struct LatticeSolveGraph {
         e = cudaStreamEndCapture(cs, &graph);
         if (le != cudaSuccess) return le;
         if (e != cudaSuccess) return e;
-        // one round of cycles
+        // one round of cycles: the lattices' restarts side by side, the inner loop, then each
+        // lattice's reliable update (if its solution moved) side by side
         if ((e = cudaGraphConditionalHandleCreate(&inner, round, 1, cudaGraphCondAssignDefault)) != cudaSuccess)
             return e;
         for (int l = 0; l < n; ++l)
@@ -366,17 +410,19 @@ struct LatticeSolveGraph {
         if ((e = cudaStreamBeginCaptureToGraph(cs, round, nullptr, nullptr, 0, mode)) != cudaSuccess) return e;
         ctl_arm_kernel<<<1, 32, 0, cs>>>(inner);
         le = cudaGetLastError();
-        for (int l = 0; l < n && le == cudaSuccess; ++l) le = sv[l].launch_restart(cs, true);
+        if (le == cudaSuccess)
+            le = branches([&](int l, cudaStream_t s) { return sv[l].launch_restart(s, true); });
         if (le == cudaSuccess) {
             lattice_loop_base<<<1, 32, 0, cs>>>(la);
             le = cudaGetLastError();
         }
         if (le == cudaSuccess) le = capture_conditional(cs, inner, cudaGraphCondTypeWhile, &body);
-        for (int l = 0; l < n && le == cudaSuccess; ++l) {
-            lat_mid_kernel<<<1, 32, 0, cs>>>(sv[l].dstate, run[l]);
-            le = cudaGetLastError();
-            if (le == cudaSuccess) le = capture_conditional(cs, run[l], cudaGraphCondTypeIf, &tail[l]);
-        }
+        if (le == cudaSuccess)
+            le = branches([&](int l, cudaStream_t s) {
+                lat_mid_kernel<<<1, 32, 0, s>>>(sv[l].dstate, run[l]);
+                cudaError_t r = cudaGetLastError();
+                return r == cudaSuccess ? capture_conditional(s, run[l], cudaGraphCondTypeIf, &tail[l]) : r;
+            });
         if (le == cudaSuccess) {
             lat_decide_kernel<<<1, 32, 0, cs>>>(ca, outer);
             le = cudaGetLastError();
@@ -384,9 +430,9 @@ struct LatticeSolveGraph {
         e = cudaStreamEndCapture(cs, &round);
         if (le != cudaSuccess) return le;
         if (e != cudaSuccess) return e;
-        // one iteration of every lattice and the loop test
+        // one iteration of every lattice (side by side) and the loop test
         if ((e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, mode)) != cudaSuccess) return e;
-        le = il.iteration(cs);
+        le = branches([&](int l, cudaStream_t s) { return il.iteration_of(l, s); });
         if (le == cudaSuccess) {
             lattice_loop_cond<<<1, 32, 0, cs>>>(inner, la);
             le = cudaGetLastError();
