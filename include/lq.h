@@ -390,13 +390,14 @@ int lq_cg_solve_schur(const int32_t dims[4], double m_q, int32_t mode, int32_t n
  *            inner block size) and LQ_CG_NO_GRAPH.
  *   workspace at least lq_cg_workspace_bytes_lattices(n, lats, mode) bytes.
  *   info     optional, sum of nrhs records in lattice order (block = the inner block size).
- * Each inner-loop kernel's grid is shared out among the lattices in proportion to their
- * sites.  By default the whole batch runs as one CUDA graph launch: rounds of cycles in a
- * conditional WHILE node, each round restarting every lattice that needs a cycle, iterating
- * all of them (each lattice's kernels a parallel branch of the graph) until every inner loop
- * has stopped, and taking each moved lattice's reliable update (Algorithm 1's outer step)
- * under a conditional IF node; all decisions are taken on the device.  Host-driven cycles
- * issue each inner kernel as one launch over all lattices.  With LQ_CG_LATTICE_OWN_CYCLES the host takes each
+ * Each lattice's kernels use the grids a solve of that lattice alone would use, so every
+ * lattice gets the result of its own solve, bit for bit.  By default the whole batch runs as
+ * one CUDA graph launch: rounds of cycles in a conditional WHILE node, each round restarting
+ * every lattice that needs a cycle, iterating all of them (each lattice's kernels a parallel
+ * branch of the graph, running side by side) until every inner loop has stopped, and taking
+ * each moved lattice's reliable update (Algorithm 1's outer step) under a conditional IF
+ * node; all decisions are taken on the device.  Host-driven cycles issue the lattices'
+ * kernels one lattice after the other.  With LQ_CG_LATTICE_OWN_CYCLES the host takes each
  * lattice's reliable update as soon as its own inner loop stops while the others go on.
  * Returns LQ_OK if every solve converged, LQ_NOT_CONVERGED if some did not, or the most
  * negative error status.  Returns after the solves have finished.

@@ -1571,8 +1571,10 @@ struct Solve {
         return LQ_OK;
     }
 
+    // K1 alone (the block-size tuner times it)
+    cudaError_t launch_k1(cudaStream_t s) const { return launch_stencil<IBS>(imap, sK1, eK1, s); }
     // one inner CG iteration (K1, K2, K3; Schur: with the two hops to the odd sites)
-    cudaError_t launch_iteration(cudaStream_t s) {
+    cudaError_t launch_iteration(cudaStream_t s) const {
         cudaError_t r;
         if constexpr (SCHUR)
             if ((r = launch_stencil<IBS>(omap, sPre1, ePre, s)) != cudaSuccess) return r;

@@ -1,21 +1,18 @@
 // Several lattices of different sizes solved together (Algorithm 1 for each).  The paper
 // solves one system at a time; this is the library's batching of uneven problems.
 //
-// The grid of each inner kernel (K1, K2, K3 of solver_impl.cuh) is shared out among the
-// lattices in proportion to their tiles (split_blocks), and a lattice's blocks run the
-// ordinary kernel body with its share as their virtual grid, so reductions and tickets stay
-// per lattice.  By default the whole batch is one CUDA graph (LatticeSolveGraph): rounds of
-// cycles with each lattice's outer steps (restart, reliable update) and every decision on
-// the device, and in the inner loop each lattice's K1, K2, K3 as launches of its own over its
-// share, parallel branches of the graph that run side by side.  Host-driven forms remain for
-// LQ_CG_LATTICE_OWN_CYCLES (a conditional graph over the inner iterations that returns when
-// one lattice's cycle ends), for LQ_CG_NO_GRAPH and for drivers without nested conditional
-// nodes; they issue each inner kernel as ONE launch over every lattice (a table of
-// per-lattice work descriptors: map, stencil, epilogue; a block finds its lattice by its
-// index) and the host reads the state records between launches and runs the outer steps of
-// the lattices whose cycle ended, on the same stream.  Both forms give every lattice the same
-// blocks and so the same sums, bit for bit.  Lattices whose inner loop has stopped leave
-// their blocks idle.
+// Each lattice keeps its own solver (state record, fields, kernels with the grids a solve of
+// that lattice alone would use).  By default the whole batch is one CUDA graph
+// (LatticeSolveGraph): rounds of cycles with each lattice's outer steps (restart, reliable
+// update) and every decision on the device, and in the inner loop each lattice's K1, K2, K3
+// as a parallel branch of the graph, so that the small lattices' kernels run beside the large
+// one's instead of after them.  Host-driven forms remain for LQ_CG_LATTICE_OWN_CYCLES (a
+// conditional graph over the inner iterations that returns when one lattice's cycle ends),
+// for LQ_CG_NO_GRAPH and for drivers without nested conditional nodes: they issue the
+// lattices' inner kernels one lattice after the other, the host reads the state records
+// between launches and runs the outer steps of the lattices whose cycle ended, on the same
+// stream.  Every form gives each lattice the sums of its own solve, bit for bit.  Lattices
+// whose inner loop has stopped leave their kernels idle.
 //
 // The inner block size (threads per block of K1/K2) is a template parameter; the tuner
 // times K1 over the actual lattices for each candidate and caches the winner by a JSON key
@@ -34,115 +31,29 @@ namespace solver_detail {
 
 constexpr int kMaxLat = 8;
 
-template <class Map, class Sten, class Epi> struct StencilJob {
-    Map map;
-    Sten sten;
-    Epi epi;
-};
-template <class Map, class Op> struct SiteJob {
-    Map map;
-    Op op;
-};
-template <class Job> struct JobTable {
-    Job job[kMaxLat];
-    int boff[kMaxLat + 1];   // blocks [boff[l], boff[l+1]) serve lattice l
-    int n;
-};
-
-template <class Table> __device__ __forceinline__ int job_of_block(const Table& t) {
-    int l = 0;
-    while (l + 1 < t.n && (int)blockIdx.x >= t.boff[l + 1]) ++l;
-    return l;
-}
-
-template <int BS, class Map, class Sten, class Epi>
-__global__ void __launch_bounds__(BS) multi_stencil_kernel(const __grid_constant__ JobTable<StencilJob<Map, Sten, Epi>> t) {
-    const int l = job_of_block(t);
-    const VGrid vg{(int)blockIdx.x - t.boff[l], t.boff[l + 1] - t.boff[l]};
-    Epi epi = t.job[l].epi;
-    stencil_body<BS>(t.job[l].map, t.job[l].sten, epi, vg);
-}
-
-template <int BS, class Map, class Op>
-__global__ void __launch_bounds__(BS) multi_site_kernel(const __grid_constant__ JobTable<SiteJob<Map, Op>> t) {
-    const int l = job_of_block(t);
-    const VGrid vg{(int)blockIdx.x - t.boff[l], t.boff[l + 1] - t.boff[l]};
-    Op op = t.job[l].op;
-    site_body<BS>(t.job[l].map, op, vg);
-}
-
-// Blocks per lattice: the kernel's full-occupancy grid shared in proportion to the tiles,
-// at least one block and at most one per tile (and kMaxPartials) for each lattice.
-template <class KernelPtr, class Table>
-inline void split_blocks(KernelPtr k, int bs, const int* ntiles, int n, Table& t) {
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, bs, 0);
-    if (per_sm < 1) per_sm = 1;
-    const long long G = (long long)sms * per_sm;
-    long long T = 0;
-    for (int l = 0; l < n; ++l) T += ntiles[l];
-    t.n = n;
-    t.boff[0] = 0;
-    for (int l = 0; l < n; ++l) {
-        long long b = (G * ntiles[l] + T - 1) / T;
-        if (b > ntiles[l]) b = ntiles[l];
-        if (b > kMaxPartials) b = kMaxPartials;
-        if (b < 1) b = 1;
-        t.boff[l + 1] = t.boff[l] + (int)b;
-    }
-}
-
-// The three inner launches over all lattices of one solve.
+// One inner iteration of every lattice of a batch: each lattice's K1, K2, K3 are its own
+// launches, with the grids a solve of that lattice alone would use (so each lattice's sums
+// are those of its own solve, bit for bit).  iteration() issues them one lattice after the
+// other on one stream (host-driven cycles); iteration_of(l, s) issues lattice l's on s, the
+// branch of a graph in which the lattices' kernels run side by side.
 template <class S> struct InnerLaunches {
-    using T1 = JobTable<StencilJob<typename S::IMap, typename S::K1Sten, typename S::K1Epi>>;
-    using T2 = JobTable<StencilJob<typename S::IMap, typename S::K2Sten, typename S::K2Epi>>;
-    using T3 = JobTable<SiteJob<typename S::ISiteMap, typename S::K3Op>>;
-    static constexpr int BS = S::kBlock;
-    T1 t1;
-    T2 t2;
-    T3 t3;
-
-    static constexpr auto k1() { return multi_stencil_kernel<BS, typename S::IMap, typename S::K1Sten, typename S::K1Epi>; }
-    static constexpr auto k2() { return multi_stencil_kernel<BS, typename S::IMap, typename S::K2Sten, typename S::K2Epi>; }
-    static constexpr auto k3() { return multi_site_kernel<kSiteBS, typename S::ISiteMap, typename S::K3Op>; }
-
-    void build(const S* sv, int n) {
-        int nt[kMaxLat], ns[kMaxLat];
-        for (int l = 0; l < n; ++l) {
-            t1.job[l] = {sv[l].imap, sv[l].sK1, sv[l].eK1};
-            t2.job[l] = {sv[l].imap, sv[l].sK2, sv[l].eK2};
-            t3.job[l] = {sv[l].isite, sv[l].oK3};
-            nt[l] = sv[l].imap.ntiles();
-            ns[l] = sv[l].isite.ntiles();
-        }
-        split_blocks(k1(), BS, nt, n, t1);
-        split_blocks(k2(), BS, nt, n, t2);
-        split_blocks(k3(), kSiteBS, ns, n, t3);
+    const S* sv = nullptr;
+    int n = 0;
+    void build(const S* sv_, int n_) {
+        sv = sv_;
+        n = n_;
     }
     cudaError_t k1_only(cudaStream_t s) const {
-        k1()<<<t1.boff[t1.n], BS, 0, s>>>(t1);
-        return cudaGetLastError();
+        cudaError_t e = cudaSuccess;
+        for (int l = 0; l < n && e == cudaSuccess; ++l) e = sv[l].launch_k1(s);
+        return e;
     }
     cudaError_t iteration(cudaStream_t s) const {
-        k1()<<<t1.boff[t1.n], BS, 0, s>>>(t1);
-        k2()<<<t2.boff[t2.n], BS, 0, s>>>(t2);
-        k3()<<<t3.boff[t3.n], kSiteBS, 0, s>>>(t3);
-        return cudaGetLastError();
+        cudaError_t e = cudaSuccess;
+        for (int l = 0; l < n && e == cudaSuccess; ++l) e = sv[l].launch_iteration(s);
+        return e;
     }
-    // lattice l's share of one iteration as launches of its own (the single-lattice kernels,
-    // with the blocks the shared launches give it, so the same sums in the same order): the
-    // branches of a graph in which the lattices' kernels run side by side
-    cudaError_t iteration_of(int l, cudaStream_t s) const {
-        stencil_kernel<BS, typename S::IMap, typename S::K1Sten, typename S::K1Epi>
-            <<<t1.boff[l + 1] - t1.boff[l], BS, 0, s>>>(t1.job[l].map, t1.job[l].sten, t1.job[l].epi);
-        stencil_kernel<BS, typename S::IMap, typename S::K2Sten, typename S::K2Epi>
-            <<<t2.boff[l + 1] - t2.boff[l], BS, 0, s>>>(t2.job[l].map, t2.job[l].sten, t2.job[l].epi);
-        site_kernel<kSiteBS, typename S::ISiteMap, typename S::K3Op>
-            <<<t3.boff[l + 1] - t3.boff[l], kSiteBS, 0, s>>>(t3.job[l].map, t3.job[l].op);
-        return cudaGetLastError();
-    }
+    cudaError_t iteration_of(int l, cudaStream_t s) const { return sv[l].launch_iteration(s); }
 };
 
 // One lattice of a multi-lattice solve as the drivers see it.
@@ -282,10 +193,9 @@ struct LoopGraph {
 //   lattice_loop_base; WHILE (some lattice's inner loop runs) { one iteration of every
 //   lattice; lattice_loop_cond }; for each lattice { lat_mid; IF (its solution moved)
 //   { its update and outer residual; lat_end } }; lat_decide }
-// The lattices' kernels are parallel branches of the graph, each lattice with its own
-// launches over the blocks the shared launches would give it, so a small lattice's kernels
-// run beside a large one's instead of inside its launches.  A lattice with nothing left to
-// do takes part with idle blocks and no-op cycle kernels.
+// The lattices' kernels are parallel branches of the graph, so a small lattice's kernels run
+// beside a large one's.  A lattice with nothing left to do takes part with idle kernels and
+// no-op cycle kernels.
 struct LatCtlArgs {
     SolverState* st[kMaxLat];
     int n;
