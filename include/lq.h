@@ -26,7 +26,7 @@
  *           LQ_LINK10: [n][mu 4][entry 5][re, im] = row 0 (u00, u01, u02), then the two
  *           entries of row 1 outside column k, in increasing column order.  k is the column
  *           of row 0 whose larger component max(|Re u0k|, |Im u0k|) is the largest (the lowest
- *           such column on ties), judged on the stored values.  Rebuilt: row 1's entry k from
+ *           such column on ties), decided on the stored values.  Rebuilt: row 1's entry k from
  *           the orthogonality of rows 0 and 1, u1k = -(sum_{j != k} u1j conj(u0j)) / conj(u0k)
  *           (|u0k| >= 1/sqrt(6), so the division amplifies rounding by at most ~2.5), then
  *           row 2 as for LQ_LINK12; exact for SU(3) up to rounding.  The paper streams links

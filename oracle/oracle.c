@@ -439,7 +439,7 @@ void lq_oracle_reconstruct12(int64_t nlinks, const double *rows_reals, double *f
  * construction it cites is not in the text.  This one follows from unitarity alone:
  *   stored: row 0 (u00, u01, u02) and the two entries of row 1 outside column k, in
  *     increasing column order, where k is the column of row 0 whose larger component
- *     max(|Re u0k|, |Im u0k|) is the largest (the lowest such column on ties), judged on
+ *     max(|Re u0k|, |Im u0k|) is the largest (the lowest such column on ties), decided on
  *     the stored values;
  *   rebuilt: rows 0 and 1 of a unitary matrix are orthogonal, sum_j u1j conj(u0j) = 0, so
  *       u1k = -(sum_{j != k} u1j conj(u0j)) / conj(u0k),
