@@ -630,6 +630,11 @@ template <> struct StencilMaxBlocks<float> { static constexpr int value = LQ_STE
 template <class Real> struct StencilMinBlocks { static constexpr int value = 0; };
 template <> struct StencilMinBlocks<float> { static constexpr int value = LQ_STENCIL_MINB_F32; };
 template <> struct StencilMinBlocks<dd> { static constexpr int value = LQ_STENCIL_MINB_PAIR; };
+// Resident blocks per SM asked of ptxas for one stencil kernel (0: ptxas chooses): by default
+// by arithmetic type; the solver specialises it for its K1 and K2 beside their epilogues.
+template <class Sten, class Epi> struct KernelMinBlocks {
+    static constexpr int value = StencilMinBlocks<typename Sten::Real>::value;
+};
 
 // Generic stencil kernel: grid-stride over tiles, one thread per site.
 template <int BS, class Map, class Sten, class Epi>
@@ -690,7 +695,7 @@ inline int grid_for(KernelPtr k, int bs, int ntiles, int max_per_sm = 0) {
 
 template <int BS, class Map, class Sten, class Epi>
 inline cudaError_t launch_stencil(const Map& map, const Sten& sten, const Epi& epi, cudaStream_t st) {
-    constexpr int MINB = StencilMinBlocks<typename Sten::Real>::value;
+    constexpr int MINB = KernelMinBlocks<Sten, Epi>::value;
     auto k = [] {
         if constexpr (MINB > 0) return stencil_kernel_minb<BS, MINB, Map, Sten, Epi>;
         else return stencil_kernel<BS, Map, Sten, Epi>;

@@ -234,6 +234,33 @@ struct EpiK2 {
     }
 };
 
+}  // namespace solver_detail
+
+// stored precision of a spinor accessor and link format of a gauge accessor
+template <class A> struct SpinorPrec { static constexpr int value = -1; };
+template <int P, int L, bool RO> struct SpinorPrec<SpinorAcc<P, L, RO>> { static constexpr int value = P; };
+template <class A> struct GaugeFmt { static constexpr int value = -1; };
+template <int P, int F, int L> struct GaugeFmt<GaugeAcc<P, F, L>> { static constexpr int value = F; };
+
+// The inner K1 and K2 with 12-real links ask for at least 5 resident blocks of 128 threads (at
+// most 102 registers).  On the 32^4 solves: FP32 fields K1 96.5 / K2 141.5 us against 102.0 /
+// 153.8 with ptxas's own choice (104 registers, 4 blocks); scaled FP16 K1 75.1 against 78.7
+// (ptxas's 80 registers, 6 blocks), while its K2 is faster as ptxas leaves it (96.2 against
+// 100.7 us at 5 blocks).
+template <class GA, class SA, bool DAG, class TA, class PA>
+struct KernelMinBlocks<Stencil<GA, SA, DAG>, solver_detail::EpiK1<TA, PA>> {
+    static constexpr bool kSet = GaugeFmt<GA>::value == 12 &&
+                                 (SpinorPrec<SA>::value == LQ_F32 || SpinorPrec<SA>::value == LQ_F16S);
+    static constexpr int value = kSet ? 5 : StencilMinBlocks<typename GA::Real>::value;
+};
+template <class GA, class SA, bool DAG, class TA, class PA, class XA, class RA>
+struct KernelMinBlocks<Stencil<GA, SA, DAG>, solver_detail::EpiK2<TA, PA, XA, RA>> {
+    static constexpr bool kSet = GaugeFmt<GA>::value == 12 && SpinorPrec<SA>::value == LQ_F32;
+    static constexpr int value = kSet ? 5 : StencilMinBlocks<typename GA::Real>::value;
+};
+
+namespace solver_detail {
+
 // The right-hand sides a thread serves: RB consecutive ones starting at this value (the
 // maps give every thread a fixed group).
 LQ_HD int thread_rhs0(int nr, int rb) {
