@@ -645,7 +645,9 @@ __device__ __forceinline__ void stencil_body(const Map& map, const Sten& sten, E
 #pragma unroll
     for (int j = 0; j < NR; ++j) red[j] = 0.0;
     const int nt = epi.active() ? map.ntiles() : 0;
-    for (int tile = vg.bid; tile < nt; tile += vg.nblk) {
+    const bool rev = reverse_tiles(epi);
+    for (int k = vg.bid; k < nt; k += vg.nblk) {
+        const int tile = rev ? nt - 1 - k : k;
         Site s;
         int c[4];
         if (!map.site(tile, s, c)) continue;

@@ -11,6 +11,9 @@
 #include <stdint.h>
 #include <stddef.h>
 
+#include <type_traits>
+#include <utility>
+
 #include "../../include/lq.h"
 #include "dd.cuh"
 
@@ -882,6 +885,16 @@ struct SolverState {
     unsigned int ticket[4];
     CycleCtl ctl;
 };
+
+// Tile order of a grid-stride kernel: an epilogue or site operation may walk its tiles from
+// the last to the first (reverse_tiles() const, read once per thread after init()).
+template <class E, class = void> struct HasTileOrder : std::false_type {};
+template <class E>
+struct HasTileOrder<E, std::void_t<decltype(std::declval<const E&>().reverse_tiles())>> : std::true_type {};
+template <class E> LQ_HD bool reverse_tiles(const E& e) {
+    if constexpr (HasTileOrder<E>::value) return e.reverse_tiles();
+    else return false;
+}
 
 constexpr int kMaxPartials = 4096;     // blocks per reducing kernel
 constexpr int kMaxRedValues = 4;       // values reduced per thread

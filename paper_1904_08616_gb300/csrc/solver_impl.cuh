@@ -187,6 +187,12 @@ struct EpiK2 {
         return true;
     }
     LQ_HD bool active() const { return on; }
+    // K2 walks its tiles from the last to the first: it starts on the sites K1 wrote last,
+    // whose t, links and p are still in L2, and ends on the ones K3 reads first, leaving
+    // their r and p in L2 (32^4 scaled FP16: K2 96.5 -> 94.6 us, K3 32.9 -> 30.8 us).
+    // Alternating all three kernels' order every iteration, so that K1 would start on
+    // K3's last sites as well, made K1 slower on its backward sweeps and is not used.
+    LQ_HD bool reverse_tiles() const { return true; }
     // psi is read once per site and never by a neighbour: asked for before the stencil, its
     // load after the eight hops hits L1 (K2 6% faster on the 32^4 workload; prefetching the
     // other fields as well gained nothing more)
