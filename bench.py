@@ -568,8 +568,9 @@ def run_workload(args):
         eta_d = spinors(dims, [500 + r for r in range(nr)])
         sb = lq.field_bytes(dims, "spinor", "f64")
 
-        def multi(rb=None):
-            _, infos, st = lq.cg_solve_multi(dims, 0.1, nr, U_d, eta_d, mode=args.mode, tol=TOL, rhs_block=rb)
+        def multi(rb=None, tuned=False):
+            _, infos, st = lq.cg_solve_multi(dims, 0.1, nr, U_d, eta_d, mode=args.mode, tol=TOL, rhs_block=rb,
+                                             autotune=tuned)
             assert st == 0
             return infos
 
@@ -583,10 +584,15 @@ def run_workload(args):
 
         ms, infos = _timed(multi, args.steps, args.warmup)
         by_rb = {rb: _timed(lambda rb=rb: multi(rb), args.steps, args.warmup)[0] for rb in (1, 2, 4)}
+        # right-hand sides per thread chosen by the library's tuner (the first, untimed warm-up
+        # call times the candidates; the timed calls take the cached choice)
+        ms_tuned, infos_tuned = _timed(lambda: multi(tuned=True), args.steps, args.warmup)
         ms_single, _ = _timed(single, args.steps, args.warmup)
         line.update({"config": {"lattice": list(dims), "nrhs": nr, "m_q": 0.1, "links": "haar", "tol": TOL},
                      "value": _updates(dims, infos) / (ms * 1e-3), "ms_per_solve": ms,
                      "ms_per_solve_by_rhs_per_thread": by_rb,
+                     "autotuned": {"rhs_per_thread": sorted({i["rhs_block"] for i in infos_tuned}),
+                                   "ms_per_solve": ms_tuned},
                      "ms_one_by_one": ms_single, "speedup_vs_one_by_one": ms_single / ms,
                      "iters": max(i["iters"] for i in infos)})
     elif args.workload == "cycles":

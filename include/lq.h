@@ -225,7 +225,11 @@ typedef struct lq_cg_params {
                                 with the FP32-pair outer loop; not with LQ_CG_LINK18 or
                                 LQ_CG_NATIVE_F64)                                          */
 #define LQ_CG_AUTOTUNE 8     /* lq_cg_solve_lattices: pick the inner block size by timing
-                                (cached per lattice set and GPU); default 128 threads      */
+                                (cached per lattice set and GPU); default 128 threads.
+                                lq_cg_solve_multi without an LQ_CG_RHS_BLOCK_* flag: pick the
+                                right-hand sides per thread (1, 2 or 4) by timing the inner
+                                D kernel on each batch of 2 or more (cached per GPU, modes,
+                                lattice and batch size); default 1                         */
 #define LQ_CG_NO_GRAPH 16    /* drive the cycles from the host and launch the inner kernels
                                 one by one, instead of running the whole solve's cycles in
                                 one CUDA graph with conditional WHILE nodes (the default; if
@@ -269,6 +273,7 @@ typedef struct lq_cg_info {
     int32_t block;           /* threads per block of the inner stencil kernels               */
     double kernel_ms[4];     /* LQ_CG_PROFILE: summed device time per role (events)         */
     int32_t kernel_calls[4]; /* LQ_CG_PROFILE: launches that did work, per role             */
+    int32_t rhs_block;       /* right-hand sides per thread of the inner stencil kernels     */
 } lq_cg_info;
 
 /* Workspace bytes lq_cg_solve needs for these dims and mode (0 on bad arguments). */

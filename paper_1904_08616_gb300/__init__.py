@@ -52,7 +52,7 @@ class CgInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("cycles", ctypes.c_int32),
                 ("high_applies", ctypes.c_int32), ("true_rel_resid", ctypes.c_double),
                 ("eta_norm", ctypes.c_double), ("launches", ctypes.c_int32), ("block", ctypes.c_int32),
-                ("kernel_ms", ctypes.c_double * 4), ("kernel_calls", ctypes.c_int32 * 4)]
+                ("kernel_ms", ctypes.c_double * 4), ("kernel_calls", ctypes.c_int32 * 4), ("rhs_block", ctypes.c_int32)]
 
 
 class Lattice(ctypes.Structure):
@@ -359,11 +359,12 @@ def cg_solve(dims, m_q, U, eta, x=None, mode="f64", tol=1e-10, max_iter=100000, 
 
 def cg_solve_multi(dims, m_q, nrhs, U, eta, x=None, mode="f64", tol=1e-10, max_iter=100000, max_cycles=0,
                    delta=0.0, chunk=0, max_inner=0, workspace=None, stream=None, profile=False, native_f64=False, link18=False, link10=False,
-                   graph=True, rhs_block=None):
+                   graph=True, rhs_block=None, autotune=False):
     """nrhs independent solves D^dag D x_r = eta_r sharing the links (eta, x: nrhs stacked FP64
     LEX fields).  rhs_block (1, 2 or 4; None: the library's default) sets how many right-hand
-    sides one thread of the inner stencil kernels serves.  Returns (x, [info per right-hand
-    side], status)."""
+    sides one thread of the inner stencil kernels serves; autotune (with rhs_block None) lets
+    the library choose it by timing (info["rhs_block"] reports the choice).  Returns (x,
+    [info per right-hand side], status)."""
     import torch
     m = CG_MODE[mode] if isinstance(mode, str) else int(mode)
     n = int(nrhs)
@@ -375,7 +376,7 @@ def cg_solve_multi(dims, m_q, nrhs, U, eta, x=None, mode="f64", tol=1e-10, max_i
     if workspace is None:
         workspace = _empty_bytes(wb, eta)
     flags = (CG_PROFILE if profile else 0) | (CG_NATIVE_F64 if native_f64 else 0) | (CG_LINK18 if link18 else 0) \
-        | (CG_LINK10 if link10 else 0) | (0 if graph else CG_NO_GRAPH)
+        | (CG_LINK10 if link10 else 0) | (0 if graph else CG_NO_GRAPH) | (CG_AUTOTUNE if autotune else 0)
     if rhs_block is not None:
         flags |= {1: CG_RHS_BLOCK_1, 2: CG_RHS_BLOCK_2, 4: CG_RHS_BLOCK_4}[int(rhs_block)]
     prm = CgParams(float(tol), int(max_iter), int(max_cycles), float(delta), int(chunk), flags, int(max_inner))

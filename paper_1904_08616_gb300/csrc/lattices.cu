@@ -1,4 +1,5 @@
-// Multi-lattice solves: workspace layout, mode dispatch, and the block-size tuning cache.
+// Multi-lattice solves: workspace layout, mode dispatch, and the tuning cache (the inner
+// block size of a lattice batch, the right-hand sides per thread of a batched solve).
 #include <stdio.h>
 #include <stdlib.h>
 
@@ -24,7 +25,15 @@ const char* tune_path() {
 
 bool valid_block(int b) { return b == 64 || b == 128 || b == 256; }
 
-// cache file: one JSON object per line, {"block": N, "key": {...}}
+// a stored value is a block size, or right-hand sides per thread for the keys of
+// tune_key_rhs_block
+bool valid_value(const std::string& key, int v) {
+    if (key.find("\"what\":\"rhs_block\"") != std::string::npos) return v == 1 || v == 2 || v == 4;
+    return valid_block(v);
+}
+
+// cache file: one JSON object per line, {"block": N, "key": {...}}; N is the tuned value (a
+// block size, or right-hand sides per thread for the keys of tune_key_rhs_block)
 void load_locked() {
     if (g_tune_loaded) return;
     g_tune_loaded = true;
@@ -40,7 +49,7 @@ void load_locked() {
         while (!key.empty() && (key.back() == '\n' || key.back() == '\r' || key.back() == ' ')) key.pop_back();
         if (key.empty() || key.back() != '}') continue;
         key.pop_back();
-        if (valid_block(bs)) g_tune[key] = bs;
+        if (valid_value(key, bs)) g_tune[key] = bs;
     }
     fclose(f);
 }
@@ -68,7 +77,10 @@ void tune_store(const std::string& key, int block) {
     }
 }
 
-std::string tune_key(int mode, int n, const LatticeJob* jobs) {
+namespace {
+
+// {"gpu":"<name>","sm":<major minor>, -- the start of every key, for the current device
+std::string tune_key_gpu() {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceProp prop;
@@ -80,8 +92,20 @@ std::string tune_key(int mode, int n, const LatticeJob* jobs) {
     }
     for (char& c : name)
         if (c == '"' || c == '\\') c = '\'';
-    std::string k = "{\"gpu\":\"" + name + "\",\"sm\":" + std::to_string(sm) + ",\"mode\":" + std::to_string(mode) +
-                    ",\"lattices\":[";
+    return "{\"gpu\":\"" + name + "\",\"sm\":" + std::to_string(sm) + ",";
+}
+
+}  // namespace
+
+std::string tune_key_rhs_block(int ip, int fmt, int hp, const Geom& g, int nb) {
+    return tune_key_gpu() + "\"what\":\"rhs_block\",\"inner\":" + std::to_string(ip) + ",\"links\":" +
+           std::to_string(fmt) + ",\"outer\":" + std::to_string(hp) + ",\"dims\":[" + std::to_string(g.L[0]) + "," +
+           std::to_string(g.L[1]) + "," + std::to_string(g.L[2]) + "," + std::to_string(g.L[3]) + "],\"nrhs\":" +
+           std::to_string(nb) + "}";
+}
+
+std::string tune_key(int mode, int n, const LatticeJob* jobs) {
+    std::string k = tune_key_gpu() + "\"mode\":" + std::to_string(mode) + ",\"lattices\":[";
     for (int l = 0; l < n; ++l) {
         if (l) k += ",";
         k += "[" + std::to_string(jobs[l].g.L[0]) + "," + std::to_string(jobs[l].g.L[1]) + "," +

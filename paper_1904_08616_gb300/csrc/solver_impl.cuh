@@ -37,6 +37,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <string>
 #include <type_traits>
 #include <vector>
 
@@ -1772,6 +1773,7 @@ struct Solve {
             out[j].status = sj;
             out[j].launches = launches;
             out[j].block = IBS;
+            out[j].rhs_block = RB;
             for (int q = 0; q < 4; ++q) {
                 out[j].kernel_ms[q] = kms[q];
                 out[j].kernel_calls[q] = kcalls[q];
@@ -1819,11 +1821,77 @@ inline int rhs_block(const lq_cg_params& prm, int nb) {
     return rb;
 }
 
+// The tuning cache (lattices.cu): tuned values by key, kept for the life of the process and
+// appended to the file named by LQ_TUNE_CACHE.
+bool tune_lookup(const std::string& key, int* value);
+void tune_store(const std::string& key, int value);
+std::string tune_key_rhs_block(int ip, int fmt, int hp, const Geom& g, int nb);
+
+// Mean device time of K1 with RB right-hand sides per thread on this batch (the inner links
+// converted from U, p filled with a small constant, a zeroed state record in which every
+// right-hand side runs: K1 keeps finding alpha = 0 and never stops); ms, or < 0 on error.
+// The solve that follows re-initialises everything the probe writes.
+template <int IP, int IF, int IL, int HP, int RB>
+double time_k1_rb(const Geom& g, double m_q, int nb, const void* U, const void* eta, void* x, const lq_cg_params& prm,
+                  const WsLayout& w, char* ws, cudaStream_t st) {
+    Solve<IP, IF, IL, HP, kBS, false, RB> sv;
+    sv.init(g, m_q, nb, U, eta, x, prm, 0.0, w, ws, st);
+    if (cudaMemsetAsync(sv.dstate, 0, sizeof(SolverState), st) != cudaSuccess ||
+        cudaMemsetAsync(ws + w.p, 0x3c, spinor_bytes((int64_t)g.V * nb, IP), st) != cudaSuccess ||
+        convert_gauge(g, LQ_F64, LQ_LAYOUT_LEX, U, IP, IF, IL, ws + w.u_low, st) != cudaSuccess)
+        return -1.0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess) return -1.0;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return -1.0;
+    }
+    constexpr int kWarm = 2, kReps = 6;
+    bool ok = true;
+    for (int i = 0; i < kWarm; ++i) ok &= sv.launch_k1(st) == cudaSuccess;
+    ok &= cudaEventRecord(e0, st) == cudaSuccess;
+    for (int i = 0; i < kReps; ++i) ok &= sv.launch_k1(st) == cudaSuccess;
+    ok &= cudaEventRecord(e1, st) == cudaSuccess;
+    ok &= cudaEventSynchronize(e1) == cudaSuccess;
+    float ms = 0.f;
+    ok &= cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ok ? ms / kReps : -1.0;
+}
+
+// Right-hand sides per thread chosen by timing (LQ_CG_AUTOTUNE without an LQ_CG_RHS_BLOCK_*
+// flag): K1 with 1, 2 and 4 (at most nb), the fastest kept in the tuning cache per GPU, link
+// format, precisions, lattice and batch size; 0 if a probe failed.
+template <int IP, int IF, int IL, int HP>
+int tuned_rhs_block(const Geom& g, double m_q, int nb, const void* U, const void* eta, void* x,
+                    const lq_cg_params& prm, const WsLayout& w, char* ws, cudaStream_t st) {
+    const std::string key = tune_key_rhs_block(IP, IF, HP, g, nb);
+    int rb = 1;
+    if (tune_lookup(key, &rb) && rb >= 1 && rb <= nb) return rb;
+    const double t[3] = {time_k1_rb<IP, IF, IL, HP, 1>(g, m_q, nb, U, eta, x, prm, w, ws, st),
+                         nb >= 2 ? time_k1_rb<IP, IF, IL, HP, 2>(g, m_q, nb, U, eta, x, prm, w, ws, st) : -1.0,
+                         nb >= 4 ? time_k1_rb<IP, IF, IL, HP, 4>(g, m_q, nb, U, eta, x, prm, w, ws, st) : -1.0};
+    if (t[0] < 0.0 || (nb >= 2 && t[1] < 0.0) || (nb >= 4 && t[2] < 0.0)) return 0;
+    int best = 0;
+    for (int i = 1; i < 3; ++i)
+        if (t[i] >= 0.0 && t[i] < t[best]) best = i;
+    rb = 1 << best;
+    tune_store(key, rb);
+    return rb;
+}
+
 template <int IP, int IF, int IL, int HP, bool SCHUR = false>
 int run_solver(const Geom& g, double m_q, int nb, const void* U, const void* eta, void* x, const lq_cg_params& prm,
                double delta, const WsLayout& w, char* ws, lq_cg_info* info, cudaStream_t st) {
     if constexpr (!SCHUR && IL == LQ_LAYOUT_EO && IF == 12 && !std::is_same<typename PrecT<IP>::Real, dd>::value) {
-        const int rb = rhs_block(prm, nb);
+        int rb = rhs_block(prm, nb);
+        const int rsel = prm.flags & (LQ_CG_RHS_BLOCK_1 | LQ_CG_RHS_BLOCK_2 | LQ_CG_RHS_BLOCK_4);
+        if ((prm.flags & LQ_CG_AUTOTUNE) && rsel == 0 && nb > 1) {
+            rb = tuned_rhs_block<IP, IF, IL, HP>(g, m_q, nb, U, eta, x, prm, w, ws, st);
+            if (rb == 0) return fail(LQ_ERR_CUDA, "right-hand-side block tuning failed: %s",
+                                     cudaGetErrorString(cudaGetLastError()));
+        }
         if (rb == 4) return run_solver_rb<IP, IF, IL, HP, SCHUR, 4>(g, m_q, nb, U, eta, x, prm, delta, w, ws, info, st);
         if (rb == 2) return run_solver_rb<IP, IF, IL, HP, SCHUR, 2>(g, m_q, nb, U, eta, x, prm, delta, w, ws, info, st);
     }

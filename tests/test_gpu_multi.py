@@ -147,6 +147,7 @@ def test_cg_multi_register_blocking(lqlib, mode, nrhs, rhs_block):
     etas = [synth.gaussian_spinor(dims, seed=700 + i) for i in range(nrhs)]
     xs, infos, st = _solve_multi(lqlib, dims, m, U, etas, mode, tol=1e-10, rhs_block=rhs_block)
     assert st == 0
+    assert all(i["rhs_block"] == rhs_block for i in infos)
     _, infos1, _ = _solve_multi(lqlib, dims, m, U, etas, mode, tol=1e-10, rhs_block=1)
     Ud = to_dev(F.encode_gauge(U, dims))
     for i in range(nrhs):
@@ -156,6 +157,38 @@ def test_cg_multi_register_blocking(lqlib, mode, nrhs, rhs_block):
     for i in (0, nrhs - 1):
         x1, _, _ = lqlib.cg_solve(dims, m, Ud, to_dev(F.encode_spinor(etas[i], dims)), mode=mode, tol=1e-10)
         assert oracle.rel_l2(xs[i], F.decode_spinor(to_host(x1), dims)) <= 1e-7
+
+
+@pytest.mark.parametrize("mode", ["mixed_f32", "mixed_f16"])
+def test_cg_multi_autotuned_rhs_block(lqlib, mode, tmp_path, monkeypatch):
+    """LQ_CG_AUTOTUNE without a blocking flag: the library times the inner D kernel with 1, 2
+    and 4 right-hand sides per thread and keeps the fastest. The choice is reported in every
+    info record and appended to the tuning cache file, and the solve gives the same bits and
+    counts as a solve with that choice fixed; a batch of one is not tuned."""
+    cache = tmp_path / "tune.jsonl"
+    monkeypatch.setenv("LQ_TUNE_CACHE", str(cache))
+    dims = (8, 6, 4, 6)
+    m = 0.05
+    U = synth.gauge_field(dims, seed=72, kind="near_identity", eps=0.3)
+    etas = [synth.gaussian_spinor(dims, seed=720 + i) for i in range(8)]
+    xs, infos, st = _solve_multi(lqlib, dims, m, U, etas, mode, tol=1e-10, autotune=True)
+    assert st == 0
+    rb = infos[0]["rhs_block"]
+    assert rb in (1, 2, 4) and all(i["rhs_block"] == rb for i in infos)
+    lines = [ln for ln in cache.read_text().splitlines() if '"what":"rhs_block"' in ln]
+    assert len(lines) == 1 and lines[0].startswith('{"block": %d, "key": ' % rb)
+    assert '"dims":[8,6,4,6],"nrhs":8' in lines[0]
+    xf, infof, stf = _solve_multi(lqlib, dims, m, U, etas, mode, tol=1e-10, rhs_block=rb)
+    assert stf == 0 and np.array_equal(xs, xf)
+    assert [i["iters"] for i in infos] == [i["iters"] for i in infof]
+    for i in (0, 7):
+        assert _true_resid(dims, m, U, etas[i], xs[i]) <= 1e-10 * RESID_SLACK
+    # a second tuned solve takes the cached choice: nothing more is appended
+    _, infos2, _ = _solve_multi(lqlib, dims, m, U, etas, mode, tol=1e-10, autotune=True)
+    assert infos2[0]["rhs_block"] == rb
+    assert len([ln for ln in cache.read_text().splitlines() if '"what":"rhs_block"' in ln]) == 1
+    _, info1, _ = _solve_multi(lqlib, dims, m, U, etas[:1], mode, tol=1e-10, autotune=True)
+    assert info1[0]["rhs_block"] == 1
 
 
 def test_cg_multi_full_size_24x24x24x48(lqlib):
