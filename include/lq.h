@@ -227,9 +227,9 @@ typedef struct lq_cg_params {
 #define LQ_CG_AUTOTUNE 8     /* lq_cg_solve_lattices: pick the inner block size by timing
                                 (cached per lattice set and GPU); default 128 threads.
                                 lq_cg_solve_multi without an LQ_CG_RHS_BLOCK_* flag: pick the
-                                right-hand sides per thread (1, 2 or 4) by timing the inner
-                                D kernel on each batch of 2 or more (cached per GPU, modes,
-                                lattice and batch size); default 1                         */
+                                right-hand sides per thread (1, 2 or 4) by timing the two
+                                inner stencil kernels on each batch of 2 or more (cached per
+                                GPU, modes, lattice and batch size); default 1             */
 #define LQ_CG_NO_GRAPH 16    /* drive the cycles from the host and launch the inner kernels
                                 one by one, instead of running the whole solve's cycles in
                                 one CUDA graph with conditional WHILE nodes (the default; if

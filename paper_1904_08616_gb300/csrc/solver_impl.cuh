@@ -1607,6 +1607,7 @@ struct Solve {
 
     // K1 alone (the block-size tuner times it)
     cudaError_t launch_k1(cudaStream_t s) const { return launch_stencil<IBS>(imap, sK1, eK1, s); }
+    cudaError_t launch_k2(cudaStream_t s) const { return launch_stencil<IBS>(imap, sK2, eK2, s); }
     // one inner CG iteration (K1, K2, K3; Schur: with the two hops to the odd sites)
     cudaError_t launch_iteration(cudaStream_t s) const {
         cudaError_t r;
@@ -1827,17 +1828,21 @@ bool tune_lookup(const std::string& key, int* value);
 void tune_store(const std::string& key, int value);
 std::string tune_key_rhs_block(int ip, int fmt, int hp, const Geom& g, int nb);
 
-// Mean device time of K1 with RB right-hand sides per thread on this batch (the inner links
-// converted from U, p filled with a small constant, a zeroed state record in which every
-// right-hand side runs: K1 keeps finding alpha = 0 and never stops); ms, or < 0 on error.
-// The solve that follows re-initialises everything the probe writes.
+// Mean device time of K1 + K2 (the two stencil kernels; K3 does not depend on the blocking)
+// with RB right-hand sides per thread on this batch: the inner links converted from U, p, r and
+// psi filled with a small constant, and the state record zeroed before each pair, so that K1
+// finds alpha = 0, K2 leaves psi and r as they are and every repetition does the same work on
+// the same finite values; ms, or < 0 on error.  The solve that follows re-initialises
+// everything the probe writes.
 template <int IP, int IF, int IL, int HP, int RB>
-double time_k1_rb(const Geom& g, double m_q, int nb, const void* U, const void* eta, void* x, const lq_cg_params& prm,
-                  const WsLayout& w, char* ws, cudaStream_t st) {
+double time_k12_rb(const Geom& g, double m_q, int nb, const void* U, const void* eta, void* x, const lq_cg_params& prm,
+                   const WsLayout& w, char* ws, cudaStream_t st) {
     Solve<IP, IF, IL, HP, kBS, false, RB> sv;
     sv.init(g, m_q, nb, U, eta, x, prm, 0.0, w, ws, st);
-    if (cudaMemsetAsync(sv.dstate, 0, sizeof(SolverState), st) != cudaSuccess ||
-        cudaMemsetAsync(ws + w.p, 0x3c, spinor_bytes((int64_t)g.V * nb, IP), st) != cudaSuccess ||
+    const int64_t vn = (int64_t)g.V * nb;
+    if (cudaMemsetAsync(ws + w.p, 0x3c, spinor_bytes(vn, IP), st) != cudaSuccess ||
+        cudaMemsetAsync(ws + w.r, 0x3c, spinor_bytes(vn, IP), st) != cudaSuccess ||
+        cudaMemsetAsync(ws + w.psi, 0x3c, spinor_bytes(vn, psi_prec(IP)), st) != cudaSuccess ||
         convert_gauge(g, LQ_F64, LQ_LAYOUT_LEX, U, IP, IF, IL, ws + w.u_low, st) != cudaSuccess)
         return -1.0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1846,11 +1851,15 @@ double time_k1_rb(const Geom& g, double m_q, int nb, const void* U, const void* 
         cudaEventDestroy(e0);
         return -1.0;
     }
+    auto pair = [&] {
+        return cudaMemsetAsync(sv.dstate, 0, sizeof(SolverState), st) == cudaSuccess &&
+               sv.launch_k1(st) == cudaSuccess && sv.launch_k2(st) == cudaSuccess;
+    };
     constexpr int kWarm = 2, kReps = 6;
     bool ok = true;
-    for (int i = 0; i < kWarm; ++i) ok &= sv.launch_k1(st) == cudaSuccess;
+    for (int i = 0; i < kWarm; ++i) ok &= pair();
     ok &= cudaEventRecord(e0, st) == cudaSuccess;
-    for (int i = 0; i < kReps; ++i) ok &= sv.launch_k1(st) == cudaSuccess;
+    for (int i = 0; i < kReps; ++i) ok &= pair();
     ok &= cudaEventRecord(e1, st) == cudaSuccess;
     ok &= cudaEventSynchronize(e1) == cudaSuccess;
     float ms = 0.f;
@@ -1861,17 +1870,17 @@ double time_k1_rb(const Geom& g, double m_q, int nb, const void* U, const void* 
 }
 
 // Right-hand sides per thread chosen by timing (LQ_CG_AUTOTUNE without an LQ_CG_RHS_BLOCK_*
-// flag): K1 with 1, 2 and 4 (at most nb), the fastest kept in the tuning cache per GPU, link
-// format, precisions, lattice and batch size; 0 if a probe failed.
+// flag): K1 + K2 with 1, 2 and 4 (at most nb), the fastest kept in the tuning cache per GPU,
+// link format, precisions, lattice and batch size; 0 if a probe failed.
 template <int IP, int IF, int IL, int HP>
 int tuned_rhs_block(const Geom& g, double m_q, int nb, const void* U, const void* eta, void* x,
                     const lq_cg_params& prm, const WsLayout& w, char* ws, cudaStream_t st) {
     const std::string key = tune_key_rhs_block(IP, IF, HP, g, nb);
     int rb = 1;
     if (tune_lookup(key, &rb) && rb >= 1 && rb <= nb) return rb;
-    const double t[3] = {time_k1_rb<IP, IF, IL, HP, 1>(g, m_q, nb, U, eta, x, prm, w, ws, st),
-                         nb >= 2 ? time_k1_rb<IP, IF, IL, HP, 2>(g, m_q, nb, U, eta, x, prm, w, ws, st) : -1.0,
-                         nb >= 4 ? time_k1_rb<IP, IF, IL, HP, 4>(g, m_q, nb, U, eta, x, prm, w, ws, st) : -1.0};
+    const double t[3] = {time_k12_rb<IP, IF, IL, HP, 1>(g, m_q, nb, U, eta, x, prm, w, ws, st),
+                         nb >= 2 ? time_k12_rb<IP, IF, IL, HP, 2>(g, m_q, nb, U, eta, x, prm, w, ws, st) : -1.0,
+                         nb >= 4 ? time_k12_rb<IP, IF, IL, HP, 4>(g, m_q, nb, U, eta, x, prm, w, ws, st) : -1.0};
     if (t[0] < 0.0 || (nb >= 2 && t[1] < 0.0) || (nb >= 4 && t[2] < 0.0)) return 0;
     int best = 0;
     for (int i = 1; i < 3; ++i)

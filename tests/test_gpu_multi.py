@@ -161,8 +161,8 @@ def test_cg_multi_register_blocking(lqlib, mode, nrhs, rhs_block):
 
 @pytest.mark.parametrize("mode", ["mixed_f32", "mixed_f16"])
 def test_cg_multi_autotuned_rhs_block(lqlib, mode, tmp_path, monkeypatch):
-    """LQ_CG_AUTOTUNE without a blocking flag: the library times the inner D kernel with 1, 2
-    and 4 right-hand sides per thread and keeps the fastest. The choice is reported in every
+    """LQ_CG_AUTOTUNE without a blocking flag: the library times the two inner stencil kernels
+    with 1, 2 and 4 right-hand sides per thread and keeps the fastest. The choice is reported in every
     info record and appended to the tuning cache file, and the solve gives the same bits and
     counts as a solve with that choice fixed; a batch of one is not tuned."""
     cache = tmp_path / "tune.jsonl"
