@@ -588,12 +588,23 @@ def run_workload(args):
         # call times the candidates; the timed calls take the cached choice)
         ms_tuned, infos_tuned = _timed(lambda: multi(tuned=True), args.steps, args.warmup)
         ms_single, _ = _timed(single, args.steps, args.warmup)
+        # the same batch in plain FP64 CG (one timed solve: about two seconds at this size)
+        f64 = None
+        if not args.no_compare:
+            def multi_f64():
+                _, inf, st = lq.cg_solve_multi(dims, 0.1, nr, U_d, eta_d, mode="f64", tol=TOL)
+                assert st == 0
+                return inf
+            ms_f64, infos_f64 = _timed(multi_f64, 1, 0)
+            f64 = {"ms_per_solve": ms_f64, "iters": max(i["iters"] for i in infos_f64),
+                   "mixed_speedup": ms_f64 / ms}
         line.update({"config": {"lattice": list(dims), "nrhs": nr, "m_q": 0.1, "links": "haar", "tol": TOL},
                      "value": _updates(dims, infos) / (ms * 1e-3), "ms_per_solve": ms,
                      "ms_per_solve_by_rhs_per_thread": by_rb,
                      "autotuned": {"rhs_per_thread": sorted({i["rhs_block"] for i in infos_tuned}),
                                    "ms_per_solve": ms_tuned},
                      "ms_one_by_one": ms_single, "speedup_vs_one_by_one": ms_single / ms,
+                     "fp64_cg_same_batch": f64,
                      "iters": max(i["iters"] for i in infos)})
     elif args.workload == "cycles":
         # the whole solve's cycles in one graph launch (the default) against host-driven
