@@ -62,3 +62,40 @@ def test_kernel_bytes_match_the_stored_formats():
     assert bench.kernel_bytes("mixed_f16") == {"K1": 52 + 96 + 52, "K2": 4 * 52 + 2 * 96 + 96, "K3": 3 * 52}
     assert bench.kernel_bytes("mixed_f32") == {"K1": 96 + 192 + 96, "K2": 6 * 96 + 192, "K3": 3 * 96}
     assert bench.kernel_bytes("f64")["K1"] == 192 + 576 + 192
+
+
+def test_traffic_record_follows_the_kernel_sources(monkeypatch):
+    """roofline.traffic comes from the committed ncu record only while the inner-loop kernel
+    sources hash to the value it was captured on; any other hash gives None (no stale
+    counters), and a role the record does not hold gives None."""
+    sys.path.insert(0, ROOT)
+    import bench
+    rec = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
+    monkeypatch.setattr(bench, "source_hash", lambda: rec["source_hash"])
+    for role in ("K1", "K2"):
+        assert bench.ncu_traffic(role) == rec["kernels"][role]["dram_bytes_per_launch_full_size"]
+    assert bench.ncu_traffic("K9") is None
+    monkeypatch.setattr(bench, "source_hash", lambda: "0" * 16)
+    assert bench.ncu_traffic("K2") is None
+
+
+def test_source_hash_covers_every_kernel_source(tmp_path, monkeypatch):
+    """The hash changes when any one of the files the inner-loop kernels are built from
+    changes, and only then."""
+    import shutil
+    sys.path.insert(0, ROOT)
+    import bench
+    src = os.path.join(ROOT, "paper_1904_08616_gb300", "csrc")
+    dst = tmp_path / "paper_1904_08616_gb300" / "csrc"
+    dst.mkdir(parents=True)
+    for fn in bench.KERNEL_SOURCES:
+        shutil.copy(os.path.join(src, fn), dst / fn)
+    base = bench.source_hash()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.source_hash() == base
+    for fn in bench.KERNEL_SOURCES:
+        orig = (dst / fn).read_bytes()
+        (dst / fn).write_bytes(orig + b"\n")
+        assert bench.source_hash() != base, fn
+        (dst / fn).write_bytes(orig)
+    assert bench.source_hash() == base
