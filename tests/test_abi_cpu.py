@@ -215,3 +215,33 @@ def test_checked_build_exports_every_declared_symbol(lqlib):
     L = ctypes.CDLL(path)
     for name in declared_functions():
         assert hasattr(L, name), name
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """The binding's ctypes mirrors of lq_cg_params, lq_cg_info and lq_lattice have the C
+    structs' size and every field's offset, as a C compiler lays them out from include/lq.h."""
+    import shutil
+    import subprocess
+    import paper_1904_08616_gb300 as lq
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    mirrors = {"lq_cg_params": lq.CgParams, "lq_cg_info": lq.CgInfo, "lq_lattice": lq.Lattice}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lq.h"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append(f'    printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'    printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {tuple(ln.split()[:2]): int(ln.split()[2]) for ln in out if ln.strip()}
+    for cname, py in mirrors.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
