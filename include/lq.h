@@ -345,6 +345,10 @@ size_t lq_cg_noalloc_max_workspace_bytes(void);
  * (<= 8) whose kernels read each link once per site for the whole batch; each right-hand
  * side keeps its own CG scalars and stops on its own criterion while the batch goes on,
  * and the reliable updates of a batch are taken together.  Batching is not in the paper.
+ * The mixed modes with 12-real inner links may serve several right-hand sides per thread
+ * (LQ_CG_RHS_BLOCK_2/4), or choose that number per batch by timing (LQ_CG_AUTOTUNE; the
+ * choice is cached per GPU, modes, lattice and batch size, and appended to the file named by
+ * the environment variable LQ_TUNE_CACHE if set); info[r].rhs_block reports it.
  * Returns LQ_OK if every solve converged, LQ_NOT_CONVERGED if some did not, or the most
  * negative error status.
  */
