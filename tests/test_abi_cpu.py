@@ -245,3 +245,33 @@ def test_binding_structs_match_the_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for fname, _ in py._fields_:
             assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
+
+def test_compute_calls_refuse_host_tensors(lqlib):
+    """No CPU fallback: every compute call of the binding refuses host (CPU) tensors with an
+    error before anything runs, rather than computing on the host."""
+    torch = pytest.importorskip("torch")
+    dims = (4, 4, 4, 4)
+    U = torch.zeros(lqlib.field_bytes(dims, "gauge", "f64", 18) // 8, dtype=torch.float64)
+    psi = torch.zeros(lqlib.field_bytes(dims, "spinor", "f64") // 8, dtype=torch.float64)
+    psi2 = torch.zeros(2 * psi.numel(), dtype=torch.float64)
+    Ueo = torch.zeros(lqlib.field_bytes(dims, "gauge", "f32", 12, "eo") // 4, dtype=torch.float32)
+    half = torch.zeros(lqlib.field_bytes(dims, "spinor", "f32") // 8, dtype=torch.float32)
+    calls = [
+        lambda: lqlib.dslash_apply(dims, 0.1, U, psi),
+        lambda: lqlib.dslash_adjoint(dims, 0.1, U, psi),
+        lambda: lqlib.dslash_apply_multi(dims, 0.1, 2, U, psi2),
+        lambda: lqlib.dslash_adjoint_multi(dims, 0.1, 2, U, psi2),
+        lambda: lqlib.dslash_hop(dims, 0, Ueo, half, prec="f32", link_fmt=12),
+        lambda: lqlib.link_grad(dims, psi, psi),
+        lambda: lqlib.convert_spinor(dims, psi),
+        lambda: lqlib.convert_spinor_multi(dims, 2, psi2),
+        lambda: lqlib.convert_gauge(dims, U),
+        lambda: lqlib.cg_solve(dims, 0.1, U, psi, mode="mixed_f16"),
+        lambda: lqlib.cg_solve_multi(dims, 0.1, 2, U, psi2, mode="mixed_f32"),
+        lambda: lqlib.cg_solve_schur(dims, 0.1, U, psi, mode="mixed_f32"),
+        lambda: lqlib.cg_solve_lattices([{"dims": dims, "m_q": 0.1, "U": U, "eta": psi}]),
+    ]
+    for i, call in enumerate(calls):
+        with pytest.raises(ValueError, match="CUDA tensor"):
+            call()
